@@ -1,0 +1,227 @@
+"""Seeded synthetic inputs for the MPM substep: particle clouds, states and collider scripts.
+
+This module only generates inputs. It holds none of the method's arithmetic
+(no weights, stress, transfer or contact), so both the FP64 oracle and the CUDA
+path can be fed from it without sharing any of the computation.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014) used as a
+counter-based generator: the i-th 64-bit word of stream ``seed`` is
+``mix(seed + (i + 1) * 0x9E3779B97F4A7C15)``; a double in [0, 1) takes its top
+53 bits. Every state is generated in FP64 and rounded to FP32, and those FP32
+values are what both sides consume.
+
+Workloads (the paper's soft-body tasks and assets are not available, so these
+synthetic scenes stand in for the Pinch and Pour scenes of Sec. 2 / App. C;
+parameters follow the ranges of Table 4 where the workload does not fix them):
+  * ``cube_scene``   -- 32^3 grid, 8,192 particles stratified-jittered in a
+    0.25-side plasticine cube, rho 1e3, E 5e3, nu 0.3, yield 50, dt 2e-4.
+  * ``pinch_scene``  -- 64^3 grid, 200,000 particles uniform in a seeded
+    ellipsoid of plasticine, two kinematic capsule fingers (radius 0.02) closing
+    on seeded sinusoidal paths, friction 0.5, 25 substeps per env step.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+PLASTICINE = 0
+FLUID = 1
+BOX = 0
+CAPSULE = 1
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Words ``offset .. offset+count-1`` of the splitmix64 stream ``seed`` (uint64)."""
+    i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of each word."""
+    return (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Standard normal variates by the Box-Muller transform of pairs of uniforms."""
+    u = uniform(seed, 2 * count, 2 * offset)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+@dataclass
+class Material:
+    kind: int = PLASTICINE
+    rho: float = 1e3
+    E: float = 5e3
+    nu: float = 0.3
+    yield_stress: float = 50.0
+    bulk_modulus: float = 1e4
+    p_vol: float = 1.0
+
+
+@dataclass
+class Shape:
+    """Collider shape: box half extents, or capsule (radius, half length along local z, 0)."""
+
+    type: int
+    half: tuple
+    friction: float
+
+
+@dataclass
+class Scene:
+    n: int
+    dt: float
+    material: Material
+    x: np.ndarray                      # (3, N) float32
+    v: np.ndarray                      # (3, N) float32
+    C: np.ndarray                      # (9, N) float32
+    F: np.ndarray                      # (9, N) float32 (identity for a fresh body)
+    gravity: tuple = (0.0, -9.8, 0.0)
+    bound: int = 3
+    shapes: list = field(default_factory=list)
+    substeps_per_env_step: int = 25
+    script: dict = field(default_factory=dict)   # collider path parameters
+
+    @property
+    def N(self) -> int:
+        return self.x.shape[1]
+
+
+def _identity_F(N: int) -> np.ndarray:
+    F = np.zeros((9, N), dtype=np.float32)
+    F[0] = F[4] = F[8] = 1.0
+    return F
+
+
+def cube_particles(lower, side: float, lattice=(16, 16, 32), seed: int = 1) -> np.ndarray:
+    """One jittered sample per sub-cell of a ``lattice`` over an axis-aligned cube (FP32, (3, N))."""
+    nx, ny, nz = lattice
+    N = nx * ny * nz
+    u = uniform(seed, 3 * N).reshape(N, 3)
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    cell = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.float64)
+    size = np.array([side / nx, side / ny, side / nz])
+    x = np.asarray(lower, dtype=np.float64)[None, :] + (cell + u) * size[None, :]
+    return np.ascontiguousarray(x.T.astype(np.float32))
+
+
+def cube_scene(variant: str = "floor", seed: int = 1) -> Scene:
+    """The 32^3 / 8,192-particle plasticine cube.
+
+    ``floor``: lower face at y = 3.25 dx so the first layer rests against the sticky floor band.
+    ``ff``:    centred (lower face at y = 0.375), free fall for the whole 50-substep rollout.
+    ``rand``:  the ``floor`` positions with random v ~ N(0, 0.5^2), C ~ N(0, 5^2),
+               F = I + N(0, 0.05^2) (seed 2), to exercise every branch in one substep.
+    """
+    n = 32
+    dx = 1.0 / n
+    side = 0.25
+    ylow = 0.375 if variant == "ff" else 3.25 * dx
+    x = cube_particles((0.375, ylow, 0.375), side, seed=seed)
+    N = x.shape[1]
+    mat = Material(PLASTICINE, rho=1e3, E=5e3, nu=0.3, yield_stress=50.0, p_vol=side ** 3 / N)
+    v = np.zeros((3, N), np.float32)
+    C = np.zeros((9, N), np.float32)
+    F = _identity_F(N)
+    if variant == "rand":
+        v, C, F = random_state(N, seed=2)
+    return Scene(n=n, dt=2e-4, material=mat, x=x, v=v, C=C, F=F, substeps_per_env_step=50)
+
+
+def random_state(N: int, seed: int, v_std: float = 0.5, C_std: float = 5.0, F_std: float = 0.05):
+    """Random v, C and F = I + noise (det F > 0 is checked), rounded to FP32."""
+    z = normal(seed, 21 * N).reshape(21, N)
+    v = (v_std * z[0:3]).astype(np.float32)
+    C = (C_std * z[3:12]).astype(np.float32)
+    F = (np.eye(3).reshape(9, 1) + F_std * z[12:21]).astype(np.float32)
+    det = np.linalg.det(F.T.reshape(N, 3, 3).astype(np.float64))
+    if not np.all(det > 0):
+        raise ValueError("random deformation gradient with det <= 0; lower F_std")
+    return v, C, F
+
+
+def ellipsoid_particles(N: int, center, semi, seed: int) -> np.ndarray:
+    """N points uniform in an axis-aligned ellipsoid by rejection from its bounding box (FP32, (3, N))."""
+    center = np.asarray(center, np.float64)
+    semi = np.asarray(semi, np.float64)
+    out = []
+    have = 0
+    offset = 0
+    while have < N:
+        m = 2 * (N - have) + 1024
+        u = uniform(seed, 3 * m, offset).reshape(m, 3)
+        offset += 3 * m
+        p = 2.0 * u - 1.0
+        keep = p[(p * p).sum(axis=1) < 1.0]
+        out.append(keep)
+        have += len(keep)
+    p = np.concatenate(out)[:N]
+    x = center[None, :] + p * semi[None, :]
+    return np.ascontiguousarray(x.T.astype(np.float32))
+
+
+def pinch_scene(seed: int = 1000, N: int = 200_000, n: int = 64) -> Scene:
+    """Plasticine pinch: a seeded ellipsoid on the floor band and two capsule fingers closing along x.
+
+    Semi-axes ~ U[0.18, 0.26]^3, centre (0.5, 3 dx + b, 0.5). Each finger is a capsule of radius 0.02
+    and half length 0.05 with its axis along world x (tips facing each other), starting 0.01 outside
+    the ellipsoid at its mid height. Finger c moves as c0 +- x A (1 - cos 2 pi f t) / 2 with
+    A ~ U[0.05, 0.12], f ~ U[1, 3] Hz, friction 0.5.
+    """
+    dx = 1.0 / n
+    u = uniform(seed, 8, offset=0)
+    semi = 0.18 + 0.08 * u[0:3]
+    center = (0.5, 3 * dx + semi[1], 0.5)
+    x = ellipsoid_particles(N, center, semi, seed=seed + 1)
+    vol = 4.0 / 3.0 * math.pi * semi[0] * semi[1] * semi[2]
+    mat = Material(PLASTICINE, rho=1e3, E=5e3, nu=0.3, yield_stress=50.0, p_vol=vol / N)
+    r, h = 0.02, 0.05
+    amp = 0.05 + 0.07 * u[3:5]
+    freq = 1.0 + 2.0 * u[5:7]
+    shapes = [Shape(CAPSULE, (r, h, 0.0), 0.5), Shape(CAPSULE, (r, h, 0.0), 0.5)]
+    c0 = [
+        (0.5 - (semi[0] + 0.01 + h + r), center[1], 0.5),
+        (0.5 + (semi[0] + 0.01 + h + r), center[1], 0.5),
+    ]
+    s = math.sqrt(0.5)
+    script = {
+        "c0": np.array(c0),
+        "dir": np.array([1.0, -1.0]),
+        "amp": amp,
+        "freq": freq,
+        "quat": np.array([[s, 0.0, s, 0.0], [s, 0.0, s, 0.0]]),  # local z -> world x
+    }
+    return Scene(n=n, dt=2e-4, material=mat, x=x, v=np.zeros((3, N), np.float32),
+                 C=np.zeros((9, N), np.float32), F=_identity_F(N), shapes=shapes, script=script,
+                 substeps_per_env_step=25)
+
+
+def finger_state(scene: Scene, t: float):
+    """Collider inputs at time t of a scripted scene.
+
+    Returns float32 arrays pose (k,7: position, quaternion w x y z), lin_vel (k,3), ang_vel (k,3),
+    com (k,3)."""
+    sc = scene.script
+    k = len(sc["c0"])
+    pose = np.zeros((k, 7))
+    lin = np.zeros((k, 3))
+    for i in range(k):
+        A, f, d = sc["amp"][i], sc["freq"][i], sc["dir"][i]
+        pose[i, :3] = sc["c0"][i] + np.array([d * A * (1.0 - math.cos(2 * math.pi * f * t)) / 2.0, 0.0, 0.0])
+        pose[i, 3:] = sc["quat"][i]
+        lin[i, 0] = d * A * math.pi * f * math.sin(2 * math.pi * f * t)
+    return (pose.astype(np.float32), lin.astype(np.float32), np.zeros((k, 3), np.float32),
+            pose[:, :3].astype(np.float32))
