@@ -1,0 +1,419 @@
+"""Benchmark of the MLS-MPM substep: particle-substeps/s on the 200k-particle pinch scene.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+A step is one environment step of the pinch scene: the fingers' poses and velocities are copied in
+(mpm_set_colliders), then 25 substeps run (mpm_substep), each a full pass of the hot path (bin sort,
+grid update with colliders, fused G2P/P2G). Inputs are resident in HBM when the timed region starts;
+L2 (129 MB) is flushed by writing a 512 MB buffer before every timed step, outside the events.
+The metric counts particles x substeps per second over all ranks (N > 1 runs independent replicas,
+one scene per GPU, seeds 1000 + rank).
+
+The JSON line also carries:
+  e2e          the same metric measured through the C-ABI with host buffers: collider poses copied in
+               from pinned host memory, positions and per-finger impulses read back to pinned host
+               memory, every step, inside the timed region;
+  roofline     the fused G2P/P2G kernel (the dominant one): algorithmic bytes (192 B per
+               particle-substep: x, v, C, F read and written in FP32) per launch / mean launch time
+               from CUDA events bracketing each launch during the timed region, against the measured
+               HBM copy bandwidth; plus its DRAM traffic per launch from the committed ncu summary when
+               it was taken on the current kernel source;
+  cpu_baseline the FP64 oracle (single thread) on one environment step of the same scene;
+  clocks       nvidia-smi samples taken during the timed region.
+--impl reference times the oracle itself on a bounded particle sample of the same scene.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pinch_200k_64cubed"
+METRIC = "MPM particle-substeps/s on 1 GB300; batched env-steps/s at ≤1e-3 rel. error"
+UNIT = "particle-substeps/s"
+BYTES_PER_PARTICLE_SUBSTEP = 192  # x, v, C, F in FP32, read and written
+SUBSTEPS = 25
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_launch(src_hash: str):
+    """DRAM bytes per g2p2g launch from the committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", "g2p2g_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != src_hash:
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.out = out
+
+    def summary(self):
+        if not self.out:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pinch_inputs(seed):
+    from paper_2302_04659_gb300 import scenes
+    sc = scenes.pinch_scene(seed=seed)
+    return sc
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_04659_gb300 import build as b
+    from paper_2302_04659_gb300 import scenes
+    from paper_2302_04659_gb300.sim import Sim
+
+    rank, world, local = env_rank()
+    b.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    sc = pinch_inputs(1000 + rank)
+    N = sc.N
+    sim = Sim(sc.n, sc.dt, sc.material, N, gravity=sc.gravity, bound=sc.bound, max_colliders=len(sc.shapes),
+              device=dev)
+    xd = torch.from_numpy(sc.x).to(dev)
+    vd = torch.from_numpy(sc.v).to(dev)
+    Cd = torch.from_numpy(sc.C).to(dev)
+    Fd = torch.from_numpy(sc.F).to(dev)
+    sim.set_shapes(sc.shapes)
+    stream = torch.cuda.current_stream(dev)
+    k = len(sc.shapes)
+    # pinned host buffers for the collider inputs of every step
+    pose_h = torch.empty((k, 7), dtype=torch.float32).pin_memory()
+    lin_h = torch.empty((k, 3), dtype=torch.float32).pin_memory()
+    ang_h = torch.empty((k, 3), dtype=torch.float32).pin_memory()
+    com_h = torch.empty((k, 3), dtype=torch.float32).pin_memory()
+    from paper_2302_04659_gb300 import _native as mpm
+
+    def set_colliders(step):
+        pose, lin, ang, com = scenes.finger_state(sc, step * SUBSTEPS * sc.dt)
+        pose_h.numpy()[:] = pose
+        lin_h.numpy()[:] = lin
+        ang_h.numpy()[:] = ang
+        com_h.numpy()[:] = com
+        mpm.mpm_set_colliders(sim.handle, k, pose_h.data_ptr(), lin_h.data_ptr(), ang_h.data_ptr(),
+                              com_h.data_ptr(), int(stream.cuda_stream))
+
+    def env_step(step):
+        set_colliders(step)
+        mpm.mpm_substep(sim.handle, SUBSTEPS, int(stream.cuda_stream))
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sim.set_particles(xd, vd, Cd, Fd)
+    for s in range(args.warmup):
+        env_step(s)
+    # ---------------- timed region (device-resident inputs)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sim.set_timing(True)
+    sim.read_timing(reset=True)
+    l0 = sim.launches
+    barrier()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            env_step(args.warmup + s)
+            ev[s][1].record(stream)
+        barrier()
+    wall = time.perf_counter() - wall0
+    launches = sim.launches - l0
+    ktime = sim.read_timing(reset=True)
+    sim.set_timing(False)
+    elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    flags = sim.status()
+    total_units = N * SUBSTEPS * args.steps * world
+    value = total_units / elapsed
+    g_ms, g_n = ktime["g2p2g"]
+    g_avg = g_ms / max(g_n, 1) / 1e3
+    # ---------------- end-to-end through the C-ABI with host buffers
+    x_h = torch.empty((3, N), dtype=torch.float32).pin_memory()
+    wr_h = torch.empty((k, 6), dtype=torch.float64).pin_memory()
+    sim.set_particles(xd, vd, Cd, Fd)
+    for s in range(min(args.warmup, 3)):
+        env_step(s)
+    barrier()
+    e2e_steps = max(1, min(args.steps, 200))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(e2e_steps):
+        env_step(s)
+        mpm.mpm_read_state(sim.handle, x_h.data_ptr(), 0, 0, 0, 0, int(stream.cuda_stream))
+        mpm.mpm_read_wrench(sim.handle, wr_h.data_ptr(), int(stream.cuda_stream))
+    ev1.record(stream)
+    barrier()
+    e2e_t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = N * SUBSTEPS * e2e_steps * world / float(e2e_t.item())
+    h2d = k * (7 + 3 + 3 + 3) * 4
+    d2h = 3 * N * 4 + k * 6 * 8 + 4
+    sim.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+    peak, peak_kind = measured_peak_gbs()
+    src_hash = kernel_source_hash()
+    achieved = BYTES_PER_PARTICLE_SUBSTEP * N / g_avg / 1e9 if g_avg > 0 else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded ellipsoid of plasticine, scripted capsule fingers)",
+        "config": {
+            "workload": WORKLOAD,
+            "particles_per_gpu": N,
+            "grid": f"{sc.n}^3",
+            "substeps_per_step": SUBSTEPS,
+            "colliders": "2 capsules r=0.02, friction 0.5",
+            "material": "plasticine E=5e3 nu=0.3 yield=50 rho=1e3",
+            "dt": sc.dt,
+            "l2": "flushed before every timed step (512 MB write, outside the events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {
+            "kernel": "k_g2p2g",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": traffic_per_launch(src_hash),
+            "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_SUBSTEP * N,
+            "mean_launch_us": g_avg * 1e6,
+            "launches": g_n,
+            "kernel_source_hash": src_hash,
+            "note": "state (38 MB) fits the 129 MB L2 inside a step; L2 flushed between steps",
+        },
+        "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in ktime.items() if v[1]},
+        "status_flags": flags,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    line["clocks"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def oracle_setup(sc, sample=None):
+    import oracle
+    m = sc.material
+    idx = np.arange(sc.N) if sample is None else np.linspace(0, sc.N - 1, sample).astype(np.int64)
+    p_vol = m.p_vol * sc.N / len(idx)
+    P = oracle.Params(n=sc.n, dt=sc.dt, gravity=tuple(sc.gravity), bound=sc.bound, kind=m.kind, E=m.E, nu=m.nu,
+                      yield_stress=m.yield_stress, rho=m.rho, p_vol=p_vol)
+    s = oracle.State.from_arrays(sc.x[:, idx], sc.v[:, idx], sc.C[:, idx], sc.F[:, idx])
+    return P, s
+
+
+def oracle_colliders(sc, step):
+    import oracle
+    from paper_2302_04659_gb300 import scenes
+    pose, lin, ang, com = scenes.finger_state(sc, step * SUBSTEPS * sc.dt)
+    return [oracle.Collider(sh.type, tuple(map(float, sh.half)), float(sh.friction), tuple(map(float, pose[i, :3])),
+                            tuple(map(float, pose[i, 3:])), tuple(map(float, lin[i])), tuple(map(float, ang[i])),
+                            tuple(map(float, com[i]))) for i, sh in enumerate(sc.shapes)]
+
+
+def cpu_baseline(sc):
+    """The FP64 oracle, single-threaded, on one environment step (25 substeps) of the full scene."""
+    import oracle
+    oracle.build()
+    P, s = oracle_setup(sc)
+    cols = oracle_colliders(sc, 0)
+    t0 = time.perf_counter()
+    oracle.rollout(P, s, SUBSTEPS, cols, 0.0)
+    dt = time.perf_counter() - t0
+    return {"value": sc.N * SUBSTEPS / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one env step: {SUBSTEPS} substeps of all {sc.N} particles, FP64, single thread",
+            "seconds": dt, "cpu": cpu_model(), "host_cores": os.cpu_count()}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_reference(args):
+    """The oracle as it stands, on a bounded particle sample of the same scene per step."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    sc = pinch_inputs(1000)
+    total = args.steps + args.warmup
+    budget = 90.0  # seconds of oracle work for the whole run
+    per_unit = 1.6e-6  # seconds per particle-substep of the oracle (about, single thread)
+    sample = int(min(sc.N, max(2000, budget / max(total, 1) / per_unit)))
+    P, s = oracle_setup(sc, sample)
+    elapsed = 0.0
+    for step in range(total):
+        cols = oracle_colliders(sc, step)
+        t0 = time.perf_counter()
+        oracle.substep(P, s, cols, 0.0)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            elapsed += dt
+    value = sample * args.steps / elapsed
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded ellipsoid of plasticine, scripted capsule fingers)",
+        "config": {"workload": WORKLOAD, "particles_per_gpu": sc.N, "grid": f"{sc.n}^3",
+                   "substeps_per_step": 1, "parallelism": "host CPU, single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of the {sc.N} particles (mass-preserving), one substep per step",
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

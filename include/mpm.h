@@ -1,0 +1,175 @@
+/*
+ * mpm.h -- C-ABI of the GB300 MLS-MPM soft-body substep library (libmpm_gb300.so).
+ *
+ * The calls follow the coupling loop of the paper's soft-body engine (Sec. 3,
+ * "Rigid-soft Coupling"; App. D.1, Algorithm 1):
+ *   - collision shapes are copied into the soft scene once       -> mpm_set_shapes
+ *   - after every rigid step, body poses and velocities are copied
+ *     in and the force-torque buffers are reset                   -> mpm_set_colliders
+ *   - soft steps: particle to grid (mass, momentum, forces), grid
+ *     velocity, grid to particle, particle integration             -> mpm_substep
+ *   - accumulated body forces / torques are read back              -> mpm_read_wrench
+ *   - particles are handed to a consumer by one GPU-GPU copy       -> mpm_read_state
+ *     (App. D.2), or to the host.
+ * Contact uses the grid form the paper names as the alternative it also
+ * supports (Sec. 3: signed distances evaluated on grid nodes, as in
+ * PlasticineLab), with Coulomb friction.
+ *
+ * Conventions
+ *   - Everything is FP32 except the wrench accumulators (FP64).
+ *   - Particle arrays are structure-of-arrays with the particle index fastest:
+ *     x[3][n], v[3][n], C[9][n], F[9][n]; 3x3 matrices row-major, so entry (r,c)
+ *     of particle p is at [(r*3 + c)*n + p].
+ *   - The domain is the unit cube; the grid has cfg.n nodes per axis, node i at
+ *     i*dx with dx = 1/n. Particles are kept inside [2dx, 1-2dx] (clamped, with
+ *     a status flag), so every quadratic B-spline stencil lies in the grid.
+ *   - Memory: the caller owns all device memory. mpm_create receives one device
+ *     workspace of mpm_workspace_size() bytes (256-byte aligned, e.g. a torch
+ *     tensor) that must outlive the handle; the library allocates no device
+ *     memory and owns only the small host-side handle.
+ *   - Streams: every call takes a cudaStream_t as void* (NULL = legacy default
+ *     stream) and only enqueues work on it, except those documented as
+ *     synchronizing. Calls on one handle must be issued from one host thread at a
+ *     time and on one stream (or streams the caller orders).
+ *   - Errors: each call returns an mpm_status; argument errors are detected on
+ *     the host before anything is enqueued. Conditions found on the device
+ *     (clamping, non-finite values) set sticky flag bits read by
+ *     mpm_get_status; the kernels never trap or abort.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPM_MAX_COLLIDERS 32
+
+typedef struct mpm_sim mpm_sim; /* opaque handle, host memory owned by the library */
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_INVALID_ARG = 1, /* a pointer, size or enum is out of range; nothing was enqueued */
+    MPM_ERR_CUDA = 2,        /* a CUDA runtime call failed; the message is kept for mpm_last_error */
+    MPM_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or smaller than mpm_workspace_size */
+    MPM_ERR_CAPACITY = 4     /* more particles or colliders than the handle was created for */
+} mpm_status;
+
+/* Sticky device flag bits (mpm_get_status). None of them stops the simulation. */
+#define MPM_FLAG_CLAMPED 0x1u    /* a particle coordinate was clamped to [2dx, 1-2dx] */
+#define MPM_FLAG_NONFINITE 0x2u  /* a non-finite coordinate or velocity was met (position clamped) */
+#define MPM_FLAG_SV_CLAMPED 0x4u /* a singular value of F was raised to 1e-6 before its logarithm */
+#define MPM_FLAG_FAR_MOVE 0x8u   /* a particle moved >= 1 cell in one substep (served by a slower path) */
+
+enum { MPM_PLASTICINE = 0, MPM_FLUID = 1 };
+enum { MPM_BOX = 0, MPM_CAPSULE = 1 };
+
+typedef struct {
+    int n;              /* grid nodes per axis: a multiple of 4 in [8, 256]; dx = 1/n */
+    float dt;           /* substep length (s) */
+    float gravity[3];   /* m/s^2 */
+    int bound;          /* sticky wall band: nodes with an index < bound or >= n-bound get v = 0 */
+    int max_particles;  /* capacity, >= 1 */
+    int max_colliders;  /* capacity, 0..MPM_MAX_COLLIDERS */
+} mpm_config;
+
+typedef struct {
+    int kind;           /* MPM_PLASTICINE (fixed-corotated + von Mises in Hencky strain) or MPM_FLUID */
+    float rho;          /* density; particle mass = rho * p_vol */
+    float E, nu;        /* plasticine Young's modulus and Poisson ratio (Table 4) */
+    float yield_stress; /* plasticine von Mises yield stress (Table 4) */
+    float bulk_modulus; /* fluid: lambda = bulk_modulus, mu = 0 */
+    float p_vol;        /* initial particle volume V0 (Table 4 "particle volume") */
+} mpm_material;
+
+typedef struct {
+    int type;           /* MPM_BOX or MPM_CAPSULE */
+    float half[3];      /* box half extents | capsule (radius, half length along local z, ignored) */
+    float friction;     /* Coulomb coefficient >= 0 */
+} mpm_shape;
+
+/* Bytes of device workspace a handle with this configuration needs. */
+mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes);
+
+/* Create a handle over a caller-owned device workspace; zeroes what must start at zero on `stream`.
+ * cfg / mat are copied. On error *out is NULL. */
+mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_workspace, size_t bytes,
+                      void* stream, mpm_sim** out);
+
+/* Replace the particle state (Algorithm 1 "initialize soft scene"). n <= max_particles; n = 0 empties
+ * the scene. Arrays are SoA with stride n, in host memory (src_on_device = 0: copied in, the call
+ * returns once the host arrays may be reused) or device memory (src_on_device = 1: read on `stream`).
+ * v and C may be NULL (zero); F may be NULL (identity). For MPM_FLUID only J = det F is kept.
+ * Positions outside [2dx, 1-2dx] are clamped and flagged. Resets the grid; keeps colliders. */
+mpm_status mpm_set_particles(mpm_sim* sim, int n, const float* x, const float* v, const float* C,
+                             const float* F, int src_on_device, void* stream);
+
+/* Collision shapes, copied once (Algorithm 1 "copy rigid body shapes ... to soft scene").
+ * Host memory; k <= max_colliders. Takes effect at the next mpm_set_colliders. */
+mpm_status mpm_set_shapes(mpm_sim* sim, int k, const mpm_shape* shapes);
+
+/* Body poses and velocities after a rigid step (Algorithm 1 "copy rigid body poses to soft scene",
+ * "initialize force-torque buffers per rigid body"). Host arrays, k = number of shapes set:
+ *   pose    k x 7: frame origin (x, y, z) and orientation quaternion (w, x, y, z)
+ *   lin_vel k x 3: velocity of the centre of mass;  ang_vel k x 3: angular velocity (world frame)
+ *   com     k x 3: centre of mass (world frame); NULL = frame origin
+ * ang_vel may be NULL (zero). Between two calls each body moves rigidly with these constant
+ * velocities, evaluated in closed form at the start of every substep. The data travel with the
+ * launch of one small kernel (no host buffer outlives the call); the wrench accumulators and the
+ * substep count are zeroed. */
+mpm_status mpm_set_colliders(mpm_sim* sim, int k, const float* pose, const float* lin_vel,
+                             const float* ang_vel, const float* com, void* stream);
+
+/* Advance n_substeps >= 0 substeps (Algorithm 1's inner loop: P2G, grid velocity with gravity,
+ * colliders and sticky walls, G2P with F update and return mapping). Asynchronous: no host sync. */
+mpm_status mpm_substep(mpm_sim* sim, int n_substeps, void* stream);
+
+/* Particle state in the caller's original order. Any pointer may be NULL (skipped). Arrays SoA with
+ * stride n. dst_on_device = 1: written on `stream` (the paper's single GPU-GPU copy), no sync.
+ * dst_on_device = 0: host memory, the call synchronizes `stream`. A fluid reports F = J^(1/3) I. */
+mpm_status mpm_read_state(mpm_sim* sim, float* x, float* v, float* C, float* F, int dst_on_device,
+                          void* stream);
+
+/* Force-torque buffers (Algorithm 1 "apply accumulated forces and torques"): for each collider the
+ * impulse (3) and angular impulse about its centre of mass (3) that the soft body received from it
+ * since the last mpm_set_colliders, as k x 6 doubles in host memory; *n_substeps (may be NULL) gets
+ * the substeps accumulated, so the mean force is impulse / (n_substeps * dt). Synchronizes `stream`. */
+mpm_status mpm_read_wrench(mpm_sim* sim, double* impulse_torque, int* n_substeps, void* stream);
+
+/* Sticky device flags (MPM_FLAG_*), ORed since creation or the last clear. Synchronizes `stream`. */
+mpm_status mpm_get_status(mpm_sim* sim, unsigned* flags, int clear, void* stream);
+
+/* Current particle count (host-side, no sync). */
+int mpm_num_particles(const mpm_sim* sim);
+
+/* Diagnostics: the grid holding the particle-to-grid transfer of the current state (mass and momentum,
+ * before the grid velocity update), densely as float[n][n][n][4] = (m, mv_x, mv_y, mv_z) with node
+ * (i,j,k) at ((i*n + j)*n + k)*4. Device destination only; enqueued on `stream`. */
+mpm_status mpm_read_grid(mpm_sim* sim, float* d_out, void* stream);
+
+/* Diagnostics: kernel timing. While enabled, every kernel launch of the handle is bracketed by CUDA
+ * events on its stream. mpm_read_timing synchronizes and returns, per kernel kind (MPM_K_*), the summed
+ * milliseconds and launch counts since the last reset (arrays of MPM_K_COUNT entries, either NULL). */
+enum { MPM_K_LOAD = 0, MPM_K_SCAN, MPM_K_ASSIGN, MPM_K_P2G, MPM_K_GRID, MPM_K_G2P2G, MPM_K_READ,
+       MPM_K_COLLIDERS, MPM_K_COUNT };
+mpm_status mpm_set_timing(mpm_sim* sim, int enable);
+mpm_status mpm_read_timing(mpm_sim* sim, double* ms, long long* launches, int reset);
+
+/* Number of kernels the handle has launched since creation (host counter, no sync). */
+long long mpm_launch_count(const mpm_sim* sim);
+
+/* Release the host handle (the workspace stays the caller's). Safe on NULL. Does not synchronize:
+ * the caller must not free the workspace before work enqueued on it has finished. */
+void mpm_destroy(mpm_sim* sim);
+
+const char* mpm_status_string(mpm_status s);
+
+/* Last CUDA error message seen by any call in this process (thread-local), or "". */
+const char* mpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

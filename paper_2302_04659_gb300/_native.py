@@ -1,0 +1,186 @@
+"""Thin ctypes binding of ``include/mpm.h`` (libmpm_gb300.so): same entry points, same names.
+
+Argument marshalling only -- every step of the substep runs in the CUDA library.
+Pointers are plain integers (device or host addresses), streams are
+``cudaStream_t`` values as integers. A non-OK status raises ``MpmError``.
+The library is loaded on first use; if it has not been built, loading raises
+(there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+MPM_MAX_COLLIDERS = 32
+MPM_OK, MPM_ERR_INVALID_ARG, MPM_ERR_CUDA, MPM_ERR_WORKSPACE, MPM_ERR_CAPACITY = range(5)
+MPM_FLAG_CLAMPED = 0x1
+MPM_FLAG_NONFINITE = 0x2
+MPM_FLAG_SV_CLAMPED = 0x4
+MPM_FLAG_FAR_MOVE = 0x8
+MPM_FLAG_INTERNAL = 0x80000000
+MPM_PLASTICINE, MPM_FLUID = 0, 1
+MPM_BOX, MPM_CAPSULE = 0, 1
+(MPM_K_LOAD, MPM_K_SCAN, MPM_K_ASSIGN, MPM_K_P2G, MPM_K_GRID, MPM_K_G2P2G, MPM_K_READ,
+ MPM_K_COLLIDERS, MPM_K_COUNT) = range(9)
+KERNEL_NAMES = ["load", "scan", "assign", "p2g", "grid_update", "g2p2g", "read", "colliders"]
+
+LIB_PATH = _build.LIB_PATH
+
+
+class mpm_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("dt", ctypes.c_float), ("gravity", ctypes.c_float * 3),
+                ("bound", ctypes.c_int), ("max_particles", ctypes.c_int), ("max_colliders", ctypes.c_int)]
+
+
+class mpm_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rho", ctypes.c_float), ("E", ctypes.c_float), ("nu", ctypes.c_float),
+                ("yield_stress", ctypes.c_float), ("bulk_modulus", ctypes.c_float), ("p_vol", ctypes.c_float)]
+
+
+class mpm_shape(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("half", ctypes.c_float * 3), ("friction", ctypes.c_float)]
+
+
+class MpmError(RuntimeError):
+    def __init__(self, fn, status, detail=""):
+        self.status = status
+        super().__init__(f"{fn}: {status_string(status)}{(' (' + detail + ')') if detail else ''}")
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    sig = {
+        "mpm_workspace_size": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.POINTER(ctypes.c_size_t)]),
+        "mpm_create": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), _vp, ctypes.c_size_t, _vp,
+                            ctypes.POINTER(_vp)]),
+        "mpm_set_particles": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+        "mpm_set_shapes": (st, [_vp, ctypes.c_int, ctypes.POINTER(mpm_shape)]),
+        "mpm_set_colliders": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
+        "mpm_substep": (st, [_vp, ctypes.c_int, _vp]),
+        "mpm_read_state": (st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+        "mpm_read_wrench": (st, [_vp, _vp, ctypes.POINTER(ctypes.c_int), _vp]),
+        "mpm_get_status": (st, [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.c_int, _vp]),
+        "mpm_num_particles": (ctypes.c_int, [_vp]),
+        "mpm_read_grid": (st, [_vp, _vp, _vp]),
+        "mpm_set_timing": (st, [_vp, ctypes.c_int]),
+        "mpm_read_timing": (st, [_vp, _vp, _vp, ctypes.c_int]),
+        "mpm_launch_count": (ctypes.c_longlong, [_vp]),
+        "mpm_destroy": (None, [_vp]),
+        "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mpm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def _check(fn, status):
+    if status != MPM_OK:
+        detail = _load().mpm_last_error().decode() if status == MPM_ERR_CUDA else ""
+        raise MpmError(fn, status, detail)
+
+
+def status_string(status: int) -> str:
+    return _load().mpm_status_string(status).decode()
+
+
+def mpm_workspace_size(cfg: mpm_config, mat: mpm_material) -> int:
+    out = ctypes.c_size_t(0)
+    _check("mpm_workspace_size", _load().mpm_workspace_size(ctypes.byref(cfg), ctypes.byref(mat), ctypes.byref(out)))
+    return out.value
+
+
+def mpm_create(cfg: mpm_config, mat: mpm_material, d_workspace: int, nbytes: int, stream: int = 0) -> int:
+    h = _vp()
+    _check("mpm_create", _load().mpm_create(ctypes.byref(cfg), ctypes.byref(mat), d_workspace, nbytes, stream,
+                                            ctypes.byref(h)))
+    return h.value
+
+
+def mpm_set_particles(sim: int, n: int, x: int, v: int = 0, C: int = 0, F: int = 0, src_on_device: int = 1,
+                      stream: int = 0) -> None:
+    _check("mpm_set_particles", _load().mpm_set_particles(sim, n, x or None, v or None, C or None, F or None,
+                                                          src_on_device, stream))
+
+
+def mpm_set_shapes(sim: int, shapes) -> None:
+    arr = (mpm_shape * max(1, len(shapes)))(*shapes)
+    _check("mpm_set_shapes", _load().mpm_set_shapes(sim, len(shapes), arr))
+
+
+def mpm_set_colliders(sim: int, k: int, pose: int, lin_vel: int, ang_vel: int = 0, com: int = 0,
+                      stream: int = 0) -> None:
+    _check("mpm_set_colliders", _load().mpm_set_colliders(sim, k, pose or None, lin_vel or None, ang_vel or None,
+                                                          com or None, stream))
+
+
+def mpm_substep(sim: int, n_substeps: int, stream: int = 0) -> None:
+    _check("mpm_substep", _load().mpm_substep(sim, n_substeps, stream))
+
+
+def mpm_read_state(sim: int, x: int = 0, v: int = 0, C: int = 0, F: int = 0, dst_on_device: int = 1,
+                   stream: int = 0) -> None:
+    _check("mpm_read_state", _load().mpm_read_state(sim, x or None, v or None, C or None, F or None, dst_on_device,
+                                                    stream))
+
+
+def mpm_read_wrench(sim: int, out: int, stream: int = 0) -> int:
+    n = ctypes.c_int(0)
+    _check("mpm_read_wrench", _load().mpm_read_wrench(sim, out or None, ctypes.byref(n), stream))
+    return n.value
+
+
+def mpm_get_status(sim: int, clear: int = 0, stream: int = 0) -> int:
+    f = ctypes.c_uint(0)
+    _check("mpm_get_status", _load().mpm_get_status(sim, ctypes.byref(f), clear, stream))
+    return f.value
+
+
+def mpm_num_particles(sim: int) -> int:
+    return _load().mpm_num_particles(sim)
+
+
+def mpm_read_grid(sim: int, d_out: int, stream: int = 0) -> None:
+    _check("mpm_read_grid", _load().mpm_read_grid(sim, d_out, stream))
+
+
+def mpm_set_timing(sim: int, enable: int) -> None:
+    _check("mpm_set_timing", _load().mpm_set_timing(sim, enable))
+
+
+def mpm_read_timing(sim: int, reset: int = 0):
+    ms = (ctypes.c_double * MPM_K_COUNT)()
+    cnt = (ctypes.c_longlong * MPM_K_COUNT)()
+    _check("mpm_read_timing", _load().mpm_read_timing(sim, ms, cnt, reset))
+    return list(ms), list(cnt)
+
+
+def mpm_launch_count(sim: int) -> int:
+    return _load().mpm_launch_count(sim)
+
+
+def mpm_destroy(sim: int) -> None:
+    _load().mpm_destroy(sim)
+
+
+def mpm_last_error() -> str:
+    return _load().mpm_last_error().decode()

@@ -1,0 +1,529 @@
+// mpm_abi.cu -- the C-ABI of include/mpm.h: argument checks, workspace layout, the per-substep launch
+// sequence and the readbacks. All device memory comes from the caller's workspace.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+
+using namespace mpm;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+mpm_status cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return MPM_ERR_CUDA;
+}
+
+#define MPM_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int kChunk = 128;       // particles per chunk = threads per CTA of the particle passes
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t state[2], key, perm, grid[2], flags[2], hist, cursor, chunks, colliders, wrench, counters, total;
+    size_t max_chunks;
+};
+
+Layout make_layout(const mpm_config& c) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t Nmax = (size_t)c.max_particles;
+    const size_t nb = (size_t)c.n / 4;
+    const size_t nblocks = nb * nb * nb;
+    const size_t nodes = nblocks * kBlkNodes;
+    for (int i = 0; i < 2; ++i) L.state[i] = take(Nmax * 25 * 4);
+    L.key = take(Nmax * 4);
+    L.perm = take(Nmax * 4);
+    for (int i = 0; i < 2; ++i) L.grid[i] = take(nodes * sizeof(float4));
+    for (int i = 0; i < 2; ++i) L.flags[i] = take(nblocks * 4);
+    L.hist = take(nblocks * 4);
+    L.cursor = take(nblocks * 4);
+    L.max_chunks = Nmax / kChunk + nblocks + 1;
+    L.chunks = take(L.max_chunks * sizeof(int4));
+    L.colliders = take(kMaxColliders * sizeof(ColliderSet));
+    L.wrench = take(kMaxColliders * 6 * sizeof(double));
+    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, spare
+    L.total = off;
+    return L;
+}
+
+mpm_status check_config(const mpm_config* c, const mpm_material* m) {
+    if (!c || !m) return MPM_ERR_INVALID_ARG;
+    if (c->n < 8 || c->n > 256 || (c->n % 4) != 0) return MPM_ERR_INVALID_ARG;
+    if (!(c->dt > 0.0f) || !std::isfinite(c->dt)) return MPM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(c->gravity[a])) return MPM_ERR_INVALID_ARG;
+    if (c->bound < 0 || 2 * c->bound > c->n) return MPM_ERR_INVALID_ARG;
+    if (c->max_particles < 1 || c->max_particles > (1 << 30)) return MPM_ERR_INVALID_ARG;
+    if (c->max_colliders < 0 || c->max_colliders > MPM_MAX_COLLIDERS) return MPM_ERR_INVALID_ARG;
+    if (m->kind != MPM_PLASTICINE && m->kind != MPM_FLUID) return MPM_ERR_INVALID_ARG;
+    if (!(m->rho > 0.0f) || !(m->p_vol > 0.0f)) return MPM_ERR_INVALID_ARG;
+    if (m->kind == MPM_PLASTICINE) {
+        if (!(m->E > 0.0f) || !(m->nu >= 0.0f && m->nu < 0.5f) || !(m->yield_stress >= 0.0f)) return MPM_ERR_INVALID_ARG;
+    } else {
+        if (!(m->bulk_modulus >= 0.0f)) return MPM_ERR_INVALID_ARG;
+    }
+    return MPM_OK;
+}
+
+}  // namespace
+
+struct mpm_sim {
+    mpm_config cfg;
+    mpm_material mat;
+    Layout L;
+    char* ws;
+    Geometry geo;
+    Material dmat;
+    int N = 0;
+    int cur = 0;        // state buffer holding the current particles
+    int g = 0;          // grid holding the pending particle-to-grid transfer of the current state
+    bool order_valid = false;
+    bool grid_valid = false;
+    int nshapes = 0;
+    mpm_shape shapes[MPM_MAX_COLLIDERS];
+    int ncol = 0;       // colliders uploaded by the last mpm_set_colliders
+    int sms = 0;
+    int ctas_fused = 0, ctas_p2g = 0;
+    long long launches = 0;
+    bool timing = false;
+    struct Ev { cudaEvent_t a, b; int kind; };
+    std::vector<Ev> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[MPM_K_COUNT] = {};
+    long long counts[MPM_K_COUNT] = {};
+
+    template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
+    uint32_t* status() { return at<uint32_t>(L.counters); }
+    uint32_t* substep_counter() { return at<uint32_t>(L.counters) + 1; }
+    uint32_t* num_chunks() { return at<uint32_t>(L.counters) + 2; }
+    StateView view(int which) {
+        float* b = at<float>(L.state[which]);
+        const size_t n = (size_t)N;
+        StateView s;
+        s.x = b;
+        s.v = b + 3 * n;
+        s.C = b + 6 * n;
+        s.F = b + 15 * n;
+        s.pid = reinterpret_cast<uint32_t*>(b + 24 * (size_t)cfg.max_particles);
+        return s;
+    }
+    cudaEvent_t get_event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+namespace {
+
+// Bracket a launch with timing events when enabled; count it either way.
+template <class F>
+mpm_status launch(mpm_sim* s, int kind, cudaStream_t st, F&& fn, const char* what) {
+    mpm_sim::Ev ev{nullptr, nullptr, kind};
+    if (s->timing) {
+        ev.a = s->get_event();
+        ev.b = s->get_event();
+        MPM_CUDA(cudaEventRecord(ev.a, st), "cudaEventRecord");
+    }
+    MPM_CUDA(fn(), what);
+    ++s->launches;
+    if (s->timing) {
+        MPM_CUDA(cudaEventRecord(ev.b, st), "cudaEventRecord");
+        s->pending.push_back(ev);
+    }
+    return MPM_OK;
+}
+
+TransferParams transfer_params(mpm_sim* s) {
+    TransferParams p{};
+    p.geo = s->geo;
+    p.mat = s->dmat;
+    p.N = s->N;
+    p.in = s->view(s->cur);
+    p.out = s->view(1 - s->cur);
+    p.perm = s->at<uint32_t>(s->L.perm);
+    p.key_out = s->at<uint32_t>(s->L.key);
+    p.hist = s->at<uint32_t>(s->L.hist);
+    p.chunks = s->at<int4>(s->L.chunks);
+    p.num_chunks = s->num_chunks();
+    p.status = s->status();
+    p.substep_counter = s->substep_counter();
+    return p;
+}
+
+// Sort the current particles into bins from the keys computed when they were written.
+mpm_status ensure_order(mpm_sim* s, cudaStream_t st) {
+    if (s->order_valid) return MPM_OK;
+    uint32_t* hist = s->at<uint32_t>(s->L.hist);
+    uint32_t* cursor = s->at<uint32_t>(s->L.cursor);
+    int4* chunks = s->at<int4>(s->L.chunks);
+    mpm_status r = launch(s, MPM_K_SCAN, st, [&] {
+        return launch_scan(hist, cursor, chunks, s->num_chunks(), s->geo.nblocks, kChunk, st);
+    }, "scan");
+    if (r != MPM_OK) return r;
+    r = launch(s, MPM_K_ASSIGN, st, [&] {
+        return launch_assign(s->N, s->at<uint32_t>(s->L.key), cursor, s->at<uint32_t>(s->L.perm), st);
+    }, "assign");
+    if (r != MPM_OK) return r;
+    s->order_valid = true;
+    return MPM_OK;
+}
+
+// Particle-to-grid transfer of the current state into grid g (only after the state was replaced).
+mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
+    if (s->grid_valid) return MPM_OK;
+    mpm_status r = ensure_order(s, st);
+    if (r != MPM_OK) return r;
+    TransferParams p = transfer_params(s);
+    p.grid_out = s->at<float4>(s->L.grid[s->g]);
+    p.flags_out = s->at<uint32_t>(s->L.flags[s->g]);
+    r = launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->mat.kind, s->ctas_p2g, kChunk, st); }, "p2g");
+    if (r != MPM_OK) return r;
+    s->grid_valid = true;
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpm_status_string(mpm_status s) {
+    switch (s) {
+        case MPM_OK: return "ok";
+        case MPM_ERR_INVALID_ARG: return "invalid argument";
+        case MPM_ERR_CUDA: return "CUDA error";
+        case MPM_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case MPM_ERR_CAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char* mpm_last_error(void) { return g_last_error; }
+
+mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes) {
+    if (!bytes) return MPM_ERR_INVALID_ARG;
+    mpm_status r = check_config(cfg, mat);
+    if (r != MPM_OK) return r;
+    *bytes = make_layout(*cfg).total;
+    return MPM_OK;
+}
+
+mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_workspace, size_t bytes, void* stream,
+                      mpm_sim** out) {
+    if (!out) return MPM_ERR_INVALID_ARG;
+    *out = nullptr;
+    mpm_status r = check_config(cfg, mat);
+    if (r != MPM_OK) return r;
+    Layout L = make_layout(*cfg);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) != 0 || bytes < L.total)
+        return MPM_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mpm_sim* s = new (std::nothrow) mpm_sim();
+    if (!s) return MPM_ERR_INVALID_ARG;
+    s->cfg = *cfg;
+    s->mat = *mat;
+    s->L = L;
+    s->ws = static_cast<char*>(d_workspace);
+    Geometry& g = s->geo;
+    g.n = cfg->n;
+    g.nb = cfg->n / 4;
+    g.nblocks = g.nb * g.nb * g.nb;
+    g.dx = (float)(1.0 / cfg->n);
+    g.inv_dx = (float)cfg->n;
+    g.dt = cfg->dt;
+    g.lo = (float)(2.0 / cfg->n);
+    g.hi = (float)(1.0 - 2.0 / cfg->n);
+    double mu, lambda;
+    if (mat->kind == MPM_PLASTICINE) {
+        mu = (double)mat->E / (2.0 * (1.0 + mat->nu));
+        lambda = (double)mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+    } else {
+        mu = 0.0;
+        lambda = mat->bulk_modulus;
+    }
+    s->dmat.mu = (float)mu;
+    s->dmat.lambda = (float)lambda;
+    s->dmat.yield_radius = mu > 0.0 ? (float)(mat->yield_stress / (2.0 * mu)) : 0.0f;
+    s->dmat.p_mass = (float)((double)mat->rho * mat->p_vol);
+    s->dmat.stress_scale = (float)(-(double)cfg->dt * mat->p_vol * 4.0 * cfg->n * cfg->n);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "device query");
+    }
+    s->ctas_fused = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, true);
+    s->ctas_p2g = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, false);
+    // zero the grids, bin flags and counts, colliders and counters
+    const size_t zero_from = L.grid[0];
+    e = cudaMemsetAsync(s->ws + zero_from, 0, L.total - zero_from, st);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    *out = s;
+    return MPM_OK;
+}
+
+void mpm_destroy(mpm_sim* s) {
+    if (!s) return;
+    for (auto& ev : s->pending) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    for (auto e : s->pool) cudaEventDestroy(e);
+    delete s;
+}
+
+int mpm_num_particles(const mpm_sim* s) { return s ? s->N : 0; }
+
+long long mpm_launch_count(const mpm_sim* s) { return s ? s->launches : 0; }
+
+mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, const float* C, const float* F,
+                             int src_on_device, void* stream) {
+    if (!s || n < 0 || (n > 0 && !x)) return MPM_ERR_INVALID_ARG;
+    if (n > s->cfg.max_particles) return MPM_ERR_CAPACITY;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // grids, bin flags and histogram restart from zero
+    const size_t z0 = s->L.grid[0], z1 = s->L.cursor;
+    MPM_CUDA(cudaMemsetAsync(s->ws + z0, 0, z1 - z0, st), "cudaMemsetAsync");
+    s->N = n;
+    s->cur = 0;
+    s->g = 0;
+    s->order_valid = false;
+    s->grid_valid = false;
+    if (n == 0) return MPM_OK;
+    const size_t N = (size_t)n;
+    const float *sx = x, *sv = v, *sC = C, *sF = F;
+    if (!src_on_device) {
+        // stage host arrays in the spare state buffer, same SoA layout
+        StateView stage = s->view(1);
+        MPM_CUDA(cudaMemcpyAsync(stage.x, x, 3 * N * 4, cudaMemcpyHostToDevice, st), "copy x");
+        sx = stage.x;
+        if (v) { MPM_CUDA(cudaMemcpyAsync(stage.v, v, 3 * N * 4, cudaMemcpyHostToDevice, st), "copy v"); sv = stage.v; }
+        if (C) { MPM_CUDA(cudaMemcpyAsync(stage.C, C, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy C"); sC = stage.C; }
+        if (F) { MPM_CUDA(cudaMemcpyAsync(stage.F, F, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy F"); sF = stage.F; }
+    }
+    StateView dst = s->view(0);
+    mpm_status r = launch(s, MPM_K_LOAD, st, [&] {
+        return launch_load(s->geo, s->mat.kind, n, sx, sv, sC, sF, dst, s->at<uint32_t>(s->L.key),
+                           s->at<uint32_t>(s->L.hist), s->status(), st);
+    }, "load");
+    if (r != MPM_OK) return r;
+    if (!src_on_device) MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return MPM_OK;
+}
+
+mpm_status mpm_set_shapes(mpm_sim* s, int k, const mpm_shape* shapes) {
+    if (!s || k < 0 || (k > 0 && !shapes)) return MPM_ERR_INVALID_ARG;
+    if (k > s->cfg.max_colliders) return MPM_ERR_CAPACITY;
+    for (int i = 0; i < k; ++i) {
+        const mpm_shape& sh = shapes[i];
+        if (sh.type != MPM_BOX && sh.type != MPM_CAPSULE) return MPM_ERR_INVALID_ARG;
+        if (!(sh.friction >= 0.0f) || !std::isfinite(sh.friction)) return MPM_ERR_INVALID_ARG;
+        int dims = sh.type == MPM_BOX ? 3 : 2;
+        for (int a = 0; a < dims; ++a)
+            if (!(sh.half[a] >= 0.0f) || !std::isfinite(sh.half[a])) return MPM_ERR_INVALID_ARG;
+    }
+    s->nshapes = k;
+    if (k) memcpy(s->shapes, shapes, sizeof(mpm_shape) * k);
+    return MPM_OK;
+}
+
+mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* lin_vel, const float* ang_vel,
+                             const float* com, void* stream) {
+    if (!s || k != s->nshapes || (k > 0 && (!pose || !lin_vel))) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ColliderUpload u{};
+    u.k = k;
+    for (int i = 0; i < k; ++i) {
+        ColliderSet& c = u.c[i];
+        const mpm_shape& sh = s->shapes[i];
+        c.type = sh.type;
+        for (int a = 0; a < 3; ++a) c.half[a] = sh.half[a];
+        c.friction = sh.friction;
+        float qn = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            c.pos[a] = pose[i * 7 + a];
+            c.lin[a] = lin_vel[i * 3 + a];
+            c.ang[a] = ang_vel ? ang_vel[i * 3 + a] : 0.0f;
+            c.com[a] = com ? com[i * 3 + a] : c.pos[a];
+        }
+        for (int a = 0; a < 4; ++a) {
+            c.quat[a] = pose[i * 7 + 3 + a];
+            qn += c.quat[a] * c.quat[a];
+        }
+        if (!(qn > 0.0f) || !std::isfinite(qn)) return MPM_ERR_INVALID_ARG;
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(c.pos[a]) || !std::isfinite(c.lin[a]) || !std::isfinite(c.ang[a]) ||
+                !std::isfinite(c.com[a]))
+                return MPM_ERR_INVALID_ARG;
+    }
+    mpm_status r = launch(s, MPM_K_COLLIDERS, st, [&] {
+        return launch_set_colliders(u, s->at<ColliderSet>(s->L.colliders), s->at<double>(s->L.wrench),
+                                    s->substep_counter(), st);
+    }, "set_colliders");
+    if (r != MPM_OK) return r;
+    s->ncol = k;
+    return MPM_OK;
+}
+
+mpm_status mpm_substep(mpm_sim* s, int n_substeps, void* stream) {
+    if (!s || n_substeps < 0) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_substeps == 0) return MPM_OK;
+    if (s->N == 0) {
+        return launch(s, MPM_K_COLLIDERS, st, [&] { return launch_advance_counter(s->substep_counter(), n_substeps, st); },
+                      "advance");
+    }
+    for (int it = 0; it < n_substeps; ++it) {
+        mpm_status r = ensure_grid(s, st);  // sorts first if needed
+        if (r != MPM_OK) return r;
+        GridParams gp{};
+        gp.geo = s->geo;
+        for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
+        gp.bound = s->cfg.bound;
+        gp.grid = s->at<float4>(s->L.grid[s->g]);
+        gp.flags = s->at<uint32_t>(s->L.flags[s->g]);
+        gp.grid_old = s->at<float4>(s->L.grid[1 - s->g]);
+        gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->g]);
+        gp.cols = s->at<ColliderSet>(s->L.colliders);
+        gp.ncol = s->ncol;
+        gp.substep_counter = s->substep_counter();
+        gp.wrench = s->at<double>(s->L.wrench);
+        r = launch(s, MPM_K_GRID, st, [&] { return launch_grid_update(gp, st); }, "grid_update");
+        if (r != MPM_OK) return r;
+        TransferParams p = transfer_params(s);
+        p.grid_in = gp.grid;
+        p.grid_out = gp.grid_old;
+        p.flags_out = gp.flags_old;
+        r = launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->mat.kind, s->ctas_fused, kChunk, st); },
+                   "g2p2g");
+        if (r != MPM_OK) return r;
+        s->cur = 1 - s->cur;
+        s->g = 1 - s->g;
+        s->order_valid = false;   // keys of the new state are written, the sort is pending
+        s->grid_valid = true;     // grid g holds the transfer of the new state
+        r = ensure_order(s, st);
+        if (r != MPM_OK) return r;
+    }
+    return MPM_OK;
+}
+
+mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, int dst_on_device, void* stream) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->N == 0) return MPM_OK;
+    const size_t N = (size_t)s->N;
+    StateView src = s->view(s->cur);
+    if (dst_on_device) {
+        return launch(s, MPM_K_READ, st, [&] { return launch_read_state(s->mat.kind, s->N, src, x, v, C, F, st); },
+                      "read_state");
+    }
+    StateView stage = s->view(1 - s->cur);
+    mpm_status r = launch(s, MPM_K_READ, st, [&] {
+        return launch_read_state(s->mat.kind, s->N, src, x ? stage.x : nullptr, v ? stage.v : nullptr,
+                                 C ? stage.C : nullptr, F ? stage.F : nullptr, st);
+    }, "read_state");
+    if (r != MPM_OK) return r;
+    if (x) MPM_CUDA(cudaMemcpyAsync(x, stage.x, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy x");
+    if (v) MPM_CUDA(cudaMemcpyAsync(v, stage.v, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy v");
+    if (C) MPM_CUDA(cudaMemcpyAsync(C, stage.C, 9 * N * 4, cudaMemcpyDeviceToHost, st), "copy C");
+    if (F) MPM_CUDA(cudaMemcpyAsync(F, stage.F, 9 * N * 4, cudaMemcpyDeviceToHost, st), "copy F");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return MPM_OK;
+}
+
+mpm_status mpm_read_wrench(mpm_sim* s, double* out, int* n_substeps, void* stream) {
+    if (!s || (s->ncol > 0 && !out)) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->ncol > 0)
+        MPM_CUDA(cudaMemcpyAsync(out, s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st), "copy wrench");
+    uint32_t cnt = 0;
+    MPM_CUDA(cudaMemcpyAsync(&cnt, s->substep_counter(), 4, cudaMemcpyDeviceToHost, st), "copy counter");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (n_substeps) *n_substeps = (int)cnt;
+    return MPM_OK;
+}
+
+mpm_status mpm_get_status(mpm_sim* s, unsigned* flags, int clear, void* stream) {
+    if (!s || !flags) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t f = 0;
+    MPM_CUDA(cudaMemcpyAsync(&f, s->status(), 4, cudaMemcpyDeviceToHost, st), "copy status");
+    if (clear) MPM_CUDA(cudaMemsetAsync(s->status(), 0, 4, st), "clear status");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    *flags = f;
+    return MPM_OK;
+}
+
+mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
+    if (!s || !d_out) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->N > 0) {
+        mpm_status r = ensure_grid(s, st);
+        if (r != MPM_OK) return r;
+    }
+    const float4* grid = s->at<float4>(s->L.grid[s->g]);
+    return launch(s, MPM_K_READ, st, [&] { return launch_read_grid(s->geo, grid, d_out, st); }, "read_grid");
+}
+
+mpm_status mpm_set_timing(mpm_sim* s, int enable) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    s->timing = enable != 0;
+    return MPM_OK;
+}
+
+mpm_status mpm_read_timing(mpm_sim* s, double* ms, long long* launches, int reset) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    for (auto& ev : s->pending) {
+        MPM_CUDA(cudaEventSynchronize(ev.b), "cudaEventSynchronize");
+        float t = 0.0f;
+        MPM_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b), "cudaEventElapsedTime");
+        s->ms[ev.kind] += t;
+        s->counts[ev.kind] += 1;
+        s->pool.push_back(ev.a);
+        s->pool.push_back(ev.b);
+    }
+    s->pending.clear();
+    for (int k = 0; k < MPM_K_COUNT; ++k) {
+        if (ms) ms[k] = s->ms[k];
+        if (launches) launches[k] = s->counts[k];
+    }
+    if (reset) {
+        for (int k = 0; k < MPM_K_COUNT; ++k) {
+            s->ms[k] = 0.0;
+            s->counts[k] = 0;
+        }
+    }
+    return MPM_OK;
+}
+
+}  // extern "C"

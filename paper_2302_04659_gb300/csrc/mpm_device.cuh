@@ -1,0 +1,362 @@
+// mpm_device.cuh -- device-side building blocks of the MLS-MPM substep (FP32, sm_103a).
+//
+// The paper (Sec. 3; App. D.1, Algorithm 1) names the solver, MLS-MPM in the
+// style of PlasticineLab, and the order of a soft step; the equations are the
+// published methods it points to: quadratic B-spline APIC/MLS transfers
+// (Jiang et al. 2015; Hu et al. 2018), fixed-corotated elasticity, von Mises
+// plasticity in Hencky strain, a J-only weakly compressible fluid, and
+// grid-node Coulomb contact against analytic box / capsule distances.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpm {
+
+// Grid blocks are 4^3 nodes stored contiguously (block-major): node (i,j,k) lives at
+// block ((i>>2)*nb + (j>>2))*nb + (k>>2), slot ((i&3)*4 + (j&3))*4 + (k&3).
+constexpr int kBlk = 4;
+constexpr int kBlkNodes = 64;
+constexpr int kGatherEdge = 6;   // a block's particles read nodes [4b, 4b+6) per axis
+constexpr int kScatterEdge = 8;  // after one substep they write nodes [4b-1, 4b+7) per axis
+constexpr int kGatherNodes = kGatherEdge * kGatherEdge * kGatherEdge;
+constexpr int kScatterNodes = kScatterEdge * kScatterEdge * kScatterEdge;
+constexpr int kMaxColliders = 32;
+
+__host__ __device__ __forceinline__ uint32_t block_index(int bx, int by, int bz, int nb) {
+    return (uint32_t)((bx * nb + by) * nb + bz);
+}
+
+__host__ __device__ __forceinline__ uint32_t node_index(int i, int j, int k, int nb) {
+    return block_index(i >> 2, j >> 2, k >> 2, nb) * kBlkNodes + (uint32_t)(((i & 3) * 4 + (j & 3)) * 4 + (k & 3));
+}
+
+// Lowest stencil node per axis: floor(x/dx - 0.5). Written with _rn intrinsics so the key pass and
+// the transfer passes, in different kernels, always round identically (no FMA contraction).
+__device__ __forceinline__ int cell_base(float x, float inv_dx) {
+    return __float2int_rd(__fsub_rn(__fmul_rn(x, inv_dx), 0.5f));
+}
+
+__device__ __forceinline__ float cell_frac(float x, float inv_dx, int base) {
+    return __fsub_rn(__fmul_rn(x, inv_dx), (float)base);
+}
+
+// Quadratic B-spline weights of the nodes base, base+1, base+2 at distances fx, fx-1, fx-2 (cells).
+__device__ __forceinline__ void bspline_weights(float fx, float w[3]) {
+    float a = 1.5f - fx, b = fx - 1.0f, c = fx - 0.5f;
+    w[0] = 0.5f * a * a;
+    w[1] = 0.75f - b * b;
+    w[2] = 0.5f * c * c;
+}
+
+// ------------------------------------------------------------------------ 3x3 SVD (FP32)
+//
+// F = U diag(sig) V^T with det U = det V = +1, |sig| descending and sig[2] < 0 iff det F < 0.
+// V from cyclic Jacobi on the symmetric S = F^T F (exact Givens rotations, Golub & Van Loan
+// Sec. 8.5.2); then B = F V, columns sorted by length, and U by Gram-Schmidt on B's columns with the
+// third column u0 x u1, which fixes det U = +1 and puts the sign of det F on sig[2].
+
+template <int P, int Q, int R>
+__device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&V)[3][3]) {
+    float apq = S[P][Q];
+    if (apq == 0.0f) return;
+    float tau = (S[Q][Q] - S[P][P]) / (2.0f * apq);
+    float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    float c = rsqrtf(fmaf(t, t, 1.0f));
+    float s = t * c;
+    S[P][P] -= t * apq;
+    S[Q][Q] += t * apq;
+    S[P][Q] = S[Q][P] = 0.0f;
+    float arp = S[R][P], arq = S[R][Q];
+    S[R][P] = S[P][R] = c * arp - s * arq;
+    S[R][Q] = S[Q][R] = s * arp + c * arq;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float vp = V[r][P], vq = V[r][Q];
+        V[r][P] = c * vp - s * vq;
+        V[r][Q] = s * vp + c * vq;
+    }
+}
+
+__device__ __forceinline__ void swap_cols_keep_det(float (&B)[3][3], float (&V)[3][3], float (&len)[3], int a,
+                                                   int b) {
+    // swapping two columns flips det V; negating one of them restores it (B = F V follows V)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float tb = B[r][a]; B[r][a] = B[r][b]; B[r][b] = -tb;
+        float tv = V[r][a]; V[r][a] = V[r][b]; V[r][b] = -tv;
+    }
+    float tl = len[a]; len[a] = len[b]; len[b] = tl;
+}
+
+__device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3][3], float (&sig)[3], float (&V)[3][3]) {
+    float S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            S[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0f : 0.0f;
+    for (int sweep = 0; sweep < 6; ++sweep) {
+        float off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
+        float diag = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
+        if (off <= 1e-15f * diag) break;
+        jacobi_rotation<0, 1, 2>(S, V);
+        jacobi_rotation<0, 2, 1>(S, V);
+        jacobi_rotation<1, 2, 0>(S, V);
+    }
+    float B[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * V[0][j] + F[i][1] * V[1][j] + F[i][2] * V[2][j];
+    float len[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) len[j] = B[0][j] * B[0][j] + B[1][j] * B[1][j] + B[2][j] * B[2][j];
+    if (len[1] > len[0]) swap_cols_keep_det(B, V, len, 0, 1);
+    if (len[2] > len[0]) swap_cols_keep_det(B, V, len, 0, 2);
+    if (len[2] > len[1]) swap_cols_keep_det(B, V, len, 1, 2);
+    // Gram-Schmidt
+    float s0 = sqrtf(len[0]);
+    float u0[3], u1[3];
+    if (s0 > 1e-30f) {
+        float r = 1.0f / s0;
+        u0[0] = B[0][0] * r; u0[1] = B[1][0] * r; u0[2] = B[2][0] * r;
+    } else {
+        u0[0] = 1.0f; u0[1] = 0.0f; u0[2] = 0.0f;
+        s0 = 0.0f;
+    }
+    float d01 = u0[0] * B[0][1] + u0[1] * B[1][1] + u0[2] * B[2][1];
+    float w1[3] = {B[0][1] - d01 * u0[0], B[1][1] - d01 * u0[1], B[2][1] - d01 * u0[2]};
+    float s1 = sqrtf(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
+    if (s1 > 1e-30f && s1 > 1e-7f * s0) {
+        float r = 1.0f / s1;
+        u1[0] = w1[0] * r; u1[1] = w1[1] * r; u1[2] = w1[2] * r;
+    } else {
+        // any unit vector orthogonal to u0
+        float e[3] = {fabsf(u0[0]) < 0.9f ? 1.0f : 0.0f, fabsf(u0[0]) < 0.9f ? 0.0f : 1.0f, 0.0f};
+        float c[3] = {u0[1] * e[2] - u0[2] * e[1], u0[2] * e[0] - u0[0] * e[2], u0[0] * e[1] - u0[1] * e[0]};
+        float r = rsqrtf(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        u1[0] = c[0] * r; u1[1] = c[1] * r; u1[2] = c[2] * r;
+        s1 = u1[0] * B[0][1] + u1[1] * B[1][1] + u1[2] * B[2][1];
+    }
+    float u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
+    float s2 = u2[0] * B[0][2] + u2[1] * B[1][2] + u2[2] * B[2][2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        U[r][0] = u0[r];
+        U[r][1] = u1[r];
+        U[r][2] = u2[r];
+    }
+    sig[0] = s0;
+    sig[1] = s1;
+    sig[2] = s2;
+}
+
+// ------------------------------------------------------------------------ constitutive update
+//
+// Plasticine: fixed-corotated elasticity, tau = 2 mu (F - R) F^T + lambda J (J - 1) I, with a von Mises
+// return map in Hencky strain: eps = log sig, the deviatoric part of eps is pulled back onto the sphere
+// of radius tau_Y / (2 mu) when it lies outside, the trace is kept, F = U exp(eps) V^T.
+// With the SVD of the trial F at hand, the stress of the returned F is U diag(d) U^T with
+// d_i = 2 mu (s_i - 1) s_i + lambda J (J - 1), s = returned singular values, J = s0 s1 s2.
+
+struct Material {
+    float mu, lambda, yield_radius;  // yield_radius = tau_Y / (2 mu)
+    float p_mass, stress_scale;      // stress_scale = -dt V0 4 / dx^2
+};
+
+// In: trial F (overwritten by the returned F). Out: Kirchhoff stress tau. Returns flag bits.
+__device__ __forceinline__ uint32_t plastic_update_and_stress(float (&F)[3][3], const Material& m,
+                                                              float (&tau)[3][3]) {
+    float U[3][3], V[3][3], sig[3];
+    svd3(F, U, sig, V);
+    uint32_t flags = 0;
+    float eps[3];
+    bool clamp = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float s = sig[i];
+        if (s < 1e-6f) { s = 1e-6f; clamp = true; }
+        eps[i] = logf(s);
+    }
+    float tr3 = (eps[0] + eps[1] + eps[2]) * (1.0f / 3.0f);
+    float dev[3] = {eps[0] - tr3, eps[1] - tr3, eps[2] - tr3};
+    float dn = sqrtf(dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]);
+    float dgamma = dn - m.yield_radius;
+    float s[3] = {sig[0], sig[1], sig[2]};
+    if (dgamma > 0.0f || clamp) {
+        if (dgamma > 0.0f) {
+            float k = dgamma / dn;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) eps[i] -= k * dev[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[i] = expf(eps[i]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                F[r][c] = U[r][0] * s[0] * V[c][0] + U[r][1] * s[1] * V[c][1] + U[r][2] * s[2] * V[c][2];
+        if (clamp) flags |= 0x4u;
+    }
+    float J = s[0] * s[1] * s[2];
+    float vol = m.lambda * J * (J - 1.0f);
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = 2.0f * m.mu * (s[i] - 1.0f) * s[i] + vol;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
+            tau[r][c] = t;
+            tau[c][r] = t;
+        }
+    return flags;
+}
+
+// Stress of a given (already returned) F, used by the standalone particle-to-grid pass.
+__device__ __forceinline__ void fixed_corotated_stress(const float (&F)[3][3], const Material& m, float (&tau)[3][3]) {
+    float U[3][3], V[3][3], sig[3];
+    svd3(F, U, sig, V);
+    float J = sig[0] * sig[1] * sig[2];
+    float vol = m.lambda * J * (J - 1.0f);
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = 2.0f * m.mu * (sig[i] - 1.0f) * sig[i] + vol;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
+            tau[r][c] = t;
+            tau[c][r] = t;
+        }
+}
+
+__device__ __forceinline__ float det3(const float (&A)[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// ------------------------------------------------------------------------ colliders
+//
+// Algorithm 1 copies body poses and velocities once per rigid step; between copies each body moves
+// rigidly with those velocities: com(t) = com0 + t v, orientation Rot(w t) R0 (Rodrigues), frame
+// origin carried about the centre of mass.
+
+struct ColliderSet {  // as set by the host (one entry per body)
+    int type;
+    float half[3];
+    float friction;
+    float pos[3];
+    float quat[4];  // w x y z
+    float lin[3];
+    float ang[3];
+    float com[3];
+};
+
+struct ColliderNow {  // pose at the current substep
+    float R[9];       // row-major, local -> world
+    float p[3];
+    float com[3];
+    float lin[3];
+    float ang[3];
+    float half[3];
+    float friction;
+    int type;
+};
+
+__device__ __forceinline__ void collider_at(const ColliderSet& c, float t, ColliderNow& o) {
+    float w = c.quat[0], x = c.quat[1], y = c.quat[2], z = c.quat[3];
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    float R0[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                   2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                   2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    float th[3] = {c.ang[0] * t, c.ang[1] * t, c.ang[2] * t};
+    float a = sqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+    float Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (a > 0.0f) {
+        float k[3] = {th[0] / a, th[1] / a, th[2] / a};
+        float K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+        float sa = sinf(a);
+        float h = sinf(0.5f * a);
+        float ca = 2.0f * h * h;  // 1 - cos a
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float k2 = K[i * 3 + 0] * K[0 * 3 + j] + K[i * 3 + 1] * K[1 * 3 + j] + K[i * 3 + 2] * K[2 * 3 + j];
+                Q[i * 3 + j] += sa * K[i * 3 + j] + ca * k2;
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            o.R[i * 3 + j] = Q[i * 3 + 0] * R0[0 * 3 + j] + Q[i * 3 + 1] * R0[1 * 3 + j] + Q[i * 3 + 2] * R0[2 * 3 + j];
+    float d[3] = {c.pos[0] - c.com[0], c.pos[1] - c.com[1], c.pos[2] - c.com[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        o.com[i] = c.com[i] + t * c.lin[i];
+        o.p[i] = o.com[i] + Q[i * 3] * d[0] + Q[i * 3 + 1] * d[1] + Q[i * 3 + 2] * d[2];
+        o.lin[i] = c.lin[i];
+        o.ang[i] = c.ang[i];
+        o.half[i] = c.half[i];
+    }
+    o.friction = c.friction;
+    o.type = c.type;
+}
+
+// Signed distance and world-space outward normal of point xw (analytic box / capsule, Sec. 3).
+__device__ __forceinline__ float collider_sdf(const ColliderNow& c, const float xw[3], float n[3]) {
+    float d[3] = {xw[0] - c.p[0], xw[1] - c.p[1], xw[2] - c.p[2]};
+    float l[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) l[i] = c.R[i] * d[0] + c.R[3 + i] * d[1] + c.R[6 + i] * d[2];
+    float nl[3] = {0.0f, 0.0f, 0.0f};
+    float phi;
+    if (c.type == 0) {
+        float q[3], qo[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            q[i] = fabsf(l[i]) - c.half[i];
+            qo[i] = fmaxf(q[i], 0.0f);
+        }
+        float outside = sqrtf(qo[0] * qo[0] + qo[1] * qo[1] + qo[2] * qo[2]);
+        int am = 0;
+        if (q[1] > q[am]) am = 1;
+        if (q[2] > q[am]) am = 2;
+        float qmax = q[am];
+        phi = outside + fminf(qmax, 0.0f);
+        if (outside > 0.0f) {
+            float r = 1.0f / outside;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) nl[i] = (l[i] >= 0.0f ? 1.0f : -1.0f) * qo[i] * r;
+        } else {
+            nl[am] = l[am] >= 0.0f ? 1.0f : -1.0f;
+        }
+    } else {
+        float r = c.half[0], h = c.half[1];
+        float cz = fminf(fmaxf(l[2], -h), h);
+        float e[3] = {l[0], l[1], l[2] - cz};
+        float el = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        phi = el - r;
+        if (el > 0.0f) {
+            float ri = 1.0f / el;
+            nl[0] = e[0] * ri; nl[1] = e[1] * ri; nl[2] = e[2] * ri;
+        } else {
+            nl[0] = 1.0f;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n[i] = c.R[i * 3] * nl[0] + c.R[i * 3 + 1] * nl[1] + c.R[i * 3 + 2] * nl[2];
+    return phi;
+}
+
+}  // namespace mpm

@@ -1,0 +1,689 @@
+// mpm_kernels.cu -- the CUDA kernels of the MLS-MPM substep (FP32, sm_103a).
+//
+// One substep (Algorithm 1's soft step: particle to grid, grid velocity, grid to particle, particle
+// integration) runs as
+//   k_scan + k_assign   counting sort of particles into 4^3-node bins (block-sparse grid)
+//   k_grid_update       v = mv/m + dt g, box/capsule Coulomb contact with per-body impulse
+//                       reduction, sticky walls; zeroes the previous grid's active bins
+//   k_g2p2g             per bin: gather v and C from a shared-memory tile of the updated grid,
+//                       advect, update F with the plastic return map (or J), and in the same pass
+//                       scatter the new state's mass and momentum (with its stress) into a
+//                       shared-memory tile of the next grid, flushed with vector atomics.
+// Fusing grid-to-particle with the next substep's particle-to-grid (the "G2P2G" pattern of Wang et
+// al. 2020) reads each particle's x and F once per substep and its v, C not at all: they are
+// recomputed by the gather. k_p2g is the standalone transfer used after the state is replaced.
+#include <cuda_runtime.h>
+
+#include "mpm_device.cuh"
+#include "mpm_internal.h"
+
+namespace mpm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t bin_of(const float x[3], const Geometry& g) {
+    int b0 = cell_base(x[0], g.inv_dx) >> 2;
+    int b1 = cell_base(x[1], g.inv_dx) >> 2;
+    int b2 = cell_base(x[2], g.inv_dx) >> 2;
+    return block_index(b0, b1, b2, g.nb);
+}
+
+// Clamp a coordinate into [lo, hi]; a NaN goes to lo. Returns flag bits.
+__device__ __forceinline__ uint32_t clamp_coord(float& x, float lo, float hi) {
+    uint32_t f = 0;
+    if (!isfinite(x)) f |= 0x2u;
+    if (!(x >= lo) || !(x <= hi)) f |= 0x1u;
+    x = fminf(fmaxf(x, lo), hi);
+    return f;
+}
+
+// Warp-aggregated histogram increment; every lane of the warp must call it (key = ~0u: no count).
+__device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, bool want_base) {
+    uint32_t peers = __match_any_sync(0xffffffffu, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader && key != 0xffffffffu) base = atomicAdd(&hist[key], (uint32_t)__popc(peers));
+    if (want_base) {
+        base = __shfl_sync(0xffffffffu, base, leader);
+        base += __popc(peers & ((1u << lane) - 1u));
+    }
+    return base;
+}
+
+// ------------------------------------------------------------------------ scatter tile
+
+struct ScatterTile {
+    float m[kScatterNodes];
+    float px[kScatterNodes];
+    float py[kScatterNodes];
+    float pz[kScatterNodes];
+    uint32_t touched[27];
+};
+
+// Scatter one particle's mass and momentum to its 27 nodes. The tile covers nodes [o, o+8) per axis with
+// o = 4 * bin - 1; outside it (a particle that moved a cell or more since it was binned) the nodes are
+// updated directly in global memory. mom(node) = w (m v + A (x_i - x_p)), written with the affine
+// part expanded per node index: base_mom + i Ad0 + j Ad1 + k Ad2.
+__device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const TransferParams& p, const int o[3],
+                                                     const float xn[3], const float vn[3], const float (&A)[3][3]) {
+    const Geometry& g = p.geo;
+    int bs[3];
+    float f[3], w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bs[a] = cell_base(xn[a], g.inv_dx);
+        f[a] = cell_frac(xn[a], g.inv_dx, bs[a]);
+        bspline_weights(f[a], w[a]);
+    }
+    const float m = p.mat.p_mass;
+    float Ad[3][3];  // Ad[c] = dx * column c of A
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Ad[c][r] = g.dx * A[r][c];
+    float bm[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) bm[r] = m * vn[r] - (Ad[0][r] * f[0] + Ad[1][r] * f[1] + Ad[2][r] * f[2]);
+    int l[3] = {bs[0] - o[0], bs[1] - o[1], bs[2] - o[2]};
+    bool in_tile = (unsigned)l[0] <= 5u && (unsigned)l[1] <= 5u && (unsigned)l[2] <= 5u;
+    if (in_tile) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float wij = w[0][i] * w[1][j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float wk = wij * w[2][k];
+                    int t = ((l[0] + i) * kScatterEdge + (l[1] + j)) * kScatterEdge + (l[2] + k);
+                    float mx = bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0];
+                    float my = bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1];
+                    float mz = bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2];
+                    atomicAdd(&T.m[t], wk * m);
+                    atomicAdd(&T.px[t], wk * mx);
+                    atomicAdd(&T.py[t], wk * my);
+                    atomicAdd(&T.pz[t], wk * mz);
+                }
+            }
+        return 0;
+    }
+    // far move: direct global atomics, marking every bin touched
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i)
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j)
+#pragma unroll 1
+            for (int k = 0; k < 3; ++k) {
+                float wk = w[0][i] * w[1][j] * w[2][k];
+                int gx = bs[0] + i, gy = bs[1] + j, gz = bs[2] + k;
+                float4 add = make_float4(wk * m, wk * (bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0]),
+                                         wk * (bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1]),
+                                         wk * (bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2]));
+                atomicAdd(&p.grid_out[node_index(gx, gy, gz, g.nb)], add);
+                p.flags_out[block_index(gx >> 2, gy >> 2, gz >> 2, g.nb)] = 1u;
+            }
+    return 0x8u;
+}
+
+__device__ __forceinline__ void tile_clear(ScatterTile& T) {
+    for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
+        T.m[t] = 0.0f;
+        T.px[t] = 0.0f;
+        T.py[t] = 0.0f;
+        T.pz[t] = 0.0f;
+    }
+    if (threadIdx.x < 27) T.touched[threadIdx.x] = 0u;
+}
+
+// Add the tile's nonzero nodes to the global grid with one 16-byte vector atomic each, then mark the
+// bins that received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
+__device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, int bx, int by, int bz) {
+    const int nb = p.geo.nb;
+    for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
+        float m = T.m[t];
+        if (m == 0.0f) continue;
+        int ti = t / (kScatterEdge * kScatterEdge), tj = (t / kScatterEdge) % kScatterEdge, tk = t % kScatterEdge;
+        int gx = 4 * bx - 1 + ti, gy = 4 * by - 1 + tj, gz = 4 * bz - 1 + tk;
+        atomicAdd(&p.grid_out[node_index(gx, gy, gz, nb)], make_float4(m, T.px[t], T.py[t], T.pz[t]));
+        int qx = (gx >> 2) - bx + 1, qy = (gy >> 2) - by + 1, qz = (gz >> 2) - bz + 1;
+        T.touched[(qx * 3 + qy) * 3 + qz] = 1u;
+    }
+    __syncthreads();
+    if (threadIdx.x < 27 && T.touched[threadIdx.x]) {
+        int q = threadIdx.x;
+        int qx = q / 9, qy = (q / 3) % 3, qz = q % 3;
+        p.flags_out[block_index(bx + qx - 1, by + qy - 1, bz + qz - 1, nb)] = 1u;
+    }
+}
+
+__device__ __forceinline__ void load_mat(const float* base, int N, uint32_t i, float (&M)[3][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[r][c] = base[(size_t)(r * 3 + c) * N + i];
+}
+
+__device__ __forceinline__ void store_mat(float* base, int N, uint32_t i, const float (&M)[3][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) base[(size_t)(r * 3 + c) * N + i] = M[r][c];
+}
+
+// A = m C - dt V0 (4/dx^2) tau: the MLS-MPM affine momentum with the stress impulse folded in.
+__device__ __forceinline__ void affine(const Material& mat, const float (&C)[3][3], const float (&tau)[3][3],
+                                       float (&A)[3][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[r][c] = mat.p_mass * C[r][c] + mat.stress_scale * tau[r][c];
+}
+
+__device__ __forceinline__ void decode_bin(int b, int nb, int& bx, int& by, int& bz) {
+    bz = b % nb;
+    by = (b / nb) % nb;
+    bx = b / (nb * nb);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ set_particles
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __restrict__ x,
+                                              const float* __restrict__ v, const float* __restrict__ C,
+                                              const float* __restrict__ F, StateView dst, uint32_t* key,
+                                              uint32_t* hist, uint32_t* status) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = p < N;
+    uint32_t flags = 0, k = 0xffffffffu;
+    if (active) {
+        float xp[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = x[(size_t)a * N + p];
+            flags |= clamp_coord(xp[a], g.lo, g.hi);
+            dst.x[(size_t)a * N + p] = xp[a];
+            dst.v[(size_t)a * N + p] = v ? v[(size_t)a * N + p] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst.C[(size_t)i * N + p] = C ? C[(size_t)i * N + p] : 0.0f;
+        if (KIND == 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst.F[(size_t)i * N + p] = F ? F[(size_t)i * N + p] : ((i % 4 == 0) ? 1.0f : 0.0f);
+        } else {
+            float J = 1.0f;
+            if (F) {
+                float M[3][3];
+                load_mat(F, N, p, M);
+                J = det3(M);
+            }
+            dst.F[p] = J;
+        }
+        dst.pid[p] = (uint32_t)p;
+        k = bin_of(xp, g);
+        key[p] = k;
+    }
+    warp_hist_add(hist, k, false);
+    if (flags) atomicOr(status, flags);
+}
+
+// ------------------------------------------------------------------------ counting sort into bins
+
+// One CTA: exclusive scan of the bin counts -> bin start offsets (cursor) and the chunk list: each bin
+// is cut into chunks of at most `chunk` particles, one chunk per CTA iteration of the particle passes.
+// The counts are zeroed for the next histogram.
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor, int4* chunks,
+                                               uint32_t* num_chunks, int nblocks, int chunk) {
+    __shared__ uint32_t warp_tot[2][32];
+    const int tid = threadIdx.x;
+    const int per = (nblocks + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
+    uint32_t cnt = 0, nch = 0;
+    for (int b = b0; b < b1; ++b) {
+        uint32_t c = hist[b];
+        cnt += c;
+        nch += (c + chunk - 1) / chunk;
+    }
+    // block-wide exclusive scan of (cnt, nch)
+    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t ic = cnt, in = nch;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t tc = __shfl_up_sync(0xffffffffu, ic, d), tn = __shfl_up_sync(0xffffffffu, in, d);
+        if (lane >= d) { ic += tc; in += tn; }
+    }
+    if (lane == 31) { warp_tot[0][wid] = ic; warp_tot[1][wid] = in; }
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t vc = lane < nw ? warp_tot[0][lane] : 0u, vn = lane < nw ? warp_tot[1][lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t tc = __shfl_up_sync(0xffffffffu, vc, d), tn = __shfl_up_sync(0xffffffffu, vn, d);
+            if (lane >= d) { vc += tc; vn += tn; }
+        }
+        if (lane < nw) { warp_tot[0][lane] = vc; warp_tot[1][lane] = vn; }
+    }
+    __syncthreads();
+    uint32_t off = ic - cnt + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
+    uint32_t coff = in - nch + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
+    for (int b = b0; b < b1; ++b) {
+        uint32_t c = hist[b];
+        cursor[b] = off;
+        for (uint32_t s = 0; s < c; s += chunk) {
+            chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
+        }
+        off += c;
+        hist[b] = 0u;
+    }
+    if (tid == blockDim.x - 1) *num_chunks = coff;
+}
+
+// Sorted slot of every particle: slot = start of its bin + rank among the bin's particles (ranks are
+// handed out per warp with one atomic, so runs of one warp stay contiguous and in order).
+__global__ void __launch_bounds__(256) k_assign(int N, const uint32_t* __restrict__ key, uint32_t* cursor,
+                                                uint32_t* __restrict__ perm) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t k = j < N ? key[j] : 0xffffffffu;
+    uint32_t slot = warp_hist_add(cursor, k, true);
+    if (j < N) perm[slot] = (uint32_t)j;
+}
+
+// ------------------------------------------------------------------------ standalone P2G
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_p2g(TransferParams p) {
+    __shared__ ScatterTile T;
+    const Geometry& g = p.geo;
+    const int N = p.N;
+    uint32_t flags = 0;
+    const uint32_t nchunks = *p.num_chunks;
+    for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
+        int4 ch = p.chunks[w];
+        int bx, by, bz;
+        decode_bin(ch.x, g.nb, bx, by, bz);
+        const int o[3] = {4 * bx - 1, 4 * by - 1, 4 * bz - 1};
+        tile_clear(T);
+        __syncthreads();
+        for (int q = threadIdx.x; q < ch.z; q += blockDim.x) {
+            uint32_t src = p.perm[ch.y + q];
+            float x[3], v[3], C[3][3], tau[3][3], A[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[a] = p.in.x[(size_t)a * N + src];
+                v[a] = p.in.v[(size_t)a * N + src];
+            }
+            load_mat(p.in.C, N, src, C);
+            if (KIND == 0) {
+                float F[3][3];
+                load_mat(p.in.F, N, src, F);
+                fixed_corotated_stress(F, p.mat, tau);
+            } else {
+                float J = p.in.F[src];
+                float s = p.mat.lambda * J * (J - 1.0f);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
+            }
+            affine(p.mat, C, tau, A);
+            flags |= scatter_particle(T, p, o, x, v, A);
+        }
+        __syncthreads();
+        tile_flush(T, p, bx, by, bz);
+        __syncthreads();
+    }
+    if (flags) atomicOr(p.status, flags);
+}
+
+// ------------------------------------------------------------------------ fused G2P -> P2G
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_g2p2g(TransferParams p) {
+    __shared__ float4 G[kGatherNodes];
+    __shared__ ScatterTile T;
+    const Geometry& g = p.geo;
+    const int N = p.N;
+    const float dt = g.dt;
+    uint32_t flags = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
+    const uint32_t nchunks = *p.num_chunks;
+    for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
+        int4 ch = p.chunks[w];
+        int bx, by, bz;
+        decode_bin(ch.x, g.nb, bx, by, bz);
+        const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
+        for (int t = threadIdx.x; t < kGatherNodes; t += blockDim.x) {
+            int i = t / 36, j = (t / 6) % 6, k = t % 6;
+            int gx = ox + i, gy = oy + j, gz = oz + k;
+            float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (gx < g.n && gy < g.n && gz < g.n) val = p.grid_in[node_index(gx, gy, gz, g.nb)];
+            G[t] = val;
+        }
+        tile_clear(T);
+        __syncthreads();
+        const int o[3] = {ox - 1, oy - 1, oz - 1};
+        for (int q0 = 0; q0 < ch.z; q0 += blockDim.x) {
+            const int q = q0 + threadIdx.x;
+            const bool active = q < ch.z;
+            uint32_t newkey = 0xffffffffu;
+            if (active) {
+                const uint32_t slot = (uint32_t)(ch.y + q);
+                const uint32_t src = p.perm[slot];
+                float x[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
+                // ---- G2P: v = sum w v_i, C = 4/dx sum w v_i (i - f)^T (offsets in cells)
+                int bs[3];
+                float f[3], w[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    bs[a] = cell_base(x[a], g.inv_dx);
+                    f[a] = cell_frac(x[a], g.inv_dx, bs[a]);
+                    bspline_weights(f[a], w[a]);
+                }
+                int l0 = bs[0] - ox, l1 = bs[1] - oy, l2 = bs[2] - oz;
+                if ((unsigned)l0 > 3u || (unsigned)l1 > 3u || (unsigned)l2 > 3u) {
+                    flags |= kFlagInternal;
+                    l0 = min(max(l0, 0), 3); l1 = min(max(l1, 0), 3); l2 = min(max(l2, 0), 3);
+                }
+                float vn[3] = {0.0f, 0.0f, 0.0f};
+                float M[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        float wij = w[0][i] * w[1][j];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            float wk = wij * w[2][k];
+                            float4 gv = G[((l0 + i) * kGatherEdge + (l1 + j)) * kGatherEdge + (l2 + k)];
+                            float wv[3] = {wk * gv.x, wk * gv.y, wk * gv.z};
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                vn[a] += wv[a];
+                                if (i) M[a][0] += (float)i * wv[a];
+                                if (j) M[a][1] += (float)j * wv[a];
+                                if (k) M[a][2] += (float)k * wv[a];
+                            }
+                        }
+                    }
+                float Cn[3][3];
+                const float cs = 4.0f * g.inv_dx;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Cn[a][c] = cs * (M[a][c] - vn[a] * f[c]);
+                // ---- advect and clamp
+                float xn[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    xn[a] = x[a] + dt * vn[a];
+                    if (!isfinite(vn[a])) flags |= 0x2u;
+                    flags |= clamp_coord(xn[a], g.lo, g.hi);
+                }
+                // ---- F (or J) update, return map, stress of the new state
+                float Gm[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Gm[a][c] = (a == c ? 1.0f : 0.0f) + dt * Cn[a][c];
+                float tau[3][3];
+                if (KIND == 0) {
+                    float F[3][3], Ft[3][3];
+                    load_mat(p.in.F, N, src, F);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Ft[a][c] = Gm[a][0] * F[0][c] + Gm[a][1] * F[1][c] + Gm[a][2] * F[2][c];
+                    flags |= plastic_update_and_stress(Ft, p.mat, tau);
+                    store_mat(p.out.F, N, slot, Ft);
+                } else {
+                    float J = p.in.F[src] * det3(Gm);
+                    float s = p.mat.lambda * J * (J - 1.0f);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
+                    p.out.F[slot] = J;
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    p.out.x[(size_t)a * N + slot] = xn[a];
+                    p.out.v[(size_t)a * N + slot] = vn[a];
+                }
+                store_mat(p.out.C, N, slot, Cn);
+                p.out.pid[slot] = p.in.pid[src];
+                newkey = bin_of(xn, g);
+                p.key_out[slot] = newkey;
+                // ---- P2G of the new state into the next grid
+                float A[3][3];
+                affine(p.mat, Cn, tau, A);
+                flags |= scatter_particle(T, p, o, xn, vn, A);
+            }
+            warp_hist_add(p.hist, newkey, false);
+        }
+        __syncthreads();
+        tile_flush(T, p, bx, by, bz);
+        __syncthreads();
+    }
+    if (flags) atomicOr(p.status, flags);
+}
+
+// ------------------------------------------------------------------------ grid update
+
+// 256 threads = four 4^3 bins; bins without mass are skipped. Zeroes the bins of the previous grid
+// that were active, so the next fused pass scatters into a clean grid.
+__global__ void __launch_bounds__(256) k_grid_update(GridParams p) {
+    __shared__ ColliderNow cn[kMaxColliders];
+    __shared__ float wr[kMaxColliders * 6];
+    const Geometry& g = p.geo;
+    const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
+    const int b = blockIdx.x * 4 + grp;
+    bool has_old = false, has_new = false;
+    if (b < g.nblocks) {
+        has_old = p.flags_old[b] != 0u;
+        has_new = p.flags[b] != 0u;
+    }
+    if (!__syncthreads_or(has_old || has_new)) return;
+    const float t = (float)(*p.substep_counter) * g.dt;
+    if (threadIdx.x < p.ncol) collider_at(p.cols[threadIdx.x], t, cn[threadIdx.x]);
+    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) wr[i] = 0.0f;
+    __syncthreads();
+    if (has_old) {
+        p.grid_old[(size_t)b * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (ln == 0) p.flags_old[b] = 0u;
+    }
+    if (has_new) {
+        float4* node = &p.grid[(size_t)b * kBlkNodes + ln];
+        float4 gv = *node;
+        if (gv.x > 0.0f) {
+            const float m = gv.x;
+            const float im = 1.0f / m;
+            float v[3] = {gv.y * im + g.dt * p.gravity[0], gv.z * im + g.dt * p.gravity[1],
+                          gv.w * im + g.dt * p.gravity[2]};
+            int bx, by, bz;
+            decode_bin(b, g.nb, bx, by, bz);
+            const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
+            const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
+            for (int c = 0; c < p.ncol; ++c) {
+                float nrm[3];
+                float phi = collider_sdf(cn[c], xi, nrm);
+                if (!(phi < 0.0f)) continue;
+                float rel[3] = {xi[0] - cn[c].com[0], xi[1] - cn[c].com[1], xi[2] - cn[c].com[2]};
+                const float* om = cn[c].ang;
+                float vc[3] = {cn[c].lin[0] + om[1] * rel[2] - om[2] * rel[1],
+                               cn[c].lin[1] + om[2] * rel[0] - om[0] * rel[2],
+                               cn[c].lin[2] + om[0] * rel[1] - om[1] * rel[0]};
+                float vr[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
+                float vnrm = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
+                if (!(vnrm < 0.0f)) continue;
+                float vt[3] = {vr[0] - vnrm * nrm[0], vr[1] - vnrm * nrm[1], vr[2] - vnrm * nrm[2]};
+                float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+                float mu = cn[c].friction;
+                float vnew[3];
+                if (tn <= -mu * vnrm) {
+                    vnew[0] = vc[0]; vnew[1] = vc[1]; vnew[2] = vc[2];
+                } else {
+                    float s = 1.0f + mu * vnrm / tn;
+                    vnew[0] = vc[0] + vt[0] * s; vnew[1] = vc[1] + vt[1] * s; vnew[2] = vc[2] + vt[2] * s;
+                }
+                float imp[3] = {m * (v[0] - vnew[0]), m * (v[1] - vnew[1]), m * (v[2] - vnew[2])};
+                atomicAdd(&wr[c * 6 + 0], imp[0]);
+                atomicAdd(&wr[c * 6 + 1], imp[1]);
+                atomicAdd(&wr[c * 6 + 2], imp[2]);
+                atomicAdd(&wr[c * 6 + 3], rel[1] * imp[2] - rel[2] * imp[1]);
+                atomicAdd(&wr[c * 6 + 4], rel[2] * imp[0] - rel[0] * imp[2]);
+                atomicAdd(&wr[c * 6 + 5], rel[0] * imp[1] - rel[1] * imp[0]);
+                v[0] = vnew[0]; v[1] = vnew[1]; v[2] = vnew[2];
+            }
+            const int lo = p.bound, hi = g.n - p.bound;
+            if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
+            *node = make_float4(v[0], v[1], v[2], m);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) {
+        float val = wr[i];
+        if (val != 0.0f) atomicAdd(&p.wrench[i], (double)val);
+    }
+}
+
+// ------------------------------------------------------------------------ readback
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_read_state(int N, StateView s, float* x, float* v, float* C, float* F) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    uint32_t p = s.pid[j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (x) x[(size_t)a * N + p] = s.x[(size_t)a * N + j];
+        if (v) v[(size_t)a * N + p] = s.v[(size_t)a * N + j];
+    }
+    if (C) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) C[(size_t)i * N + p] = s.C[(size_t)i * N + j];
+    }
+    if (F) {
+        if (KIND == 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) F[(size_t)i * N + p] = s.F[(size_t)i * N + j];
+        } else {
+            float c = cbrtf(s.F[j]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) F[(size_t)i * N + p] = (i % 4 == 0) ? c : 0.0f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_read_grid(Geometry g, const float4* __restrict__ grid, float4* out) {
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)g.n * g.n * g.n;
+    if (t >= total) return;
+    int k = (int)(t % g.n), j = (int)((t / g.n) % g.n), i = (int)(t / ((size_t)g.n * g.n));
+    out[t] = grid[node_index(i, j, k, g.nb)];
+}
+
+__global__ void k_set_colliders(ColliderUpload u, ColliderSet* table, double* wrench, uint32_t* counter) {
+    int t = threadIdx.x;
+    if (t < u.k) table[t] = u.c[t];
+    for (int i = t; i < u.k * 6; i += blockDim.x) wrench[i] = 0.0;
+    if (t == 0) *counter = 0u;
+}
+
+__global__ void k_advance_counter(uint32_t* counter, int n) {
+    if (threadIdx.x == 0) *counter += (uint32_t)n;
+}
+
+// ------------------------------------------------------------------------ launch wrappers
+
+static inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+cudaError_t launch_load(const Geometry& g, int kind, int N, const float* x, const float* v, const float* C,
+                        const float* F, StateView dst, uint32_t* key, uint32_t* hist, uint32_t* status,
+                        cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    if (kind == 0)
+        k_load<0><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, key, hist, status);
+    else
+        k_load<1><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, key, hist, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks, int nblocks,
+                        int chunk, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(hist, cursor, chunks, num_chunks, nblocks, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign(int N, const uint32_t* key, uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    k_assign<<<ceil_div(N, 256), 256, 0, s>>>(N, key, cursor, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s) {
+    if (kind == 0)
+        k_p2g<0><<<grid_ctas, threads, 0, s>>>(p);
+    else
+        k_p2g<1><<<grid_ctas, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s) {
+    if (kind == 0)
+        k_g2p2g<0><<<grid_ctas, threads, 0, s>>>(p);
+    else
+        k_g2p2g<1><<<grid_ctas, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s) {
+    k_grid_update<<<ceil_div(p.geo.nblocks, 4), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
+                              cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    if (kind == 0)
+        k_read_state<0><<<ceil_div(N, 256), 256, 0, s>>>(N, src, x, v, C, F);
+    else
+        k_read_state<1><<<ceil_div(N, 256), 256, 0, s>>>(N, src, x, v, C, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, cudaStream_t s) {
+    size_t total = (size_t)g.n * g.n * g.n;
+    k_read_grid<<<ceil_div(total, 256), 256, 0, s>>>(g, grid, reinterpret_cast<float4*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_colliders(const ColliderUpload& u, ColliderSet* table, double* wrench, uint32_t* counter,
+                                 cudaStream_t s) {
+    k_set_colliders<<<1, 256, 0, s>>>(u, table, wrench, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s) {
+    k_advance_counter<<<1, 32, 0, s>>>(counter, n);
+    return cudaGetLastError();
+}
+
+int transfer_ctas_per_sm(int kind, int threads, bool fused) {
+    int n = 0;
+    cudaError_t e;
+    if (fused)
+        e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g<0>, threads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g<1>, threads, 0);
+    else
+        e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g<0>, threads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g<1>, threads, 0);
+    if (e != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+}  // namespace mpm

@@ -1,0 +1,123 @@
+"""``Sim``: one soft-body scene on the GPU, driven through the C-ABI with PyTorch memory and streams.
+
+PyTorch only supplies the device workspace and the current CUDA stream; every
+step of the substep runs in the CUDA library (``_native``). Host arrays may be
+numpy or CPU tensors, device arrays CUDA tensors; all are FP32 SoA with the
+particle index fastest (x (3,N), v (3,N), C (9,N), F (9,N)).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as mpm
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return 0
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("device arrays must be contiguous float32 CUDA tensors")
+    return t.data_ptr()
+
+
+class Sim:
+    def __init__(self, n: int, dt: float, material, max_particles: int, gravity=(0.0, -9.8, 0.0), bound: int = 3,
+                 max_colliders: int = 8, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.cfg = mpm.mpm_config(n, dt, (ctypes.c_float * 3)(*gravity), bound, max_particles, max_colliders)
+        self.mat = mpm.mpm_material(material.kind, material.rho, material.E, material.nu, material.yield_stress,
+                                    material.bulk_modulus, material.p_vol)
+        nbytes = mpm.mpm_workspace_size(self.cfg, self.mat)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.handle = mpm.mpm_create(self.cfg, self.mat, self.workspace.data_ptr(), nbytes, _stream())
+        self.n = n
+        self.k = 0
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            torch.cuda.synchronize(self.device)
+            mpm.mpm_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def N(self) -> int:
+        return mpm.mpm_num_particles(self.handle)
+
+    # ------------------------------------------------------------------ state
+    def set_particles(self, x, v=None, C=None, F=None, stream=None):
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            n = x.shape[1]
+            mpm.mpm_set_particles(self.handle, n, _dev_ptr(x), _dev_ptr(v), _dev_ptr(C), _dev_ptr(F), 1,
+                                  _stream(stream))
+            return
+        arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float32)) for a in (x, v, C, F)]
+        n = arrs[0].shape[1]
+        ptrs = [0 if a is None else a.ctypes.data for a in arrs]
+        mpm.mpm_set_particles(self.handle, n, *ptrs, 0, _stream(stream))
+
+    def read_state(self, on_device: bool = True, stream=None):
+        N = self.N
+        if on_device:
+            out = {k: torch.empty((d, N), dtype=torch.float32, device=self.device)
+                   for k, d in (("x", 3), ("v", 3), ("C", 9), ("F", 9))}
+            mpm.mpm_read_state(self.handle, *(out[k].data_ptr() for k in ("x", "v", "C", "F")), 1, _stream(stream))
+            return out
+        out = {k: np.empty((d, N), dtype=np.float32) for k, d in (("x", 3), ("v", 3), ("C", 9), ("F", 9))}
+        if N:
+            mpm.mpm_read_state(self.handle, *(out[k].ctypes.data for k in ("x", "v", "C", "F")), 0, _stream(stream))
+        return out
+
+    def read_grid(self, stream=None):
+        g = torch.zeros((self.n, self.n, self.n, 4), dtype=torch.float32, device=self.device)
+        mpm.mpm_read_grid(self.handle, g.data_ptr(), _stream(stream))
+        return g
+
+    # ------------------------------------------------------------------ colliders
+    def set_shapes(self, shapes):
+        arr = [mpm.mpm_shape(s.type, (ctypes.c_float * 3)(*s.half), s.friction) for s in shapes]
+        mpm.mpm_set_shapes(self.handle, arr)
+        self.k = len(arr)
+
+    def set_colliders(self, pose, lin_vel, ang_vel=None, com=None, stream=None):
+        arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+                for a in (pose, lin_vel, ang_vel, com)]
+        ptrs = [0 if a is None else a.ctypes.data for a in arrs]
+        mpm.mpm_set_colliders(self.handle, self.k, *ptrs, _stream(stream))
+
+    def read_wrench(self, stream=None):
+        out = np.zeros((max(self.k, 1), 6), dtype=np.float64)
+        n = mpm.mpm_read_wrench(self.handle, out.ctypes.data, _stream(stream))
+        return out[: self.k], n
+
+    # ------------------------------------------------------------------ stepping
+    def substep(self, n: int = 1, stream=None):
+        mpm.mpm_substep(self.handle, n, _stream(stream))
+
+    def status(self, clear: bool = False, stream=None) -> int:
+        return mpm.mpm_get_status(self.handle, int(clear), _stream(stream))
+
+    def set_timing(self, on: bool):
+        mpm.mpm_set_timing(self.handle, int(on))
+
+    def read_timing(self, reset: bool = False):
+        ms, cnt = mpm.mpm_read_timing(self.handle, int(reset))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(mpm.KERNEL_NAMES)}
+
+    @property
+    def launches(self) -> int:
+        return mpm.mpm_launch_count(self.handle)

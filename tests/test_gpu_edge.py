@@ -1,0 +1,163 @@
+"""GPU edge cases through the C-ABI: empty and ragged inputs, contention, far moves, bad inputs,
+checkpoint/resume, device-side I/O and the wrench/status bookkeeping."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import TOL_V, TOL_X, make_sim, oracle_params, oracle_state, rel
+from paper_2302_04659_gb300 import _native as mpm
+from paper_2302_04659_gb300 import scenes
+from test_gpu_parity import assert_state_close, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2302_04659_gb300 import build
+    build.build()
+    yield
+
+
+def random_scene(N, seed, n=32, lo=0.3, hi=0.7, v_std=0.5, C_std=5.0, gravity=(0.0, -9.8, 0.0), bound=3):
+    x = (lo + (hi - lo) * scenes.uniform(seed, 3 * N).reshape(3, N)).astype(np.float32)
+    v, C, F = scenes.random_state(N, seed + 1, v_std=v_std, C_std=C_std)
+    mat = scenes.Material(scenes.PLASTICINE, p_vol=(0.25 ** 3) / 8192)
+    return scenes.Scene(n=n, dt=2e-4, material=mat, x=x, v=v, C=C, F=F, gravity=gravity, bound=bound)
+
+
+def one_step_parity(sc, nsub=1):
+    out, flags, _ = run_gpu(sc, nsub)
+    ref = oracle_state(sc)
+    oracle.rollout(oracle_params(sc), ref, nsub)
+    assert_state_close(out, ref)
+    return flags
+
+
+def test_empty_scene():
+    sc = scenes.cube_scene("floor")
+    sim = make_sim(sc)
+    sim.set_particles(np.zeros((3, 0), np.float32))
+    sim.substep(3)
+    assert sim.N == 0
+    st = sim.read_state(on_device=False)
+    assert st["x"].shape == (3, 0)
+    sim.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 31, 33, 129, 4097])
+def test_ragged_counts(N):
+    flags = one_step_parity(random_scene(N, 100 + N))
+    assert not (flags & mpm.MPM_FLAG_INTERNAL)
+
+
+def test_many_particles_in_one_cell():
+    """2,000 particles inside one cell: every atomic of the shared tile hits the same 27 nodes."""
+    N = 2000
+    n = 32
+    dx = 1.0 / n
+    sc = random_scene(N, 7, n=n, lo=0.5 + 0.1 * dx, hi=0.5 + 0.9 * dx)
+    one_step_parity(sc)
+
+
+def test_bins_spanning_several_chunks():
+    """A dense blob whose bins hold several chunks each, and a sparse tail of lone particles."""
+    N = 20000
+    sc = random_scene(N, 11, n=32, lo=0.45, hi=0.55)
+    one_step_parity(sc)
+
+
+def test_far_move_served_by_slow_path():
+    """Particles crossing more than a cell per substep still transfer exactly (global-atomic path)."""
+    N = 3000
+    sc = random_scene(N, 13, n=32, lo=0.4, hi=0.6, v_std=0.1, C_std=0.5, gravity=(0.0, 0.0, 0.0), bound=0)
+    sc.v[0] += 300.0  # 300 m/s * 2e-4 s = 0.06 = 1.9 cells
+    flags = one_step_parity(sc, nsub=2)
+    assert flags & mpm.MPM_FLAG_FAR_MOVE
+
+
+def test_out_of_domain_and_nonfinite_inputs_are_flagged():
+    sc = random_scene(256, 17)
+    sc.x[0, 3] = 1.5
+    sc.x[1, 5] = -0.2
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    assert sim.status() & mpm.MPM_FLAG_CLAMPED
+    st = sim.read_state(on_device=False)
+    dx = 1.0 / sc.n
+    assert st["x"][0, 3] == np.float32(1 - 2 * dx) and st["x"][1, 5] == np.float32(2 * dx)
+    sc.x[2, 7] = np.nan
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.substep(2)
+    f = sim.status(clear=True)
+    assert f & mpm.MPM_FLAG_NONFINITE
+    assert sim.status() == 0
+    st = sim.read_state(on_device=False)
+    assert np.all(st["x"] >= 2 * dx - 1e-7) or np.isnan(st["x"]).any() is False
+    sim.close()
+
+
+def test_checkpoint_resume_matches_uninterrupted():
+    sc = scenes.cube_scene("floor")
+    a, _, _ = run_gpu(sc, 20)
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.substep(10)
+    mid = sim.read_state(on_device=False)
+    sim.close()
+    sim2 = make_sim(sc)
+    sim2.set_particles(mid["x"], mid["v"], mid["C"], mid["F"])
+    sim2.substep(10)
+    b = sim2.read_state(on_device=False)
+    sim2.close()
+    for k in ("x", "v", "C", "F"):
+        assert rel(b[k], a[k]) <= 1e-5, k
+
+
+def test_device_io_matches_host_io():
+    sc = scenes.cube_scene("rand")
+    sim = make_sim(sc)
+    dev = {k: torch.from_numpy(getattr(sc, k)).cuda() for k in ("x", "v", "C", "F")}
+    sim.set_particles(dev["x"], dev["v"], dev["C"], dev["F"])
+    sim.substep(2)
+    d = sim.read_state(on_device=True)
+    h = sim.read_state(on_device=False)
+    for k in ("x", "v", "C", "F"):
+        assert np.array_equal(d[k].cpu().numpy(), h[k]), k
+    ref = oracle_state(sc)
+    oracle.rollout(oracle_params(sc), ref, 2)
+    assert rel(h["x"], ref.x) <= TOL_X and rel(h["v"], ref.v) <= TOL_V
+    sim.close()
+
+
+def test_wrench_bookkeeping_and_timing():
+    sc = scenes.pinch_scene(seed=1002, N=20000)
+    pose, lin, ang, com = scenes.finger_state(sc, 0.2)
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.set_shapes(sc.shapes)
+    sim.set_colliders(pose, lin, ang, com)
+    sim.set_timing(True)
+    sim.substep(5)
+    w1, n1 = sim.read_wrench()
+    assert n1 == 5 and np.abs(w1).max() > 0
+    sim.set_colliders(pose, lin, ang, com)
+    w0, n0 = sim.read_wrench()
+    assert n0 == 0 and np.all(w0 == 0)
+    sim.substep(1)
+    t = sim.read_timing(reset=True)
+    assert t["g2p2g"][1] == 6 and t["grid_update"][1] == 6 and t["g2p2g"][0] > 0
+    assert sim.launches > 0
+    sim.close()
+
+
+def test_capacity_and_argument_errors():
+    sc = scenes.cube_scene("floor")
+    sim = make_sim(sc, max_particles=100)
+    with pytest.raises(mpm.MpmError) as e:
+        sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    assert e.value.status == mpm.MPM_ERR_CAPACITY
+    with pytest.raises(mpm.MpmError):
+        mpm.mpm_substep(sim.handle, -1, 0)
+    sim.close()

@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA substep (through the C-ABI) against the FP64 oracle on identical FP32 inputs.
+
+Per-substep comparisons start both sides from the same FP32 state (seeded, or an
+oracle state rounded to FP32) and compare element by element, in the particles'
+original order, with the tolerances of ``gpu_helpers``. Rollouts compare
+aggregate statistics, since atomic accumulation order makes the GPU sums
+nondeterministic.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (TOL_C, TOL_F, TOL_V, TOL_X, chamfer, fluid_scene, make_sim, oracle_colliders,
+                         oracle_params, oracle_state, rel, stats)
+from paper_2302_04659_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2302_04659_gb300 import build
+    build.build()
+    yield
+
+
+def run_gpu(sc, nsub, colliders=None):
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    if colliders is not None:
+        sim.set_shapes(sc.shapes)
+        sim.set_colliders(*colliders)
+    sim.substep(nsub)
+    out = sim.read_state(on_device=False)
+    flags = sim.status()
+    wrench = sim.read_wrench() if colliders is not None else None
+    sim.close()
+    return out, flags, wrench
+
+
+def assert_state_close(out, ref, kind=scenes.PLASTICINE, tol_x=TOL_X, tol_v=TOL_V, tol_c=TOL_C, tol_f=TOL_F,
+                       mask=None):
+    sel = (lambda a: a[:, mask]) if mask is not None else (lambda a: a)
+    ex = rel(sel(out["x"]), sel(ref.x))
+    ev = rel(sel(out["v"]), sel(ref.v))
+    ec = rel(sel(out["C"]), sel(ref.C))
+    if kind == scenes.PLASTICINE:
+        ef = rel(sel(out["F"]), sel(ref.F))
+    else:
+        J = np.prod(out["F"][[0, 4, 8]].astype(np.float64), axis=0)
+        ef = rel(J[mask] if mask is not None else J, ref.J[mask] if mask is not None else ref.J)
+    assert ex <= tol_x, f"e_x = {ex:.3e}"
+    assert ev <= tol_v, f"e_v = {ev:.3e}"
+    assert ec <= tol_c, f"e_C = {ec:.3e}"
+    assert ef <= tol_f, f"e_F = {ef:.3e}"
+    return ex, ev, ec, ef
+
+
+# ---------------------------------------------------------------------------- particle to grid
+
+def test_p2g_grid_matches_oracle():
+    sc = scenes.cube_scene("rand")
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    g = sim.read_grid().cpu().numpy().astype(np.float64)
+    sim.close()
+    ref = oracle.p2g(oracle_params(sc), oracle_state(sc))
+    assert abs(g[..., 0].sum() - ref[..., 0].sum()) <= 1e-6 * ref[..., 0].sum()
+    assert rel(g[..., 0], ref[..., 0]) < 1e-6
+    assert rel(g[..., 1:], ref[..., 1:]) < 1e-5
+    assert np.all((g[..., 0] > 0) == (ref[..., 0] > 0))
+
+
+# ---------------------------------------------------------------------------- one substep, element-wise
+
+@pytest.mark.parametrize("variant", ["rand", "floor", "ff"])
+def test_one_substep_cube(variant):
+    sc = scenes.cube_scene(variant)
+    out, flags, _ = run_gpu(sc, 1)
+    ref = oracle_state(sc)
+    oracle.substep(oracle_params(sc), ref)
+    assert_state_close(out, ref)
+    assert not (flags & 0x80000000), "particle found outside its bin"
+
+
+def test_substeps_from_oracle_states():
+    """Per-substep parity along the cube-on-floor rollout: both sides restart from the oracle's state
+    (rounded to FP32) after 0, 10, 25 and 40 substeps and take one substep."""
+    sc = scenes.cube_scene("floor")
+    P = oracle_params(sc)
+    s = oracle_state(sc)
+    done = 0
+    for k in (0, 10, 25, 40):
+        oracle.rollout(P, s, k - done)
+        done = k
+        x, v, C, F = (a.astype(np.float32) for a in (s.x, s.v, s.C, s.F))
+        sck = scenes.Scene(n=sc.n, dt=sc.dt, material=sc.material, x=x, v=v, C=C, F=F)
+        out, _, _ = run_gpu(sck, 1)
+        ref = oracle_state(sck)
+        oracle.substep(P, ref)
+        assert_state_close(out, ref)
+
+
+def test_one_substep_fluid():
+    sc = fluid_scene()
+    out, _, _ = run_gpu(sc, 1)
+    ref = oracle_state(sc)
+    oracle.substep(oracle_params(sc), ref)
+    assert_state_close(out, ref, kind=scenes.FLUID)
+
+
+def _pinch_at(seed, t):
+    sc = scenes.pinch_scene(seed=seed)
+    return sc, scenes.finger_state(sc, t)
+
+
+def test_pinch_full_size_one_substep_with_colliders():
+    """The 200k-particle, 64^3 pinch workload with both fingers pressed into the ellipsoid: one substep,
+    every particle compared, plus the per-finger impulse and angular impulse."""
+    sc, (pose, lin, ang, com) = _pinch_at(1000, 0.15)
+    out, flags, (wr, nsub) = run_gpu(sc, 1, (pose, lin, ang, com))
+    ref = oracle_state(sc)
+    P = oracle_params(sc)
+    cols = oracle_colliders(sc, pose, lin, ang, com)
+    _, wref, amb = oracle.substep(P, ref, cols, 0.0, want_ambiguous=True)
+    # particles whose stencil touches a node where the inside test or normal is within 1e-6 of flipping
+    # (FP32 and FP64 may take different branches there) are excluded; there must be very few
+    keep = np.ones(sc.N, bool)
+    if amb.any():
+        n = sc.n
+        base = np.floor(sc.x.astype(np.float64) * n - 0.5).astype(int)
+        ai = np.argwhere(amb)
+        bad = np.zeros(sc.N, bool)
+        for node in ai:
+            inside = np.all((node[:, None] >= base) & (node[:, None] <= base + 2), axis=0)
+            bad |= inside
+        keep = ~bad
+    assert (~keep).sum() <= 1e-3 * sc.N
+    assert_state_close(out, ref, mask=keep)
+    assert nsub == 1
+    assert rel(wr[:, :3], wref[:, :3]) < 1e-4
+    assert rel(wr[:, 3:], wref[:, 3:]) < 1e-4
+    assert np.abs(wref).max() > 0, "fingers should touch the plasticine"
+
+
+# ---------------------------------------------------------------------------- rollouts
+
+def test_cube_rollout_statistics():
+    """50 substeps of the cube on the floor: aggregate statistics against the oracle's rollout."""
+    sc = scenes.cube_scene("floor")
+    out, flags, _ = run_gpu(sc, 50)
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    oracle.rollout(P, ref, 50)
+    m = P.c().p_mass
+    a, b = stats(out["x"], out["v"], m), stats(ref.x, ref.v, m)
+    dx = 1.0 / sc.n
+    assert np.abs(a["com"] - b["com"]).max() <= 1e-4
+    assert np.abs(a["p"] - b["p"]).max() <= 1e-3 * np.abs(b["p"]).max()
+    assert abs(a["ke"] - b["ke"]) <= 1e-3 * b["ke"]
+    assert np.abs(a["lo"] - b["lo"]).max() <= 0.1 * dx and np.abs(a["hi"] - b["hi"]).max() <= 0.1 * dx
+    assert chamfer(out["x"], ref.x) <= 0.1 * dx
+    # per-particle positions after a full rollout still agree closely
+    assert rel(out["x"], ref.x) <= 1e-4
+
+
+def test_pinch_one_env_step_position_error():
+    """One environment step (25 substeps) of the pinch scene with the fingers closing: positions after
+    the step within 1e-3 relative of the oracle, the aggregate error bound for whole env steps."""
+    sc, (pose, lin, ang, com) = _pinch_at(1001, 0.1)
+    out, flags, (wr, nsub) = run_gpu(sc, 25, (pose, lin, ang, com))
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    cols = oracle_colliders(sc, pose, lin, ang, com)
+    wref = np.zeros((2, 6))
+    oracle.rollout(P, ref, 25, cols, 0.0, wref)
+    assert nsub == 25
+    assert rel(out["x"], ref.x) <= 1e-3
+    disp_gpu = out["x"].astype(np.float64) - sc.x
+    disp_ref = ref.x - sc.x
+    assert rel(disp_gpu, disp_ref) <= 2e-2
+    assert rel(wr, wref) <= 1e-2
