@@ -149,13 +149,24 @@ int mpm_num_particles(const mpm_sim* sim);
  * (i,j,k) at ((i*n + j)*n + k)*4. Device destination only; enqueued on `stream`. */
 mpm_status mpm_read_grid(mpm_sim* sim, float* d_out, void* stream);
 
-/* Diagnostics: kernel timing. While enabled, every kernel launch of the handle is bracketed by CUDA
- * events on its stream. mpm_read_timing synchronizes and returns, per kernel kind (MPM_K_*), the summed
- * milliseconds and launch counts since the last reset (arrays of MPM_K_COUNT entries, either NULL). */
+/* Diagnostics: kernel timing. Every launch of a kernel kind whose bit (1 << MPM_K_*) is set in
+ * kernel_mask is bracketed by CUDA events on its stream (inside replayed graphs too: the events are
+ * swapped on every replay); 0 turns timing off. mpm_read_timing synchronizes and returns, per kernel kind,
+ * the summed milliseconds and launch counts since the last reset (arrays of MPM_K_COUNT entries, either
+ * may be NULL). Kinds: load (set_particles), scan and assign (bin sort after set_particles), p2g
+ * (transfer after set_particles), grid (sort-assign + grid update, once per substep), g2p2g (fused
+ * grid-to-particle / particle-to-grid with the bin scan, once per substep), read (readbacks),
+ * colliders (collider upload). */
 enum { MPM_K_LOAD = 0, MPM_K_SCAN, MPM_K_ASSIGN, MPM_K_P2G, MPM_K_GRID, MPM_K_G2P2G, MPM_K_READ,
        MPM_K_COLLIDERS, MPM_K_COUNT };
-mpm_status mpm_set_timing(mpm_sim* sim, int enable);
+mpm_status mpm_set_timing(mpm_sim* sim, unsigned kernel_mask);
 mpm_status mpm_read_timing(mpm_sim* sim, double* ms, long long* launches, int reset);
+
+/* CUDA-graph replay of mpm_substep (default on): the launches of a call are captured once per distinct
+ * (substep count, particle count, collider count, timing mask, pipeline state) and replayed with one
+ * graph launch on the caller's stream. Off: every launch is issued directly. Calls on a stream that the
+ * caller is capturing are always issued directly, so they land in the caller's graph. */
+mpm_status mpm_set_graphs(mpm_sim* sim, int enable);
 
 /* Number of kernels the handle has launched since creation (host counter, no sync). */
 long long mpm_launch_count(const mpm_sim* sim);

@@ -74,7 +74,8 @@ def _load():
         "mpm_get_status": (st, [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.c_int, _vp]),
         "mpm_num_particles": (ctypes.c_int, [_vp]),
         "mpm_read_grid": (st, [_vp, _vp, _vp]),
-        "mpm_set_timing": (st, [_vp, ctypes.c_int]),
+        "mpm_set_timing": (st, [_vp, ctypes.c_uint]),
+        "mpm_set_graphs": (st, [_vp, ctypes.c_int]),
         "mpm_read_timing": (st, [_vp, _vp, _vp, ctypes.c_int]),
         "mpm_launch_count": (ctypes.c_longlong, [_vp]),
         "mpm_destroy": (None, [_vp]),
@@ -163,8 +164,12 @@ def mpm_read_grid(sim: int, d_out: int, stream: int = 0) -> None:
     _check("mpm_read_grid", _load().mpm_read_grid(sim, d_out, stream))
 
 
-def mpm_set_timing(sim: int, enable: int) -> None:
-    _check("mpm_set_timing", _load().mpm_set_timing(sim, enable))
+def mpm_set_timing(sim: int, kernel_mask: int) -> None:
+    _check("mpm_set_timing", _load().mpm_set_timing(sim, kernel_mask & 0xFFFFFFFF))
+
+
+def mpm_set_graphs(sim: int, enable: int) -> None:
+    _check("mpm_set_graphs", _load().mpm_set_graphs(sim, enable))
 
 
 def mpm_read_timing(sim: int, reset: int = 0):

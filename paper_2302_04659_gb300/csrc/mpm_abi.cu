@@ -1,5 +1,6 @@
 // mpm_abi.cu -- the C-ABI of include/mpm.h: argument checks, workspace layout, the per-substep launch
-// sequence and the readbacks. All device memory comes from the caller's workspace.
+// sequence (optionally replayed from a CUDA graph) and the readbacks. All device memory comes from the
+// caller's workspace.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,14 +23,20 @@ mpm_status cuda_fail(cudaError_t e, const char* what) {
     return MPM_ERR_CUDA;
 }
 
-#define MPM_CUDA(call, what)                      \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
+#define MPM_CUDA(call, what)                               \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-constexpr int kChunk = 128;       // particles per chunk = threads per CTA of the particle passes
+#define MPM_TRY(call)                   \
+    do {                                \
+        mpm_status r_ = (call);         \
+        if (r_ != MPM_OK) return r_;    \
+    } while (0)
+
 constexpr size_t kAlign = 256;
+constexpr int kMaxGraphs = 8;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -61,7 +68,7 @@ Layout make_layout(const mpm_config& c) {
     L.chunks = take(L.max_chunks * sizeof(int4));
     L.colliders = take(kMaxColliders * sizeof(ColliderSet));
     L.wrench = take(kMaxColliders * 6 * sizeof(double));
-    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, spare
+    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, CTAs done
     L.total = off;
     return L;
 }
@@ -78,12 +85,42 @@ mpm_status check_config(const mpm_config* c, const mpm_material* m) {
     if (m->kind != MPM_PLASTICINE && m->kind != MPM_FLUID) return MPM_ERR_INVALID_ARG;
     if (!(m->rho > 0.0f) || !(m->p_vol > 0.0f)) return MPM_ERR_INVALID_ARG;
     if (m->kind == MPM_PLASTICINE) {
-        if (!(m->E > 0.0f) || !(m->nu >= 0.0f && m->nu < 0.5f) || !(m->yield_stress >= 0.0f)) return MPM_ERR_INVALID_ARG;
+        if (!(m->E > 0.0f) || !(m->nu >= 0.0f && m->nu < 0.5f) || !(m->yield_stress >= 0.0f))
+            return MPM_ERR_INVALID_ARG;
     } else {
         if (!(m->bulk_modulus >= 0.0f)) return MPM_ERR_INVALID_ARG;
     }
     return MPM_OK;
 }
+
+// Host-side pipeline state that the enqueued work depends on (and that a cached graph assumes).
+struct PipeState {
+    int cur = 0;               // state buffer holding the current particles
+    int g = 0;                 // grid holding the particle-to-grid transfer of the current state
+    bool scanned = false;      // bin offsets and chunk list match the current keys
+    bool order_valid = false;  // perm (sorted slot -> particle) matches them too
+    bool grid_valid = false;   // grid g holds the transfer of the current state
+    bool operator==(const PipeState& o) const {
+        return cur == o.cur && g == o.g && scanned == o.scanned && order_valid == o.order_valid &&
+               grid_valid == o.grid_valid;
+    }
+};
+
+struct TimedNode {  // an event-record node of a cached graph bracketing one launch
+    cudaGraphNode_t start, stop;
+    int kind;
+};
+
+struct GraphEntry {
+    int n_substeps, N, ncol;
+    unsigned timing_mask;
+    PipeState before, after;
+    long long launches;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    std::vector<TimedNode> timed;
+    unsigned long long last_use;
+};
 
 }  // namespace
 
@@ -95,27 +132,38 @@ struct mpm_sim {
     Geometry geo;
     Material dmat;
     int N = 0;
-    int cur = 0;        // state buffer holding the current particles
-    int g = 0;          // grid holding the pending particle-to-grid transfer of the current state
-    bool order_valid = false;
-    bool grid_valid = false;
+    PipeState ps;
     int nshapes = 0;
     mpm_shape shapes[MPM_MAX_COLLIDERS];
-    int ncol = 0;       // colliders uploaded by the last mpm_set_colliders
+    int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
     int sms = 0;
     int ctas_fused = 0, ctas_p2g = 0;
     long long launches = 0;
-    bool timing = false;
-    struct Ev { cudaEvent_t a, b; int kind; };
+    unsigned timing_mask = 0;
+    struct Ev {
+        cudaEvent_t a, b;
+        int kind;
+    };
     std::vector<Ev> pending;
     std::vector<cudaEvent_t> pool;
     double ms[MPM_K_COUNT] = {};
     long long counts[MPM_K_COUNT] = {};
+    // graph capture and replay of mpm_substep
+    bool use_graphs = true;
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    std::vector<std::pair<cudaEvent_t, int>> cap_events;  // (event, kind), start/stop alternating
+    unsigned long long use_clock = 0;
 
-    template <class T> T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
+    template <class T>
+    T* at(size_t off) {
+        return reinterpret_cast<T*>(ws + off);
+    }
     uint32_t* status() { return at<uint32_t>(L.counters); }
     uint32_t* substep_counter() { return at<uint32_t>(L.counters) + 1; }
     uint32_t* num_chunks() { return at<uint32_t>(L.counters) + 2; }
+    uint32_t* done() { return at<uint32_t>(L.counters) + 3; }
     StateView view(int which) {
         float* b = at<float>(L.state[which]);
         const size_t n = (size_t)N;
@@ -137,24 +185,42 @@ struct mpm_sim {
         cudaEventCreate(&e);
         return e;
     }
+    void drop_graphs() {
+        for (auto& ge : graphs) {
+            cudaGraphExecDestroy(ge.exec);
+            cudaGraphDestroy(ge.graph);
+        }
+        graphs.clear();
+    }
 };
 
 namespace {
 
-// Bracket a launch with timing events when enabled; count it either way.
+// Enqueue one launch; bracket it with timing events when its kind is selected. While capturing a graph
+// the events become event-record nodes whose events are swapped on every replay.
 template <class F>
 mpm_status launch(mpm_sim* s, int kind, cudaStream_t st, F&& fn, const char* what) {
-    mpm_sim::Ev ev{nullptr, nullptr, kind};
-    if (s->timing) {
-        ev.a = s->get_event();
-        ev.b = s->get_event();
-        MPM_CUDA(cudaEventRecord(ev.a, st), "cudaEventRecord");
+    const bool timed = (s->timing_mask >> kind) & 1u;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+        a = s->get_event();
+        b = s->get_event();
+        if (s->capturing)
+            MPM_CUDA(cudaEventRecordWithFlags(a, st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+        else
+            MPM_CUDA(cudaEventRecord(a, st), "cudaEventRecord");
     }
     MPM_CUDA(fn(), what);
     ++s->launches;
-    if (s->timing) {
-        MPM_CUDA(cudaEventRecord(ev.b, st), "cudaEventRecord");
-        s->pending.push_back(ev);
+    if (timed) {
+        if (s->capturing) {
+            MPM_CUDA(cudaEventRecordWithFlags(b, st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+            s->cap_events.push_back({a, kind});
+            s->cap_events.push_back({b, kind});
+        } else {
+            MPM_CUDA(cudaEventRecord(b, st), "cudaEventRecord");
+            s->pending.push_back({a, b, kind});
+        }
     }
     return MPM_OK;
 }
@@ -164,8 +230,8 @@ TransferParams transfer_params(mpm_sim* s) {
     p.geo = s->geo;
     p.mat = s->dmat;
     p.N = s->N;
-    p.in = s->view(s->cur);
-    p.out = s->view(1 - s->cur);
+    p.in = s->view(s->ps.cur);
+    p.out = s->view(1 - s->ps.cur);
     p.perm = s->at<uint32_t>(s->L.perm);
     p.key_out = s->at<uint32_t>(s->L.key);
     p.hist = s->at<uint32_t>(s->L.hist);
@@ -173,39 +239,156 @@ TransferParams transfer_params(mpm_sim* s) {
     p.num_chunks = s->num_chunks();
     p.status = s->status();
     p.substep_counter = s->substep_counter();
+    p.cursor = s->at<uint32_t>(s->L.cursor);
+    p.chunks_next = s->at<int4>(s->L.chunks);
+    p.num_chunks_next = s->num_chunks();
+    p.done = s->done();
     return p;
 }
 
-// Sort the current particles into bins from the keys computed when they were written.
+GridParams grid_params(mpm_sim* s) {
+    GridParams gp{};
+    gp.geo = s->geo;
+    for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
+    gp.bound = s->cfg.bound;
+    gp.grid = s->at<float4>(s->L.grid[s->ps.g]);
+    gp.flags = s->at<uint32_t>(s->L.flags[s->ps.g]);
+    gp.grid_old = s->at<float4>(s->L.grid[1 - s->ps.g]);
+    gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
+    gp.cols = s->at<ColliderSet>(s->L.colliders);
+    gp.ncol = s->ncol;
+    gp.substep_counter = s->substep_counter();
+    gp.wrench = s->at<double>(s->L.wrench);
+    return gp;
+}
+
+mpm_status ensure_scanned(mpm_sim* s, cudaStream_t st) {
+    if (s->ps.scanned) return MPM_OK;
+    MPM_TRY(launch(s, MPM_K_SCAN, st, [&] {
+        return launch_scan(s->at<uint32_t>(s->L.hist), s->at<uint32_t>(s->L.cursor), s->at<int4>(s->L.chunks),
+                           s->num_chunks(), s->geo.nblocks, kChunk, st);
+    }, "scan"));
+    s->ps.scanned = true;
+    return MPM_OK;
+}
+
 mpm_status ensure_order(mpm_sim* s, cudaStream_t st) {
-    if (s->order_valid) return MPM_OK;
-    uint32_t* hist = s->at<uint32_t>(s->L.hist);
-    uint32_t* cursor = s->at<uint32_t>(s->L.cursor);
-    int4* chunks = s->at<int4>(s->L.chunks);
-    mpm_status r = launch(s, MPM_K_SCAN, st, [&] {
-        return launch_scan(hist, cursor, chunks, s->num_chunks(), s->geo.nblocks, kChunk, st);
-    }, "scan");
-    if (r != MPM_OK) return r;
-    r = launch(s, MPM_K_ASSIGN, st, [&] {
-        return launch_assign(s->N, s->at<uint32_t>(s->L.key), cursor, s->at<uint32_t>(s->L.perm), st);
-    }, "assign");
-    if (r != MPM_OK) return r;
-    s->order_valid = true;
+    MPM_TRY(ensure_scanned(s, st));
+    if (s->ps.order_valid) return MPM_OK;
+    MPM_TRY(launch(s, MPM_K_ASSIGN, st, [&] {
+        return launch_assign(s->N, s->at<uint32_t>(s->L.key), s->at<uint32_t>(s->L.cursor), s->at<uint32_t>(s->L.perm),
+                             st);
+    }, "assign"));
+    s->ps.order_valid = true;
     return MPM_OK;
 }
 
 // Particle-to-grid transfer of the current state into grid g (only after the state was replaced).
 mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
-    if (s->grid_valid) return MPM_OK;
-    mpm_status r = ensure_order(s, st);
-    if (r != MPM_OK) return r;
+    if (s->ps.grid_valid) return MPM_OK;
+    MPM_TRY(ensure_order(s, st));
     TransferParams p = transfer_params(s);
-    p.grid_out = s->at<float4>(s->L.grid[s->g]);
-    p.flags_out = s->at<uint32_t>(s->L.flags[s->g]);
-    r = launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->mat.kind, s->ctas_p2g, kChunk, st); }, "p2g");
-    if (r != MPM_OK) return r;
-    s->grid_valid = true;
+    p.grid_out = s->at<float4>(s->L.grid[s->ps.g]);
+    p.flags_out = s->at<uint32_t>(s->L.flags[s->ps.g]);
+    MPM_TRY(launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->mat.kind, s->ctas_p2g, kChunk, st); }, "p2g"));
+    s->ps.grid_valid = true;
     return MPM_OK;
+}
+
+// The launches of n substeps: per substep one sort-assign + grid-update launch and one fused
+// G2P->P2G launch (whose last CTA sorts the new positions into bins).
+mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
+    for (int it = 0; it < n; ++it) {
+        MPM_TRY(ensure_scanned(s, st));
+        MPM_TRY(ensure_grid(s, st));
+        AssignGridParams ap{};
+        ap.grid = grid_params(s);
+        ap.N = s->N;
+        ap.key = s->at<uint32_t>(s->L.key);
+        ap.cursor = s->at<uint32_t>(s->L.cursor);
+        ap.perm = s->at<uint32_t>(s->L.perm);
+        ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 255) / 256;
+        MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
+        s->ps.order_valid = true;
+        TransferParams p = transfer_params(s);
+        p.grid_in = ap.grid.grid;
+        p.grid_out = ap.grid.grid_old;
+        p.flags_out = ap.grid.flags_old;
+        MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->mat.kind, s->ctas_fused, kChunk, st); },
+                       "g2p2g"));
+        s->ps.cur = 1 - s->ps.cur;
+        s->ps.g = 1 - s->ps.g;
+        s->ps.scanned = true;       // the fused pass's last CTA wrote the new bins
+        s->ps.order_valid = false;  // assigned by the next launch
+        s->ps.grid_valid = true;
+    }
+    return MPM_OK;
+}
+
+// Capture the launches of n substeps from the current pipeline state into a graph.
+mpm_status capture_graph(mpm_sim* s, int n, GraphEntry& ge) {
+    if (!s->cap_stream) MPM_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    ge.n_substeps = n;
+    ge.N = s->N;
+    ge.ncol = s->ncol;
+    ge.timing_mask = s->timing_mask;
+    ge.before = s->ps;
+    const long long l0 = s->launches;
+    s->cap_events.clear();
+    MPM_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    s->capturing = true;
+    mpm_status r = enqueue_substeps(s, n, s->cap_stream);
+    s->capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    // the host-side state after the captured sequence is the state after every replay of it
+    ge.after = s->ps;
+    ge.launches = s->launches - l0;
+    s->ps = ge.before;
+    s->launches = l0;
+    if (r != MPM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    ge.graph = graph;
+    ge.exec = exec;
+    // event-record nodes, matched to the capture order
+    size_t count = 0;
+    MPM_CUDA(cudaGraphGetNodes(graph, nullptr, &count), "cudaGraphGetNodes");
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count) MPM_CUDA(cudaGraphGetNodes(graph, nodes.data(), &count), "cudaGraphGetNodes");
+    std::vector<cudaGraphNode_t> by_event(s->cap_events.size(), nullptr);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        MPM_CUDA(cudaGraphNodeGetType(nd, &t), "cudaGraphNodeGetType");
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        MPM_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev), "cudaGraphEventRecordNodeGetEvent");
+        for (size_t i = 0; i < s->cap_events.size(); ++i)
+            if (s->cap_events[i].first == ev) by_event[i] = nd;
+    }
+    for (size_t i = 0; i + 1 < s->cap_events.size(); i += 2) {
+        if (!by_event[i] || !by_event[i + 1]) continue;
+        ge.timed.push_back({by_event[i], by_event[i + 1], s->cap_events[i].second});
+    }
+    for (auto& pe : s->cap_events) s->pool.push_back(pe.first);
+    s->cap_events.clear();
+    return MPM_OK;
+}
+
+GraphEntry* find_graph(mpm_sim* s, int n) {
+    for (auto& ge : s->graphs)
+        if (ge.n_substeps == n && ge.N == s->N && ge.ncol == s->ncol && ge.timing_mask == s->timing_mask &&
+            ge.before == s->ps)
+            return &ge;
+    return nullptr;
 }
 
 }  // namespace
@@ -227,8 +410,7 @@ const char* mpm_last_error(void) { return g_last_error; }
 
 mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes) {
     if (!bytes) return MPM_ERR_INVALID_ARG;
-    mpm_status r = check_config(cfg, mat);
-    if (r != MPM_OK) return r;
+    MPM_TRY(check_config(cfg, mat));
     *bytes = make_layout(*cfg).total;
     return MPM_OK;
 }
@@ -237,8 +419,7 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_wo
                       mpm_sim** out) {
     if (!out) return MPM_ERR_INVALID_ARG;
     *out = nullptr;
-    mpm_status r = check_config(cfg, mat);
-    if (r != MPM_OK) return r;
+    MPM_TRY(check_config(cfg, mat));
     Layout L = make_layout(*cfg);
     if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) != 0 || bytes < L.total)
         return MPM_ERR_WORKSPACE;
@@ -293,11 +474,13 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_wo
 
 void mpm_destroy(mpm_sim* s) {
     if (!s) return;
+    s->drop_graphs();
     for (auto& ev : s->pending) {
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
     for (auto e : s->pool) cudaEventDestroy(e);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
 }
 
@@ -314,11 +497,11 @@ mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, 
     const size_t z0 = s->L.grid[0], z1 = s->L.cursor;
     MPM_CUDA(cudaMemsetAsync(s->ws + z0, 0, z1 - z0, st), "cudaMemsetAsync");
     s->N = n;
-    s->cur = 0;
-    s->g = 0;
-    s->order_valid = false;
-    s->grid_valid = false;
-    if (n == 0) return MPM_OK;
+    s->ps = PipeState{};
+    if (n == 0) {
+        s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;
+        return MPM_OK;
+    }
     const size_t N = (size_t)n;
     const float *sx = x, *sv = v, *sC = C, *sF = F;
     if (!src_on_device) {
@@ -326,16 +509,24 @@ mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, 
         StateView stage = s->view(1);
         MPM_CUDA(cudaMemcpyAsync(stage.x, x, 3 * N * 4, cudaMemcpyHostToDevice, st), "copy x");
         sx = stage.x;
-        if (v) { MPM_CUDA(cudaMemcpyAsync(stage.v, v, 3 * N * 4, cudaMemcpyHostToDevice, st), "copy v"); sv = stage.v; }
-        if (C) { MPM_CUDA(cudaMemcpyAsync(stage.C, C, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy C"); sC = stage.C; }
-        if (F) { MPM_CUDA(cudaMemcpyAsync(stage.F, F, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy F"); sF = stage.F; }
+        if (v) {
+            MPM_CUDA(cudaMemcpyAsync(stage.v, v, 3 * N * 4, cudaMemcpyHostToDevice, st), "copy v");
+            sv = stage.v;
+        }
+        if (C) {
+            MPM_CUDA(cudaMemcpyAsync(stage.C, C, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy C");
+            sC = stage.C;
+        }
+        if (F) {
+            MPM_CUDA(cudaMemcpyAsync(stage.F, F, 9 * N * 4, cudaMemcpyHostToDevice, st), "copy F");
+            sF = stage.F;
+        }
     }
     StateView dst = s->view(0);
-    mpm_status r = launch(s, MPM_K_LOAD, st, [&] {
+    MPM_TRY(launch(s, MPM_K_LOAD, st, [&] {
         return launch_load(s->geo, s->mat.kind, n, sx, sv, sC, sF, dst, s->at<uint32_t>(s->L.key),
                            s->at<uint32_t>(s->L.hist), s->status(), st);
-    }, "load");
-    if (r != MPM_OK) return r;
+    }, "load"));
     if (!src_on_device) MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return MPM_OK;
 }
@@ -385,11 +576,10 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
                 !std::isfinite(c.com[a]))
                 return MPM_ERR_INVALID_ARG;
     }
-    mpm_status r = launch(s, MPM_K_COLLIDERS, st, [&] {
+    MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
         return launch_set_colliders(u, s->at<ColliderSet>(s->L.colliders), s->at<double>(s->L.wrench),
                                     s->substep_counter(), st);
-    }, "set_colliders");
-    if (r != MPM_OK) return r;
+    }, "set_colliders"));
     s->ncol = k;
     return MPM_OK;
 }
@@ -399,40 +589,44 @@ mpm_status mpm_substep(mpm_sim* s, int n_substeps, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_substeps == 0) return MPM_OK;
     if (s->N == 0) {
-        return launch(s, MPM_K_COLLIDERS, st, [&] { return launch_advance_counter(s->substep_counter(), n_substeps, st); },
-                      "advance");
+        return launch(s, MPM_K_COLLIDERS, st,
+                      [&] { return launch_advance_counter(s->substep_counter(), n_substeps, st); }, "advance");
     }
-    for (int it = 0; it < n_substeps; ++it) {
-        mpm_status r = ensure_grid(s, st);  // sorts first if needed
-        if (r != MPM_OK) return r;
-        GridParams gp{};
-        gp.geo = s->geo;
-        for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
-        gp.bound = s->cfg.bound;
-        gp.grid = s->at<float4>(s->L.grid[s->g]);
-        gp.flags = s->at<uint32_t>(s->L.flags[s->g]);
-        gp.grid_old = s->at<float4>(s->L.grid[1 - s->g]);
-        gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->g]);
-        gp.cols = s->at<ColliderSet>(s->L.colliders);
-        gp.ncol = s->ncol;
-        gp.substep_counter = s->substep_counter();
-        gp.wrench = s->at<double>(s->L.wrench);
-        r = launch(s, MPM_K_GRID, st, [&] { return launch_grid_update(gp, st); }, "grid_update");
-        if (r != MPM_OK) return r;
-        TransferParams p = transfer_params(s);
-        p.grid_in = gp.grid;
-        p.grid_out = gp.grid_old;
-        p.flags_out = gp.flags_old;
-        r = launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->mat.kind, s->ctas_fused, kChunk, st); },
-                   "g2p2g");
-        if (r != MPM_OK) return r;
-        s->cur = 1 - s->cur;
-        s->g = 1 - s->g;
-        s->order_valid = false;   // keys of the new state are written, the sort is pending
-        s->grid_valid = true;     // grid g holds the transfer of the new state
-        r = ensure_order(s, st);
-        if (r != MPM_OK) return r;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MPM_CUDA(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+    if (!s->use_graphs || cs != cudaStreamCaptureStatusNone) return enqueue_substeps(s, n_substeps, st);
+    GraphEntry* ge = find_graph(s, n_substeps);
+    if (!ge) {
+        if ((int)s->graphs.size() >= kMaxGraphs) {
+            size_t victim = 0;
+            for (size_t i = 1; i < s->graphs.size(); ++i)
+                if (s->graphs[i].last_use < s->graphs[victim].last_use) victim = i;
+            cudaGraphExecDestroy(s->graphs[victim].exec);
+            cudaGraphDestroy(s->graphs[victim].graph);
+            s->graphs.erase(s->graphs.begin() + victim);
+        }
+        GraphEntry fresh{};
+        MPM_TRY(capture_graph(s, n_substeps, fresh));
+        s->graphs.push_back(fresh);
+        ge = &s->graphs.back();
     }
+    ge->last_use = ++s->use_clock;
+    for (auto& tn : ge->timed) {
+        cudaEvent_t a = s->get_event(), b = s->get_event();
+        MPM_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge->exec, tn.start, a), "cudaGraphExecEventRecordNodeSetEvent");
+        MPM_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge->exec, tn.stop, b), "cudaGraphExecEventRecordNodeSetEvent");
+        s->pending.push_back({a, b, tn.kind});
+    }
+    MPM_CUDA(cudaGraphLaunch(ge->exec, st), "cudaGraphLaunch");
+    s->ps = ge->after;
+    s->launches += ge->launches;
+    return MPM_OK;
+}
+
+mpm_status mpm_set_graphs(mpm_sim* s, int enable) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    s->use_graphs = enable != 0;
+    if (!s->use_graphs) s->drop_graphs();
     return MPM_OK;
 }
 
@@ -441,17 +635,16 @@ mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, in
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->N == 0) return MPM_OK;
     const size_t N = (size_t)s->N;
-    StateView src = s->view(s->cur);
+    StateView src = s->view(s->ps.cur);
     if (dst_on_device) {
         return launch(s, MPM_K_READ, st, [&] { return launch_read_state(s->mat.kind, s->N, src, x, v, C, F, st); },
                       "read_state");
     }
-    StateView stage = s->view(1 - s->cur);
-    mpm_status r = launch(s, MPM_K_READ, st, [&] {
+    StateView stage = s->view(1 - s->ps.cur);
+    MPM_TRY(launch(s, MPM_K_READ, st, [&] {
         return launch_read_state(s->mat.kind, s->N, src, x ? stage.x : nullptr, v ? stage.v : nullptr,
                                  C ? stage.C : nullptr, F ? stage.F : nullptr, st);
-    }, "read_state");
-    if (r != MPM_OK) return r;
+    }, "read_state"));
     if (x) MPM_CUDA(cudaMemcpyAsync(x, stage.x, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy x");
     if (v) MPM_CUDA(cudaMemcpyAsync(v, stage.v, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy v");
     if (C) MPM_CUDA(cudaMemcpyAsync(C, stage.C, 9 * N * 4, cudaMemcpyDeviceToHost, st), "copy C");
@@ -464,8 +657,9 @@ mpm_status mpm_read_wrench(mpm_sim* s, double* out, int* n_substeps, void* strea
     if (!s || (s->ncol > 0 && !out)) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->ncol > 0)
-        MPM_CUDA(cudaMemcpyAsync(out, s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st), "copy wrench");
+        MPM_CUDA(cudaMemcpyAsync(out, s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 st),
+                 "copy wrench");
     uint32_t cnt = 0;
     MPM_CUDA(cudaMemcpyAsync(&cnt, s->substep_counter(), 4, cudaMemcpyDeviceToHost, st), "copy counter");
     MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -487,17 +681,14 @@ mpm_status mpm_get_status(mpm_sim* s, unsigned* flags, int clear, void* stream) 
 mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
     if (!s || !d_out) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->N > 0) {
-        mpm_status r = ensure_grid(s, st);
-        if (r != MPM_OK) return r;
-    }
-    const float4* grid = s->at<float4>(s->L.grid[s->g]);
+    if (s->N > 0) MPM_TRY(ensure_grid(s, st));
+    const float4* grid = s->at<float4>(s->L.grid[s->ps.g]);
     return launch(s, MPM_K_READ, st, [&] { return launch_read_grid(s->geo, grid, d_out, st); }, "read_grid");
 }
 
-mpm_status mpm_set_timing(mpm_sim* s, int enable) {
+mpm_status mpm_set_timing(mpm_sim* s, unsigned kernel_mask) {
     if (!s) return MPM_ERR_INVALID_ARG;
-    s->timing = enable != 0;
+    s->timing_mask = kernel_mask & ((1u << MPM_K_COUNT) - 1u);
     return MPM_OK;
 }
 

@@ -60,8 +60,12 @@ template <int P, int Q, int R>
 __device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&V)[3][3]) {
     float apq = S[P][Q];
     if (apq == 0.0f) return;
-    float tau = (S[Q][Q] - S[P][P]) / (2.0f * apq);
-    float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    // tan of the rotation angle, the smaller root of t^2 + 2 tau t - 1 = 0; for |tau| >= 2^30 the
+    // asymptote t = 1 / (2 tau) avoids overflowing tau^2
+    float tau = __fdividef(S[Q][Q] - S[P][P], 2.0f * apq);
+    float at = fabsf(tau);
+    float t = at < 1073741824.0f ? __fdividef(copysignf(1.0f, tau), at + sqrtf(fmaf(tau, tau, 1.0f)))
+                                 : __fdividef(0.5f, tau);
     float c = rsqrtf(fmaf(t, t, 1.0f));
     float s = t * c;
     S[P][P] -= t * apq;
@@ -120,10 +124,11 @@ __device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3][3], f
     if (len[2] > len[0]) swap_cols_keep_det(B, V, len, 0, 2);
     if (len[2] > len[1]) swap_cols_keep_det(B, V, len, 1, 2);
     // Gram-Schmidt
-    float s0 = sqrtf(len[0]);
+    float s0;
     float u0[3], u1[3];
-    if (s0 > 1e-30f) {
-        float r = 1.0f / s0;
+    if (len[0] > 1e-36f) {
+        float r = rsqrtf(len[0]);
+        s0 = len[0] * r;
         u0[0] = B[0][0] * r; u0[1] = B[1][0] * r; u0[2] = B[2][0] * r;
     } else {
         u0[0] = 1.0f; u0[1] = 0.0f; u0[2] = 0.0f;
@@ -131,9 +136,11 @@ __device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3][3], f
     }
     float d01 = u0[0] * B[0][1] + u0[1] * B[1][1] + u0[2] * B[2][1];
     float w1[3] = {B[0][1] - d01 * u0[0], B[1][1] - d01 * u0[1], B[2][1] - d01 * u0[2]};
-    float s1 = sqrtf(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
-    if (s1 > 1e-30f && s1 > 1e-7f * s0) {
-        float r = 1.0f / s1;
+    float l1 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
+    float s1 = 0.0f;
+    if (l1 > 1e-36f && l1 > 1e-14f * len[0]) {
+        float r = rsqrtf(l1);
+        s1 = l1 * r;
         u1[0] = w1[0] * r; u1[1] = w1[1] * r; u1[2] = w1[2] * r;
     } else {
         // any unit vector orthogonal to u0
@@ -181,21 +188,23 @@ __device__ __forceinline__ uint32_t plastic_update_and_stress(float (&F)[3][3], 
     for (int i = 0; i < 3; ++i) {
         float s = sig[i];
         if (s < 1e-6f) { s = 1e-6f; clamp = true; }
-        eps[i] = logf(s);
+        eps[i] = __logf(s);
     }
     float tr3 = (eps[0] + eps[1] + eps[2]) * (1.0f / 3.0f);
     float dev[3] = {eps[0] - tr3, eps[1] - tr3, eps[2] - tr3};
-    float dn = sqrtf(dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]);
+    float dn2 = dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2];
+    float rdn = rsqrtf(fmaxf(dn2, 1e-30f));
+    float dn = dn2 * rdn;
     float dgamma = dn - m.yield_radius;
     float s[3] = {sig[0], sig[1], sig[2]};
     if (dgamma > 0.0f || clamp) {
         if (dgamma > 0.0f) {
-            float k = dgamma / dn;
+            float k = dgamma * rdn;
 #pragma unroll
             for (int i = 0; i < 3; ++i) eps[i] -= k * dev[i];
         }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s[i] = expf(eps[i]);
+        for (int i = 0; i < 3; ++i) s[i] = __expf(eps[i]);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll

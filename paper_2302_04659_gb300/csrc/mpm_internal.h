@@ -9,6 +9,9 @@
 
 namespace mpm {
 
+// Particles per chunk of a bin = threads per CTA of the particle passes.
+constexpr int kChunk = 128;
+
 // Internal-consistency flag: a particle was found outside the bin it was sorted into.
 constexpr uint32_t kFlagInternal = 0x80000000u;
 
@@ -45,6 +48,12 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     const uint32_t* num_chunks;
     uint32_t* status;
     uint32_t* substep_counter;
+    // fused pass only: the last CTA to finish scans `hist` into these (the same buffers as chunks /
+    // num_chunks, rewritten once every CTA is done reading them)
+    uint32_t* cursor;
+    int4* chunks_next;
+    uint32_t* num_chunks_next;
+    uint32_t* done;           // CTAs finished, reset by the last one
 };
 
 struct GridParams {
@@ -59,6 +68,15 @@ struct GridParams {
     int ncol;
     const uint32_t* substep_counter;
     double* wrench;           // ncol x 6
+};
+
+struct AssignGridParams {  // the sort-assign of the new state and the grid update, one launch
+    GridParams grid;
+    int N;
+    const uint32_t* key;
+    uint32_t* cursor;
+    uint32_t* perm;
+    int assign_ctas;          // the first assign_ctas CTAs assign sorted slots (0: no assign)
 };
 
 struct ColliderUpload {
@@ -76,6 +94,7 @@ cudaError_t launch_assign(int N, const uint32_t* key, uint32_t* cursor, uint32_t
 cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
 cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
 cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s);
+cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s);
 cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
                               cudaStream_t s);
 cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, cudaStream_t s);

@@ -52,21 +52,65 @@ __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, 
 }
 
 // ------------------------------------------------------------------------ scatter tile
+//
+// The particle-to-grid scatter of one chunk (at most kChunk particles of one bin) goes into a shared
+// tile of the 8^3 nodes its particles can reach, accumulated with 32-bit integer atomics: shared-memory
+// integer adds are single native instructions, FP32 ones are not. Values are fixed point:
+//   mass      sum of weights, scaled by 2^24 (a node sums at most kChunk weights <= 0.75^3 each, so the
+//             sum stays below 54 * 2^24 < 2^31);
+//   momentum  scaled by 2^k with k = 24 - e, where 2^e bounds (from above, within a factor 2) the largest
+//             per-particle magnitude B_p = max_a (m |v_a| + 1.5 dx sum_c |A_ac|) of the chunk, so every node
+//             sum stays below 54 * 2^24 as well. Rounding is then at most 2^-25 of that bound per term --
+//             no coarser than an FP32 accumulation of the same terms.
+// The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
+
+
+constexpr int kMassBits = 24;
 
 struct ScatterTile {
-    float m[kScatterNodes];
-    float px[kScatterNodes];
-    float py[kScatterNodes];
-    float pz[kScatterNodes];
+    int m[kScatterNodes];
+    int px[kScatterNodes];
+    int py[kScatterNodes];
+    int pz[kScatterNodes];
     uint32_t touched[27];
+    uint32_t bound_bits;  // max over the chunk of B_p, as FP32 bits (non-negative floats order as integers)
 };
 
-// Scatter one particle's mass and momentum to its 27 nodes. The tile covers nodes [o, o+8) per axis with
-// o = 4 * bin - 1; outside it (a particle that moved a cell or more since it was binned) the nodes are
-// updated directly in global memory. mom(node) = w (m v + A (x_i - x_p)), written with the affine
-// part expanded per node index: base_mom + i Ad0 + j Ad1 + k Ad2.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// Storage slot of tile node (lx, ly, lz): row-major with bit 2 of lz flipped for odd lx. A bin's particles
+// sit in 4 consecutive cells per axis, so for any one stencil offset their nodes then spread over all 32
+// banks (two cells per bank) instead of 16. The map is its own inverse for a fixed lx.
+__device__ __forceinline__ int tile_slot(int lx, int ly, int lz) {
+    return ((lx * kScatterEdge + ly) * kScatterEdge + lz) ^ ((lx & 1) << 2);
+}
+
+// Scale exponent k of a chunk from the FP32 bits of its bound (clamped so 2^k and 2^-k stay normal).
+__device__ __forceinline__ int momentum_scale_exp(uint32_t bound_bits) {
+    int e = (int)((bound_bits >> 23) & 0xffu) - 126;  // bound < 2^e
+    int k = kMassBits - e;
+    return min(max(k, -100), 100);
+}
+
+// B_p: bound on |m v_a + (A (x_i - x_p))_a| over the 27 nodes, (x_i - x_p) within 1.5 dx per axis.
+__device__ __forceinline__ float particle_bound(float m, const float vn[3], const float (&A)[3][3], float dx) {
+    float b = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float r = fmaf(1.5f * dx, fabsf(A[a][0]) + fabsf(A[a][1]) + fabsf(A[a][2]), m * fabsf(vn[a]));
+        b = fmaxf(b, r);
+    }
+    return b;
+}
+
+// Scatter one particle's mass and momentum to its 27 nodes: mom(node) = w (m v + A (x_i - x_p)),
+// expanded per node index as base_mom + i Ad0 + j Ad1 + k Ad2 with Ad[c] = dx * column c of A.
+// The tile covers nodes [o, o+8) per axis with o = 4 * bin - 1; a particle outside it (one that moved a
+// cell or more since it was binned) updates the global grid directly in FP32 and marks the bins it
+// touches. Returns flag bits.
 __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const TransferParams& p, const int o[3],
-                                                     const float xn[3], const float vn[3], const float (&A)[3][3]) {
+                                                     const float xn[3], const float vn[3], const float (&A)[3][3],
+                                                     float mscale) {
     const Geometry& g = p.geo;
     int bs[3];
     float f[3], w[3][3];
@@ -77,7 +121,7 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
         bspline_weights(f[a], w[a]);
     }
     const float m = p.mat.p_mass;
-    float Ad[3][3];  // Ad[c] = dx * column c of A
+    float Ad[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -85,30 +129,36 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
     float bm[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) bm[r] = m * vn[r] - (Ad[0][r] * f[0] + Ad[1][r] * f[1] + Ad[2][r] * f[2]);
-    int l[3] = {bs[0] - o[0], bs[1] - o[1], bs[2] - o[2]};
-    bool in_tile = (unsigned)l[0] <= 5u && (unsigned)l[1] <= 5u && (unsigned)l[2] <= 5u;
+    const int l0 = bs[0] - o[0], l1 = bs[1] - o[1], l2 = bs[2] - o[2];
+    const bool in_tile = (unsigned)l0 <= 5u && (unsigned)l1 <= 5u && (unsigned)l2 <= 5u;
     if (in_tile) {
+        const float wscale = pow2f(kMassBits);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            bm[r] *= mscale;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ad[c][r] *= mscale;
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                float wij = w[0][i] * w[1][j];
+                const float wij = w[0][i] * w[1][j];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    float wk = wij * w[2][k];
-                    int t = ((l[0] + i) * kScatterEdge + (l[1] + j)) * kScatterEdge + (l[2] + k);
-                    float mx = bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0];
-                    float my = bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1];
-                    float mz = bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2];
-                    atomicAdd(&T.m[t], wk * m);
-                    atomicAdd(&T.px[t], wk * mx);
-                    atomicAdd(&T.py[t], wk * my);
-                    atomicAdd(&T.pz[t], wk * mz);
+                    const float wk = wij * w[2][k];
+                    const int t = tile_slot(l0 + i, l1 + j, l2 + k);
+                    const float mx = bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0];
+                    const float my = bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1];
+                    const float mz = bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2];
+                    atomicAdd(&T.m[t], __float2int_rn(wk * wscale));
+                    atomicAdd(&T.px[t], __float2int_rn(wk * mx));
+                    atomicAdd(&T.py[t], __float2int_rn(wk * my));
+                    atomicAdd(&T.pz[t], __float2int_rn(wk * mz));
                 }
             }
         return 0;
     }
-    // far move: direct global atomics, marking every bin touched
 #pragma unroll 1
     for (int i = 0; i < 3; ++i)
 #pragma unroll 1
@@ -128,24 +178,37 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
 
 __device__ __forceinline__ void tile_clear(ScatterTile& T) {
     for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
-        T.m[t] = 0.0f;
-        T.px[t] = 0.0f;
-        T.py[t] = 0.0f;
-        T.pz[t] = 0.0f;
+        T.m[t] = 0;
+        T.px[t] = 0;
+        T.py[t] = 0;
+        T.pz[t] = 0;
     }
     if (threadIdx.x < 27) T.touched[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) T.bound_bits = 0u;
 }
 
-// Add the tile's nonzero nodes to the global grid with one 16-byte vector atomic each, then mark the
-// bins that received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
-__device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, int bx, int by, int bz) {
+// CTA-wide max of the particle bounds into T.bound_bits; every thread of the CTA must call it.
+__device__ __forceinline__ void tile_bound(ScatterTile& T, float bp) {
+    uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(bp));
+    if ((threadIdx.x & 31) == 0) atomicMax(&T.bound_bits, wmax);
+}
+
+// Add the tile's nonzero nodes to the global grid (FP32, one vector atomic each), then mark the bins that
+// received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
+__device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, int bx, int by, int bz,
+                                           float inv_mscale) {
     const int nb = p.geo.nb;
+    const float mass_unit = p.mat.p_mass * pow2f(-kMassBits);
     for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
-        float m = T.m[t];
-        if (m == 0.0f) continue;
-        int ti = t / (kScatterEdge * kScatterEdge), tj = (t / kScatterEdge) % kScatterEdge, tk = t % kScatterEdge;
+        int mq = T.m[t];
+        if (mq == 0) continue;
+        const int ti = t / (kScatterEdge * kScatterEdge);
+        const int u = t ^ ((ti & 1) << 2);  // tile_slot is its own inverse for a fixed lx
+        const int tj = (u / kScatterEdge) % kScatterEdge, tk = u % kScatterEdge;
         int gx = 4 * bx - 1 + ti, gy = 4 * by - 1 + tj, gz = 4 * bz - 1 + tk;
-        atomicAdd(&p.grid_out[node_index(gx, gy, gz, nb)], make_float4(m, T.px[t], T.py[t], T.pz[t]));
+        float4 add = make_float4((float)mq * mass_unit, (float)T.px[t] * inv_mscale, (float)T.py[t] * inv_mscale,
+                                 (float)T.pz[t] * inv_mscale);
+        atomicAdd(&p.grid_out[node_index(gx, gy, gz, nb)], add);
         int qx = (gx >> 2) - bx + 1, qy = (gy >> 2) - by + 1, qz = (gz >> 2) - bz + 1;
         T.touched[(qx * 3 + qy) * 3 + qz] = 1u;
     }
@@ -231,18 +294,18 @@ __global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __
 
 // ------------------------------------------------------------------------ counting sort into bins
 
-// One CTA: exclusive scan of the bin counts -> bin start offsets (cursor) and the chunk list: each bin
-// is cut into chunks of at most `chunk` particles, one chunk per CTA iteration of the particle passes.
-// The counts are zeroed for the next histogram.
-__global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor, int4* chunks,
-                                               uint32_t* num_chunks, int nblocks, int chunk) {
-    __shared__ uint32_t warp_tot[2][32];
+// One CTA (a multiple of 32 threads, at most 1024): exclusive scan of the bin counts -> bin start
+// offsets (cursor) and the chunk list: each bin is cut into chunks of at most `chunk` particles, one
+// chunk per CTA iteration of the particle passes. The counts are read from L2 (they were accumulated by
+// other CTAs' atomics) and zeroed for the next histogram.
+__device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
+                                          int nblocks, int chunk, uint32_t (&warp_tot)[2][32]) {
     const int tid = threadIdx.x;
     const int per = (nblocks + blockDim.x - 1) / blockDim.x;
     const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
     uint32_t cnt = 0, nch = 0;
     for (int b = b0; b < b1; ++b) {
-        uint32_t c = hist[b];
+        uint32_t c = __ldcg(&hist[b]);
         cnt += c;
         nch += (c + chunk - 1) / chunk;
     }
@@ -270,7 +333,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor,
     uint32_t off = ic - cnt + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
     uint32_t coff = in - nch + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
     for (int b = b0; b < b1; ++b) {
-        uint32_t c = hist[b];
+        uint32_t c = __ldcg(&hist[b]);
         cursor[b] = off;
         for (uint32_t s = 0; s < c; s += chunk) {
             chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
@@ -281,35 +344,49 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor,
     if (tid == blockDim.x - 1) *num_chunks = coff;
 }
 
-// Sorted slot of every particle: slot = start of its bin + rank among the bin's particles (ranks are
-// handed out per warp with one atomic, so runs of one warp stay contiguous and in order).
-__global__ void __launch_bounds__(256) k_assign(int N, const uint32_t* __restrict__ key, uint32_t* cursor,
-                                                uint32_t* __restrict__ perm) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor, int4* chunks,
+                                               uint32_t* num_chunks, int nblocks, int chunk) {
+    __shared__ uint32_t warp_tot[2][32];
+    scan_bins(hist, cursor, chunks, num_chunks, nblocks, chunk, warp_tot);
+}
+
+// Sorted slot of particle j: slot = start of its bin + rank among the bin's particles (ranks are handed
+// out per warp with one atomic, so runs of one warp stay contiguous and in order). All lanes of the warp
+// must call it.
+__device__ __forceinline__ void assign_slot(int j, int N, const uint32_t* __restrict__ key, uint32_t* cursor,
+                                            uint32_t* __restrict__ perm) {
     uint32_t k = j < N ? key[j] : 0xffffffffu;
     uint32_t slot = warp_hist_add(cursor, k, true);
     if (j < N) perm[slot] = (uint32_t)j;
 }
 
+__global__ void __launch_bounds__(256) k_assign(int N, const uint32_t* __restrict__ key, uint32_t* cursor,
+                                                uint32_t* __restrict__ perm) {
+    assign_slot(blockIdx.x * blockDim.x + threadIdx.x, N, key, cursor, perm);
+}
+
 // ------------------------------------------------------------------------ standalone P2G
 
 template <int KIND>
-__global__ void __launch_bounds__(128) k_p2g(TransferParams p) {
+__global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
     __shared__ ScatterTile T;
     const Geometry& g = p.geo;
     const int N = p.N;
     uint32_t flags = 0;
     const uint32_t nchunks = *p.num_chunks;
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
-        int4 ch = p.chunks[w];
+        const int4 ch = p.chunks[w];
         int bx, by, bz;
         decode_bin(ch.x, g.nb, bx, by, bz);
         const int o[3] = {4 * bx - 1, 4 * by - 1, 4 * bz - 1};
         tile_clear(T);
         __syncthreads();
-        for (int q = threadIdx.x; q < ch.z; q += blockDim.x) {
-            uint32_t src = p.perm[ch.y + q];
-            float x[3], v[3], C[3][3], tau[3][3], A[3][3];
+        const bool active = (int)threadIdx.x < ch.z;
+        float x[3] = {0.0f, 0.0f, 0.0f}, v[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
+        float bp = 0.0f;
+        if (active) {
+            const uint32_t src = p.perm[ch.y + threadIdx.x];
+            float C[3][3], tau[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 x[a] = p.in.x[(size_t)a * N + src];
@@ -321,18 +398,22 @@ __global__ void __launch_bounds__(128) k_p2g(TransferParams p) {
                 load_mat(p.in.F, N, src, F);
                 fixed_corotated_stress(F, p.mat, tau);
             } else {
-                float J = p.in.F[src];
-                float s = p.mat.lambda * J * (J - 1.0f);
+                const float J = p.in.F[src];
+                const float s = p.mat.lambda * J * (J - 1.0f);
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
             }
             affine(p.mat, C, tau, A);
-            flags |= scatter_particle(T, p, o, x, v, A);
+            bp = particle_bound(p.mat.p_mass, v, A, g.dx);
         }
+        tile_bound(T, bp);
         __syncthreads();
-        tile_flush(T, p, bx, by, bz);
+        const int k = momentum_scale_exp(T.bound_bits);
+        if (active) flags |= scatter_particle(T, p, o, x, v, A, pow2f(k));
+        __syncthreads();
+        tile_flush(T, p, bx, by, bz, pow2f(-k));
         __syncthreads();
     }
     if (flags) atomicOr(p.status, flags);
@@ -341,7 +422,7 @@ __global__ void __launch_bounds__(128) k_p2g(TransferParams p) {
 // ------------------------------------------------------------------------ fused G2P -> P2G
 
 template <int KIND>
-__global__ void __launch_bounds__(128) k_g2p2g(TransferParams p) {
+__global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
     __shared__ float4 G[kGatherNodes];
     __shared__ ScatterTile T;
     const Geometry& g = p.geo;
@@ -351,137 +432,153 @@ __global__ void __launch_bounds__(128) k_g2p2g(TransferParams p) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
-        int4 ch = p.chunks[w];
+        const int4 ch = p.chunks[w];
         int bx, by, bz;
         decode_bin(ch.x, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
         for (int t = threadIdx.x; t < kGatherNodes; t += blockDim.x) {
-            int i = t / 36, j = (t / 6) % 6, k = t % 6;
-            int gx = ox + i, gy = oy + j, gz = oz + k;
+            const int i = t / 36, j = (t / 6) % 6, k = t % 6;
+            const int gx = ox + i, gy = oy + j, gz = oz + k;
             float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (gx < g.n && gy < g.n && gz < g.n) val = p.grid_in[node_index(gx, gy, gz, g.nb)];
             G[t] = val;
         }
         tile_clear(T);
         __syncthreads();
-        const int o[3] = {ox - 1, oy - 1, oz - 1};
-        for (int q0 = 0; q0 < ch.z; q0 += blockDim.x) {
-            const int q = q0 + threadIdx.x;
-            const bool active = q < ch.z;
-            uint32_t newkey = 0xffffffffu;
-            if (active) {
-                const uint32_t slot = (uint32_t)(ch.y + q);
-                const uint32_t src = p.perm[slot];
-                float x[3];
+        const bool active = (int)threadIdx.x < ch.z;
+        float xn[3] = {0.0f, 0.0f, 0.0f}, vn[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
+        float bp = 0.0f;
+        uint32_t newkey = 0xffffffffu;
+        if (active) {
+            const uint32_t slot = (uint32_t)(ch.y + threadIdx.x);
+            const uint32_t src = p.perm[slot];
+            float x[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
-                // ---- G2P: v = sum w v_i, C = 4/dx sum w v_i (i - f)^T (offsets in cells)
-                int bs[3];
-                float f[3], w[3][3];
+            for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
+            // ---- G2P: v = sum w v_i, C = 4/dx sum w v_i (i - f)^T (offsets in cells)
+            int bs[3];
+            float f[3], w[3][3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    bs[a] = cell_base(x[a], g.inv_dx);
-                    f[a] = cell_frac(x[a], g.inv_dx, bs[a]);
-                    bspline_weights(f[a], w[a]);
-                }
-                int l0 = bs[0] - ox, l1 = bs[1] - oy, l2 = bs[2] - oz;
-                if ((unsigned)l0 > 3u || (unsigned)l1 > 3u || (unsigned)l2 > 3u) {
-                    flags |= kFlagInternal;
-                    l0 = min(max(l0, 0), 3); l1 = min(max(l1, 0), 3); l2 = min(max(l2, 0), 3);
-                }
-                float vn[3] = {0.0f, 0.0f, 0.0f};
-                float M[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+            for (int a = 0; a < 3; ++a) {
+                bs[a] = cell_base(x[a], g.inv_dx);
+                f[a] = cell_frac(x[a], g.inv_dx, bs[a]);
+                bspline_weights(f[a], w[a]);
+            }
+            int l0 = bs[0] - ox, l1 = bs[1] - oy, l2 = bs[2] - oz;
+            if ((unsigned)l0 > 3u || (unsigned)l1 > 3u || (unsigned)l2 > 3u) {
+                flags |= kFlagInternal;
+                l0 = min(max(l0, 0), 3);
+                l1 = min(max(l1, 0), 3);
+                l2 = min(max(l2, 0), 3);
+            }
+            float M[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        float wij = w[0][i] * w[1][j];
+                for (int j = 0; j < 3; ++j) {
+                    const float wij = w[0][i] * w[1][j];
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            float wk = wij * w[2][k];
-                            float4 gv = G[((l0 + i) * kGatherEdge + (l1 + j)) * kGatherEdge + (l2 + k)];
-                            float wv[3] = {wk * gv.x, wk * gv.y, wk * gv.z};
+                    for (int k = 0; k < 3; ++k) {
+                        const float wk = wij * w[2][k];
+                        const float4 gv = G[((l0 + i) * kGatherEdge + (l1 + j)) * kGatherEdge + (l2 + k)];
+                        const float wv[3] = {wk * gv.x, wk * gv.y, wk * gv.z};
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                vn[a] += wv[a];
-                                if (i) M[a][0] += (float)i * wv[a];
-                                if (j) M[a][1] += (float)j * wv[a];
-                                if (k) M[a][2] += (float)k * wv[a];
-                            }
+                        for (int a = 0; a < 3; ++a) {
+                            vn[a] += wv[a];
+                            if (i) M[a][0] += (float)i * wv[a];
+                            if (j) M[a][1] += (float)j * wv[a];
+                            if (k) M[a][2] += (float)k * wv[a];
                         }
                     }
-                float Cn[3][3];
-                const float cs = 4.0f * g.inv_dx;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) Cn[a][c] = cs * (M[a][c] - vn[a] * f[c]);
-                // ---- advect and clamp
-                float xn[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    xn[a] = x[a] + dt * vn[a];
-                    if (!isfinite(vn[a])) flags |= 0x2u;
-                    flags |= clamp_coord(xn[a], g.lo, g.hi);
                 }
-                // ---- F (or J) update, return map, stress of the new state
-                float Gm[3][3];
+            float Cn[3][3];
+            const float cs = 4.0f * g.inv_dx;
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+            for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) Gm[a][c] = (a == c ? 1.0f : 0.0f) + dt * Cn[a][c];
-                float tau[3][3];
-                if (KIND == 0) {
-                    float F[3][3], Ft[3][3];
-                    load_mat(p.in.F, N, src, F);
+                for (int c = 0; c < 3; ++c) Cn[a][c] = cs * (M[a][c] - vn[a] * f[c]);
+            // ---- advect and clamp
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) Ft[a][c] = Gm[a][0] * F[0][c] + Gm[a][1] * F[1][c] + Gm[a][2] * F[2][c];
-                    flags |= plastic_update_and_stress(Ft, p.mat, tau);
-                    store_mat(p.out.F, N, slot, Ft);
-                } else {
-                    float J = p.in.F[src] * det3(Gm);
-                    float s = p.mat.lambda * J * (J - 1.0f);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
-                    p.out.F[slot] = J;
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    p.out.x[(size_t)a * N + slot] = xn[a];
-                    p.out.v[(size_t)a * N + slot] = vn[a];
-                }
-                store_mat(p.out.C, N, slot, Cn);
-                p.out.pid[slot] = p.in.pid[src];
-                newkey = bin_of(xn, g);
-                p.key_out[slot] = newkey;
-                // ---- P2G of the new state into the next grid
-                float A[3][3];
-                affine(p.mat, Cn, tau, A);
-                flags |= scatter_particle(T, p, o, xn, vn, A);
+            for (int a = 0; a < 3; ++a) {
+                xn[a] = x[a] + dt * vn[a];
+                if (!isfinite(vn[a])) flags |= 0x2u;
+                flags |= clamp_coord(xn[a], g.lo, g.hi);
             }
-            warp_hist_add(p.hist, newkey, false);
+            // ---- F (or J) update, return map, stress of the new state
+            float Gm[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Gm[a][c] = (a == c ? 1.0f : 0.0f) + dt * Cn[a][c];
+            float tau[3][3];
+            if (KIND == 0) {
+                float F[3][3], Ft[3][3];
+                load_mat(p.in.F, N, src, F);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        Ft[a][c] = Gm[a][0] * F[0][c] + Gm[a][1] * F[1][c] + Gm[a][2] * F[2][c];
+                flags |= plastic_update_and_stress(Ft, p.mat, tau);
+                store_mat(p.out.F, N, slot, Ft);
+            } else {
+                const float J = p.in.F[src] * det3(Gm);
+                const float s = p.mat.lambda * J * (J - 1.0f);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
+                p.out.F[slot] = J;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                p.out.x[(size_t)a * N + slot] = xn[a];
+                p.out.v[(size_t)a * N + slot] = vn[a];
+            }
+            store_mat(p.out.C, N, slot, Cn);
+            p.out.pid[slot] = p.in.pid[src];
+            newkey = bin_of(xn, g);
+            p.key_out[slot] = newkey;
+            affine(p.mat, Cn, tau, A);
+            bp = particle_bound(p.mat.p_mass, vn, A, g.dx);
         }
+        warp_hist_add(p.hist, newkey, false);
+        tile_bound(T, bp);
         __syncthreads();
-        tile_flush(T, p, bx, by, bz);
+        // ---- P2G of the new state into the next grid
+        const int k = momentum_scale_exp(T.bound_bits);
+        const int o[3] = {ox - 1, oy - 1, oz - 1};
+        if (active) flags |= scatter_particle(T, p, o, xn, vn, A, pow2f(k));
+        __syncthreads();
+        tile_flush(T, p, bx, by, bz, pow2f(-k));
         __syncthreads();
     }
     if (flags) atomicOr(p.status, flags);
+    // The last CTA to finish turns the new bin counts into offsets and the next chunk list. Every CTA
+    // has read its chunks and added to the counts before taking its ticket.
+    __shared__ uint32_t warp_tot[2][32];
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        scan_bins(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, g.nblocks, kChunk, warp_tot);
+        if (threadIdx.x == 0) *p.done = 0u;
+    }
 }
 
 // ------------------------------------------------------------------------ grid update
 
-// 256 threads = four 4^3 bins; bins without mass are skipped. Zeroes the bins of the previous grid
-// that were active, so the next fused pass scatters into a clean grid.
-__global__ void __launch_bounds__(256) k_grid_update(GridParams p) {
+// One CTA of 256 threads = four 4^3 bins (cta selects which); bins without mass are skipped. Zeroes the
+// bins of the previous grid that were active, so the next fused pass scatters into a clean grid.
+__device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
     __shared__ ColliderNow cn[kMaxColliders];
     __shared__ float wr[kMaxColliders * 6];
     const Geometry& g = p.geo;
     const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
-    const int b = blockIdx.x * 4 + grp;
+    const int b = cta * 4 + grp;
     bool has_old = false, has_new = false;
     if (b < g.nblocks) {
         has_old = p.flags_old[b] != 0u;
@@ -549,6 +646,18 @@ __global__ void __launch_bounds__(256) k_grid_update(GridParams p) {
         float val = wr[i];
         if (val != 0.0f) atomicAdd(&p.wrench[i], (double)val);
     }
+}
+
+__global__ void __launch_bounds__(256) k_grid_update(GridParams p) { grid_update_cta(p, blockIdx.x); }
+
+// The sort-assign of the state the previous fused pass wrote (first assign_ctas CTAs) and the grid
+// update of the transfer it scattered (the remaining CTAs): independent work, one launch.
+__global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
+    if ((int)blockIdx.x < p.assign_ctas) {
+        assign_slot(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.key, p.cursor, p.perm);
+        return;
+    }
+    grid_update_cta(p.grid, blockIdx.x - p.assign_ctas);
 }
 
 // ------------------------------------------------------------------------ readback
@@ -643,6 +752,11 @@ cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int t
 
 cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s) {
     k_grid_update<<<ceil_div(p.geo.nblocks, 4), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
+    k_assign_grid<<<p.assign_ctas + ceil_div(p.grid.geo.nblocks, 4), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

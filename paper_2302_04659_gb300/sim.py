@@ -111,8 +111,20 @@ class Sim:
     def status(self, clear: bool = False, stream=None) -> int:
         return mpm.mpm_get_status(self.handle, int(clear), _stream(stream))
 
-    def set_timing(self, on: bool):
-        mpm.mpm_set_timing(self.handle, int(on))
+    def set_timing(self, kinds=True):
+        """Time launches of the given kernel kinds (names of ``KERNEL_NAMES``), all (True) or none."""
+        if kinds is True:
+            mask = (1 << mpm.MPM_K_COUNT) - 1
+        elif not kinds:
+            mask = 0
+        else:
+            mask = 0
+            for k in kinds:
+                mask |= 1 << mpm.KERNEL_NAMES.index(k)
+        mpm.mpm_set_timing(self.handle, mask)
+
+    def set_graphs(self, on: bool):
+        mpm.mpm_set_graphs(self.handle, int(on))
 
     def read_timing(self, reset: bool = False):
         ms, cnt = mpm.mpm_read_timing(self.handle, int(reset))

@@ -24,6 +24,16 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def rel_C(C, C_ref, v_ref, dx):
+    """Error of the affine velocity C relative to its natural scale, |C_ref| + |v_ref| / dx: C is a
+    velocity gradient gathered from node velocities with weights summing to a cancellation, so its FP32
+    rounding error scales with |v| / dx even where C itself is near zero (e.g. free fall)."""
+    C = np.asarray(C, np.float64)
+    C_ref = np.asarray(C_ref, np.float64)
+    scale = np.linalg.norm(C_ref) + np.linalg.norm(np.asarray(v_ref, np.float64)) / dx
+    return np.linalg.norm(C - C_ref) / (scale if scale > 0 else 1.0)
+
+
 def oracle_params(sc: scenes.Scene) -> oracle.Params:
     m = sc.material
     return oracle.Params(n=sc.n, dt=sc.dt, gravity=tuple(sc.gravity), bound=sc.bound, kind=m.kind, E=m.E, nu=m.nu,
