@@ -193,25 +193,33 @@ def run_native(args):
     sim.set_particles(xd, vd, Cd, Fd)
     for s in range(args.warmup):
         env_step(s)
-    # ---------------- timed region (device-resident inputs)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sim.set_timing(["g2p2g"])  # only the dominant kernel: events stay out of the other launches
-    sim.read_timing(reset=True)
-    l0 = sim.launches
-    barrier()
-    wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
+    def timed_pass(first_step):
+        """K env steps, each bracketed by events on the launching stream, L2 flushed before each."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier()
         for s in range(args.steps):
             flush.fill_(float(s))
             ev[s][0].record(stream)
-            env_step(args.warmup + s)
+            env_step(first_step + s)
             ev[s][1].record(stream)
         barrier()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    # ---------------- timed region (device-resident inputs), no instrumentation inside the steps
+    l0 = sim.launches
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        elapsed = timed_pass(args.warmup)
     wall = time.perf_counter() - wall0
     launches = sim.launches - l0
+    # ---------------- the same steps again with CUDA events bracketing every launch of the fused
+    # G2P/P2G kernel (event nodes inside the replayed graphs), for its mean launch duration
+    sim.set_timing(["g2p2g"])
+    sim.read_timing(reset=True)
+    elapsed_instrumented = timed_pass(args.warmup + args.steps)
     ktime = sim.read_timing(reset=True)
     sim.set_timing(False)
-    elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -290,6 +298,10 @@ def run_native(args):
             "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_SUBSTEP * N,
             "mean_launch_us": g_avg * 1e6,
             "launches": g_n,
+            "timing": ("CUDA events around every k_g2p2g launch in a second pass over the same number of "
+                       f"steps (that pass took {elapsed_instrumented / args.steps * 1e3:.3f} ms/step; the "
+                       "headline pass runs without events, which would break the programmatic launch "
+                       "overlap between kernels)"),
             "kernel_source_hash": src_hash,
             "note": "state (38 MB) fits the 129 MB L2 inside a step; L2 flushed between steps",
         },

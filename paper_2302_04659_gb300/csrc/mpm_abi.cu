@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -58,7 +59,7 @@ Layout make_layout(const mpm_config& c) {
     const size_t nblocks = nb * nb * nb;
     const size_t nodes = nblocks * kBlkNodes;
     for (int i = 0; i < 2; ++i) L.state[i] = take(Nmax * 25 * 4);
-    L.key = take(Nmax * 4);
+    L.key = take(Nmax * 8);  // (bin, rank within bin) per particle
     L.perm = take(Nmax * 4);
     for (int i = 0; i < 2; ++i) L.grid[i] = take(nodes * sizeof(float4));
     for (int i = 0; i < 2; ++i) L.flags[i] = take(nblocks * 4);
@@ -137,7 +138,7 @@ struct mpm_sim {
     mpm_shape shapes[MPM_MAX_COLLIDERS];
     int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
     int sms = 0;
-    int ctas_fused = 0, ctas_p2g = 0;
+    int ctas_fused = 0, ctas_p2g = 0, ctas_grid = 0;
     long long launches = 0;
     unsigned timing_mask = 0;
     struct Ev {
@@ -233,7 +234,7 @@ TransferParams transfer_params(mpm_sim* s) {
     p.in = s->view(s->ps.cur);
     p.out = s->view(1 - s->ps.cur);
     p.perm = s->at<uint32_t>(s->L.perm);
-    p.key_out = s->at<uint32_t>(s->L.key);
+    p.keyrank_out = s->at<uint2>(s->L.key);
     p.hist = s->at<uint32_t>(s->L.hist);
     p.chunks = s->at<int4>(s->L.chunks);
     p.num_chunks = s->num_chunks();
@@ -258,6 +259,7 @@ GridParams grid_params(mpm_sim* s) {
     gp.cols = s->at<ColliderSet>(s->L.colliders);
     gp.ncol = s->ncol;
     gp.substep_counter = s->substep_counter();
+    gp.ctas = s->ctas_grid;
     gp.wrench = s->at<double>(s->L.wrench);
     return gp;
 }
@@ -276,7 +278,7 @@ mpm_status ensure_order(mpm_sim* s, cudaStream_t st) {
     MPM_TRY(ensure_scanned(s, st));
     if (s->ps.order_valid) return MPM_OK;
     MPM_TRY(launch(s, MPM_K_ASSIGN, st, [&] {
-        return launch_assign(s->N, s->at<uint32_t>(s->L.key), s->at<uint32_t>(s->L.cursor), s->at<uint32_t>(s->L.perm),
+        return launch_assign(s->N, s->at<uint2>(s->L.key), s->at<uint32_t>(s->L.cursor), s->at<uint32_t>(s->L.perm),
                              st);
     }, "assign"));
     s->ps.order_valid = true;
@@ -304,7 +306,7 @@ mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
         AssignGridParams ap{};
         ap.grid = grid_params(s);
         ap.N = s->N;
-        ap.key = s->at<uint32_t>(s->L.key);
+        ap.keyrank = s->at<uint2>(s->L.key);
         ap.cursor = s->at<uint32_t>(s->L.cursor);
         ap.perm = s->at<uint32_t>(s->L.perm);
         ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 255) / 256;
@@ -461,6 +463,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_wo
     }
     s->ctas_fused = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, true);
     s->ctas_p2g = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, false);
+    // persistent grid update: two CTAs per SM, or one per group of four bins if that is fewer
+    s->ctas_grid = std::min(2 * s->sms, (g.nblocks + 3) / 4);
     // zero the grids, bin flags and counts, colliders and counters
     const size_t zero_from = L.grid[0];
     e = cudaMemsetAsync(s->ws + zero_from, 0, L.total - zero_from, st);
@@ -524,7 +528,7 @@ mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, 
     }
     StateView dst = s->view(0);
     MPM_TRY(launch(s, MPM_K_LOAD, st, [&] {
-        return launch_load(s->geo, s->mat.kind, n, sx, sv, sC, sF, dst, s->at<uint32_t>(s->L.key),
+        return launch_load(s->geo, s->mat.kind, n, sx, sv, sC, sF, dst, s->at<uint2>(s->L.key),
                            s->at<uint32_t>(s->L.hist), s->status(), st);
     }, "load"));
     if (!src_on_device) MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");

@@ -39,7 +39,7 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     StateView in;           // read through perm
     StateView out;          // written at the sorted slot (fused pass only)
     const uint32_t* perm;   // sorted slot -> position in `in`
-    uint32_t* key_out;      // fused pass: bin of the new position, per sorted slot
+    uint2* keyrank_out;     // fused pass: (bin of the new position, rank within that bin), per sorted slot
     uint32_t* hist;         // fused pass: particles per bin of the new positions
     const float4* grid_in;  // fused pass: node velocities (x, y, z, mass)
     float4* grid_out;       // mass and momentum accumulated (m, mx, my, mz)
@@ -64,17 +64,18 @@ struct GridParams {
     const uint32_t* flags;    // active bins of grid
     float4* grid_old;         // the previous grid, zeroed here for its next use
     uint32_t* flags_old;
-    const ColliderSet* cols;
+    const ColliderSet* cols;  // as set; posed at t = substep counter * dt
     int ncol;
     const uint32_t* substep_counter;
     double* wrench;           // ncol x 6
+    int ctas;                 // CTAs of the (persistent) grid update
 };
 
 struct AssignGridParams {  // the sort-assign of the new state and the grid update, one launch
     GridParams grid;
     int N;
-    const uint32_t* key;
-    uint32_t* cursor;
+    const uint2* keyrank;
+    const uint32_t* cursor;
     uint32_t* perm;
     int assign_ctas;          // the first assign_ctas CTAs assign sorted slots (0: no assign)
 };
@@ -86,11 +87,11 @@ struct ColliderUpload {
 
 // launch wrappers (mpm_kernels.cu); each returns cudaGetLastError() after enqueueing
 cudaError_t launch_load(const Geometry& g, int kind, int N, const float* x, const float* v, const float* C,
-                        const float* F, StateView dst, uint32_t* key, uint32_t* hist, uint32_t* status,
+                        const float* F, StateView dst, uint2* keyrank, uint32_t* hist, uint32_t* status,
                         cudaStream_t s);
 cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks, int nblocks,
                         int chunk, cudaStream_t s);
-cudaError_t launch_assign(int N, const uint32_t* key, uint32_t* cursor, uint32_t* perm, cudaStream_t s);
+cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s);
 cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
 cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
 cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s);
@@ -98,8 +99,8 @@ cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s);
 cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
                               cudaStream_t s);
 cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, cudaStream_t s);
-cudaError_t launch_set_colliders(const ColliderUpload& u, ColliderSet* table, double* wrench,
-                                 uint32_t* counter, cudaStream_t s);
+cudaError_t launch_set_colliders(const ColliderUpload& u, ColliderSet* table, double* wrench, uint32_t* counter,
+                                 cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s);
 
 // occupancy of the particle kernels (CTAs per SM at the given block size)

@@ -37,6 +37,12 @@ __device__ __forceinline__ uint32_t clamp_coord(float& x, float lo, float hi) {
     return f;
 }
 
+// Programmatic dependent launch: the two per-substep kernels are launched so that the next one may be
+// scheduled while the previous one drains. A kernel waits for its predecessor's completion (and memory)
+// before touching its outputs, and releases its successor once its own main work is issued.
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // Warp-aggregated histogram increment; every lane of the warp must call it (key = ~0u: no count).
 __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, bool want_base) {
     uint32_t peers = __match_any_sync(0xffffffffu, key);
@@ -56,16 +62,23 @@ __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, 
 // The particle-to-grid scatter of one chunk (at most kChunk particles of one bin) goes into a shared
 // tile of the 8^3 nodes its particles can reach, accumulated with 32-bit integer atomics: shared-memory
 // integer adds are single native instructions, FP32 ones are not. Values are fixed point:
-//   mass      sum of weights, scaled by 2^24 (a node sums at most kChunk weights <= 0.75^3 each, so the
-//             sum stays below 54 * 2^24 < 2^31);
-//   momentum  scaled by 2^k with k = 24 - e, where 2^e bounds (from above, within a factor 2) the largest
+//   mass      sum of weights, scaled by 2^22 (a node sums at most kChunk weights <= 0.75^3 each, so the
+//             sum stays below 54 * 2^22 < 2^31);
+//   momentum  scaled by 2^k with k = 22 - e, where 2^e bounds (from above, within a factor 2) the largest
 //             per-particle magnitude B_p = max_a (m |v_a| + 1.5 dx sum_c |A_ac|) of the chunk, so every node
-//             sum stays below 54 * 2^24 as well. Rounding is then at most 2^-25 of that bound per term --
-//             no coarser than an FP32 accumulation of the same terms.
+//             sum stays below 54 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term,
+//             comparable to an FP32 accumulation of the same terms. Every scaled term is below 2^22, so it
+//             is rounded to an integer by one FP32 add (round_fixed).
 // The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
 
 
-constexpr int kMassBits = 24;
+constexpr int kMassBits = 22;
+
+// round(x) for |x| < 2^22 with one FP32 add: x + 1.5 * 2^23 lands where one unit is one ulp, so the
+// low mantissa bits hold round-to-nearest-even(x), offset by the constant's own bit pattern.
+__device__ __forceinline__ int round_fixed(float x) {
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
 
 struct ScatterTile {
     int m[kScatterNodes];
@@ -144,17 +157,17 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const float wij = w[0][i] * w[1][j];
+                const float wijm = wij * wscale;
+                const float mij[3] = {bm[0] + i * Ad[0][0] + j * Ad[1][0], bm[1] + i * Ad[0][1] + j * Ad[1][1],
+                                      bm[2] + i * Ad[0][2] + j * Ad[1][2]};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float wk = wij * w[2][k];
                     const int t = tile_slot(l0 + i, l1 + j, l2 + k);
-                    const float mx = bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0];
-                    const float my = bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1];
-                    const float mz = bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2];
-                    atomicAdd(&T.m[t], __float2int_rn(wk * wscale));
-                    atomicAdd(&T.px[t], __float2int_rn(wk * mx));
-                    atomicAdd(&T.py[t], __float2int_rn(wk * my));
-                    atomicAdd(&T.pz[t], __float2int_rn(wk * mz));
+                    atomicAdd(&T.m[t], round_fixed(wijm * w[2][k]));
+                    atomicAdd(&T.px[t], round_fixed(wk * (mij[0] + k * Ad[2][0])));
+                    atomicAdd(&T.py[t], round_fixed(wk * (mij[1] + k * Ad[2][1])));
+                    atomicAdd(&T.pz[t], round_fixed(wk * (mij[2] + k * Ad[2][2])));
                 }
             }
         return 0;
@@ -256,7 +269,7 @@ __device__ __forceinline__ void decode_bin(int b, int nb, int& bx, int& by, int&
 template <int KIND>
 __global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __restrict__ x,
                                               const float* __restrict__ v, const float* __restrict__ C,
-                                              const float* __restrict__ F, StateView dst, uint32_t* key,
+                                              const float* __restrict__ F, StateView dst, uint2* keyrank,
                                               uint32_t* hist, uint32_t* status) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool active = p < N;
@@ -286,9 +299,9 @@ __global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __
         }
         dst.pid[p] = (uint32_t)p;
         k = bin_of(xp, g);
-        key[p] = k;
     }
-    warp_hist_add(hist, k, false);
+    const uint32_t rank = warp_hist_add(hist, k, true);
+    if (active) keyrank[p] = make_uint2(k, rank);
     if (flags) atomicOr(status, flags);
 }
 
@@ -298,16 +311,29 @@ __global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __
 // offsets (cursor) and the chunk list: each bin is cut into chunks of at most `chunk` particles, one
 // chunk per CTA iteration of the particle passes. The counts are read from L2 (they were accumulated by
 // other CTAs' atomics) and zeroed for the next histogram.
+// Each thread owns a run of 4-bin groups, read as 16-byte vectors in batches of 8 independent loads so
+// one L2 round trip covers 32 bins. The count arrays are padded to a multiple of 4 bins (zeros).
 __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
                                           int nblocks, int chunk, uint32_t (&warp_tot)[2][32]) {
     const int tid = threadIdx.x;
-    const int per = (nblocks + blockDim.x - 1) / blockDim.x;
-    const int b0 = min(tid * per, nblocks), b1 = min(b0 + per, nblocks);
+    const int nq = (nblocks + 3) >> 2;
+    const int per = (nq + blockDim.x - 1) / blockDim.x;
+    const int q0 = min(tid * per, nq), q1 = min(q0 + per, nq);
+    uint4* H = reinterpret_cast<uint4*>(hist);
     uint32_t cnt = 0, nch = 0;
-    for (int b = b0; b < b1; ++b) {
-        uint32_t c = __ldcg(&hist[b]);
-        cnt += c;
-        nch += (c + chunk - 1) / chunk;
+    for (int q = q0; q < q1; q += 8) {
+        uint4 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = q + u < q1 ? __ldcg(&H[q + u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t c4[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                cnt += c4[e];
+                nch += (c4[e] + chunk - 1) / chunk;
+            }
+        }
     }
     // block-wide exclusive scan of (cnt, nch)
     const int lane = tid & 31, wid = tid >> 5;
@@ -332,14 +358,28 @@ __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4
     __syncthreads();
     uint32_t off = ic - cnt + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
     uint32_t coff = in - nch + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
-    for (int b = b0; b < b1; ++b) {
-        uint32_t c = __ldcg(&hist[b]);
-        cursor[b] = off;
-        for (uint32_t s = 0; s < c; s += chunk) {
-            chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
+    uint4* Cur = reinterpret_cast<uint4*>(cursor);
+    for (int q = q0; q < q1; q += 8) {
+        uint4 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = q + u < q1 ? __ldcg(&H[q + u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q + u >= q1) break;
+            const uint32_t c4[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
+            uint32_t o4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t c = c4[e];
+                o4[e] = off;
+                const int b = 4 * (q + u) + e;
+                for (uint32_t s = 0; s < c; s += chunk)
+                    chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
+                off += c;
+            }
+            Cur[q + u] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+            H[q + u] = make_uint4(0u, 0u, 0u, 0u);
         }
-        off += c;
-        hist[b] = 0u;
     }
     if (tid == blockDim.x - 1) *num_chunks = coff;
 }
@@ -350,19 +390,19 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor,
     scan_bins(hist, cursor, chunks, num_chunks, nblocks, chunk, warp_tot);
 }
 
-// Sorted slot of particle j: slot = start of its bin + rank among the bin's particles (ranks are handed
-// out per warp with one atomic, so runs of one warp stay contiguous and in order). All lanes of the warp
-// must call it.
-__device__ __forceinline__ void assign_slot(int j, int N, const uint32_t* __restrict__ key, uint32_t* cursor,
-                                            uint32_t* __restrict__ perm) {
-    uint32_t k = j < N ? key[j] : 0xffffffffu;
-    uint32_t slot = warp_hist_add(cursor, k, true);
-    if (j < N) perm[slot] = (uint32_t)j;
+// Sorted slot of particle j: slot = start of its bin + its rank within the bin. The rank was handed out
+// when the particle's bin count was taken (one atomic per warp and bin, lanes ranked in order), so this
+// pass needs no atomics.
+__device__ __forceinline__ void assign_slot(int j, int N, const uint2* __restrict__ keyrank,
+                                            const uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
+    if (j >= N) return;
+    const uint2 kr = keyrank[j];
+    perm[cursor[kr.x] + kr.y] = (uint32_t)j;
 }
 
-__global__ void __launch_bounds__(256) k_assign(int N, const uint32_t* __restrict__ key, uint32_t* cursor,
-                                                uint32_t* __restrict__ perm) {
-    assign_slot(blockIdx.x * blockDim.x + threadIdx.x, N, key, cursor, perm);
+__global__ void __launch_bounds__(256) k_assign(int N, const uint2* __restrict__ keyrank,
+                                                const uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
+    assign_slot(blockIdx.x * blockDim.x + threadIdx.x, N, keyrank, cursor, perm);
 }
 
 // ------------------------------------------------------------------------ standalone P2G
@@ -422,13 +462,16 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
 // ------------------------------------------------------------------------ fused G2P -> P2G
 
 template <int KIND>
-__global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
-    __shared__ float4 G[kGatherNodes];
+__global__ void __launch_bounds__(kChunk, 8) k_g2p2g(TransferParams p) {
+    // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots
+    // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
+    __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
     __shared__ ScatterTile T;
     const Geometry& g = p.geo;
     const int N = p.N;
     const float dt = g.dt;
     uint32_t flags = 0;
+    wait_for_predecessor();
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
@@ -436,25 +479,32 @@ __global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
         int bx, by, bz;
         decode_bin(ch.x, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
+        // this thread's particle: its loads are issued first so they overlap the tile load below
+        const bool active = (int)threadIdx.x < ch.z;
+        const uint32_t slot = (uint32_t)(ch.y + threadIdx.x);
+        uint32_t src = 0;
+        float x[3] = {0.5f, 0.5f, 0.5f};
+        if (active) {
+            src = p.perm[slot];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
+        }
         for (int t = threadIdx.x; t < kGatherNodes; t += blockDim.x) {
             const int i = t / 36, j = (t / 6) % 6, k = t % 6;
             const int gx = ox + i, gy = oy + j, gz = oz + k;
             float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (gx < g.n && gy < g.n && gz < g.n) val = p.grid_in[node_index(gx, gy, gz, g.nb)];
-            G[t] = val;
+            const int s = tile_slot(i, j, k);
+            Gx[s] = val.x;
+            Gy[s] = val.y;
+            Gz[s] = val.z;
         }
         tile_clear(T);
         __syncthreads();
-        const bool active = (int)threadIdx.x < ch.z;
         float xn[3] = {0.0f, 0.0f, 0.0f}, vn[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
         float bp = 0.0f;
         uint32_t newkey = 0xffffffffu;
         if (active) {
-            const uint32_t slot = (uint32_t)(ch.y + threadIdx.x);
-            const uint32_t src = p.perm[slot];
-            float x[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
             // ---- G2P: v = sum w v_i, C = 4/dx sum w v_i (i - f)^T (offsets in cells)
             int bs[3];
             float f[3], w[3][3];
@@ -480,8 +530,8 @@ __global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const float wk = wij * w[2][k];
-                        const float4 gv = G[((l0 + i) * kGatherEdge + (l1 + j)) * kGatherEdge + (l2 + k)];
-                        const float wv[3] = {wk * gv.x, wk * gv.y, wk * gv.z};
+                        const int s = tile_slot(l0 + i, l1 + j, l2 + k);
+                        const float wv[3] = {wk * Gx[s], wk * Gy[s], wk * Gz[s]};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             vn[a] += wv[a];
@@ -538,11 +588,13 @@ __global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
             store_mat(p.out.C, N, slot, Cn);
             p.out.pid[slot] = p.in.pid[src];
             newkey = bin_of(xn, g);
-            p.key_out[slot] = newkey;
             affine(p.mat, Cn, tau, A);
             bp = particle_bound(p.mat.p_mass, vn, A, g.dx);
         }
-        warp_hist_add(p.hist, newkey, false);
+        {
+            const uint32_t rank = warp_hist_add(p.hist, newkey, true);
+            if (active) p.keyrank_out[ch.y + threadIdx.x] = make_uint2(newkey, rank);
+        }
         tile_bound(T, bp);
         __syncthreads();
         // ---- P2G of the new state into the next grid
@@ -554,6 +606,7 @@ __global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
         __syncthreads();
     }
     if (flags) atomicOr(p.status, flags);
+    release_successor();
     // The last CTA to finish turns the new bin counts into offsets and the next chunk list. Every CTA
     // has read its chunks and added to the counts before taking its ticket.
     __shared__ uint32_t warp_tot[2][32];
@@ -571,24 +624,26 @@ __global__ void __launch_bounds__(kChunk) k_g2p2g(TransferParams p) {
 
 // ------------------------------------------------------------------------ grid update
 
-// One CTA of 256 threads = four 4^3 bins (cta selects which); bins without mass are skipped. Zeroes the
-// bins of the previous grid that were active, so the next fused pass scatters into a clean grid.
+// A persistent CTA of 256 threads works through groups of four 4^3 bins (one node per thread), cta,
+// cta + ctas, ...; groups without mass in either grid are skipped after one flag read. Zeroes the bins of
+// the previous grid that were active, so the next fused pass scatters into a clean grid.
 __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
     __shared__ ColliderNow cn[kMaxColliders];
     __shared__ float wr[kMaxColliders * 6];
     const Geometry& g = p.geo;
     const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
-    const int b = cta * 4 + grp;
+    if ((int)threadIdx.x < p.ncol)
+        collider_at(p.cols[threadIdx.x], (float)(*p.substep_counter) * g.dt, cn[threadIdx.x]);
+    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) wr[i] = 0.0f;
+    __syncthreads();
+    for (int group = cta; group * 4 < g.nblocks; group += p.ctas) {
+    const int b = group * 4 + grp;
     bool has_old = false, has_new = false;
     if (b < g.nblocks) {
         has_old = p.flags_old[b] != 0u;
         has_new = p.flags[b] != 0u;
     }
-    if (!__syncthreads_or(has_old || has_new)) return;
-    const float t = (float)(*p.substep_counter) * g.dt;
-    if (threadIdx.x < p.ncol) collider_at(p.cols[threadIdx.x], t, cn[threadIdx.x]);
-    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) wr[i] = 0.0f;
-    __syncthreads();
+    if (!__syncthreads_or(has_old || has_new)) continue;
     if (has_old) {
         p.grid_old[(size_t)b * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (ln == 0) p.flags_old[b] = 0u;
@@ -641,6 +696,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
             *node = make_float4(v[0], v[1], v[2], m);
         }
     }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) {
         float val = wr[i];
@@ -653,8 +709,9 @@ __global__ void __launch_bounds__(256) k_grid_update(GridParams p) { grid_update
 // The sort-assign of the state the previous fused pass wrote (first assign_ctas CTAs) and the grid
 // update of the transfer it scattered (the remaining CTAs): independent work, one launch.
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
+    wait_for_predecessor();  // (a CTA's exit releases the successor)
     if ((int)blockIdx.x < p.assign_ctas) {
-        assign_slot(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.key, p.cursor, p.perm);
+        assign_slot(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
         return;
     }
     grid_update_cta(p.grid, blockIdx.x - p.assign_ctas);
@@ -712,13 +769,13 @@ __global__ void k_advance_counter(uint32_t* counter, int n) {
 static inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
 cudaError_t launch_load(const Geometry& g, int kind, int N, const float* x, const float* v, const float* C,
-                        const float* F, StateView dst, uint32_t* key, uint32_t* hist, uint32_t* status,
+                        const float* F, StateView dst, uint2* keyrank, uint32_t* hist, uint32_t* status,
                         cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     if (kind == 0)
-        k_load<0><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, key, hist, status);
+        k_load<0><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, keyrank, hist, status);
     else
-        k_load<1><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, key, hist, status);
+        k_load<1><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, keyrank, hist, status);
     return cudaGetLastError();
 }
 
@@ -728,9 +785,9 @@ cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_assign(int N, const uint32_t* key, uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
+cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    k_assign<<<ceil_div(N, 256), 256, 0, s>>>(N, key, cursor, perm);
+    k_assign<<<ceil_div(N, 256), 256, 0, s>>>(N, keyrank, cursor, perm);
     return cudaGetLastError();
 }
 
@@ -742,22 +799,35 @@ cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int thr
     return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization: the kernel may start while its predecessor on the
+// stream drains; it orders itself with wait_for_predecessor().
+template <typename P>
+static cudaError_t launch_dependent(void (*kernel)(P), unsigned grid, unsigned block, cudaStream_t s, const P& p) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
 cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s) {
-    if (kind == 0)
-        k_g2p2g<0><<<grid_ctas, threads, 0, s>>>(p);
-    else
-        k_g2p2g<1><<<grid_ctas, threads, 0, s>>>(p);
-    return cudaGetLastError();
+    return kind == 0 ? launch_dependent(k_g2p2g<0>, grid_ctas, threads, s, p)
+                     : launch_dependent(k_g2p2g<1>, grid_ctas, threads, s, p);
 }
 
 cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s) {
-    k_grid_update<<<ceil_div(p.geo.nblocks, 4), 256, 0, s>>>(p);
+    k_grid_update<<<p.ctas, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
-    k_assign_grid<<<p.assign_ctas + ceil_div(p.grid.geo.nblocks, 4), 256, 0, s>>>(p);
-    return cudaGetLastError();
+    return launch_dependent(k_assign_grid, p.assign_ctas + p.grid.ctas, 256, s, p);
 }
 
 cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
