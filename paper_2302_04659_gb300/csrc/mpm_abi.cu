@@ -42,7 +42,8 @@ constexpr int kMaxGraphs = 8;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t state[2], key, perm, grid[2], flags[2], hist, cursor, chunks, colliders, wrench, counters, total;
+    size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, colliders, wrench,
+        counters, total;
     size_t max_chunks;
 };
 
@@ -64,6 +65,9 @@ Layout make_layout(const mpm_config& c) {
     for (int i = 0; i < 2; ++i) L.grid[i] = take(nodes * sizeof(float4));
     for (int i = 0; i < 2; ++i) L.flags[i] = take(nblocks * 4);
     L.hist = take(nblocks * 4);
+    for (int i = 0; i < 2; ++i) L.list[i] = take(nblocks * 4);
+    L.list_meta = take(4 * sizeof(uint32_t));  // list counts [2], grid-update CTAs done, spare
+    // everything from grid[0] up to here restarts from zero on mpm_set_particles
     L.cursor = take(nblocks * 4);
     L.max_chunks = Nmax / kChunk + nblocks + 1;
     L.chunks = take(L.max_chunks * sizeof(int4));
@@ -165,6 +169,9 @@ struct mpm_sim {
     uint32_t* substep_counter() { return at<uint32_t>(L.counters) + 1; }
     uint32_t* num_chunks() { return at<uint32_t>(L.counters) + 2; }
     uint32_t* done() { return at<uint32_t>(L.counters) + 3; }
+    uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
+    uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
+    uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
     StateView view(int which) {
         float* b = at<float>(L.state[which]);
         const size_t n = (size_t)N;
@@ -253,7 +260,11 @@ GridParams grid_params(mpm_sim* s) {
     for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
     gp.bound = s->cfg.bound;
     gp.grid = s->at<float4>(s->L.grid[s->ps.g]);
-    gp.flags = s->at<uint32_t>(s->L.flags[s->ps.g]);
+    gp.list = s->list(s->ps.g);
+    gp.list_count = s->list_count(s->ps.g);
+    gp.list_old = s->list(1 - s->ps.g);
+    gp.list_count_old = s->list_count(1 - s->ps.g);
+    gp.done = s->grid_done();
     gp.grid_old = s->at<float4>(s->L.grid[1 - s->ps.g]);
     gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
     gp.cols = s->at<ColliderSet>(s->L.colliders);
@@ -292,6 +303,8 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
     TransferParams p = transfer_params(s);
     p.grid_out = s->at<float4>(s->L.grid[s->ps.g]);
     p.flags_out = s->at<uint32_t>(s->L.flags[s->ps.g]);
+    p.list_out = s->list(s->ps.g);
+    p.list_count_out = s->list_count(s->ps.g);
     MPM_TRY(launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->mat.kind, s->ctas_p2g, kChunk, st); }, "p2g"));
     s->ps.grid_valid = true;
     return MPM_OK;
@@ -309,13 +322,15 @@ mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
         ap.keyrank = s->at<uint2>(s->L.key);
         ap.cursor = s->at<uint32_t>(s->L.cursor);
         ap.perm = s->at<uint32_t>(s->L.perm);
-        ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 255) / 256;
+        ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 1023) / 1024;  // 4 particles per thread
         MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
         s->ps.order_valid = true;
         TransferParams p = transfer_params(s);
         p.grid_in = ap.grid.grid;
         p.grid_out = ap.grid.grid_old;
         p.flags_out = ap.grid.flags_old;
+        p.list_out = s->list(1 - s->ps.g);
+        p.list_count_out = s->list_count(1 - s->ps.g);
         MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->mat.kind, s->ctas_fused, kChunk, st); },
                        "g2p2g"));
         s->ps.cur = 1 - s->ps.cur;

@@ -44,6 +44,8 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     const float4* grid_in;  // fused pass: node velocities (x, y, z, mass)
     float4* grid_out;       // mass and momentum accumulated (m, mx, my, mz)
     uint32_t* flags_out;    // bins of grid_out that received anything
+    uint32_t* list_out;     // ... and the same bins as a list, each appended once (when its flag is set)
+    uint32_t* list_count_out;
     const int4* chunks;     // (bin, first sorted slot, count, 0)
     const uint32_t* num_chunks;
     uint32_t* status;
@@ -61,9 +63,13 @@ struct GridParams {
     float gravity[3];
     int bound;
     float4* grid;             // (m, mv) in, (v, m) out
-    const uint32_t* flags;    // active bins of grid
-    float4* grid_old;         // the previous grid, zeroed here for its next use
-    uint32_t* flags_old;
+    const uint32_t* list;     // active bins of grid and their count
+    const uint32_t* list_count;
+    float4* grid_old;         // the previous grid, zeroed here (its active bins) for its next use
+    uint32_t* flags_old;      // its bin flags, cleared
+    const uint32_t* list_old;
+    uint32_t* list_count_old; // reset by the last CTA to finish
+    uint32_t* done;           // CTAs finished, reset by the last one
     const ColliderSet* cols;  // as set; posed at t = substep counter * dt
     int ncol;
     const uint32_t* substep_counter;

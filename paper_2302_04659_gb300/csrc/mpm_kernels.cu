@@ -80,7 +80,7 @@ __device__ __forceinline__ int round_fixed(float x) {
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-struct ScatterTile {
+struct __align__(16) ScatterTile {
     int m[kScatterNodes];
     int px[kScatterNodes];
     int py[kScatterNodes];
@@ -114,6 +114,12 @@ __device__ __forceinline__ float particle_bound(float m, const float vn[3], cons
         b = fmaxf(b, r);
     }
     return b;
+}
+
+// Flag bin b of the output grid as active; the thread that sets the flag appends b to the bin list.
+__device__ __forceinline__ void mark_bin(const TransferParams& p, uint32_t b) {
+    if (__ldcg(&p.flags_out[b]) == 0u && atomicExch(&p.flags_out[b], 1u) == 0u)
+        p.list_out[atomicAdd(p.list_count_out, 1u)] = b;
 }
 
 // Scatter one particle's mass and momentum to its 27 nodes: mom(node) = w (m v + A (x_i - x_p)),
@@ -184,18 +190,14 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
                                          wk * (bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1]),
                                          wk * (bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2]));
                 atomicAdd(&p.grid_out[node_index(gx, gy, gz, g.nb)], add);
-                p.flags_out[block_index(gx >> 2, gy >> 2, gz >> 2, g.nb)] = 1u;
+                mark_bin(p, block_index(gx >> 2, gy >> 2, gz >> 2, g.nb));
             }
     return 0x8u;
 }
 
 __device__ __forceinline__ void tile_clear(ScatterTile& T) {
-    for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
-        T.m[t] = 0;
-        T.px[t] = 0;
-        T.py[t] = 0;
-        T.pz[t] = 0;
-    }
+    int4* q = reinterpret_cast<int4*>(T.m);  // m, px, py, pz are contiguous: 4 * 512 ints
+    for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) q[t] = make_int4(0, 0, 0, 0);
     if (threadIdx.x < 27) T.touched[threadIdx.x] = 0u;
     if (threadIdx.x == 0) T.bound_bits = 0u;
 }
@@ -229,7 +231,7 @@ __device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams&
     if (threadIdx.x < 27 && T.touched[threadIdx.x]) {
         int q = threadIdx.x;
         int qx = q / 9, qy = (q / 3) % 3, qz = q % 3;
-        p.flags_out[block_index(bx + qx - 1, by + qy - 1, bz + qz - 1, nb)] = 1u;
+        mark_bin(p, block_index(bx + qx - 1, by + qy - 1, bz + qz - 1, nb));
     }
 }
 
@@ -400,9 +402,27 @@ __device__ __forceinline__ void assign_slot(int j, int N, const uint2* __restric
     perm[cursor[kr.x] + kr.y] = (uint32_t)j;
 }
 
+// Four consecutive particles per thread (two 16-byte loads, four independent offset lookups in flight).
+constexpr int kAssignPerThread = 4;
+__device__ __forceinline__ void assign_slots4(int t, int N, const uint2* __restrict__ keyrank,
+                                              const uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
+    const int j0 = t * kAssignPerThread;
+    if (j0 + kAssignPerThread <= N) {
+        const uint4* q = reinterpret_cast<const uint4*>(keyrank + j0);
+        const uint4 a = q[0], b = q[1];
+        const uint32_t c0 = cursor[a.x], c1 = cursor[a.z], c2 = cursor[b.x], c3 = cursor[b.z];
+        perm[c0 + a.y] = (uint32_t)j0;
+        perm[c1 + a.w] = (uint32_t)(j0 + 1);
+        perm[c2 + b.y] = (uint32_t)(j0 + 2);
+        perm[c3 + b.w] = (uint32_t)(j0 + 3);
+    } else {
+        for (int j = j0; j < N; ++j) assign_slot(j, N, keyrank, cursor, perm);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_assign(int N, const uint2* __restrict__ keyrank,
                                                 const uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
-    assign_slot(blockIdx.x * blockDim.x + threadIdx.x, N, keyrank, cursor, perm);
+    assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, N, keyrank, cursor, perm);
 }
 
 // ------------------------------------------------------------------------ standalone P2G
@@ -474,8 +494,10 @@ __global__ void __launch_bounds__(kChunk, 8) k_g2p2g(TransferParams p) {
     wait_for_predecessor();
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
+    int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
-        const int4 ch = p.chunks[w];
+        const int4 ch = next;
+        if (w + gridDim.x < nchunks) next = p.chunks[w + gridDim.x];  // prefetch the next descriptor
         int bx, by, bz;
         decode_bin(ch.x, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
@@ -591,16 +613,16 @@ __global__ void __launch_bounds__(kChunk, 8) k_g2p2g(TransferParams p) {
             affine(p.mat, Cn, tau, A);
             bp = particle_bound(p.mat.p_mass, vn, A, g.dx);
         }
-        {
-            const uint32_t rank = warp_hist_add(p.hist, newkey, true);
-            if (active) p.keyrank_out[ch.y + threadIdx.x] = make_uint2(newkey, rank);
-        }
+        // rank within the new bin: the atomic's result is only stored after the scatter, so its round
+        // trip overlaps the work in between
+        const uint32_t rank = warp_hist_add(p.hist, newkey, true);
         tile_bound(T, bp);
         __syncthreads();
         // ---- P2G of the new state into the next grid
         const int k = momentum_scale_exp(T.bound_bits);
         const int o[3] = {ox - 1, oy - 1, oz - 1};
         if (active) flags |= scatter_particle(T, p, o, xn, vn, A, pow2f(k));
+        if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
         __syncthreads();
         tile_flush(T, p, bx, by, bz, pow2f(-k));
         __syncthreads();
@@ -636,19 +658,15 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         collider_at(p.cols[threadIdx.x], (float)(*p.substep_counter) * g.dt, cn[threadIdx.x]);
     for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) wr[i] = 0.0f;
     __syncthreads();
-    for (int group = cta; group * 4 < g.nblocks; group += p.ctas) {
-    const int b = group * 4 + grp;
-    bool has_old = false, has_new = false;
-    if (b < g.nblocks) {
-        has_old = p.flags_old[b] != 0u;
-        has_new = p.flags[b] != 0u;
-    }
-    if (!__syncthreads_or(has_old || has_new)) continue;
+    // items: the previous grid's active bins (to zero), then this grid's active bins (to update)
+    const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
+    for (uint32_t item = (uint32_t)(cta * 4 + grp); item < n_old + n_new; item += (uint32_t)(p.ctas * 4)) {
+    const bool has_old = item < n_old;
+    const uint32_t b = has_old ? p.list_old[item] : p.list[item - n_old];
     if (has_old) {
         p.grid_old[(size_t)b * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (ln == 0) p.flags_old[b] = 0u;
-    }
-    if (has_new) {
+    } else {
         float4* node = &p.grid[(size_t)b * kBlkNodes + ln];
         float4 gv = *node;
         if (gv.x > 0.0f) {
@@ -702,6 +720,15 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         float val = wr[i];
         if (val != 0.0f) atomicAdd(&p.wrench[i], (double)val);
     }
+    // the last CTA to finish empties the previous grid's bin list (every CTA has read its count)
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == (uint32_t)p.ctas - 1u;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        *p.list_count_old = 0u;
+        *p.done = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_grid_update(GridParams p) { grid_update_cta(p, blockIdx.x); }
@@ -711,7 +738,7 @@ __global__ void __launch_bounds__(256) k_grid_update(GridParams p) { grid_update
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
     wait_for_predecessor();  // (a CTA's exit releases the successor)
     if ((int)blockIdx.x < p.assign_ctas) {
-        assign_slot(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
+        assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
         return;
     }
     grid_update_cta(p.grid, blockIdx.x - p.assign_ctas);
@@ -787,7 +814,7 @@ cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t
 
 cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    k_assign<<<ceil_div(N, 256), 256, 0, s>>>(N, keyrank, cursor, perm);
+    k_assign<<<ceil_div(N, 256 * kAssignPerThread), 256, 0, s>>>(N, keyrank, cursor, perm);
     return cudaGetLastError();
 }
 
