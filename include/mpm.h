@@ -171,6 +171,24 @@ mpm_status mpm_set_graphs(mpm_sim* sim, int enable);
 /* Number of kernels the handle has launched since creation (host counter, no sync). */
 long long mpm_launch_count(const mpm_sim* sim);
 
+/* Particle-to-grid transfer without any device allocation. The paper has no counterpart: this entry
+ * serves callers that cannot call cudaMalloc -- a plugin inside a host simulator that owns all device
+ * memory, or a real-time loop where cudaMalloc's implicit device synchronization is not allowed.
+ * It computes what mpm_read_grid returns after mpm_set_particles (mass and momentum with the stress
+ * impulse, before the grid velocity update) for the particle set given, straight into grid_out.
+ *   x, v, C, F  device SoA arrays with stride n, as for mpm_set_particles (v, C NULL = zero; F NULL =
+ *               identity; a fluid uses J = det F); positions are clamped into [2dx, 1-2dx] when read
+ *   grid_out    device float[cfg->n]^3 [4] = (m, mv_x, mv_y, mv_z), 16-byte aligned; zeroed by the call
+ * Scratch (bin keys and ranks, bin offsets, chunk list, sorted order; about 0.9 MB) lives in a device
+ * array owned by the library, resident on every GPU that loads it until the process exits. Limits:
+ * n <= 65,536 particles and cfg->n <= 64, else MPM_ERR_CAPACITY (nothing enqueued). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, once per device, with that device
+ * current): make that first call before any stream capture. Every call on a device shares the array, so
+ * calls that overlap on the GPU (different streams, or different host threads) race; serialize them.
+ * Enqueued on `stream`, no host synchronization; allocates nothing. */
+mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* mat, int n, const float* x, const float* v,
+                          const float* C, const float* F, float* grid_out, void* stream);
+
 /* Release the host handle (the workspace stays the caller's). Safe on NULL. Does not synchronize:
  * the caller must not free the workspace before work enqueued on it has finished. */
 void mpm_destroy(mpm_sim* sim);

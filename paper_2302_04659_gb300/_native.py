@@ -79,6 +79,8 @@ def _load():
         "mpm_read_timing": (st, [_vp, _vp, _vp, ctypes.c_int]),
         "mpm_launch_count": (ctypes.c_longlong, [_vp]),
         "mpm_destroy": (None, [_vp]),
+        "mpm_p2g_static": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.c_int, _vp, _vp, _vp,
+                                _vp, _vp, _vp]),
         "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mpm_last_error": (ctypes.c_char_p, []),
     }
@@ -185,6 +187,13 @@ def mpm_launch_count(sim: int) -> int:
 
 def mpm_destroy(sim: int) -> None:
     _load().mpm_destroy(sim)
+
+
+def mpm_p2g_static(cfg: mpm_config, mat: mpm_material, n: int, x: int, v: int = 0, C: int = 0, F: int = 0,
+                   grid_out: int = 0, stream: int = 0) -> None:
+    """Particle-to-grid transfer into a caller grid with the library's own scratch (no allocation)."""
+    _check("mpm_p2g_static", _load().mpm_p2g_static(ctypes.byref(cfg), ctypes.byref(mat), n, x or None, v or None,
+                                                    C or None, F or None, grid_out or None, stream))
 
 
 def mpm_last_error() -> str:
