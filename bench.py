@@ -133,6 +133,19 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_throughput(local_units, local_seconds, device=None):
+    """Whole-job throughput over the ranks of an initialized process group (one rank: just local):
+    units summed over ranks divided by the slowest rank's time. Returns (value, max seconds, units)."""
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return u.item() / t.item(), t.item(), u.item()
+
+
 def pinch_inputs(seed, N=200_000):
     from paper_2302_04659_gb300 import scenes
     return scenes.pinch_scene(seed=seed, N=N)
@@ -220,13 +233,8 @@ def run_native(args):
     elapsed_instrumented = timed_pass(args.warmup + args.steps)
     ktime = sim.read_timing(reset=True)
     sim.set_timing(False)
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    value, elapsed, total_units = job_throughput(N * SUBSTEPS * args.steps, elapsed, dev)
     flags = sim.status()
-    total_units = N * SUBSTEPS * args.steps * world
-    value = total_units / elapsed
     g_ms, g_n = ktime["g2p2g"]
     g_avg = g_ms / max(g_n, 1) / 1e3
     # ---------------- end-to-end through the C-ABI with host buffers
@@ -245,10 +253,8 @@ def run_native(args):
         mpm.mpm_read_wrench(sim.handle, wr_h.data_ptr(), int(stream.cuda_stream))
     ev1.record(stream)
     barrier()
-    e2e_t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = N * SUBSTEPS * e2e_steps * world / float(e2e_t.item()) if e2e_steps else None
+    e2e_value = (job_throughput(N * SUBSTEPS * e2e_steps, ev0.elapsed_time(ev1) / 1e3, dev)[0]
+                 if e2e_steps else None)
     h2d = k * (7 + 3 + 3 + 3) * 4
     d2h = 3 * N * 4 + k * 6 * 8 + 4
     sim.close()
