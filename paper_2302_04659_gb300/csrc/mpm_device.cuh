@@ -49,126 +49,102 @@ __device__ __forceinline__ void bspline_weights(float fx, float w[3]) {
     w[2] = 0.5f * c * c;
 }
 
-// ------------------------------------------------------------------------ 3x3 SVD (FP32)
+// ------------------------------------------------------------------------ polar data of F (FP32)
 //
-// F = U diag(sig) V^T with det U = det V = +1, |sig| descending and sig[2] < 0 iff det F < 0.
-// V from cyclic Jacobi on the symmetric S = F^T F (exact Givens rotations, Golub & Van Loan
-// Sec. 8.5.2); then B = F V, columns sorted by length, and U by Gram-Schmidt on B's columns with the
-// third column u0 x u1, which fixes det U = +1 and puts the sign of det F on sig[2].
+// Everything the constitutive update needs from F = U diag(sig) V^T is U and sig: with the symmetric
+// B = F F^T = U diag(sig^2) U^T,
+//   (F - R) F^T = U diag((sig - 1) sig) U^T            (R = U V^T, the polar rotation)
+//   U diag(s') V^T = U diag(s' / sig) U^T F            (F with its singular values replaced)
+// so V is never formed. U and sig^2 come from cyclic Jacobi on B (exact Givens rotations, Golub & Van
+// Loan Sec. 8.5.2). sig_i = sqrt(eigenvalue_i) >= 0; when det F < 0 the smallest one takes the sign
+// (the rotation-only SVD convention: det U = det V = +1).
 
 template <int P, int Q, int R>
-__device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&V)[3][3]) {
-    float apq = S[P][Q];
+__device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&U)[3][3]) {
+    const float apq = S[P][Q];
     if (apq == 0.0f) return;
-    // tan of the rotation angle, the smaller root of t^2 + 2 tau t - 1 = 0; for |tau| >= 2^30 the
-    // asymptote t = 1 / (2 tau) avoids overflowing tau^2
-    float tau = __fdividef(S[Q][Q] - S[P][P], 2.0f * apq);
-    float at = fabsf(tau);
-    float t = at < 1073741824.0f ? __fdividef(copysignf(1.0f, tau), at + sqrtf(fmaf(tau, tau, 1.0f)))
-                                 : __fdividef(0.5f, tau);
-    float c = rsqrtf(fmaf(t, t, 1.0f));
-    float s = t * c;
-    S[P][P] -= t * apq;
-    S[Q][Q] += t * apq;
+    // The rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) zeroes the (p,q) entry of J^T S J when
+    // tan 2theta = 2 a_pq / (a_qq - a_pp). Take |theta| <= pi/4: cos 2theta = |x| / r,
+    // sin 2theta = sign(x) y / r with x = a_qq - a_pp, y = 2 a_pq, r = |(x, y)|; then the half angle
+    // c = sqrt((1 + cos 2theta) / 2), s = sin 2theta / (2 c). Two reciprocal square roots in all.
+    const float app = S[P][P], aqq = S[Q][Q];
+    const float x = aqq - app, y = 2.0f * apq;
+    const float h = rsqrtf(fmaf(x, x, y * y));
+    const float c2 = fabsf(x) * h;
+    const float s2 = copysignf(1.0f, x) * y * h;
+    const float half = fmaf(0.5f, c2, 0.5f);
+    const float rc = rsqrtf(half);
+    const float c = half * rc;
+    const float s = 0.5f * s2 * rc;
+    const float cc = c * c, ss = s * s, cs2 = 2.0f * c * s * apq;
+    S[P][P] = fmaf(cc, app, fmaf(ss, aqq, -cs2));
+    S[Q][Q] = fmaf(ss, app, fmaf(cc, aqq, cs2));
     S[P][Q] = S[Q][P] = 0.0f;
-    float arp = S[R][P], arq = S[R][Q];
+    const float arp = S[R][P], arq = S[R][Q];
     S[R][P] = S[P][R] = c * arp - s * arq;
     S[R][Q] = S[Q][R] = s * arp + c * arq;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        float vp = V[r][P], vq = V[r][Q];
-        V[r][P] = c * vp - s * vq;
-        V[r][Q] = s * vp + c * vq;
+        const float up = U[r][P], uq = U[r][Q];
+        U[r][P] = c * up - s * uq;
+        U[r][Q] = s * up + c * uq;
     }
 }
 
-__device__ __forceinline__ void swap_cols_keep_det(float (&B)[3][3], float (&V)[3][3], float (&len)[3], int a,
-                                                   int b) {
-    // swapping two columns flips det V; negating one of them restores it (B = F V follows V)
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        float tb = B[r][a]; B[r][a] = B[r][b]; B[r][b] = -tb;
-        float tv = V[r][a]; V[r][a] = V[r][b]; V[r][b] = -tv;
-    }
-    float tl = len[a]; len[a] = len[b]; len[b] = tl;
+__device__ __forceinline__ float det3(const float (&A)[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
 }
 
-__device__ __forceinline__ void svd3(const float (&F)[3][3], float (&U)[3][3], float (&sig)[3], float (&V)[3][3]) {
+// U (left singular vectors, columns) and the signed singular values of F.
+__device__ __forceinline__ void polar_data(const float (&F)[3][3], float (&U)[3][3], float (&sig)[3]) {
     float S[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            S[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+        for (int j = i; j < 3; ++j) {
+            const float b = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
+            S[i][j] = b;
+            S[j][i] = b;
+        }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0f : 0.0f;
+        for (int j = 0; j < 3; ++j) U[i][j] = (i == j) ? 1.0f : 0.0f;
     for (int sweep = 0; sweep < 6; ++sweep) {
-        float off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
-        float diag = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
-        if (off <= 1e-15f * diag) break;
-        jacobi_rotation<0, 1, 2>(S, V);
-        jacobi_rotation<0, 2, 1>(S, V);
-        jacobi_rotation<1, 2, 0>(S, V);
+        const float off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
+        const float diag = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
+        if (off <= 1e-13f * diag) break;
+        jacobi_rotation<0, 1, 2>(S, U);
+        jacobi_rotation<0, 2, 1>(S, U);
+        jacobi_rotation<1, 2, 0>(S, U);
     }
-    float B[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * V[0][j] + F[i][1] * V[1][j] + F[i][2] * V[2][j];
-    float len[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) len[j] = B[0][j] * B[0][j] + B[1][j] * B[1][j] + B[2][j] * B[2][j];
-    if (len[1] > len[0]) swap_cols_keep_det(B, V, len, 0, 1);
-    if (len[2] > len[0]) swap_cols_keep_det(B, V, len, 0, 2);
-    if (len[2] > len[1]) swap_cols_keep_det(B, V, len, 1, 2);
-    // Gram-Schmidt
-    float s0;
-    float u0[3], u1[3];
-    if (len[0] > 1e-36f) {
-        float r = rsqrtf(len[0]);
-        s0 = len[0] * r;
-        u0[0] = B[0][0] * r; u0[1] = B[1][0] * r; u0[2] = B[2][0] * r;
-    } else {
-        u0[0] = 1.0f; u0[1] = 0.0f; u0[2] = 0.0f;
-        s0 = 0.0f;
+    for (int i = 0; i < 3; ++i) sig[i] = sqrtf(fmaxf(S[i][i], 0.0f));
+    if (det3(F) < 0.0f) {
+        const int k = (sig[0] <= sig[1] && sig[0] <= sig[2]) ? 0 : (sig[1] <= sig[2] ? 1 : 2);
+        sig[k] = -sig[k];
     }
-    float d01 = u0[0] * B[0][1] + u0[1] * B[1][1] + u0[2] * B[2][1];
-    float w1[3] = {B[0][1] - d01 * u0[0], B[1][1] - d01 * u0[1], B[2][1] - d01 * u0[2]};
-    float l1 = w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2];
-    float s1 = 0.0f;
-    if (l1 > 1e-36f && l1 > 1e-14f * len[0]) {
-        float r = rsqrtf(l1);
-        s1 = l1 * r;
-        u1[0] = w1[0] * r; u1[1] = w1[1] * r; u1[2] = w1[2] * r;
-    } else {
-        // any unit vector orthogonal to u0
-        float e[3] = {fabsf(u0[0]) < 0.9f ? 1.0f : 0.0f, fabsf(u0[0]) < 0.9f ? 0.0f : 1.0f, 0.0f};
-        float c[3] = {u0[1] * e[2] - u0[2] * e[1], u0[2] * e[0] - u0[0] * e[2], u0[0] * e[1] - u0[1] * e[0]};
-        float r = rsqrtf(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-        u1[0] = c[0] * r; u1[1] = c[1] * r; u1[2] = c[2] * r;
-        s1 = u1[0] * B[0][1] + u1[1] * B[1][1] + u1[2] * B[2][1];
-    }
-    float u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
-    float s2 = u2[0] * B[0][2] + u2[1] * B[1][2] + u2[2] * B[2][2];
+}
+
+// U diag(d) U^T (symmetric)
+__device__ __forceinline__ void sym_from_eig(const float (&U)[3][3], const float (&d)[3], float (&M)[3][3]) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        U[r][0] = u0[r];
-        U[r][1] = u1[r];
-        U[r][2] = u2[r];
-    }
-    sig[0] = s0;
-    sig[1] = s1;
-    sig[2] = s2;
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = r; c < 3; ++c) {
+            const float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
+            M[r][c] = t;
+            M[c][r] = t;
+        }
 }
 
 // ------------------------------------------------------------------------ constitutive update
 //
 // Plasticine: fixed-corotated elasticity, tau = 2 mu (F - R) F^T + lambda J (J - 1) I, with a von Mises
 // return map in Hencky strain: eps = log sig, the deviatoric part of eps is pulled back onto the sphere
-// of radius tau_Y / (2 mu) when it lies outside, the trace is kept, F = U exp(eps) V^T.
-// With the SVD of the trial F at hand, the stress of the returned F is U diag(d) U^T with
+// of radius tau_Y / (2 mu) when it lies outside, the trace is kept, F = U exp(eps) V^T. With the polar
+// data of the trial F at hand, the stress of the returned F is U diag(d) U^T with
 // d_i = 2 mu (s_i - 1) s_i + lambda J (J - 1), s = returned singular values, J = s0 s1 s2.
 
 struct Material {
@@ -179,8 +155,8 @@ struct Material {
 // In: trial F (overwritten by the returned F). Out: Kirchhoff stress tau. Returns flag bits.
 __device__ __forceinline__ uint32_t plastic_update_and_stress(float (&F)[3][3], const Material& m,
                                                               float (&tau)[3][3]) {
-    float U[3][3], V[3][3], sig[3];
-    svd3(F, U, sig, V);
+    float U[3][3], sig[3];
+    polar_data(F, U, sig);
     uint32_t flags = 0;
     float eps[3];
     bool clamp = false;
@@ -190,66 +166,56 @@ __device__ __forceinline__ uint32_t plastic_update_and_stress(float (&F)[3][3], 
         if (s < 1e-6f) { s = 1e-6f; clamp = true; }
         eps[i] = __logf(s);
     }
-    float tr3 = (eps[0] + eps[1] + eps[2]) * (1.0f / 3.0f);
-    float dev[3] = {eps[0] - tr3, eps[1] - tr3, eps[2] - tr3};
-    float dn2 = dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2];
-    float rdn = rsqrtf(fmaxf(dn2, 1e-30f));
-    float dn = dn2 * rdn;
-    float dgamma = dn - m.yield_radius;
+    const float tr3 = (eps[0] + eps[1] + eps[2]) * (1.0f / 3.0f);
+    const float dev[3] = {eps[0] - tr3, eps[1] - tr3, eps[2] - tr3};
+    const float dn2 = dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2];
+    const float rdn = rsqrtf(fmaxf(dn2, 1e-30f));
+    const float dgamma = dn2 * rdn - m.yield_radius;
     float s[3] = {sig[0], sig[1], sig[2]};
     if (dgamma > 0.0f || clamp) {
         if (dgamma > 0.0f) {
-            float k = dgamma * rdn;
+            const float k = dgamma * rdn;
 #pragma unroll
             for (int i = 0; i < 3; ++i) eps[i] -= k * dev[i];
         }
+        // F <- U diag(s' / sig) U^T F
+        float r[3], M[3][3], Fn[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s[i] = __expf(eps[i]);
+        for (int i = 0; i < 3; ++i) {
+            s[i] = __expf(eps[i]);
+            const float g = fabsf(sig[i]) > 1e-30f ? sig[i] : 1e-30f;
+            r[i] = __fdividef(s[i], g);
+        }
+        sym_from_eig(U, r, M);
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                F[r][c] = U[r][0] * s[0] * V[c][0] + U[r][1] * s[1] * V[c][1] + U[r][2] * s[2] * V[c][2];
+            for (int c = 0; c < 3; ++c) Fn[a][c] = M[a][0] * F[0][c] + M[a][1] * F[1][c] + M[a][2] * F[2][c];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) F[a][c] = Fn[a][c];
         if (clamp) flags |= 0x4u;
     }
-    float J = s[0] * s[1] * s[2];
-    float vol = m.lambda * J * (J - 1.0f);
+    const float J = s[0] * s[1] * s[2];
+    const float vol = m.lambda * J * (J - 1.0f);
     float d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = 2.0f * m.mu * (s[i] - 1.0f) * s[i] + vol;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = r; c < 3; ++c) {
-            float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
-            tau[r][c] = t;
-            tau[c][r] = t;
-        }
+    sym_from_eig(U, d, tau);
     return flags;
 }
 
-// Stress of a given (already returned) F, used by the standalone particle-to-grid pass.
+// Stress of a given (already returned) F, used by the standalone particle-to-grid passes.
 __device__ __forceinline__ void fixed_corotated_stress(const float (&F)[3][3], const Material& m, float (&tau)[3][3]) {
-    float U[3][3], V[3][3], sig[3];
-    svd3(F, U, sig, V);
-    float J = sig[0] * sig[1] * sig[2];
-    float vol = m.lambda * J * (J - 1.0f);
+    float U[3][3], sig[3];
+    polar_data(F, U, sig);
+    const float J = sig[0] * sig[1] * sig[2];
+    const float vol = m.lambda * J * (J - 1.0f);
     float d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = 2.0f * m.mu * (sig[i] - 1.0f) * sig[i] + vol;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = r; c < 3; ++c) {
-            float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
-            tau[r][c] = t;
-            tau[c][r] = t;
-        }
-}
-
-__device__ __forceinline__ float det3(const float (&A)[3][3]) {
-    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    sym_from_eig(U, d, tau);
 }
 
 // ------------------------------------------------------------------------ colliders

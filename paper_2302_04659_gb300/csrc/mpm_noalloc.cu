@@ -10,7 +10,7 @@
 
 #include <mutex>
 
-#include "../../include/mpm.h"
+#include "mpm.h"
 #include "mpm_internal.h"
 
 using namespace mpm;
