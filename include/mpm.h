@@ -93,6 +93,38 @@ typedef struct {
 /* Bytes of device workspace a handle with this configuration needs. */
 mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes);
 
+/* ---- Batches of environments.
+ * One handle can hold many independent environments (envs), each with its own grid, material,
+ * particles and colliders; all advance together with the same launches (the vectorized simulation the
+ * paper leaves as future work, App. D.3). A single-scene handle (mpm_create) is a batch of one.
+ * Arrays that span envs are concatenations in env order: particle arrays are SoA over all particles
+ * (stride = total count), collider arrays list all envs' colliders. The shared mpm_config supplies dt,
+ * gravity and bound; its n, max_particles and max_colliders are taken per env from mpm_env. */
+typedef struct {
+    int n;              /* grid nodes per axis of this env: a multiple of 4 in [8, 256] */
+    int max_particles;  /* capacity of this env, >= 1 */
+    int max_colliders;  /* capacity of this env, >= 0 */
+    mpm_material material;
+} mpm_env;
+
+#define MPM_MAX_ENVS 16384
+
+mpm_status mpm_workspace_size_batch(const mpm_config* cfg, int nenv, const mpm_env* envs, size_t* bytes);
+mpm_status mpm_create_batch(const mpm_config* cfg, int nenv, const mpm_env* envs, void* d_workspace, size_t bytes,
+                            void* stream, mpm_sim** out);
+/* counts[nenv] particles per env; arrays SoA over all sum(counts) particles, as mpm_set_particles. */
+mpm_status mpm_set_particles_batch(mpm_sim* sim, const int* counts, const float* x, const float* v, const float* C,
+                                   const float* F, int src_on_device, void* stream);
+/* counts[nenv] shapes per env, shapes concatenated in env order. */
+mpm_status mpm_set_shapes_batch(mpm_sim* sim, const int* counts, const mpm_shape* shapes);
+int mpm_num_envs(const mpm_sim* sim);
+
+/* Launch shape of the substep kernels (the autotuner's knobs): most particles per chunk of a bin
+ * (chunk, 32..128, multiple of 32), resident CTAs per SM of the fused particle pass (1..7) and of the grid
+ * update (1..8). 0 keeps a value. Takes effect at the next mpm_substep. */
+mpm_status mpm_set_launch(mpm_sim* sim, int chunk, int fused_ctas_per_sm, int grid_ctas_per_sm);
+mpm_status mpm_get_launch(const mpm_sim* sim, int* chunk, int* fused_ctas_per_sm, int* grid_ctas_per_sm);
+
 /* Create a handle over a caller-owned device workspace; zeroes what must start at zero on `stream`.
  * cfg / mat are copied. On error *out is NULL. */
 mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_workspace, size_t bytes,
@@ -116,9 +148,10 @@ mpm_status mpm_set_shapes(mpm_sim* sim, int k, const mpm_shape* shapes);
  *   lin_vel k x 3: velocity of the centre of mass;  ang_vel k x 3: angular velocity (world frame)
  *   com     k x 3: centre of mass (world frame); NULL = frame origin
  * ang_vel may be NULL (zero). Between two calls each body moves rigidly with these constant
- * velocities, evaluated in closed form at the start of every substep. The data travel with the
- * launch of one small kernel (no host buffer outlives the call); the wrench accumulators and the
- * substep count are zeroed. */
+ * velocities, evaluated in closed form at the start of every substep (tabulated on the device for the
+ * first 64 substeps). The arrays are copied into a library-owned pinned staging buffer and uploaded
+ * on `stream`: they may be reused when the call returns. The wrench accumulators and the substep
+ * count are zeroed. For a batch, k is the total over envs and the arrays are concatenated in env order. */
 mpm_status mpm_set_colliders(mpm_sim* sim, int k, const float* pose, const float* lin_vel,
                              const float* ang_vel, const float* com, void* stream);
 
@@ -146,7 +179,8 @@ int mpm_num_particles(const mpm_sim* sim);
 
 /* Diagnostics: the grid holding the particle-to-grid transfer of the current state (mass and momentum,
  * before the grid velocity update), densely as float[n][n][n][4] = (m, mv_x, mv_y, mv_z) with node
- * (i,j,k) at ((i*n + j)*n + k)*4. Device destination only; enqueued on `stream`. */
+ * (i,j,k) at ((i*n + j)*n + k)*4. Device destination only; enqueued on `stream`. For a batch, the envs'
+ * grids follow one another in env order (env e's n_e^3 * 4 floats). */
 mpm_status mpm_read_grid(mpm_sim* sim, float* d_out, void* stream);
 
 /* Diagnostics: kernel timing. Every launch of a kernel kind whose bit (1 << MPM_K_*) is set in

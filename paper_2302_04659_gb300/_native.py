@@ -14,6 +14,7 @@ import os
 from . import build as _build
 
 MPM_MAX_COLLIDERS = 32
+MPM_MAX_ENVS = 16384
 MPM_OK, MPM_ERR_INVALID_ARG, MPM_ERR_CUDA, MPM_ERR_WORKSPACE, MPM_ERR_CAPACITY = range(5)
 MPM_FLAG_CLAMPED = 0x1
 MPM_FLAG_NONFINITE = 0x2
@@ -43,6 +44,11 @@ class mpm_shape(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("half", ctypes.c_float * 3), ("friction", ctypes.c_float)]
 
 
+class mpm_env(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("max_particles", ctypes.c_int), ("max_colliders", ctypes.c_int),
+                ("material", mpm_material)]
+
+
 class MpmError(RuntimeError):
     def __init__(self, fn, status, detail=""):
         self.status = status
@@ -65,6 +71,16 @@ def _load():
         "mpm_workspace_size": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.POINTER(ctypes.c_size_t)]),
         "mpm_create": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), _vp, ctypes.c_size_t, _vp,
                             ctypes.POINTER(_vp)]),
+        "mpm_workspace_size_batch": (st, [ctypes.POINTER(mpm_config), ctypes.c_int, ctypes.POINTER(mpm_env),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+        "mpm_create_batch": (st, [ctypes.POINTER(mpm_config), ctypes.c_int, ctypes.POINTER(mpm_env), _vp,
+                                  ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+        "mpm_set_particles_batch": (st, [_vp, ctypes.POINTER(ctypes.c_int), _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+        "mpm_set_shapes_batch": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(mpm_shape)]),
+        "mpm_num_envs": (ctypes.c_int, [_vp]),
+        "mpm_set_launch": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "mpm_get_launch": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]),
         "mpm_set_particles": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "mpm_set_shapes": (st, [_vp, ctypes.c_int, ctypes.POINTER(mpm_shape)]),
         "mpm_set_colliders": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
@@ -117,6 +133,51 @@ def mpm_create(cfg: mpm_config, mat: mpm_material, d_workspace: int, nbytes: int
     _check("mpm_create", _load().mpm_create(ctypes.byref(cfg), ctypes.byref(mat), d_workspace, nbytes, stream,
                                             ctypes.byref(h)))
     return h.value
+
+
+def _env_array(envs):
+    return (mpm_env * max(1, len(envs)))(*envs)
+
+
+def mpm_workspace_size_batch(cfg: mpm_config, envs) -> int:
+    out = ctypes.c_size_t(0)
+    _check("mpm_workspace_size_batch", _load().mpm_workspace_size_batch(ctypes.byref(cfg), len(envs),
+                                                                        _env_array(envs), ctypes.byref(out)))
+    return out.value
+
+
+def mpm_create_batch(cfg: mpm_config, envs, d_workspace: int, nbytes: int, stream: int = 0) -> int:
+    h = _vp()
+    _check("mpm_create_batch", _load().mpm_create_batch(ctypes.byref(cfg), len(envs), _env_array(envs), d_workspace,
+                                                        nbytes, stream, ctypes.byref(h)))
+    return h.value
+
+
+def mpm_set_particles_batch(sim: int, counts, x: int, v: int = 0, C: int = 0, F: int = 0, src_on_device: int = 1,
+                            stream: int = 0) -> None:
+    c = (ctypes.c_int * max(1, len(counts)))(*counts)
+    _check("mpm_set_particles_batch", _load().mpm_set_particles_batch(sim, c, x or None, v or None, C or None,
+                                                                      F or None, src_on_device, stream))
+
+
+def mpm_set_shapes_batch(sim: int, counts, shapes) -> None:
+    c = (ctypes.c_int * max(1, len(counts)))(*counts)
+    arr = (mpm_shape * max(1, len(shapes)))(*shapes)
+    _check("mpm_set_shapes_batch", _load().mpm_set_shapes_batch(sim, c, arr))
+
+
+def mpm_num_envs(sim: int) -> int:
+    return _load().mpm_num_envs(sim)
+
+
+def mpm_set_launch(sim: int, chunk: int = 0, fused_ctas_per_sm: int = 0, grid_ctas_per_sm: int = 0) -> None:
+    _check("mpm_set_launch", _load().mpm_set_launch(sim, chunk, fused_ctas_per_sm, grid_ctas_per_sm))
+
+
+def mpm_get_launch(sim: int):
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check("mpm_get_launch", _load().mpm_get_launch(sim, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def mpm_set_particles(sim: int, n: int, x: int, v: int = 0, C: int = 0, F: int = 0, src_on_device: int = 1,

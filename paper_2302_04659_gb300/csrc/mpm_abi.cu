@@ -1,11 +1,12 @@
-// mpm_abi.cu -- the C-ABI of include/mpm.h: argument checks, workspace layout, the per-substep launch
-// sequence (optionally replayed from a CUDA graph) and the readbacks. All device memory comes from the
-// caller's workspace.
+// mpm_abi.cu -- the C-ABI of include/mpm.h: argument checks, workspace layout, the environment table,
+// the per-substep launch sequence (optionally replayed from a CUDA graph) and the readbacks. All device
+// memory comes from the caller's workspace; the library owns only the host handle and a small pinned
+// staging buffer for collider uploads.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -30,10 +31,10 @@ mpm_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-#define MPM_TRY(call)                   \
-    do {                                \
-        mpm_status r_ = (call);         \
-        if (r_ != MPM_OK) return r_;    \
+#define MPM_TRY(call)                \
+    do {                             \
+        mpm_status r_ = (call);      \
+        if (r_ != MPM_OK) return r_; \
     } while (0)
 
 constexpr size_t kAlign = 256;
@@ -41,13 +42,28 @@ constexpr int kMaxGraphs = 8;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-struct Layout {
-    size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, colliders, wrench,
-        counters, total;
-    size_t max_chunks;
+struct Totals {
+    size_t particles = 0, nodes = 0, bins = 0, colliders = 0;
 };
 
-Layout make_layout(const mpm_config& c) {
+Totals totals_of(int nenv, const mpm_env* envs) {
+    Totals t;
+    for (int e = 0; e < nenv; ++e) {
+        const size_t nb = (size_t)envs[e].n / 4;
+        t.particles += (size_t)envs[e].max_particles;
+        t.bins += nb * nb * nb;
+        t.nodes += nb * nb * nb * kBlkNodes;
+        t.colliders += (size_t)envs[e].max_colliders;
+    }
+    return t;
+}
+
+struct Layout {
+    size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, tile_sums, envs,
+        bin_env, colliders, upload, poses, wrench, counters, total;
+};
+
+Layout make_layout(const Totals& T, int nenv) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -55,38 +71,32 @@ Layout make_layout(const mpm_config& c) {
         off += align_up(bytes);
         return o;
     };
-    const size_t Nmax = (size_t)c.max_particles;
-    const size_t nb = (size_t)c.n / 4;
-    const size_t nblocks = nb * nb * nb;
-    const size_t nodes = nblocks * kBlkNodes;
-    for (int i = 0; i < 2; ++i) L.state[i] = take(Nmax * 25 * 4);
-    L.key = take(Nmax * 8);  // (bin, rank within bin) per particle
-    L.perm = take(Nmax * 4);
-    for (int i = 0; i < 2; ++i) L.grid[i] = take(nodes * sizeof(float4));
-    for (int i = 0; i < 2; ++i) L.flags[i] = take(nblocks * 4);
-    L.hist = take(nblocks * 4);
-    for (int i = 0; i < 2; ++i) L.list[i] = take(nblocks * 4);
+    const size_t cap = std::max<size_t>(T.particles, 1), kcap = std::max<size_t>(T.colliders, 1);
+    for (int i = 0; i < 2; ++i) L.state[i] = take(cap * 25 * 4);
+    L.key = take(cap * 8);  // (bin, rank within bin) per particle
+    L.perm = take(cap * 4);
+    for (int i = 0; i < 2; ++i) L.grid[i] = take(T.nodes * sizeof(float4));
+    for (int i = 0; i < 2; ++i) L.flags[i] = take(T.bins * 4);
+    L.hist = take(T.bins * 4 + 16);
+    for (int i = 0; i < 2; ++i) L.list[i] = take(T.bins * 4);
     L.list_meta = take(4 * sizeof(uint32_t));  // list counts [2], grid-update CTAs done, spare
     // everything from grid[0] up to here restarts from zero on mpm_set_particles
-    L.cursor = take(nblocks * 4);
-    L.max_chunks = Nmax / kChunk + nblocks + 1;
-    L.chunks = take(L.max_chunks * sizeof(int4));
-    L.colliders = take(kMaxColliders * sizeof(ColliderSet));
-    L.wrench = take(kMaxColliders * 6 * sizeof(double));
-    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, CTAs done
+    L.cursor = take(T.bins * 4 + 16);
+    L.chunks = take((cap / 32 + T.bins + 1) * sizeof(int4));
+    L.tile_sums = take(((T.bins + kScanTile - 1) / kScanTile + 1) * sizeof(uint2));
+    L.envs = take((size_t)nenv * sizeof(EnvDesc));
+    L.bin_env = take(T.bins * 4);
+    L.colliders = take(kcap * sizeof(ColliderSet));
+    L.upload = take(kcap * sizeof(ColliderSet));
+    L.poses = take((size_t)kPoseSteps * kcap * sizeof(ColliderNow));
+    L.wrench = take(kcap * 6 * sizeof(double));
+    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
     L.total = off;
     return L;
 }
 
-mpm_status check_config(const mpm_config* c, const mpm_material* m) {
-    if (!c || !m) return MPM_ERR_INVALID_ARG;
-    if (c->n < 8 || c->n > 256 || (c->n % 4) != 0) return MPM_ERR_INVALID_ARG;
-    if (!(c->dt > 0.0f) || !std::isfinite(c->dt)) return MPM_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!std::isfinite(c->gravity[a])) return MPM_ERR_INVALID_ARG;
-    if (c->bound < 0 || 2 * c->bound > c->n) return MPM_ERR_INVALID_ARG;
-    if (c->max_particles < 1 || c->max_particles > (1 << 30)) return MPM_ERR_INVALID_ARG;
-    if (c->max_colliders < 0 || c->max_colliders > MPM_MAX_COLLIDERS) return MPM_ERR_INVALID_ARG;
+mpm_status check_material(const mpm_material* m) {
+    if (!m) return MPM_ERR_INVALID_ARG;
     if (m->kind != MPM_PLASTICINE && m->kind != MPM_FLUID) return MPM_ERR_INVALID_ARG;
     if (!(m->rho > 0.0f) || !(m->p_vol > 0.0f)) return MPM_ERR_INVALID_ARG;
     if (m->kind == MPM_PLASTICINE) {
@@ -96,6 +106,34 @@ mpm_status check_config(const mpm_config* c, const mpm_material* m) {
         if (!(m->bulk_modulus >= 0.0f)) return MPM_ERR_INVALID_ARG;
     }
     return MPM_OK;
+}
+
+mpm_status check_batch(const mpm_config* c, int nenv, const mpm_env* envs) {
+    if (!c || !envs || nenv < 1 || nenv > MPM_MAX_ENVS) return MPM_ERR_INVALID_ARG;
+    if (!(c->dt > 0.0f) || !std::isfinite(c->dt)) return MPM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(c->gravity[a])) return MPM_ERR_INVALID_ARG;
+    if (c->bound < 0) return MPM_ERR_INVALID_ARG;
+    size_t particles = 0;
+    for (int e = 0; e < nenv; ++e) {
+        const mpm_env& v = envs[e];
+        if (v.n < 8 || v.n > 256 || (v.n % 4) != 0) return MPM_ERR_INVALID_ARG;
+        if (2 * c->bound > v.n) return MPM_ERR_INVALID_ARG;
+        if (v.max_particles < 1 || v.max_colliders < 0 || v.max_colliders > MPM_MAX_COLLIDERS) return MPM_ERR_INVALID_ARG;
+        MPM_TRY(check_material(&v.material));
+        particles += (size_t)v.max_particles;
+    }
+    if (particles > (size_t)(1 << 30)) return MPM_ERR_INVALID_ARG;
+    return MPM_OK;
+}
+
+mpm_env env_from_single(const mpm_config* cfg, const mpm_material* mat) {
+    mpm_env e{};
+    e.n = cfg->n;
+    e.max_particles = cfg->max_particles;
+    e.max_colliders = cfg->max_colliders;
+    e.material = *mat;
+    return e;
 }
 
 // Host-side pipeline state that the enqueued work depends on (and that a cached graph assumes).
@@ -131,18 +169,21 @@ struct GraphEntry {
 
 struct mpm_sim {
     mpm_config cfg;
-    mpm_material mat;
+    int nenv = 0;
+    std::vector<mpm_env> env_cfg;
+    std::vector<EnvDesc> envs;  // host copy of the device table
+    Totals T;
     Layout L;
-    char* ws;
-    Geometry geo;
-    Material dmat;
-    int N = 0;
+    char* ws = nullptr;
+    int N = 0;  // particles of all envs
     PipeState ps;
-    int nshapes = 0;
-    mpm_shape shapes[MPM_MAX_COLLIDERS];
+    std::vector<mpm_shape> shapes;
+    std::vector<int> shape_counts;  // shapes per env
     int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
+    ColliderSet* stage = nullptr;  // pinned staging for collider uploads
+    cudaEvent_t stage_done = nullptr;
     int sms = 0;
-    int ctas_fused = 0, ctas_p2g = 0, ctas_grid = 0;
+    int chunk = kChunk, fused_cps = 1, grid_cps = 2, p2g_cps = 1, max_fused_cps = 1;
     long long launches = 0;
     unsigned timing_mask = 0;
     struct Ev {
@@ -172,6 +213,8 @@ struct mpm_sim {
     uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
     uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
+    const EnvDesc* envs_dev() { return at<EnvDesc>(L.envs); }
+    bool tail_scan() const { return T.bins <= (size_t)kTailScanMaxBins; }
     StateView view(int which) {
         float* b = at<float>(L.state[which]);
         const size_t n = (size_t)N;
@@ -180,7 +223,7 @@ struct mpm_sim {
         s.v = b + 3 * n;
         s.C = b + 6 * n;
         s.F = b + 15 * n;
-        s.pid = reinterpret_cast<uint32_t*>(b + 24 * (size_t)cfg.max_particles);
+        s.pid = reinterpret_cast<uint32_t*>(b + 24 * std::max<size_t>(T.particles, 1));
         return s;
     }
     cudaEvent_t get_event() {
@@ -233,10 +276,16 @@ mpm_status launch(mpm_sim* s, int kind, cudaStream_t st, F&& fn, const char* wha
     return MPM_OK;
 }
 
+mpm_status upload_envs(mpm_sim* s, cudaStream_t st) {
+    MPM_CUDA(cudaMemcpyAsync(s->at<EnvDesc>(s->L.envs), s->envs.data(), sizeof(EnvDesc) * s->nenv,
+                             cudaMemcpyHostToDevice, st),
+             "copy env table");
+    return MPM_OK;
+}
+
 TransferParams transfer_params(mpm_sim* s) {
     TransferParams p{};
-    p.geo = s->geo;
-    p.mat = s->dmat;
+    p.envs = s->envs_dev();
     p.N = s->N;
     p.in = s->view(s->ps.cur);
     p.out = s->view(1 - s->ps.cur);
@@ -247,6 +296,10 @@ TransferParams transfer_params(mpm_sim* s) {
     p.num_chunks = s->num_chunks();
     p.status = s->status();
     p.substep_counter = s->substep_counter();
+    p.tail_scan = s->tail_scan() ? 1 : 0;
+    p.total_bins = (int)s->T.bins;
+    p.chunk = s->chunk;
+    p.bin_env = s->at<uint32_t>(s->L.bin_env);
     p.cursor = s->at<uint32_t>(s->L.cursor);
     p.chunks_next = s->at<int4>(s->L.chunks);
     p.num_chunks_next = s->num_chunks();
@@ -256,31 +309,54 @@ TransferParams transfer_params(mpm_sim* s) {
 
 GridParams grid_params(mpm_sim* s) {
     GridParams gp{};
-    gp.geo = s->geo;
+    gp.envs = s->envs_dev();
     for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
     gp.bound = s->cfg.bound;
     gp.grid = s->at<float4>(s->L.grid[s->ps.g]);
     gp.list = s->list(s->ps.g);
     gp.list_count = s->list_count(s->ps.g);
+    gp.grid_old = s->at<float4>(s->L.grid[1 - s->ps.g]);
+    gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
     gp.list_old = s->list(1 - s->ps.g);
     gp.list_count_old = s->list_count(1 - s->ps.g);
     gp.done = s->grid_done();
-    gp.grid_old = s->at<float4>(s->L.grid[1 - s->ps.g]);
-    gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
     gp.cols = s->at<ColliderSet>(s->L.colliders);
-    gp.ncol = s->ncol;
+    gp.poses = s->at<ColliderNow>(s->L.poses);
+    gp.k_total = std::max(s->ncol, 1);  // row stride of the pose table written by mpm_set_colliders
     gp.substep_counter = s->substep_counter();
-    gp.ctas = s->ctas_grid;
     gp.wrench = s->at<double>(s->L.wrench);
+    gp.ctas = (int)std::max<size_t>(1, std::min<size_t>((size_t)s->sms * s->grid_cps, (s->T.bins + 3) / 4));
     return gp;
+}
+
+ScanParams scan_params(mpm_sim* s) {
+    ScanParams sp{};
+    sp.hist = s->at<uint32_t>(s->L.hist);
+    sp.cursor = s->at<uint32_t>(s->L.cursor);
+    sp.chunks = s->at<int4>(s->L.chunks);
+    sp.num_chunks = s->num_chunks();
+    sp.tile_sums = s->at<uint2>(s->L.tile_sums);
+    sp.bin_env = s->at<uint32_t>(s->L.bin_env);
+    sp.total_bins = (int)s->T.bins;
+    sp.chunk = s->chunk;
+    return sp;
+}
+
+mpm_status enqueue_scan(mpm_sim* s, cudaStream_t st) {
+    if (s->tail_scan()) {
+        return launch(s, MPM_K_SCAN, st, [&] {
+            return launch_scan_binned(s->at<uint32_t>(s->L.hist), s->at<uint32_t>(s->L.cursor),
+                                      s->at<int4>(s->L.chunks), s->num_chunks(), s->at<uint32_t>(s->L.bin_env),
+                                      (int)s->T.bins, s->chunk, st);
+        }, "scan");
+    }
+    ScanParams sp = scan_params(s);
+    return launch(s, MPM_K_SCAN, st, [&] { return launch_scan_grid(sp, st); }, "scan_grid");
 }
 
 mpm_status ensure_scanned(mpm_sim* s, cudaStream_t st) {
     if (s->ps.scanned) return MPM_OK;
-    MPM_TRY(launch(s, MPM_K_SCAN, st, [&] {
-        return launch_scan(s->at<uint32_t>(s->L.hist), s->at<uint32_t>(s->L.cursor), s->at<int4>(s->L.chunks),
-                           s->num_chunks(), s->geo.nblocks, kChunk, st);
-    }, "scan"));
+    MPM_TRY(enqueue_scan(s, st));
     s->ps.scanned = true;
     return MPM_OK;
 }
@@ -305,13 +381,14 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
     p.flags_out = s->at<uint32_t>(s->L.flags[s->ps.g]);
     p.list_out = s->list(s->ps.g);
     p.list_count_out = s->list_count(s->ps.g);
-    MPM_TRY(launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->mat.kind, s->ctas_p2g, kChunk, st); }, "p2g"));
+    MPM_TRY(launch(s, MPM_K_P2G, st, [&] { return launch_p2g(p, s->sms * s->p2g_cps, st); }, "p2g"));
     s->ps.grid_valid = true;
     return MPM_OK;
 }
 
 // The launches of n substeps: per substep one sort-assign + grid-update launch and one fused
-// G2P->P2G launch (whose last CTA sorts the new positions into bins).
+// G2P->P2G launch (whose last CTA sorts the new positions into bins; with many bins two scan launches
+// follow instead).
 mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
     for (int it = 0; it < n; ++it) {
         MPM_TRY(ensure_scanned(s, st));
@@ -331,13 +408,13 @@ mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
         p.flags_out = ap.grid.flags_old;
         p.list_out = s->list(1 - s->ps.g);
         p.list_count_out = s->list_count(1 - s->ps.g);
-        MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->mat.kind, s->ctas_fused, kChunk, st); },
-                       "g2p2g"));
+        MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->sms * s->fused_cps, st); }, "g2p2g"));
         s->ps.cur = 1 - s->ps.cur;
         s->ps.g = 1 - s->ps.g;
-        s->ps.scanned = true;       // the fused pass's last CTA wrote the new bins
         s->ps.order_valid = false;  // assigned by the next launch
         s->ps.grid_valid = true;
+        s->ps.scanned = s->tail_scan();  // the fused pass's last CTA wrote the new bins
+        if (!s->ps.scanned) MPM_TRY(ensure_scanned(s, st));
     }
     return MPM_OK;
 }
@@ -408,6 +485,83 @@ GraphEntry* find_graph(mpm_sim* s, int n) {
     return nullptr;
 }
 
+mpm_status create_impl(const mpm_config* cfg, int nenv, const mpm_env* envs, void* d_workspace, size_t bytes,
+                       void* stream, mpm_sim** out) {
+    if (!out) return MPM_ERR_INVALID_ARG;
+    *out = nullptr;
+    MPM_TRY(check_batch(cfg, nenv, envs));
+    const Totals T = totals_of(nenv, envs);
+    const Layout L = make_layout(T, nenv);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) != 0 || bytes < L.total)
+        return MPM_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mpm_sim* s = new (std::nothrow) mpm_sim();
+    if (!s) return MPM_ERR_INVALID_ARG;
+    s->cfg = *cfg;
+    s->nenv = nenv;
+    s->env_cfg.assign(envs, envs + nenv);
+    s->T = T;
+    s->L = L;
+    s->ws = static_cast<char*>(d_workspace);
+    s->envs.resize(nenv);
+    std::vector<uint32_t> bin_env(T.bins);
+    uint32_t bin_base = 0, node_base = 0;
+    for (int e = 0; e < nenv; ++e) {
+        const mpm_env& v = envs[e];
+        EnvDesc& d = s->envs[e];
+        d = EnvDesc{};
+        Geometry& g = d.geo;
+        g.n = v.n;
+        g.nb = v.n / 4;
+        g.nblocks = g.nb * g.nb * g.nb;
+        g.dx = (float)(1.0 / v.n);
+        g.inv_dx = (float)v.n;
+        g.dt = cfg->dt;
+        g.lo = (float)(2.0 / v.n);
+        g.hi = (float)(1.0 - 2.0 / v.n);
+        const mpm_material& m = v.material;
+        double mu = 0.0, lambda = m.bulk_modulus;
+        if (m.kind == MPM_PLASTICINE) {
+            mu = (double)m.E / (2.0 * (1.0 + m.nu));
+            lambda = (double)m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+        }
+        d.mat.mu = (float)mu;
+        d.mat.lambda = (float)lambda;
+        d.mat.yield_radius = mu > 0.0 ? (float)(m.yield_stress / (2.0 * mu)) : 0.0f;
+        d.mat.p_mass = (float)((double)m.rho * m.p_vol);
+        d.mat.stress_scale = (float)(-(double)cfg->dt * m.p_vol * 4.0 * v.n * v.n);
+        d.kind = m.kind;
+        d.bin_base = bin_base;
+        d.node_base = node_base;
+        for (int b = 0; b < g.nblocks; ++b) bin_env[bin_base + b] = (uint32_t)e;
+        bin_base += (uint32_t)g.nblocks;
+        node_base += (uint32_t)g.nblocks * kBlkNodes;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->stage),
+                                            std::max<size_t>(T.colliders, 1) * sizeof(ColliderSet), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + L.grid[0], 0, L.total - L.grid[0], st);
+    if (e == cudaSuccess && T.bins)
+        e = cudaMemcpyAsync(s->at<uint32_t>(L.bin_env), bin_env.data(), T.bins * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->at<EnvDesc>(L.envs), s->envs.data(), sizeof(EnvDesc) * nenv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables above are temporaries
+    if (e != cudaSuccess) {
+        mpm_status r = cuda_fail(e, "create");
+        mpm_destroy(s);
+        return r;
+    }
+    s->max_fused_cps = transfer_ctas_per_sm(true);
+    s->fused_cps = s->max_fused_cps;
+    s->p2g_cps = transfer_ctas_per_sm(false);
+    s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;  // no particles yet
+    *out = s;
+    return MPM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -425,70 +579,30 @@ const char* mpm_status_string(mpm_status s) {
 
 const char* mpm_last_error(void) { return g_last_error; }
 
-mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes) {
+mpm_status mpm_workspace_size_batch(const mpm_config* cfg, int nenv, const mpm_env* envs, size_t* bytes) {
     if (!bytes) return MPM_ERR_INVALID_ARG;
-    MPM_TRY(check_config(cfg, mat));
-    *bytes = make_layout(*cfg).total;
+    MPM_TRY(check_batch(cfg, nenv, envs));
+    *bytes = make_layout(totals_of(nenv, envs), nenv).total;
     return MPM_OK;
+}
+
+mpm_status mpm_workspace_size(const mpm_config* cfg, const mpm_material* mat, size_t* bytes) {
+    if (!cfg || !mat) return MPM_ERR_INVALID_ARG;
+    const mpm_env e = env_from_single(cfg, mat);
+    return mpm_workspace_size_batch(cfg, 1, &e, bytes);
+}
+
+mpm_status mpm_create_batch(const mpm_config* cfg, int nenv, const mpm_env* envs, void* d_workspace, size_t bytes,
+                            void* stream, mpm_sim** out) {
+    return create_impl(cfg, nenv, envs, d_workspace, bytes, stream, out);
 }
 
 mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_workspace, size_t bytes, void* stream,
                       mpm_sim** out) {
-    if (!out) return MPM_ERR_INVALID_ARG;
-    *out = nullptr;
-    MPM_TRY(check_config(cfg, mat));
-    Layout L = make_layout(*cfg);
-    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) != 0 || bytes < L.total)
-        return MPM_ERR_WORKSPACE;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    mpm_sim* s = new (std::nothrow) mpm_sim();
-    if (!s) return MPM_ERR_INVALID_ARG;
-    s->cfg = *cfg;
-    s->mat = *mat;
-    s->L = L;
-    s->ws = static_cast<char*>(d_workspace);
-    Geometry& g = s->geo;
-    g.n = cfg->n;
-    g.nb = cfg->n / 4;
-    g.nblocks = g.nb * g.nb * g.nb;
-    g.dx = (float)(1.0 / cfg->n);
-    g.inv_dx = (float)cfg->n;
-    g.dt = cfg->dt;
-    g.lo = (float)(2.0 / cfg->n);
-    g.hi = (float)(1.0 - 2.0 / cfg->n);
-    double mu, lambda;
-    if (mat->kind == MPM_PLASTICINE) {
-        mu = (double)mat->E / (2.0 * (1.0 + mat->nu));
-        lambda = (double)mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
-    } else {
-        mu = 0.0;
-        lambda = mat->bulk_modulus;
-    }
-    s->dmat.mu = (float)mu;
-    s->dmat.lambda = (float)lambda;
-    s->dmat.yield_radius = mu > 0.0 ? (float)(mat->yield_stress / (2.0 * mu)) : 0.0f;
-    s->dmat.p_mass = (float)((double)mat->rho * mat->p_vol);
-    s->dmat.stress_scale = (float)(-(double)cfg->dt * mat->p_vol * 4.0 * cfg->n * cfg->n);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-        delete s;
-        return cuda_fail(e, "device query");
-    }
-    s->ctas_fused = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, true);
-    s->ctas_p2g = s->sms * transfer_ctas_per_sm(mat->kind, kChunk, false);
-    // persistent grid update: two CTAs per SM, or one per group of four bins if that is fewer
-    s->ctas_grid = std::min(2 * s->sms, (g.nblocks + 3) / 4);
-    // zero the grids, bin flags and counts, colliders and counters
-    const size_t zero_from = L.grid[0];
-    e = cudaMemsetAsync(s->ws + zero_from, 0, L.total - zero_from, st);
-    if (e != cudaSuccess) {
-        delete s;
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    *out = s;
-    return MPM_OK;
+    if (out) *out = nullptr;
+    if (!cfg || !mat) return MPM_ERR_INVALID_ARG;
+    const mpm_env e = env_from_single(cfg, mat);
+    return create_impl(cfg, 1, &e, d_workspace, bytes, stream, out);
 }
 
 void mpm_destroy(mpm_sim* s) {
@@ -500,28 +614,48 @@ void mpm_destroy(mpm_sim* s) {
     }
     for (auto e : s->pool) cudaEventDestroy(e);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->stage_done) {
+        cudaEventSynchronize(s->stage_done);
+        cudaEventDestroy(s->stage_done);
+    }
+    if (s->stage) cudaFreeHost(s->stage);
     delete s;
 }
 
 int mpm_num_particles(const mpm_sim* s) { return s ? s->N : 0; }
 
+int mpm_num_envs(const mpm_sim* s) { return s ? s->nenv : 0; }
+
 long long mpm_launch_count(const mpm_sim* s) { return s ? s->launches : 0; }
 
-mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, const float* C, const float* F,
-                             int src_on_device, void* stream) {
-    if (!s || n < 0 || (n > 0 && !x)) return MPM_ERR_INVALID_ARG;
-    if (n > s->cfg.max_particles) return MPM_ERR_CAPACITY;
+mpm_status mpm_set_particles_batch(mpm_sim* s, const int* counts, const float* x, const float* v, const float* C,
+                                   const float* F, int src_on_device, void* stream) {
+    if (!s || !counts) return MPM_ERR_INVALID_ARG;
+    size_t total = 0;
+    for (int e = 0; e < s->nenv; ++e) {
+        if (counts[e] < 0) return MPM_ERR_INVALID_ARG;
+        if (counts[e] > s->env_cfg[e].max_particles) return MPM_ERR_CAPACITY;
+        total += (size_t)counts[e];
+    }
+    if (total > 0 && !x) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // grids, bin flags and histogram restart from zero
+    uint32_t first = 0;
+    for (int e = 0; e < s->nenv; ++e) {
+        s->envs[e].part_first = first;
+        s->envs[e].part_count = (uint32_t)counts[e];
+        first += (uint32_t)counts[e];
+    }
+    MPM_TRY(upload_envs(s, st));
+    // grids, bin flags, lists and histogram restart from zero
     const size_t z0 = s->L.grid[0], z1 = s->L.cursor;
     MPM_CUDA(cudaMemsetAsync(s->ws + z0, 0, z1 - z0, st), "cudaMemsetAsync");
-    s->N = n;
+    s->N = (int)total;
     s->ps = PipeState{};
-    if (n == 0) {
+    if (total == 0) {
         s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;
         return MPM_OK;
     }
-    const size_t N = (size_t)n;
+    const size_t N = total;
     const float *sx = x, *sv = v, *sC = C, *sF = F;
     if (!src_on_device) {
         // stage host arrays in the spare state buffer, same SoA layout
@@ -541,39 +675,71 @@ mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, 
             sF = stage.F;
         }
     }
-    StateView dst = s->view(0);
-    MPM_TRY(launch(s, MPM_K_LOAD, st, [&] {
-        return launch_load(s->geo, s->mat.kind, n, sx, sv, sC, sF, dst, s->at<uint2>(s->L.key),
-                           s->at<uint32_t>(s->L.hist), s->status(), st);
-    }, "load"));
+    LoadParams lp{};
+    lp.envs = s->envs_dev();
+    lp.nenv = s->nenv;
+    lp.N = (int)N;
+    lp.x = sx;
+    lp.v = sv;
+    lp.C = sC;
+    lp.F = sF;
+    lp.dst = s->view(0);
+    lp.keyrank = s->at<uint2>(s->L.key);
+    lp.hist = s->at<uint32_t>(s->L.hist);
+    lp.status = s->status();
+    MPM_TRY(launch(s, MPM_K_LOAD, st, [&] { return launch_load(lp, st); }, "load"));
     if (!src_on_device) MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return MPM_OK;
 }
 
-mpm_status mpm_set_shapes(mpm_sim* s, int k, const mpm_shape* shapes) {
-    if (!s || k < 0 || (k > 0 && !shapes)) return MPM_ERR_INVALID_ARG;
-    if (k > s->cfg.max_colliders) return MPM_ERR_CAPACITY;
-    for (int i = 0; i < k; ++i) {
+mpm_status mpm_set_particles(mpm_sim* s, int n, const float* x, const float* v, const float* C, const float* F,
+                             int src_on_device, void* stream) {
+    if (!s || s->nenv != 1 || n < 0 || (n > 0 && !x)) return MPM_ERR_INVALID_ARG;
+    return mpm_set_particles_batch(s, &n, x, v, C, F, src_on_device, stream);
+}
+
+mpm_status mpm_set_shapes_batch(mpm_sim* s, const int* counts, const mpm_shape* shapes) {
+    if (!s || !counts) return MPM_ERR_INVALID_ARG;
+    int total = 0;
+    for (int e = 0; e < s->nenv; ++e) {
+        if (counts[e] < 0) return MPM_ERR_INVALID_ARG;
+        if (counts[e] > s->env_cfg[e].max_colliders) return MPM_ERR_CAPACITY;
+        total += counts[e];
+    }
+    if (total > 0 && !shapes) return MPM_ERR_INVALID_ARG;
+    for (int i = 0; i < total; ++i) {
         const mpm_shape& sh = shapes[i];
         if (sh.type != MPM_BOX && sh.type != MPM_CAPSULE) return MPM_ERR_INVALID_ARG;
         if (!(sh.friction >= 0.0f) || !std::isfinite(sh.friction)) return MPM_ERR_INVALID_ARG;
-        int dims = sh.type == MPM_BOX ? 3 : 2;
+        const int dims = sh.type == MPM_BOX ? 3 : 2;
         for (int a = 0; a < dims; ++a)
             if (!(sh.half[a] >= 0.0f) || !std::isfinite(sh.half[a])) return MPM_ERR_INVALID_ARG;
     }
-    s->nshapes = k;
-    if (k) memcpy(s->shapes, shapes, sizeof(mpm_shape) * k);
+    s->shapes.assign(shapes, shapes + total);
+    int first = 0;
+    for (int e = 0; e < s->nenv; ++e) {
+        s->envs[e].col_first = first;
+        s->envs[e].col_count = 0;  // active after the next mpm_set_colliders
+        first += counts[e];
+    }
+    s->shape_counts.assign(counts, counts + s->nenv);
     return MPM_OK;
+}
+
+mpm_status mpm_set_shapes(mpm_sim* s, int k, const mpm_shape* shapes) {
+    if (!s || s->nenv != 1 || k < 0 || (k > 0 && !shapes)) return MPM_ERR_INVALID_ARG;
+    if (k > s->env_cfg[0].max_colliders) return MPM_ERR_CAPACITY;
+    return mpm_set_shapes_batch(s, &k, shapes);
 }
 
 mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* lin_vel, const float* ang_vel,
                              const float* com, void* stream) {
-    if (!s || k != s->nshapes || (k > 0 && (!pose || !lin_vel))) return MPM_ERR_INVALID_ARG;
+    if (!s || k != (int)s->shapes.size() || (k > 0 && (!pose || !lin_vel))) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ColliderUpload u{};
-    u.k = k;
+    // the previous upload must have left the staging buffer before it is refilled
+    MPM_CUDA(cudaEventSynchronize(s->stage_done), "cudaEventSynchronize");
     for (int i = 0; i < k; ++i) {
-        ColliderSet& c = u.c[i];
+        ColliderSet& c = s->stage[i];
         const mpm_shape& sh = s->shapes[i];
         c.type = sh.type;
         for (int a = 0; a < 3; ++a) c.half[a] = sh.half[a];
@@ -595,10 +761,20 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
                 !std::isfinite(c.com[a]))
                 return MPM_ERR_INVALID_ARG;
     }
+    ColliderSet* up = s->at<ColliderSet>(s->L.upload);
+    if (k > 0) MPM_CUDA(cudaMemcpyAsync(up, s->stage, sizeof(ColliderSet) * k, cudaMemcpyHostToDevice, st), "copy colliders");
+    MPM_CUDA(cudaEventRecord(s->stage_done, st), "cudaEventRecord");
     MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
-        return launch_set_colliders(u, s->at<ColliderSet>(s->L.colliders), s->at<double>(s->L.wrench),
-                                    s->substep_counter(), st);
+        return launch_set_colliders(up, k, s->at<ColliderSet>(s->L.colliders), s->at<ColliderNow>(s->L.poses),
+                                    s->at<double>(s->L.wrench), s->substep_counter(), s->cfg.dt, st);
     }, "set_colliders"));
+    bool changed = s->ncol != k;
+    for (int e = 0; e < s->nenv; ++e) {
+        const int want = e < (int)s->shape_counts.size() ? s->shape_counts[e] : 0;
+        if (s->envs[e].col_count != want) changed = true;
+        s->envs[e].col_count = want;
+    }
+    if (changed) MPM_TRY(upload_envs(s, st));
     s->ncol = k;
     return MPM_OK;
 }
@@ -649,6 +825,26 @@ mpm_status mpm_set_graphs(mpm_sim* s, int enable) {
     return MPM_OK;
 }
 
+mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid_ctas_per_sm) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    if (chunk && (chunk < 32 || chunk > kChunk || chunk % 32)) return MPM_ERR_INVALID_ARG;
+    if (fused_ctas_per_sm && (fused_ctas_per_sm < 1 || fused_ctas_per_sm > s->max_fused_cps)) return MPM_ERR_INVALID_ARG;
+    if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
+    if (chunk) s->chunk = chunk;
+    if (fused_ctas_per_sm) s->fused_cps = fused_ctas_per_sm;
+    if (grid_ctas_per_sm) s->grid_cps = grid_ctas_per_sm;
+    s->drop_graphs();
+    return MPM_OK;
+}
+
+mpm_status mpm_get_launch(const mpm_sim* s, int* chunk, int* fused_ctas_per_sm, int* grid_ctas_per_sm) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    if (chunk) *chunk = s->chunk;
+    if (fused_ctas_per_sm) *fused_ctas_per_sm = s->fused_cps;
+    if (grid_ctas_per_sm) *grid_ctas_per_sm = s->grid_cps;
+    return MPM_OK;
+}
+
 mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, int dst_on_device, void* stream) {
     if (!s) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -656,12 +852,13 @@ mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, in
     const size_t N = (size_t)s->N;
     StateView src = s->view(s->ps.cur);
     if (dst_on_device) {
-        return launch(s, MPM_K_READ, st, [&] { return launch_read_state(s->mat.kind, s->N, src, x, v, C, F, st); },
-                      "read_state");
+        return launch(s, MPM_K_READ, st, [&] {
+            return launch_read_state(s->N, s->envs_dev(), s->nenv, src, x, v, C, F, st);
+        }, "read_state");
     }
     StateView stage = s->view(1 - s->ps.cur);
     MPM_TRY(launch(s, MPM_K_READ, st, [&] {
-        return launch_read_state(s->mat.kind, s->N, src, x ? stage.x : nullptr, v ? stage.v : nullptr,
+        return launch_read_state(s->N, s->envs_dev(), s->nenv, src, x ? stage.x : nullptr, v ? stage.v : nullptr,
                                  C ? stage.C : nullptr, F ? stage.F : nullptr, st);
     }, "read_state"));
     if (x) MPM_CUDA(cudaMemcpyAsync(x, stage.x, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy x");
@@ -702,7 +899,14 @@ mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->N > 0) MPM_TRY(ensure_grid(s, st));
     const float4* grid = s->at<float4>(s->L.grid[s->ps.g]);
-    return launch(s, MPM_K_READ, st, [&] { return launch_read_grid(s->geo, grid, d_out, st); }, "read_grid");
+    size_t off = 0;
+    for (int e = 0; e < s->nenv; ++e) {
+        const EnvDesc& d = s->envs[e];
+        MPM_TRY(launch(s, MPM_K_READ, st, [&] { return launch_read_grid(d.geo, grid + d.node_base, d_out + off, st); },
+                       "read_grid"));
+        off += (size_t)d.geo.n * d.geo.n * d.geo.n * 4;
+    }
+    return MPM_OK;
 }
 
 mpm_status mpm_set_timing(mpm_sim* s, unsigned kernel_mask) {

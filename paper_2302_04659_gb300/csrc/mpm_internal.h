@@ -1,5 +1,9 @@
 // mpm_internal.h -- launch parameters shared by the kernels (mpm_kernels.cu) and the C-ABI host code
 // (mpm_abi.cu). Not part of the public interface.
+//
+// A handle simulates one or more independent environments (envs) together: each env has its own grid,
+// material, particles and colliders; all of them advance with the same launches. Bins get global ids
+// (the env's first bin + its local bin), particles global indices (the caller's concatenated order).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,13 +13,22 @@
 
 namespace mpm {
 
-// Particles per chunk of a bin = threads per CTA of the particle passes.
+// Most particles per chunk of a bin = threads per CTA of the particle passes.
 constexpr int kChunk = 128;
+
+// Collider poses are tabulated for this many substeps after each mpm_set_colliders; later substeps
+// evaluate them on the fly.
+constexpr int kPoseSteps = 64;
+
+// Above this many bins (all envs), the bin counts are scanned by two grid-wide kernels instead of the
+// last CTA of the fused pass.
+constexpr int kTailScanMaxBins = 16384;
+constexpr int kScanTile = 1024;  // bins per CTA of the grid-wide scan
 
 // Internal-consistency flag: a particle was found outside the bin it was sorted into.
 constexpr uint32_t kFlagInternal = 0x80000000u;
 
-// Particle state, structure of arrays with stride N (current count):
+// Particle state, structure of arrays with stride N (all particles of all envs):
 //   x[3N] v[3N] C[9N] F[9N] (a fluid keeps J in the first N entries of F), pid[N] after the floats.
 struct StateView {
     float* x;
@@ -32,48 +45,79 @@ struct Geometry {
     float lo, hi;   // particle clamp range [2dx, 1-2dx]
 };
 
-struct TransferParams {  // particle passes: the fused G2P->P2G substep and the standalone P2G
+struct __align__(16) EnvDesc {
     Geometry geo;
     Material mat;
-    int N;
+    int kind;            // MPM_PLASTICINE / MPM_FLUID
+    uint32_t bin_base;   // first global bin
+    uint32_t node_base;  // first node of its grids (block-major, nblocks * 64 nodes)
+    int col_first, col_count;
+    uint32_t part_first, part_count;  // its particles in the caller's order
+};
+
+// A bin list entry packs the env and the local bin.
+constexpr int kLocalBinBits = 18;  // nb <= 64
+__host__ __device__ __forceinline__ uint32_t pack_bin(uint32_t env, uint32_t local) {
+    return (env << kLocalBinBits) | local;
+}
+
+struct TransferParams {  // particle passes: the fused G2P->P2G substep and the standalone P2G
+    const EnvDesc* envs;
+    int N;                  // particles of all envs (SoA stride)
     StateView in;           // read through perm
     StateView out;          // written at the sorted slot (fused pass only)
     const uint32_t* perm;   // sorted slot -> position in `in`
-    uint2* keyrank_out;     // fused pass: (bin of the new position, rank within that bin), per sorted slot
-    uint32_t* hist;         // fused pass: particles per bin of the new positions
+    uint2* keyrank_out;     // fused pass: (global bin of the new position, rank within that bin)
+    uint32_t* hist;         // fused pass: particles per global bin of the new positions
     const float4* grid_in;  // fused pass: node velocities (x, y, z, mass)
     float4* grid_out;       // mass and momentum accumulated (m, mx, my, mz)
-    uint32_t* flags_out;    // bins of grid_out that received anything
-    uint32_t* list_out;     // ... and the same bins as a list, each appended once (when its flag is set)
+    uint32_t* flags_out;    // global bins of grid_out that received anything
+    uint32_t* list_out;     // ... as packed (env, local bin) entries, each appended once
     uint32_t* list_count_out;
-    const int4* chunks;     // (bin, first sorted slot, count, 0)
+    const int4* chunks;     // (global bin, first sorted slot, count, env)
     const uint32_t* num_chunks;
     uint32_t* status;
     uint32_t* substep_counter;
-    // fused pass only: the last CTA to finish scans `hist` into these (the same buffers as chunks /
-    // num_chunks, rewritten once every CTA is done reading them)
+    // fused pass with few bins: the last CTA to finish scans `hist` into these (the same buffers as
+    // chunks / num_chunks, rewritten once every CTA is done reading them)
+    int tail_scan;
+    int total_bins;
+    int chunk;              // most particles per chunk (<= kChunk)
+    const uint32_t* bin_env;  // env of every global bin (for the chunk list)
     uint32_t* cursor;
     int4* chunks_next;
     uint32_t* num_chunks_next;
-    uint32_t* done;           // CTAs finished, reset by the last one
+    uint32_t* done;         // CTAs finished, reset by the last one
+};
+
+struct ScanParams {  // grid-wide scan of the bin counts (many bins)
+    uint32_t* hist;
+    uint32_t* cursor;
+    int4* chunks;
+    uint32_t* num_chunks;
+    uint2* tile_sums;       // (particles, chunks) per tile of kScanTile bins
+    const uint32_t* bin_env;
+    int total_bins;
+    int chunk;
 };
 
 struct GridParams {
-    Geometry geo;
+    const EnvDesc* envs;
     float gravity[3];
     int bound;
     float4* grid;             // (m, mv) in, (v, m) out
-    const uint32_t* list;     // active bins of grid and their count
+    const uint32_t* list;     // active bins of grid (packed) and their count
     const uint32_t* list_count;
     float4* grid_old;         // the previous grid, zeroed here (its active bins) for its next use
     uint32_t* flags_old;      // its bin flags, cleared
     const uint32_t* list_old;
     uint32_t* list_count_old; // reset by the last CTA to finish
     uint32_t* done;           // CTAs finished, reset by the last one
-    const ColliderSet* cols;  // as set; posed at t = substep counter * dt
-    int ncol;
+    const ColliderSet* cols;  // all envs' colliders, as set
+    const ColliderNow* poses; // [kPoseSteps][k_total] poses after each substep count
+    int k_total;
     const uint32_t* substep_counter;
-    double* wrench;           // ncol x 6
+    double* wrench;           // k_total x 6
     int ctas;                 // CTAs of the (persistent) grid update
 };
 
@@ -86,30 +130,39 @@ struct AssignGridParams {  // the sort-assign of the new state and the grid upda
     int assign_ctas;          // the first assign_ctas CTAs assign sorted slots (0: no assign)
 };
 
-struct ColliderUpload {
-    int k;
-    ColliderSet c[kMaxColliders];
+struct LoadParams {  // mpm_set_particles*: copy in, clamp, bin keys and ranks
+    const EnvDesc* envs;
+    int nenv;
+    int N;
+    const float* x;
+    const float* v;
+    const float* C;
+    const float* F;
+    StateView dst;
+    uint2* keyrank;
+    uint32_t* hist;
+    uint32_t* status;
 };
 
 // launch wrappers (mpm_kernels.cu); each returns cudaGetLastError() after enqueueing
-cudaError_t launch_load(const Geometry& g, int kind, int N, const float* x, const float* v, const float* C,
-                        const float* F, StateView dst, uint2* keyrank, uint32_t* hist, uint32_t* status,
-                        cudaStream_t s);
+cudaError_t launch_load(const LoadParams& p, cudaStream_t s);
 cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks, int nblocks,
                         int chunk, cudaStream_t s);
+cudaError_t launch_scan_binned(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
+                               const uint32_t* bin_env, int nbins, int chunk, cudaStream_t s);
+cudaError_t launch_scan_grid(const ScanParams& p, cudaStream_t s);
 cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s);
-cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
-cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s);
-cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s);
+cudaError_t launch_p2g(const TransferParams& p, int grid_ctas, cudaStream_t s);
+cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s);
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s);
-cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
-                              cudaStream_t s);
+cudaError_t launch_read_state(int N, const EnvDesc* envs, int nenv, StateView src, float* x, float* v, float* C,
+                              float* F, cudaStream_t s);
 cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, cudaStream_t s);
-cudaError_t launch_set_colliders(const ColliderUpload& u, ColliderSet* table, double* wrench, uint32_t* counter,
-                                 cudaStream_t s);
+cudaError_t launch_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
+                                 double* wrench, uint32_t* counter, float dt, cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s);
 
-// occupancy of the particle kernels (CTAs per SM at the given block size)
-int transfer_ctas_per_sm(int kind, int threads, bool fused);
+// occupancy of the particle kernels (CTAs per SM at kChunk threads)
+int transfer_ctas_per_sm(bool fused);
 
 }  // namespace mpm

@@ -1,18 +1,22 @@
 // mpm_kernels.cu -- the CUDA kernels of the MLS-MPM substep (FP32, sm_103a).
 //
 // One substep (Algorithm 1's soft step: particle to grid, grid velocity, grid to particle, particle
-// integration) runs as
-//   k_scan + k_assign   counting sort of particles into 4^3-node bins (block-sparse grid)
-//   k_grid_update       v = mv/m + dt g, box/capsule Coulomb contact with per-body impulse
-//                       reduction, sticky walls; zeroes the previous grid's active bins
-//   k_g2p2g             per bin: gather v and C from a shared-memory tile of the updated grid,
-//                       advect, update F with the plastic return map (or J), and in the same pass
-//                       scatter the new state's mass and momentum (with its stress) into a
-//                       shared-memory tile of the next grid, flushed with vector atomics.
+// integration) of every environment (env) of a handle runs as two launches:
+//   k_assign_grid   sorted slot of every particle of the state the previous launch wrote (counting sort
+//                   into 4^3-node bins), and the grid update of the transfer it scattered:
+//                   v = mv/m + dt g, box/capsule Coulomb contact with per-body impulse sums, sticky walls;
+//                   zeroes the previous grid's active bins
+//   k_g2p2g         per chunk of a bin: gather v and C from a shared-memory tile of the updated grid,
+//                   advect, update F with the plastic return map (or J), and in the same pass scatter the
+//                   new state's mass and momentum (with its stress) into a shared-memory tile of the next
+//                   grid, flushed with vector atomics; counts the new bins, and its last CTA scans them
+//                   (with many bins, k_scan_tiles + k_scan_apply do that instead)
 // Fusing grid-to-particle with the next substep's particle-to-grid (the "G2P2G" pattern of Wang et
 // al. 2020) reads each particle's x and F once per substep and its v, C not at all: they are
 // recomputed by the gather. k_p2g is the standalone transfer used after the state is replaced.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "mpm_device.cuh"
 #include "mpm_internal.h"
@@ -21,7 +25,8 @@ namespace mpm {
 
 namespace {
 
-__device__ __forceinline__ uint32_t bin_of(const float x[3], const Geometry& g) {
+// Local bin of a position in an env's grid.
+__device__ __forceinline__ uint32_t local_bin_of(const float x[3], const Geometry& g) {
     int b0 = cell_base(x[0], g.inv_dx) >> 2;
     int b1 = cell_base(x[1], g.inv_dx) >> 2;
     int b2 = cell_base(x[2], g.inv_dx) >> 2;
@@ -44,6 +49,7 @@ __device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepco
 __device__ __forceinline__ void release_successor() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // Warp-aggregated histogram increment; every lane of the warp must call it (key = ~0u: no count).
+// Returns the lane's rank among all particles counted into the same key (when want_base).
 __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, bool want_base) {
     uint32_t peers = __match_any_sync(0xffffffffu, key);
     int lane = threadIdx.x & 31;
@@ -55,6 +61,24 @@ __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, 
         base += __popc(peers & ((1u << lane) - 1u));
     }
     return base;
+}
+
+// Env of particle p (caller order): the last env whose first particle is <= p.
+__device__ __forceinline__ int env_of_particle(const EnvDesc* envs, int nenv, uint32_t p) {
+    int lo = 0, hi = nenv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (envs[mid].part_first <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copy an env descriptor into shared memory (threads 0..19).
+__device__ __forceinline__ void load_env(EnvDesc& dst, const EnvDesc* envs, int e) {
+    static_assert(sizeof(EnvDesc) % 4 == 0, "EnvDesc is copied as words");
+    constexpr int kWords = (int)(sizeof(EnvDesc) / 4);
+    if ((int)threadIdx.x < kWords)
+        reinterpret_cast<uint32_t*>(&dst)[threadIdx.x] = reinterpret_cast<const uint32_t*>(envs + e)[threadIdx.x];
 }
 
 // ------------------------------------------------------------------------ scatter tile
@@ -70,7 +94,6 @@ __device__ __forceinline__ uint32_t warp_hist_add(uint32_t* hist, uint32_t key, 
 //             comparable to an FP32 accumulation of the same terms. Every scaled term is below 2^22, so it
 //             is rounded to an integer by one FP32 add (round_fixed).
 // The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
-
 
 constexpr int kMassBits = 22;
 
@@ -116,10 +139,11 @@ __device__ __forceinline__ float particle_bound(float m, const float vn[3], cons
     return b;
 }
 
-// Flag bin b of the output grid as active; the thread that sets the flag appends b to the bin list.
-__device__ __forceinline__ void mark_bin(const TransferParams& p, uint32_t b) {
+// Flag global bin b of the output grid as active; the thread that sets the flag appends the packed
+// (env, local bin) entry to the bin list.
+__device__ __forceinline__ void mark_bin(const TransferParams& p, uint32_t b, uint32_t entry) {
     if (__ldcg(&p.flags_out[b]) == 0u && atomicExch(&p.flags_out[b], 1u) == 0u)
-        p.list_out[atomicAdd(p.list_count_out, 1u)] = b;
+        p.list_out[atomicAdd(p.list_count_out, 1u)] = entry;
 }
 
 // Scatter one particle's mass and momentum to its 27 nodes: mom(node) = w (m v + A (x_i - x_p)),
@@ -127,10 +151,10 @@ __device__ __forceinline__ void mark_bin(const TransferParams& p, uint32_t b) {
 // The tile covers nodes [o, o+8) per axis with o = 4 * bin - 1; a particle outside it (one that moved a
 // cell or more since it was binned) updates the global grid directly in FP32 and marks the bins it
 // touches. Returns flag bits.
-__device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const TransferParams& p, const int o[3],
-                                                     const float xn[3], const float vn[3], const float (&A)[3][3],
-                                                     float mscale) {
-    const Geometry& g = p.geo;
+__device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const TransferParams& p, const EnvDesc& E,
+                                                     int env, const int o[3], const float xn[3], const float vn[3],
+                                                     const float (&A)[3][3], float mscale) {
+    const Geometry& g = E.geo;
     int bs[3];
     float f[3], w[3][3];
 #pragma unroll
@@ -139,7 +163,7 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
         f[a] = cell_frac(xn[a], g.inv_dx, bs[a]);
         bspline_weights(f[a], w[a]);
     }
-    const float m = p.mat.p_mass;
+    const float m = E.mat.p_mass;
     float Ad[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -178,6 +202,7 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
             }
         return 0;
     }
+    float4* grid = p.grid_out + E.node_base;
 #pragma unroll 1
     for (int i = 0; i < 3; ++i)
 #pragma unroll 1
@@ -189,8 +214,9 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
                 float4 add = make_float4(wk * m, wk * (bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0]),
                                          wk * (bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1]),
                                          wk * (bm[2] + i * Ad[0][2] + j * Ad[1][2] + k * Ad[2][2]));
-                atomicAdd(&p.grid_out[node_index(gx, gy, gz, g.nb)], add);
-                mark_bin(p, block_index(gx >> 2, gy >> 2, gz >> 2, g.nb));
+                atomicAdd(&grid[node_index(gx, gy, gz, g.nb)], add);
+                const uint32_t lb = block_index(gx >> 2, gy >> 2, gz >> 2, g.nb);
+                mark_bin(p, E.bin_base + lb, pack_bin((uint32_t)env, lb));
             }
     return 0x8u;
 }
@@ -208,12 +234,13 @@ __device__ __forceinline__ void tile_bound(ScatterTile& T, float bp) {
     if ((threadIdx.x & 31) == 0) atomicMax(&T.bound_bits, wmax);
 }
 
-// Add the tile's nonzero nodes to the global grid (FP32, one vector atomic each), then mark the bins that
-// received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
-__device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, int bx, int by, int bz,
-                                           float inv_mscale) {
-    const int nb = p.geo.nb;
-    const float mass_unit = p.mat.p_mass * pow2f(-kMassBits);
+// Add the tile's nonzero nodes to the env's global grid (FP32, one vector atomic each), then mark the
+// bins that received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
+__device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, const EnvDesc& E, int env,
+                                           int bx, int by, int bz, float inv_mscale) {
+    const int nb = E.geo.nb;
+    float4* grid = p.grid_out + E.node_base;
+    const float mass_unit = E.mat.p_mass * pow2f(-kMassBits);
     for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
         int mq = T.m[t];
         if (mq == 0) continue;
@@ -223,7 +250,7 @@ __device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams&
         int gx = 4 * bx - 1 + ti, gy = 4 * by - 1 + tj, gz = 4 * bz - 1 + tk;
         float4 add = make_float4((float)mq * mass_unit, (float)T.px[t] * inv_mscale, (float)T.py[t] * inv_mscale,
                                  (float)T.pz[t] * inv_mscale);
-        atomicAdd(&p.grid_out[node_index(gx, gy, gz, nb)], add);
+        atomicAdd(&grid[node_index(gx, gy, gz, nb)], add);
         int qx = (gx >> 2) - bx + 1, qy = (gy >> 2) - by + 1, qz = (gz >> 2) - bz + 1;
         T.touched[(qx * 3 + qy) * 3 + qz] = 1u;
     }
@@ -231,7 +258,8 @@ __device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams&
     if (threadIdx.x < 27 && T.touched[threadIdx.x]) {
         int q = threadIdx.x;
         int qx = q / 9, qy = (q / 3) % 3, qz = q % 3;
-        mark_bin(p, block_index(bx + qx - 1, by + qy - 1, bz + qz - 1, nb));
+        const uint32_t lb = block_index(bx + qx - 1, by + qy - 1, bz + qz - 1, nb);
+        mark_bin(p, E.bin_base + lb, pack_bin((uint32_t)env, lb));
     }
 }
 
@@ -268,55 +296,58 @@ __device__ __forceinline__ void decode_bin(int b, int nb, int& bx, int& by, int&
 
 // ------------------------------------------------------------------------ set_particles
 
-template <int KIND>
-__global__ void __launch_bounds__(256) k_load(Geometry g, int N, const float* __restrict__ x,
-                                              const float* __restrict__ v, const float* __restrict__ C,
-                                              const float* __restrict__ F, StateView dst, uint2* keyrank,
-                                              uint32_t* hist, uint32_t* status) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = p < N;
-    uint32_t flags = 0, k = 0xffffffffu;
+// Copy the caller's particles in (clamped), with identity pid, and count them into bins with ranks.
+__global__ void __launch_bounds__(256) k_load(LoadParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < p.N;
+    uint32_t flags = 0, key = 0xffffffffu;
     if (active) {
+        const int e = env_of_particle(p.envs, p.nenv, (uint32_t)i);
+        const EnvDesc& E = p.envs[e];
+        const Geometry& g = E.geo;
+        const int N = p.N;
         float xp[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            xp[a] = x[(size_t)a * N + p];
+            xp[a] = p.x[(size_t)a * N + i];
             flags |= clamp_coord(xp[a], g.lo, g.hi);
-            dst.x[(size_t)a * N + p] = xp[a];
-            dst.v[(size_t)a * N + p] = v ? v[(size_t)a * N + p] : 0.0f;
+            p.dst.x[(size_t)a * N + i] = xp[a];
+            p.dst.v[(size_t)a * N + i] = p.v ? p.v[(size_t)a * N + i] : 0.0f;
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst.C[(size_t)i * N + p] = C ? C[(size_t)i * N + p] : 0.0f;
-        if (KIND == 0) {
+        for (int c = 0; c < 9; ++c) p.dst.C[(size_t)c * N + i] = p.C ? p.C[(size_t)c * N + i] : 0.0f;
+        if (E.kind == 0) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) dst.F[(size_t)i * N + p] = F ? F[(size_t)i * N + p] : ((i % 4 == 0) ? 1.0f : 0.0f);
+            for (int c = 0; c < 9; ++c)
+                p.dst.F[(size_t)c * N + i] = p.F ? p.F[(size_t)c * N + i] : ((c % 4 == 0) ? 1.0f : 0.0f);
         } else {
             float J = 1.0f;
-            if (F) {
+            if (p.F) {
                 float M[3][3];
-                load_mat(F, N, p, M);
+                load_mat(p.F, N, i, M);
                 J = det3(M);
             }
-            dst.F[p] = J;
+            p.dst.F[i] = J;
         }
-        dst.pid[p] = (uint32_t)p;
-        k = bin_of(xp, g);
+        p.dst.pid[i] = (uint32_t)i;
+        key = E.bin_base + local_bin_of(xp, g);
     }
-    const uint32_t rank = warp_hist_add(hist, k, true);
-    if (active) keyrank[p] = make_uint2(k, rank);
-    if (flags) atomicOr(status, flags);
+    const uint32_t rank = warp_hist_add(p.hist, key, true);
+    if (active) p.keyrank[i] = make_uint2(key, rank);
+    if (flags) atomicOr(p.status, flags);
 }
 
 // ------------------------------------------------------------------------ counting sort into bins
 
 // One CTA (a multiple of 32 threads, at most 1024): exclusive scan of the bin counts -> bin start
 // offsets (cursor) and the chunk list: each bin is cut into chunks of at most `chunk` particles, one
-// chunk per CTA iteration of the particle passes. The counts are read from L2 (they were accumulated by
-// other CTAs' atomics) and zeroed for the next histogram.
-// Each thread owns a run of 4-bin groups, read as 16-byte vectors in batches of 8 independent loads so
-// one L2 round trip covers 32 bins. The count arrays are padded to a multiple of 4 bins (zeros).
+// chunk per CTA iteration of the particle passes, tagged with the bin's env. The counts are read from L2
+// (they were accumulated by other CTAs' atomics) and zeroed for the next histogram. Each thread owns a run
+// of 4-bin groups, read as 16-byte vectors in batches of 8 independent loads so one L2 round trip covers
+// 32 bins. The count arrays are padded to a multiple of 4 bins (zeros).
 __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
-                                          int nblocks, int chunk, uint32_t (&warp_tot)[2][32]) {
+                                          const uint32_t* bin_env, int nblocks, int chunk,
+                                          uint32_t (&warp_tot)[2][32]) {
     const int tid = threadIdx.x;
     const int nq = (nblocks + 3) >> 2;
     const int per = (nq + blockDim.x - 1) / blockDim.x;
@@ -375,8 +406,11 @@ __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4
                 const uint32_t c = c4[e];
                 o4[e] = off;
                 const int b = 4 * (q + u) + e;
-                for (uint32_t s = 0; s < c; s += chunk)
-                    chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), 0);
+                if (c) {
+                    const int env = bin_env ? (int)bin_env[b] : 0;
+                    for (uint32_t s = 0; s < c; s += chunk)
+                        chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), env);
+                }
                 off += c;
             }
             Cur[q + u] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
@@ -387,9 +421,95 @@ __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4
 }
 
 __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor, int4* chunks,
-                                               uint32_t* num_chunks, int nblocks, int chunk) {
+                                               uint32_t* num_chunks, const uint32_t* bin_env, int nblocks,
+                                               int chunk) {
     __shared__ uint32_t warp_tot[2][32];
-    scan_bins(hist, cursor, chunks, num_chunks, nblocks, chunk, warp_tot);
+    scan_bins(hist, cursor, chunks, num_chunks, bin_env, nblocks, chunk, warp_tot);
+}
+
+// Grid-wide scan for many bins, kernel 1: per tile of kScanTile bins, the sums of particles and chunks.
+__global__ void __launch_bounds__(256) k_scan_tiles(ScanParams p) {
+    wait_for_predecessor();
+    const int t = blockIdx.x;
+    const int b0 = t * kScanTile;
+    uint32_t cnt = 0, nch = 0;
+    for (int b = b0 + (int)threadIdx.x; b < min(b0 + kScanTile, p.total_bins); b += blockDim.x) {
+        const uint32_t c = __ldcg(&p.hist[b]);
+        cnt += c;
+        nch += (c + p.chunk - 1) / p.chunk;
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    nch = __reduce_add_sync(0xffffffffu, nch);
+    __shared__ uint32_t part[2][8];
+    if ((threadIdx.x & 31) == 0) { part[0][threadIdx.x >> 5] = cnt; part[1][threadIdx.x >> 5] = nch; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += part[0][w]; b += part[1][w]; }
+        p.tile_sums[t] = make_uint2(a, b);
+    }
+}
+
+// Grid-wide scan, kernel 2: each tile adds up the sums of the tiles before it, scans its own bins into
+// offsets and chunk entries, and zeroes its counts. The last tile stores the chunk total.
+__global__ void __launch_bounds__(kScanTile) k_scan_apply(ScanParams p) {
+    __shared__ uint32_t warp_tot[2][32];
+    __shared__ uint32_t base[2];
+    const int t = blockIdx.x;
+    uint32_t pc = 0, pn = 0;
+    for (int u = (int)threadIdx.x; u < t; u += blockDim.x) {
+        const uint2 s = __ldcg(&p.tile_sums[u]);
+        pc += s.x;
+        pn += s.y;
+    }
+    pc = __reduce_add_sync(0xffffffffu, pc);
+    pn = __reduce_add_sync(0xffffffffu, pn);
+    if ((threadIdx.x & 31) == 0) { warp_tot[0][threadIdx.x >> 5] = pc; warp_tot[1][threadIdx.x >> 5] = pn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += warp_tot[0][w]; b += warp_tot[1][w]; }
+        base[0] = a;
+        base[1] = b;
+    }
+    __syncthreads();
+    // one bin per thread: block-wide exclusive scan of (count, chunks)
+    const int b = t * kScanTile + (int)threadIdx.x;
+    const uint32_t c = b < p.total_bins ? __ldcg(&p.hist[b]) : 0u;
+    const uint32_t n = (c + p.chunk - 1) / p.chunk;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t ic = c, in = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t tc = __shfl_up_sync(0xffffffffu, ic, d), tn = __shfl_up_sync(0xffffffffu, in, d);
+        if (lane >= d) { ic += tc; in += tn; }
+    }
+    __syncthreads();
+    if (lane == 31) { warp_tot[0][wid] = ic; warp_tot[1][wid] = in; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t vc = lane < nw ? warp_tot[0][lane] : 0u, vn = lane < nw ? warp_tot[1][lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t tc = __shfl_up_sync(0xffffffffu, vc, d), tn = __shfl_up_sync(0xffffffffu, vn, d);
+            if (lane >= d) { vc += tc; vn += tn; }
+        }
+        if (lane < nw) { warp_tot[0][lane] = vc; warp_tot[1][lane] = vn; }
+    }
+    __syncthreads();
+    const uint32_t off = base[0] + ic - c + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
+    uint32_t coff = base[1] + in - n + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
+    if (b < p.total_bins) {
+        p.cursor[b] = off;
+        if (c) {
+            const int env = (int)p.bin_env[b];
+            for (uint32_t s = 0; s < c; s += p.chunk)
+                p.chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)p.chunk, c - s), env);
+        }
+        p.hist[b] = 0u;
+    }
+    if (t == (int)gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *p.num_chunks = coff;
 }
 
 // Sorted slot of particle j: slot = start of its bin + its rank within the bin. The rank was handed out
@@ -427,20 +547,21 @@ __global__ void __launch_bounds__(256) k_assign(int N, const uint2* __restrict__
 
 // ------------------------------------------------------------------------ standalone P2G
 
-template <int KIND>
 __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
     __shared__ ScatterTile T;
-    const Geometry& g = p.geo;
+    __shared__ EnvDesc E;
     const int N = p.N;
     uint32_t flags = 0;
     const uint32_t nchunks = *p.num_chunks;
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
         const int4 ch = p.chunks[w];
-        int bx, by, bz;
-        decode_bin(ch.x, g.nb, bx, by, bz);
-        const int o[3] = {4 * bx - 1, 4 * by - 1, 4 * bz - 1};
+        const int env = ch.w;
+        load_env(E, p.envs, env);
         tile_clear(T);
         __syncthreads();
+        int bx, by, bz;
+        decode_bin(ch.x - (int)E.bin_base, E.geo.nb, bx, by, bz);
+        const int o[3] = {4 * bx - 1, 4 * by - 1, 4 * bz - 1};
         const bool active = (int)threadIdx.x < ch.z;
         float x[3] = {0.0f, 0.0f, 0.0f}, v[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
         float bp = 0.0f;
@@ -453,27 +574,27 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
                 v[a] = p.in.v[(size_t)a * N + src];
             }
             load_mat(p.in.C, N, src, C);
-            if (KIND == 0) {
+            if (E.kind == 0) {
                 float F[3][3];
                 load_mat(p.in.F, N, src, F);
-                fixed_corotated_stress(F, p.mat, tau);
+                fixed_corotated_stress(F, E.mat, tau);
             } else {
                 const float J = p.in.F[src];
-                const float s = p.mat.lambda * J * (J - 1.0f);
+                const float s = E.mat.lambda * J * (J - 1.0f);
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
             }
-            affine(p.mat, C, tau, A);
-            bp = particle_bound(p.mat.p_mass, v, A, g.dx);
+            affine(E.mat, C, tau, A);
+            bp = particle_bound(E.mat.p_mass, v, A, E.geo.dx);
         }
         tile_bound(T, bp);
         __syncthreads();
         const int k = momentum_scale_exp(T.bound_bits);
-        if (active) flags |= scatter_particle(T, p, o, x, v, A, pow2f(k));
+        if (active) flags |= scatter_particle(T, p, E, env, o, x, v, A, pow2f(k));
         __syncthreads();
-        tile_flush(T, p, bx, by, bz, pow2f(-k));
+        tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
         __syncthreads();
     }
     if (flags) atomicOr(p.status, flags);
@@ -481,7 +602,6 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
 
 // ------------------------------------------------------------------------ fused G2P -> P2G
 
-template <int KIND>
 // 7 resident CTAs per SM (72 registers): measured faster than 8, 9 or 10 CTAs with the spills a tighter
 // register budget forces, on both the 200k and the 600k pinch scene.
 __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
@@ -489,19 +609,25 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
     // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
     __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
     __shared__ ScatterTile T;
-    const Geometry& g = p.geo;
+    __shared__ EnvDesc Es[2];  // the current chunk's env and the next one's
     const int N = p.N;
-    const float dt = g.dt;
     uint32_t flags = 0;
     wait_for_predecessor();
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
     int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
-    for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
+    load_env(Es[0], p.envs, next.w);
+    __syncthreads();
+    int it = 0;
+    for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x, ++it) {
         const int4 ch = next;
+        const int env = ch.w;
+        const EnvDesc& E = Es[it & 1];
+        const Geometry& g = E.geo;
+        const float dt = g.dt;
         if (w + gridDim.x < nchunks) next = p.chunks[w + gridDim.x];  // prefetch the next descriptor
         int bx, by, bz;
-        decode_bin(ch.x, g.nb, bx, by, bz);
+        decode_bin(ch.x - (int)E.bin_base, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
         // this thread's particle: its loads are issued first so they overlap the tile load below
         const bool active = (int)threadIdx.x < ch.z;
@@ -513,11 +639,12 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) x[a] = p.in.x[(size_t)a * N + src];
         }
+        const float4* grid_in = p.grid_in + E.node_base;
         for (int t = threadIdx.x; t < kGatherNodes; t += blockDim.x) {
             const int i = t / 36, j = (t / 6) % 6, k = t % 6;
             const int gx = ox + i, gy = oy + j, gz = oz + k;
             float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (gx < g.n && gy < g.n && gz < g.n) val = p.grid_in[node_index(gx, gy, gz, g.nb)];
+            if (gx < g.n && gy < g.n && gz < g.n) val = grid_in[node_index(gx, gy, gz, g.nb)];
             const int s = tile_slot(i, j, k);
             Gx[s] = val.x;
             Gy[s] = val.y;
@@ -525,18 +652,19 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
         }
         tile_clear(T);
         __syncthreads();
+        if (w + gridDim.x < nchunks) load_env(Es[(it + 1) & 1], p.envs, next.w);
         float xn[3] = {0.0f, 0.0f, 0.0f}, vn[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
         float bp = 0.0f;
         uint32_t newkey = 0xffffffffu;
         if (active) {
             // ---- G2P: v = sum w v_i, C = 4/dx sum w v_i (i - f)^T (offsets in cells)
             int bs[3];
-            float f[3], w[3][3];
+            float f[3], w3[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 bs[a] = cell_base(x[a], g.inv_dx);
                 f[a] = cell_frac(x[a], g.inv_dx, bs[a]);
-                bspline_weights(f[a], w[a]);
+                bspline_weights(f[a], w3[a]);
             }
             int l0 = bs[0] - ox, l1 = bs[1] - oy, l2 = bs[2] - oz;
             if ((unsigned)l0 > 3u || (unsigned)l1 > 3u || (unsigned)l2 > 3u) {
@@ -551,10 +679,10 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const float wij = w[0][i] * w[1][j];
+                    const float wij = w3[0][i] * w3[1][j];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const float wk = wij * w[2][k];
+                        const float wk = wij * w3[2][k];
                         const int s = tile_slot(l0 + i, l1 + j, l2 + k);
                         const float wv[3] = {wk * Gx[s], wk * Gy[s], wk * Gz[s]};
 #pragma unroll
@@ -586,7 +714,7 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) Gm[a][c] = (a == c ? 1.0f : 0.0f) + dt * Cn[a][c];
             float tau[3][3];
-            if (KIND == 0) {
+            if (E.kind == 0) {
                 float F[3][3], Ft[3][3];
                 load_mat(p.in.F, N, src, F);
 #pragma unroll
@@ -594,11 +722,11 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         Ft[a][c] = Gm[a][0] * F[0][c] + Gm[a][1] * F[1][c] + Gm[a][2] * F[2][c];
-                flags |= plastic_update_and_stress(Ft, p.mat, tau);
+                flags |= plastic_update_and_stress(Ft, E.mat, tau);
                 store_mat(p.out.F, N, slot, Ft);
             } else {
                 const float J = p.in.F[src] * det3(Gm);
-                const float s = p.mat.lambda * J * (J - 1.0f);
+                const float s = E.mat.lambda * J * (J - 1.0f);
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -612,9 +740,9 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
             }
             store_mat(p.out.C, N, slot, Cn);
             p.out.pid[slot] = p.in.pid[src];
-            newkey = bin_of(xn, g);
-            affine(p.mat, Cn, tau, A);
-            bp = particle_bound(p.mat.p_mass, vn, A, g.dx);
+            newkey = E.bin_base + local_bin_of(xn, g);
+            affine(E.mat, Cn, tau, A);
+            bp = particle_bound(E.mat.p_mass, vn, A, g.dx);
         }
         // rank within the new bin: the atomic's result is only stored after the scatter, so its round
         // trip overlaps the work in between
@@ -624,16 +752,17 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
         // ---- P2G of the new state into the next grid
         const int k = momentum_scale_exp(T.bound_bits);
         const int o[3] = {ox - 1, oy - 1, oz - 1};
-        if (active) flags |= scatter_particle(T, p, o, xn, vn, A, pow2f(k));
+        if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, pow2f(k));
         if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
         __syncthreads();
-        tile_flush(T, p, bx, by, bz, pow2f(-k));
+        tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
         __syncthreads();
     }
     if (flags) atomicOr(p.status, flags);
     release_successor();
-    // The last CTA to finish turns the new bin counts into offsets and the next chunk list. Every CTA
-    // has read its chunks and added to the counts before taking its ticket.
+    if (!p.tail_scan) return;
+    // With few bins, the last CTA to finish turns the new bin counts into offsets and the next chunk
+    // list. Every CTA has read its chunks and added to the counts before taking its ticket.
     __shared__ uint32_t warp_tot[2][32];
     __shared__ bool last;
     __threadfence();
@@ -642,89 +771,88 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
     __syncthreads();
     if (last) {
         __threadfence();
-        scan_bins(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, g.nblocks, kChunk, warp_tot);
+        scan_bins(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, p.chunk, warp_tot);
         if (threadIdx.x == 0) *p.done = 0u;
     }
 }
 
 // ------------------------------------------------------------------------ grid update
 
-// A persistent CTA of 256 threads works through groups of four 4^3 bins (one node per thread), cta,
-// cta + ctas, ...; groups without mass in either grid are skipped after one flag read. Zeroes the bins of
-// the previous grid that were active, so the next fused pass scatters into a clean grid.
+// A persistent CTA of 256 threads works through the active bins, four at a time (one node per thread):
+// first the previous grid's bins (zeroed), then this grid's (updated). Each bin's env supplies its
+// geometry, gravity step and colliders; collider poses come from the table filled at mpm_set_colliders
+// (evaluated on the fly after kPoseSteps substeps).
 __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
-    __shared__ ColliderNow cn[kMaxColliders];
-    __shared__ float wr[kMaxColliders * 6];
-    const Geometry& g = p.geo;
     const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
-    if ((int)threadIdx.x < p.ncol)
-        collider_at(p.cols[threadIdx.x], (float)(*p.substep_counter) * g.dt, cn[threadIdx.x]);
-    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) wr[i] = 0.0f;
-    __syncthreads();
-    // items: the previous grid's active bins (to zero), then this grid's active bins (to update)
+    const uint32_t step = *p.substep_counter;
     const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
+    constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
     for (uint32_t item = (uint32_t)(cta * 4 + grp); item < n_old + n_new; item += (uint32_t)(p.ctas * 4)) {
-    const bool has_old = item < n_old;
-    const uint32_t b = has_old ? p.list_old[item] : p.list[item - n_old];
-    if (has_old) {
-        p.grid_old[(size_t)b * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (ln == 0) p.flags_old[b] = 0u;
-    } else {
-        float4* node = &p.grid[(size_t)b * kBlkNodes + ln];
-        float4 gv = *node;
-        if (gv.x > 0.0f) {
-            const float m = gv.x;
-            const float im = 1.0f / m;
-            float v[3] = {gv.y * im + g.dt * p.gravity[0], gv.z * im + g.dt * p.gravity[1],
-                          gv.w * im + g.dt * p.gravity[2]};
-            int bx, by, bz;
-            decode_bin(b, g.nb, bx, by, bz);
-            const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
-            const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
-            for (int c = 0; c < p.ncol; ++c) {
-                float nrm[3];
-                float phi = collider_sdf(cn[c], xi, nrm);
-                if (!(phi < 0.0f)) continue;
-                float rel[3] = {xi[0] - cn[c].com[0], xi[1] - cn[c].com[1], xi[2] - cn[c].com[2]};
-                const float* om = cn[c].ang;
-                float vc[3] = {cn[c].lin[0] + om[1] * rel[2] - om[2] * rel[1],
-                               cn[c].lin[1] + om[2] * rel[0] - om[0] * rel[2],
-                               cn[c].lin[2] + om[0] * rel[1] - om[1] * rel[0]};
-                float vr[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
-                float vnrm = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
-                if (!(vnrm < 0.0f)) continue;
-                float vt[3] = {vr[0] - vnrm * nrm[0], vr[1] - vnrm * nrm[1], vr[2] - vnrm * nrm[2]};
-                float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
-                float mu = cn[c].friction;
-                float vnew[3];
-                if (tn <= -mu * vnrm) {
-                    vnew[0] = vc[0]; vnew[1] = vc[1]; vnew[2] = vc[2];
-                } else {
-                    float s = 1.0f + mu * vnrm / tn;
-                    vnew[0] = vc[0] + vt[0] * s; vnew[1] = vc[1] + vt[1] * s; vnew[2] = vc[2] + vt[2] * s;
-                }
-                float imp[3] = {m * (v[0] - vnew[0]), m * (v[1] - vnew[1]), m * (v[2] - vnew[2])};
-                atomicAdd(&wr[c * 6 + 0], imp[0]);
-                atomicAdd(&wr[c * 6 + 1], imp[1]);
-                atomicAdd(&wr[c * 6 + 2], imp[2]);
-                atomicAdd(&wr[c * 6 + 3], rel[1] * imp[2] - rel[2] * imp[1]);
-                atomicAdd(&wr[c * 6 + 4], rel[2] * imp[0] - rel[0] * imp[2]);
-                atomicAdd(&wr[c * 6 + 5], rel[0] * imp[1] - rel[1] * imp[0]);
-                v[0] = vnew[0]; v[1] = vnew[1]; v[2] = vnew[2];
-            }
-            const int lo = p.bound, hi = g.n - p.bound;
-            if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
-            *node = make_float4(v[0], v[1], v[2], m);
+        const bool is_old = item < n_old;
+        const uint32_t entry = is_old ? p.list_old[item] : p.list[item - n_old];
+        const int env = (int)(entry >> kLocalBinBits);
+        const uint32_t lb = entry & kLocalMask;
+        const EnvDesc& E = p.envs[env];
+        if (is_old) {
+            p.grid_old[E.node_base + (size_t)lb * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (ln == 0) p.flags_old[E.bin_base + lb] = 0u;
+            continue;
         }
-    }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < p.ncol * 6; i += blockDim.x) {
-        float val = wr[i];
-        if (val != 0.0f) atomicAdd(&p.wrench[i], (double)val);
+        const Geometry& g = E.geo;
+        float4* node = &p.grid[E.node_base + (size_t)lb * kBlkNodes + ln];
+        const float4 gv = *node;
+        if (!(gv.x > 0.0f)) continue;
+        const float m = gv.x;
+        const float im = 1.0f / m;
+        float v[3] = {gv.y * im + g.dt * p.gravity[0], gv.z * im + g.dt * p.gravity[1],
+                      gv.w * im + g.dt * p.gravity[2]};
+        int bx, by, bz;
+        decode_bin((int)lb, g.nb, bx, by, bz);
+        const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
+        const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
+        for (int c = E.col_first; c < E.col_first + E.col_count; ++c) {
+            ColliderNow cn;
+            if (step < (uint32_t)kPoseSteps)
+                cn = p.poses[(size_t)step * p.k_total + c];
+            else
+                collider_at(p.cols[c], (float)step * g.dt, cn);
+            float nrm[3];
+            const float phi = collider_sdf(cn, xi, nrm);
+            if (!(phi < 0.0f)) continue;
+            const float rel[3] = {xi[0] - cn.com[0], xi[1] - cn.com[1], xi[2] - cn.com[2]};
+            const float vc[3] = {cn.lin[0] + cn.ang[1] * rel[2] - cn.ang[2] * rel[1],
+                                 cn.lin[1] + cn.ang[2] * rel[0] - cn.ang[0] * rel[2],
+                                 cn.lin[2] + cn.ang[0] * rel[1] - cn.ang[1] * rel[0]};
+            const float vr[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
+            const float vnrm = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
+            if (!(vnrm < 0.0f)) continue;
+            const float vt[3] = {vr[0] - vnrm * nrm[0], vr[1] - vnrm * nrm[1], vr[2] - vnrm * nrm[2]};
+            const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+            const float mu = cn.friction;
+            float vnew[3];
+            if (tn <= -mu * vnrm) {
+                vnew[0] = vc[0]; vnew[1] = vc[1]; vnew[2] = vc[2];
+            } else {
+                const float s = 1.0f + mu * vnrm / tn;
+                vnew[0] = vc[0] + vt[0] * s; vnew[1] = vc[1] + vt[1] * s; vnew[2] = vc[2] + vt[2] * s;
+            }
+            const float imp[3] = {m * (v[0] - vnew[0]), m * (v[1] - vnew[1]), m * (v[2] - vnew[2])};
+            double* wr = p.wrench + (size_t)c * 6;
+            atomicAdd(&wr[0], (double)imp[0]);
+            atomicAdd(&wr[1], (double)imp[1]);
+            atomicAdd(&wr[2], (double)imp[2]);
+            atomicAdd(&wr[3], (double)(rel[1] * imp[2] - rel[2] * imp[1]));
+            atomicAdd(&wr[4], (double)(rel[2] * imp[0] - rel[0] * imp[2]));
+            atomicAdd(&wr[5], (double)(rel[0] * imp[1] - rel[1] * imp[0]));
+            v[0] = vnew[0]; v[1] = vnew[1]; v[2] = vnew[2];
+        }
+        const int lo = p.bound, hi = g.n - p.bound;
+        if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
+        *node = make_float4(v[0], v[1], v[2], m);
     }
     // the last CTA to finish empties the previous grid's bin list (every CTA has read its count)
     __shared__ bool last;
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == (uint32_t)p.ctas - 1u;
     __syncthreads();
@@ -733,8 +861,6 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         *p.done = 0u;
     }
 }
-
-__global__ void __launch_bounds__(256) k_grid_update(GridParams p) { grid_update_cta(p, blockIdx.x); }
 
 // The sort-assign of the state the previous fused pass wrote (first assign_ctas CTAs) and the grid
 // update of the transfer it scattered (the remaining CTAs): independent work, one launch.
@@ -749,11 +875,11 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
 
 // ------------------------------------------------------------------------ readback
 
-template <int KIND>
-__global__ void __launch_bounds__(256) k_read_state(int N, StateView s, float* x, float* v, float* C, float* F) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_read_state(int N, const EnvDesc* envs, int nenv, StateView s, float* x,
+                                                    float* v, float* C, float* F) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    uint32_t p = s.pid[j];
+    const uint32_t p = s.pid[j];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (x) x[(size_t)a * N + p] = s.x[(size_t)a * N + j];
@@ -764,11 +890,11 @@ __global__ void __launch_bounds__(256) k_read_state(int N, StateView s, float* x
         for (int i = 0; i < 9; ++i) C[(size_t)i * N + p] = s.C[(size_t)i * N + j];
     }
     if (F) {
-        if (KIND == 0) {
+        if (envs[env_of_particle(envs, nenv, p)].kind == 0) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) F[(size_t)i * N + p] = s.F[(size_t)i * N + j];
         } else {
-            float c = cbrtf(s.F[j]);
+            const float c = cbrtf(s.F[j]);
 #pragma unroll
             for (int i = 0; i < 9; ++i) F[(size_t)i * N + p] = (i % 4 == 0) ? c : 0.0f;
         }
@@ -783,11 +909,18 @@ __global__ void __launch_bounds__(256) k_read_grid(Geometry g, const float4* __r
     out[t] = grid[node_index(i, j, k, g.nb)];
 }
 
-__global__ void k_set_colliders(ColliderUpload u, ColliderSet* table, double* wrench, uint32_t* counter) {
-    int t = threadIdx.x;
-    if (t < u.k) table[t] = u.c[t];
-    for (int i = t; i < u.k * 6; i += blockDim.x) wrench[i] = 0.0;
+// The uploaded collider table (staged by the host), the wrench reset, and the pose table: pose of
+// collider c after s substeps for s < kPoseSteps (one thread per entry).
+__global__ void k_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
+                                double* wrench, uint32_t* counter, float dt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < k) table[t] = upload[t];
+    if (t < k * 6) wrench[t] = 0.0;
     if (t == 0) *counter = 0u;
+    if (t < k * kPoseSteps) {
+        const int s = t / k, c = t % k;
+        collider_at(upload[c], (float)s * dt, poses[t]);
+    }
 }
 
 __global__ void k_advance_counter(uint32_t* counter, int n) {
@@ -797,37 +930,6 @@ __global__ void k_advance_counter(uint32_t* counter, int n) {
 // ------------------------------------------------------------------------ launch wrappers
 
 static inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
-
-cudaError_t launch_load(const Geometry& g, int kind, int N, const float* x, const float* v, const float* C,
-                        const float* F, StateView dst, uint2* keyrank, uint32_t* hist, uint32_t* status,
-                        cudaStream_t s) {
-    if (N <= 0) return cudaSuccess;
-    if (kind == 0)
-        k_load<0><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, keyrank, hist, status);
-    else
-        k_load<1><<<ceil_div(N, 256), 256, 0, s>>>(g, N, x, v, C, F, dst, keyrank, hist, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks, int nblocks,
-                        int chunk, cudaStream_t s) {
-    k_scan<<<1, 1024, 0, s>>>(hist, cursor, chunks, num_chunks, nblocks, chunk);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
-    if (N <= 0) return cudaSuccess;
-    k_assign<<<ceil_div(N, 256 * kAssignPerThread), 256, 0, s>>>(N, keyrank, cursor, perm);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s) {
-    if (kind == 0)
-        k_p2g<0><<<grid_ctas, threads, 0, s>>>(p);
-    else
-        k_p2g<1><<<grid_ctas, threads, 0, s>>>(p);
-    return cudaGetLastError();
-}
 
 // Launch with programmatic stream serialization: the kernel may start while its predecessor on the
 // stream drains; it orders itself with wait_for_predecessor().
@@ -846,27 +948,54 @@ static cudaError_t launch_dependent(void (*kernel)(P), unsigned grid, unsigned b
     return cudaLaunchKernelEx(&cfg, kernel, p);
 }
 
-cudaError_t launch_g2p2g(const TransferParams& p, int kind, int grid_ctas, int threads, cudaStream_t s) {
-    return kind == 0 ? launch_dependent(k_g2p2g<0>, grid_ctas, threads, s, p)
-                     : launch_dependent(k_g2p2g<1>, grid_ctas, threads, s, p);
+cudaError_t launch_load(const LoadParams& p, cudaStream_t s) {
+    if (p.N <= 0) return cudaSuccess;
+    k_load<<<ceil_div(p.N, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_grid_update(const GridParams& p, cudaStream_t s) {
-    k_grid_update<<<p.ctas, 256, 0, s>>>(p);
+cudaError_t launch_scan(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks, int nblocks,
+                        int chunk, cudaStream_t s) {
+    return launch_scan_binned(hist, cursor, chunks, num_chunks, nullptr, nblocks, chunk, s);
+}
+
+cudaError_t launch_scan_binned(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
+                               const uint32_t* bin_env, int nbins, int chunk, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(hist, cursor, chunks, num_chunks, bin_env, nbins, chunk);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan_grid(const ScanParams& p, cudaStream_t s) {
+    const unsigned tiles = ceil_div(p.total_bins, kScanTile);
+    cudaError_t e = launch_dependent(k_scan_tiles, tiles, 256, s, p);
+    if (e != cudaSuccess) return e;
+    k_scan_apply<<<tiles, kScanTile, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign(int N, const uint2* keyrank, const uint32_t* cursor, uint32_t* perm, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    k_assign<<<ceil_div(N, 256 * kAssignPerThread), 256, 0, s>>>(N, keyrank, cursor, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
+    k_p2g<<<grid_ctas, kChunk, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
+    return launch_dependent(k_g2p2g, grid_ctas, kChunk, s, p);
 }
 
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
     return launch_dependent(k_assign_grid, p.assign_ctas + p.grid.ctas, 256, s, p);
 }
 
-cudaError_t launch_read_state(int kind, int N, StateView src, float* x, float* v, float* C, float* F,
-                              cudaStream_t s) {
+cudaError_t launch_read_state(int N, const EnvDesc* envs, int nenv, StateView src, float* x, float* v, float* C,
+                              float* F, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    if (kind == 0)
-        k_read_state<0><<<ceil_div(N, 256), 256, 0, s>>>(N, src, x, v, C, F);
-    else
-        k_read_state<1><<<ceil_div(N, 256), 256, 0, s>>>(N, src, x, v, C, F);
+    k_read_state<<<ceil_div(N, 256), 256, 0, s>>>(N, envs, nenv, src, x, v, C, F);
     return cudaGetLastError();
 }
 
@@ -876,9 +1005,10 @@ cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_colliders(const ColliderUpload& u, ColliderSet* table, double* wrench, uint32_t* counter,
-                                 cudaStream_t s) {
-    k_set_colliders<<<1, 256, 0, s>>>(u, table, wrench, counter);
+cudaError_t launch_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
+                                 double* wrench, uint32_t* counter, float dt, cudaStream_t s) {
+    const int threads = std::max(std::max(k * kPoseSteps, k * 6), 1);
+    k_set_colliders<<<ceil_div(threads, 256), 256, 0, s>>>(upload, k, table, poses, wrench, counter, dt);
     return cudaGetLastError();
 }
 
@@ -887,15 +1017,10 @@ cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int transfer_ctas_per_sm(int kind, int threads, bool fused) {
+int transfer_ctas_per_sm(bool fused) {
     int n = 0;
-    cudaError_t e;
-    if (fused)
-        e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g<0>, threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g<1>, threads, 0);
-    else
-        e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g<0>, threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g<1>, threads, 0);
+    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g, kChunk, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g, kChunk, 0);
     if (e != cudaSuccess || n < 1) n = 1;
     return n;
 }

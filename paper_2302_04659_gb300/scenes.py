@@ -157,6 +157,8 @@ def ellipsoid_particles(N: int, center, semi, seed: int) -> np.ndarray:
     """N points uniform in an axis-aligned ellipsoid by rejection from its bounding box (FP32, (3, N))."""
     center = np.asarray(center, np.float64)
     semi = np.asarray(semi, np.float64)
+    if N == 0:
+        return np.zeros((3, 0), np.float32)
     out = []
     have = 0
     offset = 0
@@ -219,9 +221,122 @@ def finger_state(scene: Scene, t: float):
     pose = np.zeros((k, 7))
     lin = np.zeros((k, 3))
     for i in range(k):
-        A, f, d = sc["amp"][i], sc["freq"][i], sc["dir"][i]
-        pose[i, :3] = sc["c0"][i] + np.array([d * A * (1.0 - math.cos(2 * math.pi * f * t)) / 2.0, 0.0, 0.0])
+        A, f = sc["amp"][i], sc["freq"][i]
+        axis = np.asarray(sc["axis"][i], np.float64) if "axis" in sc else np.array([sc["dir"][i], 0.0, 0.0])
+        pose[i, :3] = sc["c0"][i] + axis * A * (1.0 - math.cos(2 * math.pi * f * t)) / 2.0
         pose[i, 3:] = sc["quat"][i]
-        lin[i, 0] = d * A * math.pi * f * math.sin(2 * math.pi * f * t)
+        lin[i] = axis * A * math.pi * f * math.sin(2 * math.pi * f * t)
     return (pose.astype(np.float32), lin.astype(np.float32), np.zeros((k, 3), np.float32),
             pose[:, :3].astype(np.float32))
+
+
+# ---------------------------------------------------------------------------- batched workloads
+
+def box_particles(N: int, lower, size, seed: int) -> np.ndarray:
+    """N points uniform in an axis-aligned box (FP32, (3, N))."""
+    u = uniform(seed, 3 * N).reshape(N, 3)
+    x = np.asarray(lower, np.float64)[None, :] + u * np.asarray(size, np.float64)[None, :]
+    return np.ascontiguousarray(x.T.astype(np.float32))
+
+
+def tool_scene(seed: int, kind: int, N: int, n: int = 64, extra_capsule: bool = False) -> Scene:
+    """One environment of the batched workloads: a body on the floor band and a moving box tool.
+
+    Plasticine: a seeded ellipsoid (semi-axes ~ U[0.12, 0.2]^3, centred in x and z, resting on the band
+    at 3 dx) pressed by a flat box (half extents 0.06, 0.02, 0.05) that starts 0.01 above it and moves
+    down and back, c0 - y A (1 - cos 2 pi f t) / 2, A ~ U[0.05, 0.12], f ~ U[1, 3] Hz.
+    Fluid: a seeded block of water (sides ~ U[0.3, 0.4] x U[0.12, 0.2] x U[0.3, 0.4]) stirred by a
+    paddle box (half extents 0.02, 0.08, 0.08) that starts 0.01 outside the block's -x side, its bottom
+    0.03 above the band (off the node lattice for every grid size used), and sweeps along +x with the same law. Friction 0.5 for both tools. With
+    ``extra_capsule`` a capsule finger (radius 0.02, half length 0.05, along x) closes in from the +x
+    side at mid height, as in the pinch scene.
+    """
+    dx = 1.0 / n
+    u = uniform(seed, 12, offset=0)
+    A = 0.05 + 0.07 * u[3]
+    f = 1.0 + 2.0 * u[4]
+    q_id = [1.0, 0.0, 0.0, 0.0]
+    floor = 3 * dx
+    if kind == PLASTICINE:
+        semi = 0.12 + 0.08 * u[0:3]
+        center = (0.5, floor + semi[1], 0.5)
+        x = ellipsoid_particles(N, center, semi, seed=seed + 1)
+        vol = 4.0 / 3.0 * math.pi * semi[0] * semi[1] * semi[2]
+        mat = Material(PLASTICINE, rho=1e3, E=5e3, nu=0.3, yield_stress=50.0, p_vol=vol / max(N, 1))
+        half = (0.06, 0.02, 0.05)  # unequal x, z: no interior node ties between the nearest faces
+        c0 = [(0.5, center[1] + semi[1] + 0.01 + half[1], 0.5)]
+        axis = [(0.0, -1.0, 0.0)]
+        mid_y, side_x = center[1], 0.5 + semi[0]
+    else:
+        size = (0.3 + 0.1 * u[0], 0.12 + 0.08 * u[1], 0.3 + 0.1 * u[2])
+        lower = (0.5 - size[0] / 2, floor, 0.5 - size[2] / 2)
+        x = box_particles(N, lower, size, seed=seed + 1)
+        vol = size[0] * size[1] * size[2]
+        mat = Material(FLUID, rho=1e3, bulk_modulus=1e4, p_vol=vol / max(N, 1))
+        half = (0.02, 0.08, 0.08)
+        c0 = [(lower[0] - half[0] - 0.01, floor + 0.03 + half[1], 0.5)]
+        axis = [(1.0, 0.0, 0.0)]
+        mid_y, side_x = floor + size[1] / 2, lower[0] + size[0]
+    shapes = [Shape(BOX, half, 0.5)]
+    quat = [q_id]
+    amp, freq = [A], [f]
+    if extra_capsule:
+        r, h = 0.02, 0.05
+        s2 = math.sqrt(0.5)
+        shapes.append(Shape(CAPSULE, (r, h, 0.0), 0.5))
+        c0.append((side_x + 0.01 + h + r, mid_y, 0.5))
+        axis.append((-1.0, 0.0, 0.0))
+        quat.append([s2, 0.0, s2, 0.0])
+        amp.append(0.05 + 0.07 * u[5])
+        freq.append(1.0 + 2.0 * u[6])
+    script = {"c0": np.array(c0), "axis": np.array(axis), "amp": np.array(amp), "freq": np.array(freq),
+              "quat": np.array(quat)}
+    return Scene(n=n, dt=2e-4, material=mat, x=x, v=np.zeros((3, N), np.float32),
+                 C=np.zeros((9, N), np.float32), F=_identity_F(N), shapes=shapes, script=script,
+                 substeps_per_env_step=25)
+
+
+def batch_counts(nenv: int, seed: int, lo: int, hi: int, log_uniform: bool = False) -> np.ndarray:
+    """Seeded particle counts per env: uniform in [lo, hi], or log-uniform over that range."""
+    u = uniform(seed, nenv)
+    if log_uniform:
+        c = np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+    else:
+        c = lo + u * (hi - lo + 1)
+    return np.clip(np.floor(c), lo, hi).astype(np.int64)
+
+
+def batch_workload(nenv: int = 256, seed: int = 3000, n: int = 64, lo: int = 20_000, hi: int = 120_000,
+                   counts=None) -> list:
+    """Many independent envs with their own n^3 grids: counts uniform in [lo, hi] from the seed, even envs
+    plasticine and odd envs fluid, one moving box tool each (``tool_scene``)."""
+    counts = batch_counts(nenv, seed, lo, hi) if counts is None else counts
+    return [tool_scene(seed + 7919 * (e + 1), PLASTICINE if e % 2 == 0 else FLUID, int(counts[e]), n)
+            for e in range(nenv)]
+
+
+def serving_workload(nenv: int = 1024, seed: int = 5000, lo: int = 2_000, hi: int = 200_000,
+                     grids=(48, 64, 80, 96)) -> list:
+    """The serving mix: counts log-uniform in [lo, hi], grid sizes drawn from ``grids``, plasticine and
+    fluid alternating, each env with a box tool and a capsule finger."""
+    counts = batch_counts(nenv, seed, lo, hi, log_uniform=True)
+    g = uniform(seed + 1, nenv)
+    return [tool_scene(seed + 7919 * (e + 1), PLASTICINE if e % 2 == 0 else FLUID, int(counts[e]),
+                       int(grids[min(int(g[e] * len(grids)), len(grids) - 1)]), extra_capsule=True)
+            for e in range(nenv)]
+
+
+def concat_states(envs: list):
+    """Concatenated (x, v, C, F) SoA arrays of a list of scenes, in env order, and the counts."""
+    counts = [sc.N for sc in envs]
+    cat = [np.ascontiguousarray(np.concatenate([getattr(sc, k) for sc in envs], axis=1)) for k in "xvCF"]
+    return counts, cat
+
+
+def concat_tool_states(envs: list, t: float):
+    """Concatenated collider inputs (pose, lin, ang, com) of all envs at time t."""
+    parts = [finger_state(sc, t) for sc in envs if sc.shapes]
+    if not parts:
+        z = np.zeros((0, 3), np.float32)
+        return np.zeros((0, 7), np.float32), z, z, z
+    return tuple(np.ascontiguousarray(np.concatenate([p[i] for p in parts])) for i in range(4))
