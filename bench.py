@@ -19,7 +19,12 @@ The JSON line also carries:
                HBM copy bandwidth; plus its DRAM traffic per launch from the committed ncu summary when
                it was taken on the current kernel source;
   cpu_baseline the FP64 oracle (single thread) on one environment step of the same scene;
-  clocks       nvidia-smi samples taken during the timed region.
+  clocks       nvidia-smi samples taken during the timed region;
+  batched      256 envs (64^3 grids, 20k-120k particles, plasticine and fluid, a box tool each) in one
+               handle: env-steps/s, particle-substeps/s, autotuned launch shape, and the same envs run
+               one handle per env (the per-scene form) for comparison;
+  serving      1,024 envs (2k-200k particles log-uniform, 48^3-96^3 grids, a box and a capsule each):
+               env-steps/s and p50/p99 latency of an env step that reads its impulses back.
 --impl reference times the oracle itself on a bounded particle sample of the same scene.
 """
 from __future__ import annotations
@@ -315,13 +320,176 @@ def run_native(args):
         "status_flags": flags,
         "wall_s": wall,
     }
+    line["clocks"] = clk.summary()
+    if world == 1 and not args.no_batched:
+        line["batched"] = run_batched(dev, "batch256", args.batched_steps, 3, per_scene=True, tune=True)
+        line["serving"] = run_batched(dev, "serve1024", args.batched_steps, 3, per_scene=False, tune=True)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
-    line["clocks"] = clk.summary()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune: bool):
+    """A batched workload in one handle: all envs advance together, one graph replay per env step.
+
+    ``batch256``: 256 envs, 64^3 grids, 20k-120k particles (uniform, seeded), plasticine and fluid
+    alternating, a box tool each. ``serve1024``: 1,024 envs, 2k-200k particles (log-uniform), 48^3-96^3
+    grids, a box tool and a capsule finger each. Inputs are far larger than L2, so no flush is needed.
+    Reports env-steps/s (envs x steps / time) and particle-substeps/s from a back-to-back pass, step
+    latency percentiles from a pass that reads every step's impulses back to the host, and for
+    ``batch256`` the same envs run one handle per env (the per-scene form) with the largest relative
+    difference in positions between the two forms after one env step."""
+    import torch
+
+    from paper_2302_04659_gb300 import _native as mpm
+    from paper_2302_04659_gb300 import autotune, scenes
+    from paper_2302_04659_gb300.sim import BatchSim, Sim
+
+    t_gen = time.perf_counter()
+    envs = scenes.batch_workload(256, 3000) if which == "batch256" else scenes.serving_workload(1024, 5000)
+    counts, (x, v, C, F) = scenes.concat_states(envs)
+    t_gen = time.perf_counter() - t_gen
+    sc0 = envs[0]
+    dt = sc0.dt
+    sim = BatchSim([(sc.n, sc.material, sc.N, len(sc.shapes)) for sc in envs], dt, gravity=sc0.gravity,
+                   bound=sc0.bound, device=dev)
+    xd, vd, Cd, Fd = (torch.from_numpy(a).to(dev) for a in (x, v, C, F))
+    sim.set_particles(counts, xd, vd, Cd, Fd)
+    sim.set_shapes([sc.shapes for sc in envs])
+    paths = scenes.ToolPaths(envs)
+    k = paths.k
+    stream = torch.cuda.current_stream(dev)
+    pin = {name: torch.empty((k, d), dtype=torch.float32).pin_memory()
+           for name, d in (("pose", 7), ("lin", 3), ("ang", 3), ("com", 3))}
+    wr_h = torch.empty((k, 6), dtype=torch.float64).pin_memory()
+    N = int(sum(counts))
+
+    def set_colliders(step, handle=sim.handle):
+        for name, arr in zip(("pose", "lin", "ang", "com"), paths.at(step * SUBSTEPS * dt)):
+            pin[name].numpy()[:] = arr
+        mpm.mpm_set_colliders(handle, k, pin["pose"].data_ptr(), pin["lin"].data_ptr(), pin["ang"].data_ptr(),
+                              pin["com"].data_ptr(), int(stream.cuda_stream))
+
+    def env_step(step):
+        set_colliders(step)
+        mpm.mpm_substep(sim.handle, SUBSTEPS, int(stream.cuda_stream))
+
+    def reset():
+        sim.set_particles(counts, xd, vd, Cd, Fd)
+        set_colliders(0)
+
+    tuned = None
+    if tune:
+        shape, ms, trials = autotune.tune(sim, substeps=4, reps=2, prepare=lambda: set_colliders(0), restore=reset)
+        tuned = {"shape": {"chunk": shape[0], "fused_ctas_per_sm": shape[1], "grid_ctas_per_sm": shape[2]},
+                 "ms_per_substep": ms, "trials_ms_per_substep": trials}
+    # positions after one env step from the initial state (compared with the per-scene form below)
+    reset()
+    mpm.mpm_substep(sim.handle, SUBSTEPS, int(stream.cuda_stream))
+    x_batch = sim.read_state(on_device=True)["x"]
+    reset()
+    for s_ in range(warmup):
+        env_step(s_)
+    torch.cuda.synchronize(dev)
+    # ---- throughput: back-to-back env steps, device-resident
+    l0 = sim.launches
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        a.record(stream)
+        for s_ in range(steps):
+            env_step(warmup + s_)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+    secs = a.elapsed_time(b) / 1e3
+    launches = sim.launches - l0
+    # ---- latency: every step reads its impulses back (host waits), per-step events
+    lat = []
+    for s_ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        env_step(warmup + steps + s_)
+        mpm.mpm_read_wrench(sim.handle, wr_h.data_ptr(), int(stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    flags = sim.status()
+    shape_now = sim.get_launch()
+    nenv = len(envs)
+    out = {
+        "workload": which,
+        "envs": nenv,
+        "particles": N,
+        "grids": sorted({sc.n for sc in envs}),
+        "materials": "plasticine/fluid alternating",
+        "colliders": k,
+        "substeps_per_env_step": SUBSTEPS,
+        "steps": steps,
+        "env_steps_per_s": nenv * steps / secs,
+        "particle_substeps_per_s": N * SUBSTEPS * steps / secs,
+        "ms_per_env_step": secs / steps * 1e3,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "set colliders + 25 substeps + impulses to pinned host memory, all envs"},
+        "gpu_launches": launches,
+        "launch_shape": {"chunk": shape_now[0], "fused_ctas_per_sm": shape_now[1], "grid_ctas_per_sm": shape_now[2]},
+        "autotune": tuned,
+        "status_flags": flags,
+        "clocks": clk.summary(),
+        "input_generation_s": t_gen,
+        "l2": "inputs larger than L2 (not flushed)",
+    }
+    sim.close()
+    del xd, vd, Cd, Fd
+    if per_scene:
+        # ---- the per-scene form: one handle per env, stepped one after another on the same stream
+        sims = []
+        off = np.concatenate([[0], np.cumsum(counts)])
+        col_off = np.concatenate([[0], np.cumsum([len(sc.shapes) for sc in envs])])
+        for e, sc in enumerate(envs):
+            s1 = Sim(sc.n, sc.dt, sc.material, max(sc.N, 1), gravity=sc.gravity, bound=sc.bound,
+                     max_colliders=len(sc.shapes), device=dev)
+            s1.set_particles(*(torch.from_numpy(np.ascontiguousarray(a[:, off[e]:off[e + 1]])).to(dev)
+                               for a in (x, v, C, F)))
+            s1.set_shapes(sc.shapes)
+            sims.append(s1)
+
+        def per_scene_step(step):
+            st = paths.at(step * SUBSTEPS * dt)
+            for e, s1 in enumerate(sims):
+                c0, c1 = col_off[e], col_off[e + 1]
+                s1.set_colliders(*(arr[c0:c1] for arr in st), stream=stream)
+                s1.substep(SUBSTEPS, stream=stream)
+
+        per_scene_step(0)
+        x_single = torch.cat([s1.read_state(on_device=True)["x"] for s1 in sims], dim=1)
+        diffs = []
+        for e in range(nenv):
+            xs = x_single[:, off[e]:off[e + 1]].double()
+            xb = x_batch[:, off[e]:off[e + 1]].double()
+            diffs.append(float((xb - xs).norm() / xs.norm().clamp_min(1e-30)))
+        ps_steps = max(2, min(steps, 4))
+        for s_ in range(1, 2):
+            per_scene_step(s_)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for s_ in range(ps_steps):
+            per_scene_step(2 + s_)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ps_secs = a.elapsed_time(b) / 1e3
+        for s1 in sims:
+            s1.close()
+        out["per_scene"] = {
+            "env_steps_per_s": nenv * ps_steps / ps_secs,
+            "particle_substeps_per_s": N * SUBSTEPS * ps_steps / ps_secs,
+            "steps": ps_steps,
+            "form": "one handle per env, each env step a collider upload and one graph replay, envs in turn",
+        }
+        out["speedup_vs_per_scene"] = out["env_steps_per_s"] / out["per_scene"]["env_steps_per_s"]
+        out["max_rel_x_diff_vs_per_scene_after_one_env_step"] = max(diffs)
+    return out
 
 
 def oracle_setup(sc, sample=None):
@@ -425,6 +593,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--particles", type=int, default=200_000, help="particles of the pinch scene")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving workloads")
+    ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -60,7 +60,7 @@ Totals totals_of(int nenv, const mpm_env* envs) {
 
 struct Layout {
     size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, tile_sums, envs,
-        bin_env, colliders, upload, poses, wrench, counters, total;
+        bin_env, colliders, poses, wrench, counters, total;
 };
 
 Layout make_layout(const Totals& T, int nenv) {
@@ -85,10 +85,9 @@ Layout make_layout(const Totals& T, int nenv) {
     L.chunks = take((cap / 32 + T.bins + 1) * sizeof(int4));
     L.tile_sums = take(((T.bins + kScanTile - 1) / kScanTile + 1) * sizeof(uint2));
     L.envs = take((size_t)nenv * sizeof(EnvDesc));
-    L.bin_env = take(T.bins * 4);
-    L.colliders = take(kcap * sizeof(ColliderSet));
-    L.upload = take(kcap * sizeof(ColliderSet));
-    L.poses = take((size_t)kPoseSteps * kcap * sizeof(ColliderNow));
+    L.bin_env = take(T.bins * 4 + 16);  // padded to a multiple of 4 bins, like the counts
+    L.colliders = take(kcap * sizeof(ColliderSet));  // written in stream order by each upload
+    L.poses = take((kcap > (size_t)kSharedPoses ? (size_t)kPoseSteps * kcap : 1) * sizeof(ColliderNow));
     L.wrench = take(kcap * 6 * sizeof(double));
     L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
     L.total = off;
@@ -170,6 +169,7 @@ struct GraphEntry {
 struct mpm_sim {
     mpm_config cfg;
     int nenv = 0;
+    int kind_all = 0;  // the material of every env, -1 if they differ
     std::vector<mpm_env> env_cfg;
     std::vector<EnvDesc> envs;  // host copy of the device table
     Totals T;
@@ -286,6 +286,9 @@ mpm_status upload_envs(mpm_sim* s, cudaStream_t st) {
 TransferParams transfer_params(mpm_sim* s) {
     TransferParams p{};
     p.envs = s->envs_dev();
+    p.env0 = s->envs[0];
+    p.one_env = s->nenv == 1 ? 1 : 0;
+    p.kind_all = s->kind_all;
     p.N = s->N;
     p.in = s->view(s->ps.cur);
     p.out = s->view(1 - s->ps.cur);
@@ -299,7 +302,7 @@ TransferParams transfer_params(mpm_sim* s) {
     p.tail_scan = s->tail_scan() ? 1 : 0;
     p.total_bins = (int)s->T.bins;
     p.chunk = s->chunk;
-    p.bin_env = s->at<uint32_t>(s->L.bin_env);
+    p.bin_env = s->nenv > 1 ? s->at<uint32_t>(s->L.bin_env) : nullptr;  // null: all bins are env 0's
     p.cursor = s->at<uint32_t>(s->L.cursor);
     p.chunks_next = s->at<int4>(s->L.chunks);
     p.num_chunks_next = s->num_chunks();
@@ -310,6 +313,9 @@ TransferParams transfer_params(mpm_sim* s) {
 GridParams grid_params(mpm_sim* s) {
     GridParams gp{};
     gp.envs = s->envs_dev();
+    gp.env0 = s->envs[0];
+    gp.one_env = s->nenv == 1 ? 1 : 0;
+    gp.dt = s->cfg.dt;
     for (int a = 0; a < 3; ++a) gp.gravity[a] = s->cfg.gravity[a];
     gp.bound = s->cfg.bound;
     gp.grid = s->at<float4>(s->L.grid[s->ps.g]);
@@ -322,7 +328,7 @@ GridParams grid_params(mpm_sim* s) {
     gp.done = s->grid_done();
     gp.cols = s->at<ColliderSet>(s->L.colliders);
     gp.poses = s->at<ColliderNow>(s->L.poses);
-    gp.k_total = std::max(s->ncol, 1);  // row stride of the pose table written by mpm_set_colliders
+    gp.k_total = s->ncol;  // also the row stride of the pose table mpm_set_colliders fills
     gp.substep_counter = s->substep_counter();
     gp.wrench = s->at<double>(s->L.wrench);
     gp.ctas = (int)std::max<size_t>(1, std::min<size_t>((size_t)s->sms * s->grid_cps, (s->T.bins + 3) / 4));
@@ -346,8 +352,9 @@ mpm_status enqueue_scan(mpm_sim* s, cudaStream_t st) {
     if (s->tail_scan()) {
         return launch(s, MPM_K_SCAN, st, [&] {
             return launch_scan_binned(s->at<uint32_t>(s->L.hist), s->at<uint32_t>(s->L.cursor),
-                                      s->at<int4>(s->L.chunks), s->num_chunks(), s->at<uint32_t>(s->L.bin_env),
-                                      (int)s->T.bins, s->chunk, st);
+                                      s->at<int4>(s->L.chunks), s->num_chunks(),
+                                      s->nenv > 1 ? s->at<uint32_t>(s->L.bin_env) : nullptr, (int)s->T.bins,
+                                      s->chunk, st);
         }, "scan");
     }
     ScanParams sp = scan_params(s);
@@ -554,9 +561,12 @@ mpm_status create_impl(const mpm_config* cfg, int nenv, const mpm_env* envs, voi
         mpm_destroy(s);
         return r;
     }
-    s->max_fused_cps = transfer_ctas_per_sm(true);
+    s->kind_all = envs[0].material.kind;
+    for (int e = 1; e < nenv; ++e)
+        if (envs[e].material.kind != s->kind_all) s->kind_all = -1;
+    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, nenv == 1);
     s->fused_cps = s->max_fused_cps;
-    s->p2g_cps = transfer_ctas_per_sm(false);
+    s->p2g_cps = transfer_ctas_per_sm(false, s->kind_all, nenv == 1);
     s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;  // no particles yet
     *out = s;
     return MPM_OK;
@@ -761,13 +771,24 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
                 !std::isfinite(c.com[a]))
                 return MPM_ERR_INVALID_ARG;
     }
-    ColliderSet* up = s->at<ColliderSet>(s->L.upload);
-    if (k > 0) MPM_CUDA(cudaMemcpyAsync(up, s->stage, sizeof(ColliderSet) * k, cudaMemcpyHostToDevice, st), "copy colliders");
-    MPM_CUDA(cudaEventRecord(s->stage_done, st), "cudaEventRecord");
-    MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
-        return launch_set_colliders(up, k, s->at<ColliderSet>(s->L.colliders), s->at<ColliderNow>(s->L.poses),
-                                    s->at<double>(s->L.wrench), s->substep_counter(), s->cfg.dt, st);
-    }, "set_colliders"));
+    // the device table is only read by work enqueued after this upload, so it is overwritten in place
+    ColliderSet* table = s->at<ColliderSet>(s->L.colliders);
+    if (k <= kSharedPoses) {  // few bodies: in the kernel parameters, posed per CTA each substep
+        ColliderUpload u{};
+        u.k = k;
+        for (int i = 0; i < k; ++i) u.c[i] = s->stage[i];
+        MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
+            return launch_set_colliders_small(u, table, s->at<double>(s->L.wrench), s->substep_counter(), st);
+        }, "set_colliders"));
+    } else {
+        MPM_CUDA(cudaMemcpyAsync(table, s->stage, sizeof(ColliderSet) * k, cudaMemcpyHostToDevice, st),
+                 "copy colliders");
+        MPM_CUDA(cudaEventRecord(s->stage_done, st), "cudaEventRecord");
+        MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
+            return launch_set_colliders(table, k, s->at<ColliderNow>(s->L.poses), s->at<double>(s->L.wrench),
+                                        s->substep_counter(), s->cfg.dt, st);
+        }, "set_colliders"));
+    }
     bool changed = s->ncol != k;
     for (int e = 0; e < s->nenv; ++e) {
         const int want = e < (int)s->shape_counts.size() ? s->shape_counts[e] : 0;

@@ -121,9 +121,13 @@ __device__ __forceinline__ void polar_data(const float (&F)[3][3], float (&U)[3]
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) sig[i] = sqrtf(fmaxf(S[i][i], 0.0f));
-    if (det3(F) < 0.0f) {
-        const int k = (sig[0] <= sig[1] && sig[0] <= sig[2]) ? 0 : (sig[1] <= sig[2] ? 1 : 2);
-        sig[k] = -sig[k];
+    if (det3(F) < 0.0f) {  // negate the smallest (first on ties), by selects
+        const bool k0 = sig[0] <= sig[1] && sig[0] <= sig[2];
+        const bool k1 = !k0 && sig[1] <= sig[2];
+        const bool k2 = !k0 && !k1;
+        sig[0] = k0 ? -sig[0] : sig[0];
+        sig[1] = k1 ? -sig[1] : sig[1];
+        sig[2] = k2 ? -sig[2] : sig[2];
     }
 }
 
@@ -304,17 +308,20 @@ __device__ __forceinline__ float collider_sdf(const ColliderNow& c, const float 
             qo[i] = fmaxf(q[i], 0.0f);
         }
         float outside = sqrtf(qo[0] * qo[0] + qo[1] * qo[1] + qo[2] * qo[2]);
-        int am = 0;
-        if (q[1] > q[am]) am = 1;
-        if (q[2] > q[am]) am = 2;
-        float qmax = q[am];
+        // axis of the largest q (first on ties), chosen with selects so nothing is indexed at run time
+        const bool a1 = q[1] > q[0];
+        const float q01 = a1 ? q[1] : q[0];
+        const bool a2 = q[2] > q01;
+        const float qmax = a2 ? q[2] : q01;
         phi = outside + fminf(qmax, 0.0f);
         if (outside > 0.0f) {
             float r = 1.0f / outside;
 #pragma unroll
             for (int i = 0; i < 3; ++i) nl[i] = (l[i] >= 0.0f ? 1.0f : -1.0f) * qo[i] * r;
         } else {
-            nl[am] = l[am] >= 0.0f ? 1.0f : -1.0f;
+            const bool on[3] = {!a1 && !a2, a1 && !a2, a2};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) nl[i] = on[i] ? (l[i] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
         }
     } else {
         float r = c.half[0], h = c.half[1];

@@ -16,8 +16,10 @@ namespace mpm {
 // Most particles per chunk of a bin = threads per CTA of the particle passes.
 constexpr int kChunk = 128;
 
-// Collider poses are tabulated for this many substeps after each mpm_set_colliders; later substeps
-// evaluate them on the fly.
+// With at most kSharedPoses colliders in a handle, each grid-update CTA evaluates the poses of the
+// substep into shared memory. With more, mpm_set_colliders tabulates them for the next kPoseSteps
+// substeps (later substeps evaluate them on the fly).
+constexpr int kSharedPoses = 16;
 constexpr int kPoseSteps = 64;
 
 // Above this many bins (all envs), the bin counts are scanned by two grid-wide kernels instead of the
@@ -63,6 +65,9 @@ __host__ __device__ __forceinline__ uint32_t pack_bin(uint32_t env, uint32_t loc
 
 struct TransferParams {  // particle passes: the fused G2P->P2G substep and the standalone P2G
     const EnvDesc* envs;
+    EnvDesc env0;           // a handle of one env: its descriptor, read from the kernel parameters
+    int one_env;            // 1: a single env (env0), no per-chunk descriptor loads
+    int kind_all;           // the material of every env, or -1 when they differ
     int N;                  // particles of all envs (SoA stride)
     StateView in;           // read through perm
     StateView out;          // written at the sorted slot (fused pass only)
@@ -103,6 +108,9 @@ struct ScanParams {  // grid-wide scan of the bin counts (many bins)
 
 struct GridParams {
     const EnvDesc* envs;
+    EnvDesc env0;             // a one-env handle's descriptor (see TransferParams)
+    int one_env;
+    float dt;
     float gravity[3];
     int bound;
     float4* grid;             // (m, mv) in, (v, m) out
@@ -114,8 +122,8 @@ struct GridParams {
     uint32_t* list_count_old; // reset by the last CTA to finish
     uint32_t* done;           // CTAs finished, reset by the last one
     const ColliderSet* cols;  // all envs' colliders, as set
-    const ColliderNow* poses; // [kPoseSteps][k_total] poses after each substep count
-    int k_total;
+    const ColliderNow* poses; // [kPoseSteps][k_total] poses after each substep count (k_total > kSharedPoses)
+    int k_total;              // colliders of all envs
     const uint32_t* substep_counter;
     double* wrench;           // k_total x 6
     int ctas;                 // CTAs of the (persistent) grid update
@@ -158,11 +166,17 @@ cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s);
 cudaError_t launch_read_state(int N, const EnvDesc* envs, int nenv, StateView src, float* x, float* v, float* C,
                               float* F, cudaStream_t s);
 cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, cudaStream_t s);
-cudaError_t launch_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
-                                 double* wrench, uint32_t* counter, float dt, cudaStream_t s);
+struct ColliderUpload {  // at most kSharedPoses colliders, passed by value to the upload kernel
+    int k;
+    ColliderSet c[kSharedPoses];
+};
+cudaError_t launch_set_colliders_small(const ColliderUpload& u, ColliderSet* table, double* wrench,
+                                       uint32_t* counter, cudaStream_t s);
+cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* poses, double* wrench,
+                                 uint32_t* counter, float dt, cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s);
 
-// occupancy of the particle kernels (CTAs per SM at kChunk threads)
-int transfer_ctas_per_sm(bool fused);
+// occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env);
 
 }  // namespace mpm

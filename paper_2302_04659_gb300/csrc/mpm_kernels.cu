@@ -203,13 +203,17 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
         return 0;
     }
     float4* grid = p.grid_out + E.node_base;
+    // rare path: rolled loops, weights picked by selects (no run-time indexing of register arrays)
 #pragma unroll 1
     for (int i = 0; i < 3; ++i)
 #pragma unroll 1
         for (int j = 0; j < 3; ++j)
 #pragma unroll 1
             for (int k = 0; k < 3; ++k) {
-                float wk = w[0][i] * w[1][j] * w[2][k];
+                const float wi = i == 0 ? w[0][0] : (i == 1 ? w[0][1] : w[0][2]);
+                const float wj = j == 0 ? w[1][0] : (j == 1 ? w[1][1] : w[1][2]);
+                const float wkk = k == 0 ? w[2][0] : (k == 1 ? w[2][1] : w[2][2]);
+                float wk = wi * wj * wkk;
                 int gx = bs[0] + i, gy = bs[1] + j, gz = bs[2] + k;
                 float4 add = make_float4(wk * m, wk * (bm[0] + i * Ad[0][0] + j * Ad[1][0] + k * Ad[2][0]),
                                          wk * (bm[1] + i * Ad[0][1] + j * Ad[1][1] + k * Ad[2][1]),
@@ -343,11 +347,14 @@ __global__ void __launch_bounds__(256) k_load(LoadParams p) {
 // offsets (cursor) and the chunk list: each bin is cut into chunks of at most `chunk` particles, one
 // chunk per CTA iteration of the particle passes, tagged with the bin's env. The counts are read from L2
 // (they were accumulated by other CTAs' atomics) and zeroed for the next histogram. Each thread owns a run
-// of 4-bin groups, read as 16-byte vectors in batches of 8 independent loads so one L2 round trip covers
-// 32 bins. The count arrays are padded to a multiple of 4 bins (zeros).
+// of 4-bin groups, read as 16-byte vectors in batches of independent loads so one L2 round trip covers
+// 32 (then 16) bins. The count and env arrays are padded to a multiple of 4 bins (zeros).
+// CHUNK > 0 fixes the chunk size at compile time (the divisions become shifts); 0 takes `chunk`.
+template <int CHUNK>
 __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
-                                          const uint32_t* bin_env, int nblocks, int chunk,
+                                          const uint32_t* bin_env, int nblocks, int chunk_arg,
                                           uint32_t (&warp_tot)[2][32]) {
+    const int chunk = CHUNK > 0 ? CHUNK : chunk_arg;
     const int tid = threadIdx.x;
     const int nq = (nblocks + 3) >> 2;
     const int per = (nq + blockDim.x - 1) / blockDim.x;
@@ -392,25 +399,28 @@ __device__ __forceinline__ void scan_bins(uint32_t* hist, uint32_t* cursor, int4
     uint32_t off = ic - cnt + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
     uint32_t coff = in - nch + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
     uint4* Cur = reinterpret_cast<uint4*>(cursor);
-    for (int q = q0; q < q1; q += 8) {
-        uint4 h[8];
+    const uint4* BE = reinterpret_cast<const uint4*>(bin_env);  // null: every bin is env 0's
+    for (int q = q0; q < q1; q += 4) {
+        // four 4-bin groups per batch: counts and (for several envs) the bins' envs, all loads in flight
+        uint4 h[4], be[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) h[u] = q + u < q1 ? __ldcg(&H[q + u]) : make_uint4(0u, 0u, 0u, 0u);
+        for (int u = 0; u < 4; ++u) {
+            h[u] = q + u < q1 ? __ldcg(&H[q + u]) : make_uint4(0u, 0u, 0u, 0u);
+            be[u] = (BE && q + u < q1) ? BE[q + u] : make_uint4(0u, 0u, 0u, 0u);
+        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             if (q + u >= q1) break;
             const uint32_t c4[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
+            const uint32_t e4[4] = {be[u].x, be[u].y, be[u].z, be[u].w};
             uint32_t o4[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const uint32_t c = c4[e];
                 o4[e] = off;
                 const int b = 4 * (q + u) + e;
-                if (c) {
-                    const int env = bin_env ? (int)bin_env[b] : 0;
-                    for (uint32_t s = 0; s < c; s += chunk)
-                        chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), env);
-                }
+                for (uint32_t s = 0; s < c; s += chunk)
+                    chunks[coff++] = make_int4(b, (int)(off + s), (int)min((uint32_t)chunk, c - s), (int)e4[e]);
                 off += c;
             }
             Cur[q + u] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
@@ -424,7 +434,10 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor,
                                                uint32_t* num_chunks, const uint32_t* bin_env, int nblocks,
                                                int chunk) {
     __shared__ uint32_t warp_tot[2][32];
-    scan_bins(hist, cursor, chunks, num_chunks, bin_env, nblocks, chunk, warp_tot);
+    if (chunk == kChunk)
+        scan_bins<kChunk>(hist, cursor, chunks, num_chunks, bin_env, nblocks, chunk, warp_tot);
+    else
+        scan_bins<0>(hist, cursor, chunks, num_chunks, bin_env, nblocks, chunk, warp_tot);
 }
 
 // Grid-wide scan for many bins, kernel 1: per tile of kScanTile bins, the sums of particles and chunks.
@@ -602,27 +615,41 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
 
 // ------------------------------------------------------------------------ fused G2P -> P2G
 
+// The env of a chunk: the kernel parameters' copy for a one-env handle, else the shared double buffer.
+template <bool ONE_ENV>
+__device__ __forceinline__ const EnvDesc& chunk_env(const TransferParams& p, const EnvDesc (&Es)[2], int it) {
+    if constexpr (ONE_ENV) return p.env0;
+    else return Es[it & 1];
+}
+
+// KIND: the material of every env (0 plasticine, 1 fluid) or -1 for a per-env choice at run time.
+// ONE_ENV: one env whose descriptor comes from the kernel parameters (constant bank operands) rather
+// than from shared memory, which keeps the single-scene kernel's register budget.
 // 7 resident CTAs per SM (72 registers): measured faster than 8, 9 or 10 CTAs with the spills a tighter
 // register budget forces, on both the 200k and the 600k pinch scene.
+template <int KIND, bool ONE_ENV>
 __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
     // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots
     // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
     __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
     __shared__ ScatterTile T;
-    __shared__ EnvDesc Es[2];  // the current chunk's env and the next one's
+    __shared__ EnvDesc Es[2];  // several envs: the current chunk's env and the next one's
     const int N = p.N;
     uint32_t flags = 0;
     wait_for_predecessor();
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
     int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
-    load_env(Es[0], p.envs, next.w);
-    __syncthreads();
+    if constexpr (!ONE_ENV) {
+        load_env(Es[0], p.envs, next.w);
+        __syncthreads();
+    }
     int it = 0;
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x, ++it) {
         const int4 ch = next;
-        const int env = ch.w;
-        const EnvDesc& E = Es[it & 1];
+        const int env = ONE_ENV ? 0 : ch.w;
+        const EnvDesc& E = chunk_env<ONE_ENV>(p, Es, it);
+        const int kind = KIND >= 0 ? KIND : E.kind;
         const Geometry& g = E.geo;
         const float dt = g.dt;
         if (w + gridDim.x < nchunks) next = p.chunks[w + gridDim.x];  // prefetch the next descriptor
@@ -652,7 +679,8 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
         }
         tile_clear(T);
         __syncthreads();
-        if (w + gridDim.x < nchunks) load_env(Es[(it + 1) & 1], p.envs, next.w);
+        if constexpr (!ONE_ENV)
+            if (w + gridDim.x < nchunks) load_env(Es[(it + 1) & 1], p.envs, next.w);
         float xn[3] = {0.0f, 0.0f, 0.0f}, vn[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
         float bp = 0.0f;
         uint32_t newkey = 0xffffffffu;
@@ -714,7 +742,7 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) Gm[a][c] = (a == c ? 1.0f : 0.0f) + dt * Cn[a][c];
             float tau[3][3];
-            if (E.kind == 0) {
+            if (kind == 0) {
                 float F[3][3], Ft[3][3];
                 load_mat(p.in.F, N, src, F);
 #pragma unroll
@@ -771,28 +799,51 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
     __syncthreads();
     if (last) {
         __threadfence();
-        scan_bins(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, p.chunk, warp_tot);
+        if (p.chunk == kChunk)
+            scan_bins<kChunk>(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, kChunk,
+                              warp_tot);
+        else
+            scan_bins<0>(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, p.chunk,
+                         warp_tot);
         if (threadIdx.x == 0) *p.done = 0u;
     }
 }
 
 // ------------------------------------------------------------------------ grid update
 
-// A persistent CTA of 256 threads works through the active bins, four at a time (one node per thread):
-// first the previous grid's bins (zeroed), then this grid's (updated). Each bin's env supplies its
-// geometry, gravity step and colliders; collider poses come from the table filled at mpm_set_colliders
-// (evaluated on the fly after kPoseSteps substeps).
+// A persistent CTA of 256 threads works through the active bins, four at a time (one node per thread,
+// so each warp holds half of one bin): first the previous grid's bins (zeroed), then this grid's
+// (updated). Each bin's env supplies its geometry and colliders. Collider poses of the substep are
+// evaluated by each CTA into shared memory when the handle has few colliders, else read from the table
+// filled at mpm_set_colliders (evaluated on the fly after kPoseSteps substeps). A body's impulse and
+// angular impulse are summed over the warp's nodes before one FP64 atomic per component.
+template <bool ONE_ENV>
+__device__ __forceinline__ const EnvDesc& bin_env_desc(const GridParams& p, int env) {
+    if constexpr (ONE_ENV) return p.env0;
+    else return p.envs[env];
+}
+
+template <bool ONE_ENV, bool SHARED_POSES>
 __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
-    const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
+    __shared__ ColliderNow cs[SHARED_POSES ? kSharedPoses : 1];
+    __shared__ float cw[SHARED_POSES ? kSharedPoses * 6 : 1];  // this CTA's wrench sums (few colliders)
+    const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63, lane = threadIdx.x & 31;
     const uint32_t step = *p.substep_counter;
+    constexpr bool shared_poses = SHARED_POSES;
+    if (shared_poses) {
+        if ((int)threadIdx.x < p.k_total) collider_at(p.cols[threadIdx.x], (float)step * p.dt, cs[threadIdx.x]);
+        if ((int)threadIdx.x < p.k_total * 6) cw[threadIdx.x] = 0.0f;
+        __syncthreads();
+    }
     const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
     constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
     for (uint32_t item = (uint32_t)(cta * 4 + grp); item < n_old + n_new; item += (uint32_t)(p.ctas * 4)) {
+        // item, and so env and bin, are uniform across each warp
         const bool is_old = item < n_old;
         const uint32_t entry = is_old ? p.list_old[item] : p.list[item - n_old];
         const int env = (int)(entry >> kLocalBinBits);
         const uint32_t lb = entry & kLocalMask;
-        const EnvDesc& E = p.envs[env];
+        const EnvDesc& E = bin_env_desc<ONE_ENV>(p, env);
         if (is_old) {
             p.grid_old[E.node_base + (size_t)lb * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (ln == 0) p.flags_old[E.bin_base + lb] = 0u;
@@ -801,59 +852,81 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         const Geometry& g = E.geo;
         float4* node = &p.grid[E.node_base + (size_t)lb * kBlkNodes + ln];
         const float4 gv = *node;
-        if (!(gv.x > 0.0f)) continue;
+        const bool has_mass = gv.x > 0.0f;
         const float m = gv.x;
-        const float im = 1.0f / m;
-        float v[3] = {gv.y * im + g.dt * p.gravity[0], gv.z * im + g.dt * p.gravity[1],
-                      gv.w * im + g.dt * p.gravity[2]};
+        const float im = has_mass ? 1.0f / m : 0.0f;
+        float v[3] = {gv.y * im + p.dt * p.gravity[0], gv.z * im + p.dt * p.gravity[1],
+                      gv.w * im + p.dt * p.gravity[2]};
         int bx, by, bz;
         decode_bin((int)lb, g.nb, bx, by, bz);
         const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
         const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
-        for (int c = E.col_first; c < E.col_first + E.col_count; ++c) {
+        const int c_end = __any_sync(0xffffffffu, has_mass) ? E.col_first + E.col_count : 0;
+        for (int c = E.col_first; c < c_end; ++c) {
             ColliderNow cn;
-            if (step < (uint32_t)kPoseSteps)
+            if (shared_poses)
+                cn = cs[c];
+            else if (step < (uint32_t)kPoseSteps)
                 cn = p.poses[(size_t)step * p.k_total + c];
             else
-                collider_at(p.cols[c], (float)step * g.dt, cn);
+                collider_at(p.cols[c], (float)step * p.dt, cn);
             float nrm[3];
             const float phi = collider_sdf(cn, xi, nrm);
-            if (!(phi < 0.0f)) continue;
             const float rel[3] = {xi[0] - cn.com[0], xi[1] - cn.com[1], xi[2] - cn.com[2]};
             const float vc[3] = {cn.lin[0] + cn.ang[1] * rel[2] - cn.ang[2] * rel[1],
                                  cn.lin[1] + cn.ang[2] * rel[0] - cn.ang[0] * rel[2],
                                  cn.lin[2] + cn.ang[0] * rel[1] - cn.ang[1] * rel[0]};
             const float vr[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
             const float vnrm = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
-            if (!(vnrm < 0.0f)) continue;
-            const float vt[3] = {vr[0] - vnrm * nrm[0], vr[1] - vnrm * nrm[1], vr[2] - vnrm * nrm[2]};
-            const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
-            const float mu = cn.friction;
-            float vnew[3];
-            if (tn <= -mu * vnrm) {
-                vnew[0] = vc[0]; vnew[1] = vc[1]; vnew[2] = vc[2];
-            } else {
-                const float s = 1.0f + mu * vnrm / tn;
-                vnew[0] = vc[0] + vt[0] * s; vnew[1] = vc[1] + vt[1] * s; vnew[2] = vc[2] + vt[2] * s;
+            const bool contact = has_mass && phi < 0.0f && vnrm < 0.0f;
+            float w6[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (contact) {
+                const float vt[3] = {vr[0] - vnrm * nrm[0], vr[1] - vnrm * nrm[1], vr[2] - vnrm * nrm[2]};
+                const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+                const float mu = cn.friction;
+                float vnew[3];
+                if (tn <= -mu * vnrm) {
+                    vnew[0] = vc[0]; vnew[1] = vc[1]; vnew[2] = vc[2];
+                } else {
+                    const float s = 1.0f + mu * vnrm / tn;
+                    vnew[0] = vc[0] + vt[0] * s; vnew[1] = vc[1] + vt[1] * s; vnew[2] = vc[2] + vt[2] * s;
+                }
+                const float imp[3] = {m * (v[0] - vnew[0]), m * (v[1] - vnew[1]), m * (v[2] - vnew[2])};
+                w6[0] = imp[0];
+                w6[1] = imp[1];
+                w6[2] = imp[2];
+                w6[3] = rel[1] * imp[2] - rel[2] * imp[1];
+                w6[4] = rel[2] * imp[0] - rel[0] * imp[2];
+                w6[5] = rel[0] * imp[1] - rel[1] * imp[0];
+                v[0] = vnew[0]; v[1] = vnew[1]; v[2] = vnew[2];
             }
-            const float imp[3] = {m * (v[0] - vnew[0]), m * (v[1] - vnew[1]), m * (v[2] - vnew[2])};
-            double* wr = p.wrench + (size_t)c * 6;
-            atomicAdd(&wr[0], (double)imp[0]);
-            atomicAdd(&wr[1], (double)imp[1]);
-            atomicAdd(&wr[2], (double)imp[2]);
-            atomicAdd(&wr[3], (double)(rel[1] * imp[2] - rel[2] * imp[1]));
-            atomicAdd(&wr[4], (double)(rel[2] * imp[0] - rel[0] * imp[2]));
-            atomicAdd(&wr[5], (double)(rel[0] * imp[1] - rel[1] * imp[0]));
-            v[0] = vnew[0]; v[1] = vnew[1]; v[2] = vnew[2];
+            if (__any_sync(0xffffffffu, contact)) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) w6[q] += __shfl_xor_sync(0xffffffffu, w6[q], off);
+                if (lane == 0) {
+                    if (shared_poses) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) atomicAdd(&cw[c * 6 + q], w6[q]);
+                    } else {
+                        double* wr = p.wrench + (size_t)c * 6;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) atomicAdd(&wr[q], (double)w6[q]);
+                    }
+                }
+            }
         }
+        if (!has_mass) continue;
         const int lo = p.bound, hi = g.n - p.bound;
         if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
         *node = make_float4(v[0], v[1], v[2], m);
     }
+    __syncthreads();
+    if (shared_poses && (int)threadIdx.x < p.k_total * 6 && cw[threadIdx.x] != 0.0f)
+        atomicAdd(&p.wrench[threadIdx.x], (double)cw[threadIdx.x]);
     // the last CTA to finish empties the previous grid's bin list (every CTA has read its count)
     __shared__ bool last;
-    __threadfence();
-    __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == (uint32_t)p.ctas - 1u;
     __syncthreads();
     if (last && threadIdx.x == 0) {
@@ -864,13 +937,14 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
 
 // The sort-assign of the state the previous fused pass wrote (first assign_ctas CTAs) and the grid
 // update of the transfer it scattered (the remaining CTAs): independent work, one launch.
+template <bool ONE_ENV, bool SHARED_POSES>
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
     wait_for_predecessor();  // (a CTA's exit releases the successor)
     if ((int)blockIdx.x < p.assign_ctas) {
         assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
         return;
     }
-    grid_update_cta(p.grid, blockIdx.x - p.assign_ctas);
+    grid_update_cta<ONE_ENV, SHARED_POSES>(p.grid, blockIdx.x - p.assign_ctas);
 }
 
 // ------------------------------------------------------------------------ readback
@@ -909,17 +983,24 @@ __global__ void __launch_bounds__(256) k_read_grid(Geometry g, const float4* __r
     out[t] = grid[node_index(i, j, k, g.nb)];
 }
 
-// The uploaded collider table (staged by the host), the wrench reset, and the pose table: pose of
-// collider c after s substeps for s < kPoseSteps (one thread per entry).
-__global__ void k_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
-                                double* wrench, uint32_t* counter, float dt) {
+// A collider upload of at most kSharedPoses bodies travels in the kernel parameters (no copy).
+__global__ void k_set_colliders_small(ColliderUpload u, ColliderSet* table, double* wrench, uint32_t* counter) {
+    const int t = threadIdx.x;
+    if (t < u.k) table[t] = u.c[t];
+    if (t < u.k * 6) wrench[t] = 0.0;
+    if (t == 0) *counter = 0u;
+}
+
+// After a larger upload (copied to the table): the wrench and substep count restart from zero, and the
+// pose table is filled: pose of collider c after s substeps for s < kPoseSteps (one thread per entry).
+__global__ void k_set_colliders(const ColliderSet* cols, int k, ColliderNow* poses, double* wrench,
+                                uint32_t* counter, float dt) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < k) table[t] = upload[t];
     if (t < k * 6) wrench[t] = 0.0;
     if (t == 0) *counter = 0u;
-    if (t < k * kPoseSteps) {
+    if (k > kSharedPoses && t < k * kPoseSteps) {
         const int s = t / k, c = t % k;
-        collider_at(upload[c], (float)s * dt, poses[t]);
+        collider_at(cols[c], (float)s * dt, poses[t]);
     }
 }
 
@@ -984,12 +1065,24 @@ cudaError_t launch_p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+using TransferKernel = void (*)(TransferParams);
+
+static TransferKernel g2p2g_variant(int kind_all, bool one_env) {
+    if (one_env) return kind_all == 1 ? k_g2p2g<1, true> : k_g2p2g<0, true>;
+    if (kind_all == 0) return k_g2p2g<0, false>;
+    if (kind_all == 1) return k_g2p2g<1, false>;
+    return k_g2p2g<-1, false>;
+}
+
 cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
-    return launch_dependent(k_g2p2g, grid_ctas, kChunk, s, p);
+    return launch_dependent(g2p2g_variant(p.kind_all, p.one_env != 0), grid_ctas, kChunk, s, p);
 }
 
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
-    return launch_dependent(k_assign_grid, p.assign_ctas + p.grid.ctas, 256, s, p);
+    const bool sp = p.grid.k_total <= kSharedPoses;
+    auto k = p.grid.one_env ? (sp ? k_assign_grid<true, true> : k_assign_grid<true, false>)
+                            : (sp ? k_assign_grid<false, true> : k_assign_grid<false, false>);
+    return launch_dependent(k, p.assign_ctas + p.grid.ctas, 256, s, p);
 }
 
 cudaError_t launch_read_state(int N, const EnvDesc* envs, int nenv, StateView src, float* x, float* v, float* C,
@@ -1005,10 +1098,16 @@ cudaError_t launch_read_grid(const Geometry& g, const float4* grid, float* out, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_colliders(const ColliderSet* upload, int k, ColliderSet* table, ColliderNow* poses,
-                                 double* wrench, uint32_t* counter, float dt, cudaStream_t s) {
-    const int threads = std::max(std::max(k * kPoseSteps, k * 6), 1);
-    k_set_colliders<<<ceil_div(threads, 256), 256, 0, s>>>(upload, k, table, poses, wrench, counter, dt);
+cudaError_t launch_set_colliders_small(const ColliderUpload& u, ColliderSet* table, double* wrench,
+                                       uint32_t* counter, cudaStream_t s) {
+    k_set_colliders_small<<<1, 128, 0, s>>>(u, table, wrench, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* poses, double* wrench,
+                                 uint32_t* counter, float dt, cudaStream_t s) {
+    const int threads = std::max(k > kSharedPoses ? k * kPoseSteps : k * 6, 1);
+    k_set_colliders<<<ceil_div(threads, 256), 256, 0, s>>>(cols, k, poses, wrench, counter, dt);
     return cudaGetLastError();
 }
 
@@ -1017,9 +1116,9 @@ cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int transfer_ctas_per_sm(bool fused) {
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env) {
     int n = 0;
-    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_g2p2g, kChunk, 0)
+    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, g2p2g_variant(kind_all, one_env), kChunk, 0)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g, kChunk, 0);
     if (e != cudaSuccess || n < 1) n = 1;
     return n;

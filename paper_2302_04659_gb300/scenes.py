@@ -340,3 +340,33 @@ def concat_tool_states(envs: list, t: float):
         z = np.zeros((0, 3), np.float32)
         return np.zeros((0, 7), np.float32), z, z, z
     return tuple(np.ascontiguousarray(np.concatenate([p[i] for p in parts])) for i in range(4))
+
+
+class ToolPaths:
+    """The scripted collider paths of many envs stacked into arrays: ``at(t)`` gives the concatenated
+    collider inputs of all envs (the same values as ``concat_tool_states``) in one vectorised pass."""
+
+    def __init__(self, envs: list):
+        c0, axis, amp, freq, quat = [], [], [], [], []
+        for sc in envs:
+            s = sc.script
+            for i in range(len(sc.shapes)):
+                c0.append(s["c0"][i])
+                axis.append(s["axis"][i] if "axis" in s else (s["dir"][i], 0.0, 0.0))
+                amp.append(s["amp"][i])
+                freq.append(s["freq"][i])
+                quat.append(s["quat"][i])
+        self.k = len(c0)
+        self.c0 = np.asarray(c0, np.float64).reshape(-1, 3)
+        self.axis = np.asarray(axis, np.float64).reshape(-1, 3)
+        self.amp = np.asarray(amp, np.float64)
+        self.freq = np.asarray(freq, np.float64)
+        self.quat = np.asarray(quat, np.float64).reshape(-1, 4)
+
+    def at(self, t: float):
+        ph = 2 * math.pi * self.freq * t
+        pos = self.c0 + self.axis * (self.amp * (1.0 - np.cos(ph)) / 2.0)[:, None]
+        lin = self.axis * (self.amp * math.pi * self.freq * np.sin(ph))[:, None]
+        pose = np.concatenate([pos, self.quat], axis=1).astype(np.float32)
+        return (np.ascontiguousarray(pose), np.ascontiguousarray(lin.astype(np.float32)),
+                np.zeros((self.k, 3), np.float32), np.ascontiguousarray(pos.astype(np.float32)))

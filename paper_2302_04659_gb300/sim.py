@@ -131,6 +131,7 @@ class Sim(_Handle):
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             self.handle = mpm.mpm_create(self.cfg, self.mat, self.workspace.data_ptr(), nbytes, _stream())
         self.n = n
+        self.kinds = [material.kind]
         self.k = 0
 
     def set_particles(self, x, v=None, C=None, F=None, stream=None):
@@ -172,6 +173,7 @@ class BatchSim(_Handle):
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             self.handle = mpm.mpm_create_batch(self.cfg, self.env_specs, self.workspace.data_ptr(), nbytes, _stream())
         self.ns = [int(e[0]) for e in envs]
+        self.kinds = [int(e[1].kind) for e in envs]
         self.counts = [0] * len(envs)
         self.shape_counts = [0] * len(envs)
         self.k = 0

@@ -231,3 +231,29 @@ def test_batch_capacity_and_argument_errors():
     with pytest.raises(_native.MpmError):
         sim.set_colliders(pose[:-1], lin[:-1], ang[:-1], com[:-1])
     sim.close()
+
+
+def test_many_colliders_pose_table_matches_single_handles():
+    """20 envs with a tool each (more colliders than the grid update keeps per CTA): poses come from the
+    table filled at upload for 64 substeps, then are evaluated on the fly; 70 substeps against single
+    handles, whose few colliders are posed per CTA."""
+    envs = [scenes.tool_scene(400 + e, scenes.PLASTICINE if e % 2 == 0 else scenes.FLUID, 600 + 37 * e, n=24)
+            for e in range(20)]
+    t = 0.12
+    out, counts, wr, nsub, _ = run_batch(envs, 70, t=t)
+    assert nsub == 70
+    hit = 0
+    for e, (sc, got) in enumerate(zip(envs, split(out, counts))):
+        sim = make_sim(sc)
+        sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+        sim.set_shapes(sc.shapes)
+        sim.set_colliders(*scenes.finger_state(sc, t))
+        sim.substep(70)
+        ref = sim.read_state(on_device=False)
+        wref, _ = sim.read_wrench()
+        sim.close()
+        assert rel(got["x"], ref["x"]) <= 1e-5
+        scale = max(np.abs(wref).max(), 1e-3)
+        assert np.abs(wr[e:e + 1] - wref).max() <= 1e-3 * scale
+        hit += np.abs(wref).max() > 1e-3
+    assert hit >= 5, "several tools should push their bodies"
