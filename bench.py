@@ -332,7 +332,7 @@ def run_native(args):
     return line
 
 
-def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune: bool):
+def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune: bool, nenv: int = 0):
     """A batched workload in one handle: all envs advance together, one graph replay per env step.
 
     ``batch256``: 256 envs, 64^3 grids, 20k-120k particles (uniform, seeded), plasticine and fluid
@@ -349,7 +349,10 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
     from paper_2302_04659_gb300.sim import BatchSim, Sim
 
     t_gen = time.perf_counter()
-    envs = scenes.batch_workload(256, 3000) if which == "batch256" else scenes.serving_workload(1024, 5000)
+    if which == "batch256":
+        envs = scenes.batch_workload(nenv or 256)
+    else:
+        envs = scenes.serving_workload(nenv or 1024)
     counts, (x, v, C, F) = scenes.concat_states(envs)
     t_gen = time.perf_counter() - t_gen
     sc0 = envs[0]
@@ -595,11 +598,24 @@ def main():
     ap.add_argument("--particles", type=int, default=200_000, help="particles of the pinch scene")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving workloads")
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
+    ap.add_argument("--only", choices=["batched", "serving"], default=None,
+                    help="run one batched workload alone and print its section (profiling runs)")
+    ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
+    ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        import torch
+        from paper_2302_04659_gb300 import build as b
+        b.build()
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps, 3,
+                          per_scene=False, tune=not args.no_tune, nenv=args.envs)
+        print(json.dumps(out), flush=True)
     else:
         run_native(args)
 

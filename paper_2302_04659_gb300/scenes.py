@@ -242,19 +242,24 @@ def box_particles(N: int, lower, size, seed: int) -> np.ndarray:
 def tool_scene(seed: int, kind: int, N: int, n: int = 64, extra_capsule: bool = False) -> Scene:
     """One environment of the batched workloads: a body on the floor band and a moving box tool.
 
+    The tool is a box with half extents ~ U[0.03, 0.08]^3 and friction 0.5, moving along a seeded
+    direction (a main axis plus lateral components ~ U[-0.3, 0.3], normalised) as
+    c0 + d A (1 - cos 2 pi f t) / 2, A ~ U[0.05, 0.12], f ~ U[1, 3] Hz.
     Plasticine: a seeded ellipsoid (semi-axes ~ U[0.12, 0.2]^3, centred in x and z, resting on the band
-    at 3 dx) pressed by a flat box (half extents 0.06, 0.02, 0.05) that starts 0.01 above it and moves
-    down and back, c0 - y A (1 - cos 2 pi f t) / 2, A ~ U[0.05, 0.12], f ~ U[1, 3] Hz.
-    Fluid: a seeded block of water (sides ~ U[0.3, 0.4] x U[0.12, 0.2] x U[0.3, 0.4]) stirred by a
-    paddle box (half extents 0.02, 0.08, 0.08) that starts 0.01 outside the block's -x side, its bottom
-    0.03 above the band (off the node lattice for every grid size used), and sweeps along +x with the same law. Friction 0.5 for both tools. With
-    ``extra_capsule`` a capsule finger (radius 0.02, half length 0.05, along x) closes in from the +x
+    at 3 dx); the tool starts 0.01 above it and presses down (main axis -y). Tool centres are offset by
+    U[-0.02, 0.02] in x and z from the mid-plane (no node sits where the box's face normal flips sign).
+    Fluid: a seeded block of water (half extents ~ U[0.1, 0.2]^3, centred in x and z, on the band); the
+    tool starts 0.01 outside its -x face, its bottom 0.03 above the band, and sweeps along +x.
+    With ``extra_capsule`` a capsule finger (radius 0.02, half length 0.05, along x) closes in from the +x
     side at mid height, as in the pinch scene.
     """
     dx = 1.0 / n
-    u = uniform(seed, 12, offset=0)
+    u = uniform(seed, 16, offset=0)
     A = 0.05 + 0.07 * u[3]
     f = 1.0 + 2.0 * u[4]
+    half = tuple(float(h) for h in 0.03 + 0.05 * u[7:10])
+    lateral = -0.3 + 0.6 * u[10:12]
+    off = 0.04 * (u[12:14] - 0.5)  # tool centre off the mid-plane nodes (no sign ties inside the box)
     q_id = [1.0, 0.0, 0.0, 0.0]
     floor = 3 * dx
     if kind == PLASTICINE:
@@ -263,20 +268,20 @@ def tool_scene(seed: int, kind: int, N: int, n: int = 64, extra_capsule: bool = 
         x = ellipsoid_particles(N, center, semi, seed=seed + 1)
         vol = 4.0 / 3.0 * math.pi * semi[0] * semi[1] * semi[2]
         mat = Material(PLASTICINE, rho=1e3, E=5e3, nu=0.3, yield_stress=50.0, p_vol=vol / max(N, 1))
-        half = (0.06, 0.02, 0.05)  # unequal x, z: no interior node ties between the nearest faces
-        c0 = [(0.5, center[1] + semi[1] + 0.01 + half[1], 0.5)]
-        axis = [(0.0, -1.0, 0.0)]
+        c0 = [(0.5 + off[0], center[1] + semi[1] + 0.01 + half[1], 0.5 + off[1])]
+        d = np.array([lateral[0], -1.0, lateral[1]])
         mid_y, side_x = center[1], 0.5 + semi[0]
     else:
-        size = (0.3 + 0.1 * u[0], 0.12 + 0.08 * u[1], 0.3 + 0.1 * u[2])
-        lower = (0.5 - size[0] / 2, floor, 0.5 - size[2] / 2)
+        hw = 0.1 + 0.1 * u[0:3]
+        lower = (0.5 - hw[0], floor, 0.5 - hw[2])
+        size = 2.0 * hw
         x = box_particles(N, lower, size, seed=seed + 1)
-        vol = size[0] * size[1] * size[2]
+        vol = float(np.prod(size))
         mat = Material(FLUID, rho=1e3, bulk_modulus=1e4, p_vol=vol / max(N, 1))
-        half = (0.02, 0.08, 0.08)
-        c0 = [(lower[0] - half[0] - 0.01, floor + 0.03 + half[1], 0.5)]
-        axis = [(1.0, 0.0, 0.0)]
-        mid_y, side_x = floor + size[1] / 2, lower[0] + size[0]
+        c0 = [(lower[0] - half[0] - 0.01, floor + 0.03 + half[1], 0.5 + off[1])]
+        d = np.array([1.0, lateral[0], lateral[1]])
+        mid_y, side_x = floor + hw[1], lower[0] + size[0]
+    axis = [tuple(d / np.linalg.norm(d))]
     shapes = [Shape(BOX, half, 0.5)]
     quat = [q_id]
     amp, freq = [A], [f]
@@ -306,16 +311,16 @@ def batch_counts(nenv: int, seed: int, lo: int, hi: int, log_uniform: bool = Fal
     return np.clip(np.floor(c), lo, hi).astype(np.int64)
 
 
-def batch_workload(nenv: int = 256, seed: int = 3000, n: int = 64, lo: int = 20_000, hi: int = 120_000,
+def batch_workload(nenv: int = 256, seed: int = 2000, n: int = 64, lo: int = 20_000, hi: int = 120_000,
                    counts=None) -> list:
-    """Many independent envs with their own n^3 grids: counts uniform in [lo, hi] from the seed, even envs
-    plasticine and odd envs fluid, one moving box tool each (``tool_scene``)."""
+    """Many independent envs with their own n^3 grids: counts uniform in [lo, hi] from the seed, the first
+    half plasticine and the second half fluid, one moving box tool each (``tool_scene``)."""
     counts = batch_counts(nenv, seed, lo, hi) if counts is None else counts
-    return [tool_scene(seed + 7919 * (e + 1), PLASTICINE if e % 2 == 0 else FLUID, int(counts[e]), n)
+    return [tool_scene(seed + 7919 * (e + 1), PLASTICINE if e < nenv // 2 else FLUID, int(counts[e]), n)
             for e in range(nenv)]
 
 
-def serving_workload(nenv: int = 1024, seed: int = 5000, lo: int = 2_000, hi: int = 200_000,
+def serving_workload(nenv: int = 1024, seed: int = 3000, lo: int = 2_000, hi: int = 200_000,
                      grids=(48, 64, 80, 96)) -> list:
     """The serving mix: counts log-uniform in [lo, hi], grid sizes drawn from ``grids``, plasticine and
     fluid alternating, each env with a box tool and a capsule finger."""
