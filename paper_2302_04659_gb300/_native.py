@@ -22,6 +22,7 @@ MPM_FLAG_SV_CLAMPED = 0x4
 MPM_FLAG_FAR_MOVE = 0x8
 MPM_FLAG_INTERNAL = 0x80000000
 MPM_PLASTICINE, MPM_FLUID = 0, 1
+MPM_NET_F32, MPM_NET_BF16 = 0, 1
 MPM_BOX, MPM_CAPSULE = 0, 1
 (MPM_K_LOAD, MPM_K_SCAN, MPM_K_ASSIGN, MPM_K_P2G, MPM_K_GRID, MPM_K_G2P2G, MPM_K_READ,
  MPM_K_COLLIDERS, MPM_K_COUNT) = range(9)
@@ -97,6 +98,14 @@ def _load():
         "mpm_destroy": (None, [_vp]),
         "mpm_p2g_static": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.c_int, _vp, _vp, _vp,
                                 _vp, _vp, _vp]),
+        "mpm_conv3d_forward": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+        "mpm_conv3d_backward_data": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp]),
+        "mpm_conv3d_backward_weight": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp]),
+        "mpm_mse_loss": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
+        "mpm_adam_step": (st, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, _vp, _vp]),
+        "mpm_cast_f32_to_bf16": (st, [ctypes.c_int, _vp, _vp, _vp]),
+        "mpm_cast_bf16_to_f32": (st, [ctypes.c_int, _vp, _vp, _vp]),
         "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mpm_last_error": (ctypes.c_char_p, []),
     }
@@ -259,3 +268,36 @@ def mpm_p2g_static(cfg: mpm_config, mat: mpm_material, n: int, x: int, v: int = 
 
 def mpm_last_error() -> str:
     return _load().mpm_last_error().decode()
+
+
+# ---------------------------------------------------------------------------- network kernels (mpm_net.h)
+
+def mpm_conv3d_forward(dtype, D, H, W, cin, cout, x, w, bias, relu, y_f32, y, stream=0):
+    _check("mpm_conv3d_forward", _load().mpm_conv3d_forward(dtype, D, H, W, cin, cout, x, w, bias or None, relu,
+                                                            y_f32, y, stream))
+
+
+def mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w, act_in, dx, stream=0):
+    _check("mpm_conv3d_backward_data", _load().mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w,
+                                                                        act_in or None, dx, stream))
+
+
+def mpm_conv3d_backward_weight(dtype, D, H, W, cin, cout, x, dy, dw, db, stream=0):
+    _check("mpm_conv3d_backward_weight", _load().mpm_conv3d_backward_weight(dtype, D, H, W, cin, cout, x, dy, dw,
+                                                                            db, stream))
+
+
+def mpm_mse_loss(dtype, nvox, C, pred, pred_f32, target, mask, loss, dpred, stream=0):
+    _check("mpm_mse_loss", _load().mpm_mse_loss(dtype, nvox, C, pred, pred_f32, target, mask, loss, dpred, stream))
+
+
+def mpm_adam_step(n, p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=0, stream=0):
+    _check("mpm_adam_step", _load().mpm_adam_step(n, p, g, m, v, t, lr, beta1, beta2, eps, p_bf16 or None, stream))
+
+
+def mpm_cast_f32_to_bf16(n, src, dst, stream=0):
+    _check("mpm_cast_f32_to_bf16", _load().mpm_cast_f32_to_bf16(n, src, dst, stream))
+
+
+def mpm_cast_bf16_to_f32(n, src, dst, stream=0):
+    _check("mpm_cast_bf16_to_f32", _load().mpm_cast_bf16_to_f32(n, src, dst, stream))

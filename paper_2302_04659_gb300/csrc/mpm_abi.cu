@@ -17,13 +17,17 @@
 using namespace mpm;
 
 namespace {
-
 thread_local char g_last_error[256] = "";
+}  // namespace
 
-mpm_status cuda_fail(cudaError_t e, const char* what) {
+mpm_status mpm::record_cuda_error(cudaError_t e, const char* what) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
     return MPM_ERR_CUDA;
 }
+
+namespace {
+
+mpm_status cuda_fail(cudaError_t e, const char* what) { return record_cuda_error(e, what); }
 
 #define MPM_CUDA(call, what)                               \
     do {                                                   \

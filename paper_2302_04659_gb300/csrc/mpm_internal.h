@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mpm.h"
 #include "mpm_device.cuh"
 
 namespace mpm {
@@ -151,6 +152,9 @@ struct LoadParams {  // mpm_set_particles*: copy in, clamp, bin keys and ranks
     uint32_t* hist;
     uint32_t* status;
 };
+
+// Record a CUDA error for mpm_last_error(); returns MPM_ERR_CUDA (mpm_abi.cu).
+mpm_status record_cuda_error(cudaError_t e, const char* what);
 
 // launch wrappers (mpm_kernels.cu); each returns cudaGetLastError() after enqueueing
 cudaError_t launch_load(const LoadParams& p, cudaStream_t s);

@@ -112,3 +112,21 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), fn
                 assert "mpm_oracle" not in src, fn
+
+
+def test_network_arguments_rejected_on_host(lib):
+    """Bad sizes and channel counts return MPM_ERR_INVALID_ARG before any device work."""
+    cases = [
+        lambda: lib.mpm_conv3d_forward(lib.MPM_NET_BF16, 0, 4, 4, 32, 32, 1, 1, 0, 0, 0, 1),
+        lambda: lib.mpm_conv3d_forward(lib.MPM_NET_BF16, 4, 4, 4, 65, 32, 1, 1, 0, 0, 0, 1),
+        lambda: lib.mpm_conv3d_forward(7, 4, 4, 4, 32, 32, 1, 1, 0, 0, 0, 1),
+        lambda: lib.mpm_conv3d_backward_data(lib.MPM_NET_F32, 4, -1, 4, 32, 32, 1, 1, 0, 1),
+        lambda: lib.mpm_conv3d_backward_weight(lib.MPM_NET_BF16, 4, 4, 4, 40, 32, 1, 1, 1, 1),
+        lambda: lib.mpm_mse_loss(lib.MPM_NET_BF16, 0, 3, 1, 1, 1, 1, 1, 1),
+        lambda: lib.mpm_adam_step(10, 1, 1, 1, 1, 0, 1e-3),
+    ]
+    for case in cases:
+        with pytest.raises(lib.MpmError) as e:
+            case()
+        assert e.value.status == lib.MPM_ERR_INVALID_ARG
+
