@@ -40,6 +40,7 @@
 #define MPM_GB300_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -222,6 +223,43 @@ long long mpm_launch_count(const mpm_sim* sim);
  * Enqueued on `stream`, no host synchronization; allocates nothing. */
 mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* mat, int n, const float* x, const float* v,
                           const float* C, const float* F, float* grid_out, void* stream);
+
+/* ---- Learned-surrogate window. An extension of the method (the paper's simulator has no learned
+ * component): k substeps are replaced by one plain grid update (gravity, colliders, sticky walls, as in
+ * mpm_substep), a correction dv of the updated node velocities computed by the caller's network, and one
+ * grid-to-particle transfer with time step k*dt (advection, C, and F <- (I + k dt C) F with the return
+ * map), followed by the particle-to-grid transfer of the new state. One-env handles only
+ * (MPM_ERR_INVALID_ARG otherwise). Boxes are in grid-node indices (axis order i, j, k of the grid). */
+typedef struct {
+    int i0, j0, k0; /* first node of the box (may be negative: nodes outside the grid read as empty) */
+    int D, H, W;    /* nodes along i, j, k */
+} mpm_box;
+
+/* Bounding box of the grid nodes with mass (the active 4^3 bins) of the current state, grown by
+ * `margin` nodes on every side and clamped to the grid. Synchronizes `stream`. */
+mpm_status mpm_surrogate_box(mpm_sim* sim, int margin, mpm_box* box, void* stream);
+
+/* Start a window: the sort-assign and the plain grid update of the current state, then the network
+ * input over `box`: d_feat (float[D*H*W][4], 16-byte aligned) = (m * m_scale, v_x, v_y, v_z * v_scale)
+ * of the updated nodes, channels-last with i slowest; d_mask (one byte per node) = m > 0. Enqueued
+ * only. Until mpm_surrogate_advance ends the window, mpm_substep is refused. */
+mpm_status mpm_surrogate_features(mpm_sim* sim, const mpm_box* box, float m_scale, float v_scale, float* d_feat,
+                                  uint8_t* d_mask, void* stream);
+
+/* The fallback gate of a started window, for the correction d_dv (float[D*H*W][3]; velocity change =
+ * d_dv * dv_unit at nodes with mass; zero in the sticky wall band). Writes out[0] = mass residual
+ * |sum_i m_i - sum_p m_p| / sum_p m_p, out[1] = momentum residual |P_hat - P_exp| / (M v_ref), where
+ * P_hat is the momentum of the corrected nodes and P_exp = P_0 + (k + 1)/2 (P_1 - P_0) the first-order
+ * mean momentum over k substeps from the momentum before (P_0) and after (P_1) one plain grid update;
+ * out[2] = M, out[3] = |P_hat - P_exp|. Synchronizes `stream`. */
+mpm_status mpm_surrogate_check(mpm_sim* sim, const mpm_box* box, const float* d_dv, float dv_unit, int k,
+                               double v_ref, double* out, void* stream);
+
+/* End a window. With d_dv: apply the correction, then one grid-to-particle pass with time step k*dt;
+ * body impulses of the window are the first substep's times k; the substep counter advances by k.
+ * With d_dv == NULL (the fallback): the plain grid-to-particle pass and k - 1 plain substeps. */
+mpm_status mpm_surrogate_advance(mpm_sim* sim, const mpm_box* box, const float* d_dv, float dv_unit, int k,
+                                 void* stream);
 
 /* Release the host handle (the workspace stays the caller's). Safe on NULL. Does not synchronize:
  * the caller must not free the workspace before work enqueued on it has finished. */

@@ -36,6 +36,42 @@ enum { MPM_NET_F32 = 0, MPM_NET_BF16 = 1 };
 mpm_status mpm_conv3d_forward(int dtype, int D, int H, int W, int cin, int cout, const void* x, const void* w,
                               const float* bias, int relu, int y_f32, void* y, void* stream);
 
+/* Tiled forward (BF16 only): the forward pass over tiles of 4 x 8 x 8 voxels (D, H, W), computing only the
+ * tiles whose byte in tile_flags is nonzero and writing zeros to the others. Tiles are numbered
+ * ((tz * ty_count) + ty) * tx_count + tx with tx along W; mpm_conv3d_tile_count gives their number. */
+mpm_status mpm_conv3d_forward_tiled(int D, int H, int W, int cin, int cout, const void* x, const void* w,
+                                    const float* bias, int relu, int y_f32, void* y, const uint8_t* tile_flags,
+                                    void* stream);
+int mpm_conv3d_tile_count(int D, int H, int W);
+
+/* Tile flags from a voxel mask (one byte per voxel): a tile is flagged if any voxel of it (dilate = 0),
+ * or of it and its 26 neighbouring tiles (dilate = 1), is nonzero. flags: mpm_conv3d_tile_count bytes. */
+mpm_status mpm_conv3d_tile_flags(int D, int H, int W, const uint8_t* mask, int dilate, uint8_t* flags,
+                                 void* stream);
+
+/* Forward pass on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulators in tensor memory), BF16
+ * in and out (FP32 out when y_f32 != 0). cin: 4, 16 or 32; cout: 1..32. The weights are given packed
+ * (mpm_conv3d_pack_tc). Tiles are 1 x 16 x 8 voxels (D, H, W); with tile_dist (may be NULL, see
+ * mpm_conv3d_tc_tile_dist) only tiles at distance <= radius are computed and the others written as
+ * zeros. x and w_packed 16-byte aligned. A wait that runs out records an error word readable with
+ * mpm_net_tc_status; the call returns normally. */
+mpm_status mpm_conv3d_forward_tc(int D, int H, int W, int cin, int cout, const void* x, const void* w_packed,
+                                 const float* bias, int relu, int y_f32, void* y, const uint8_t* tile_dist,
+                                 int radius, void* stream);
+
+/* Bytes of a layer's packed weights (0 for unsupported channel counts), and the packing of w
+ * ([27][cout][cin] BF16) into that layout. */
+int mpm_conv3d_tc_packed_bytes(int cin, int cout);
+mpm_status mpm_conv3d_pack_tc(int cin, int cout, const void* w, void* packed, void* stream);
+
+/* Tiles of the tensor-core forward over a D x H x W box, and per tile the Chebyshev distance (in voxels,
+ * capped at 5) from the tile to the nearest voxel whose mask byte is set. dist: one byte per tile. */
+int mpm_conv3d_tc_tile_count(int D, int H, int W);
+mpm_status mpm_conv3d_tc_tile_dist(int D, int H, int W, const uint8_t* mask, uint8_t* dist, void* stream);
+
+/* The tensor-core kernels' error word (nonzero: a wait ran out); clear != 0 resets it. Synchronizes. */
+mpm_status mpm_net_tc_status(unsigned* flags, int clear, void* stream);
+
 /* Input gradient (the adjoint of the forward map in x): dx[q][ci] = sum_{t,co} dy[q - o_t][co] w[t][co][ci],
  * multiplied by (act_in[q][ci] > 0) when act_in != NULL (the ReLU of the layer that produced x).
  * dy: D*H*W*cout, act_in and dx: D*H*W*cin, of `dtype`. */

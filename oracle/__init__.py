@@ -317,3 +317,33 @@ def rollout(params: Params, s: State, nsub: int, colliders=(), t0: float = 0.0, 
         ncl, wrench, _ = substep(params, s, colliders, t0 + k * params.dt, wrench)
         total += ncl
     return total, wrench
+
+
+def surrogate_window(params: Params, s: State, dv, box, unit: float, k: int, colliders=(), t: float = 0.0):
+    """One learned-surrogate window written out with the steps above (the surrogate is this project's
+    extension; the paper has no learned component): the transfer of the state (step A1+A2), one grid
+    update with the substep's dt (A3), the correction v += dv * unit at nodes with mass inside ``box``
+    (zero in the sticky wall band), then grid-to-particle (A4+A5) with time step k*dt, in place on ``s``.
+
+    dv: (D, H, W, 3) over box = (i0, j0, k0, D, H, W) in node indices. Returns a dict of the grid sums the
+    fallback gate compares: M, P0 (before the grid update), P1 (after), P_hat (after the correction)."""
+    n = params.n
+    g0 = p2g(params, s)                       # (m, m v)
+    g1, _, _ = grid_update(params, g0, colliders, t)  # (m, v)
+    g2 = g1.copy()
+    i0, j0, k0, D, H, W = box
+    band = params.bound
+    for i in range(max(i0, 0), min(i0 + D, n)):
+        for j in range(max(j0, 0), min(j0 + H, n)):
+            for kk in range(max(k0, 0), min(k0 + W, n)):
+                if not g1[i, j, kk, 0] > 0.0:
+                    continue
+                v = g1[i, j, kk, 1:] + unit * np.asarray(dv[i - i0, j - j0, kk - k0], np.float64)
+                if min(i, j, kk) < band or max(i, j, kk) >= n - band:
+                    v = np.zeros(3)
+                g2[i, j, kk, 1:] = v
+    big = Params(**{**params.__dict__, "dt": params.dt * k})
+    g2p(big, g2, s)
+    return {"M": g0[..., 0].sum(), "P0": g0[..., 1:].reshape(-1, 3).sum(axis=0),
+            "P1": (g1[..., :1] * g1[..., 1:]).reshape(-1, 3).sum(axis=0),
+            "P_hat": (g2[..., :1] * g2[..., 1:]).reshape(-1, 3).sum(axis=0)}

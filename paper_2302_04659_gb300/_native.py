@@ -50,6 +50,14 @@ class mpm_env(ctypes.Structure):
                 ("material", mpm_material)]
 
 
+class mpm_box(ctypes.Structure):
+    _fields_ = [("i0", ctypes.c_int), ("j0", ctypes.c_int), ("k0", ctypes.c_int), ("D", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int)]
+
+    def dims(self):
+        return (self.D, self.H, self.W)
+
+
 class MpmError(RuntimeError):
     def __init__(self, fn, status, detail=""):
         self.status = status
@@ -99,6 +107,17 @@ def _load():
         "mpm_p2g_static": (st, [ctypes.POINTER(mpm_config), ctypes.POINTER(mpm_material), ctypes.c_int, _vp, _vp, _vp,
                                 _vp, _vp, _vp]),
         "mpm_conv3d_forward": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+        "mpm_conv3d_forward_tiled": (st, [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                                               _vp]),
+        "mpm_conv3d_tile_count": (ctypes.c_int, [ctypes.c_int] * 3),
+        "mpm_conv3d_tile_flags": (st, [ctypes.c_int] * 3 + [_vp, ctypes.c_int, _vp, _vp]),
+        "mpm_conv3d_forward_tc": (st, [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                                            ctypes.c_int, _vp]),
+        "mpm_conv3d_tc_packed_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+        "mpm_conv3d_pack_tc": (st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+        "mpm_conv3d_tc_tile_count": (ctypes.c_int, [ctypes.c_int] * 3),
+        "mpm_conv3d_tc_tile_dist": (st, [ctypes.c_int] * 3 + [_vp, _vp, _vp]),
+        "mpm_net_tc_status": (st, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int, _vp]),
         "mpm_conv3d_backward_data": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp]),
         "mpm_conv3d_backward_weight": (st, [ctypes.c_int] * 6 + [_vp, _vp, _vp, _vp, _vp]),
         "mpm_mse_loss": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
@@ -106,6 +125,11 @@ def _load():
                                ctypes.c_float, ctypes.c_float, _vp, _vp]),
         "mpm_cast_f32_to_bf16": (st, [ctypes.c_int, _vp, _vp, _vp]),
         "mpm_cast_bf16_to_f32": (st, [ctypes.c_int, _vp, _vp, _vp]),
+        "mpm_surrogate_box": (st, [_vp, ctypes.c_int, ctypes.POINTER(mpm_box), _vp]),
+        "mpm_surrogate_features": (st, [_vp, ctypes.POINTER(mpm_box), ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
+        "mpm_surrogate_check": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), _vp]),
+        "mpm_surrogate_advance": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, _vp]),
         "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mpm_last_error": (ctypes.c_char_p, []),
     }
@@ -277,6 +301,46 @@ def mpm_conv3d_forward(dtype, D, H, W, cin, cout, x, w, bias, relu, y_f32, y, st
                                                             y_f32, y, stream))
 
 
+def mpm_conv3d_forward_tiled(D, H, W, cin, cout, x, w, bias, relu, y_f32, y, tile_flags, stream=0):
+    _check("mpm_conv3d_forward_tiled", _load().mpm_conv3d_forward_tiled(D, H, W, cin, cout, x, w, bias or None, relu,
+                                                                        y_f32, y, tile_flags, stream))
+
+
+def mpm_conv3d_forward_tc(D, H, W, cin, cout, x, w_packed, bias, relu, y_f32, y, tile_dist=0, radius=0, stream=0):
+    _check("mpm_conv3d_forward_tc", _load().mpm_conv3d_forward_tc(D, H, W, cin, cout, x, w_packed, bias or None, relu,
+                                                                  y_f32, y, tile_dist or None, radius, stream))
+
+
+def mpm_conv3d_tc_packed_bytes(cin, cout) -> int:
+    return _load().mpm_conv3d_tc_packed_bytes(cin, cout)
+
+
+def mpm_conv3d_pack_tc(cin, cout, w, packed, stream=0):
+    _check("mpm_conv3d_pack_tc", _load().mpm_conv3d_pack_tc(cin, cout, w, packed, stream))
+
+
+def mpm_conv3d_tc_tile_count(D, H, W) -> int:
+    return _load().mpm_conv3d_tc_tile_count(D, H, W)
+
+
+def mpm_conv3d_tc_tile_dist(D, H, W, mask, dist, stream=0):
+    _check("mpm_conv3d_tc_tile_dist", _load().mpm_conv3d_tc_tile_dist(D, H, W, mask, dist, stream))
+
+
+def mpm_net_tc_status(clear=0, stream=0) -> int:
+    f = ctypes.c_uint(0)
+    _check("mpm_net_tc_status", _load().mpm_net_tc_status(ctypes.byref(f), clear, stream))
+    return f.value
+
+
+def mpm_conv3d_tile_count(D, H, W) -> int:
+    return _load().mpm_conv3d_tile_count(D, H, W)
+
+
+def mpm_conv3d_tile_flags(D, H, W, mask, dilate, flags, stream=0):
+    _check("mpm_conv3d_tile_flags", _load().mpm_conv3d_tile_flags(D, H, W, mask, dilate, flags, stream))
+
+
 def mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w, act_in, dx, stream=0):
     _check("mpm_conv3d_backward_data", _load().mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w,
                                                                         act_in or None, dx, stream))
@@ -301,3 +365,29 @@ def mpm_cast_f32_to_bf16(n, src, dst, stream=0):
 
 def mpm_cast_bf16_to_f32(n, src, dst, stream=0):
     _check("mpm_cast_bf16_to_f32", _load().mpm_cast_bf16_to_f32(n, src, dst, stream))
+
+
+# ---------------------------------------------------------------------------- surrogate window (mpm.h)
+
+def mpm_surrogate_box(sim, margin, stream=0) -> mpm_box:
+    b = mpm_box()
+    _check("mpm_surrogate_box", _load().mpm_surrogate_box(sim, margin, ctypes.byref(b), stream))
+    return b
+
+
+def mpm_surrogate_features(sim, box: mpm_box, m_scale, v_scale, feat, mask, stream=0):
+    _check("mpm_surrogate_features", _load().mpm_surrogate_features(sim, ctypes.byref(box), m_scale, v_scale, feat,
+                                                                    mask, stream))
+
+
+def mpm_surrogate_check(sim, box: mpm_box, dv, dv_unit, k, v_ref, stream=0):
+    """Returns (mass residual, momentum residual, grid mass, |P_hat - P_exp|)."""
+    out = (ctypes.c_double * 4)()
+    _check("mpm_surrogate_check", _load().mpm_surrogate_check(sim, ctypes.byref(box), dv, dv_unit, k, v_ref, out,
+                                                              stream))
+    return tuple(out)
+
+
+def mpm_surrogate_advance(sim, box: mpm_box, dv, dv_unit, k, stream=0):
+    _check("mpm_surrogate_advance", _load().mpm_surrogate_advance(sim, ctypes.byref(box) if box is not None else None,
+                                                                  dv or None, dv_unit, k, stream))

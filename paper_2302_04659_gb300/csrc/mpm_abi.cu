@@ -64,7 +64,7 @@ Totals totals_of(int nenv, const mpm_env* envs) {
 
 struct Layout {
     size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, tile_sums, envs,
-        bin_env, colliders, poses, wrench, counters, total;
+        bin_env, colliders, poses, wrench, counters, sur, total;
 };
 
 Layout make_layout(const Totals& T, int nenv) {
@@ -94,6 +94,7 @@ Layout make_layout(const Totals& T, int nenv) {
     L.poses = take((kcap > (size_t)kSharedPoses ? (size_t)kPoseSteps * kcap : 1) * sizeof(ColliderNow));
     L.wrench = take(kcap * 6 * sizeof(double));
     L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
+    L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + kcap * 6 * sizeof(double));  // surrogate window
     L.total = off;
     return L;
 }
@@ -184,6 +185,7 @@ struct mpm_sim {
     std::vector<mpm_shape> shapes;
     std::vector<int> shape_counts;  // shapes per env
     int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
+    bool sur_pending = false;  // a surrogate window was started and not yet ended
     ColliderSet* stage = nullptr;  // pinned staging for collider uploads
     cudaEvent_t stage_done = nullptr;
     int sms = 0;
@@ -217,6 +219,9 @@ struct mpm_sim {
     uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
     uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
+    double* sur_sums() { return at<double>(L.sur); }  // M, P0[3], P1[3], P_hat[3]
+    int* sur_box() { return reinterpret_cast<int*>(at<char>(L.sur) + 16 * sizeof(double)); }
+    double* sur_wrench() { return at<double>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
     const EnvDesc* envs_dev() { return at<EnvDesc>(L.envs); }
     bool tail_scan() const { return T.bins <= (size_t)kTailScanMaxBins; }
     StateView view(int which) {
@@ -397,35 +402,49 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
     return MPM_OK;
 }
 
+// First half of a substep: the sort-assign of the current state and the grid update of its transfer.
+mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st) {
+    MPM_TRY(ensure_scanned(s, st));
+    MPM_TRY(ensure_grid(s, st));
+    AssignGridParams ap{};
+    ap.grid = grid_params(s);
+    ap.N = s->N;
+    ap.keyrank = s->at<uint2>(s->L.key);
+    ap.cursor = s->at<uint32_t>(s->L.cursor);
+    ap.perm = s->at<uint32_t>(s->L.perm);
+    ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 1023) / 1024;  // 4 particles per thread
+    MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
+    s->ps.order_valid = true;
+    return MPM_OK;
+}
+
+// Second half: the fused G2P -> P2G pass from the updated grid (advecting by advect_dt, the substep's dt
+// unless a surrogate window overrides it for a one-env handle), then the bin scan if it is separate.
+mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 0.0f) {
+    TransferParams p = transfer_params(s);
+    p.grid_in = s->at<float4>(s->L.grid[s->ps.g]);
+    p.grid_out = s->at<float4>(s->L.grid[1 - s->ps.g]);
+    p.flags_out = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
+    p.list_out = s->list(1 - s->ps.g);
+    p.list_count_out = s->list_count(1 - s->ps.g);
+    if (advect_dt > 0.0f) p.env0.geo.dt = advect_dt;
+    MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->sms * s->fused_cps, st); }, "g2p2g"));
+    s->ps.cur = 1 - s->ps.cur;
+    s->ps.g = 1 - s->ps.g;
+    s->ps.order_valid = false;  // assigned by the next launch
+    s->ps.grid_valid = true;
+    s->ps.scanned = s->tail_scan();  // the fused pass's last CTA wrote the new bins
+    if (!s->ps.scanned) MPM_TRY(ensure_scanned(s, st));
+    return MPM_OK;
+}
+
 // The launches of n substeps: per substep one sort-assign + grid-update launch and one fused
 // G2P->P2G launch (whose last CTA sorts the new positions into bins; with many bins two scan launches
 // follow instead).
 mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
     for (int it = 0; it < n; ++it) {
-        MPM_TRY(ensure_scanned(s, st));
-        MPM_TRY(ensure_grid(s, st));
-        AssignGridParams ap{};
-        ap.grid = grid_params(s);
-        ap.N = s->N;
-        ap.keyrank = s->at<uint2>(s->L.key);
-        ap.cursor = s->at<uint32_t>(s->L.cursor);
-        ap.perm = s->at<uint32_t>(s->L.perm);
-        ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 1023) / 1024;  // 4 particles per thread
-        MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
-        s->ps.order_valid = true;
-        TransferParams p = transfer_params(s);
-        p.grid_in = ap.grid.grid;
-        p.grid_out = ap.grid.grid_old;
-        p.flags_out = ap.grid.flags_old;
-        p.list_out = s->list(1 - s->ps.g);
-        p.list_count_out = s->list_count(1 - s->ps.g);
-        MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->sms * s->fused_cps, st); }, "g2p2g"));
-        s->ps.cur = 1 - s->ps.cur;
-        s->ps.g = 1 - s->ps.g;
-        s->ps.order_valid = false;  // assigned by the next launch
-        s->ps.grid_valid = true;
-        s->ps.scanned = s->tail_scan();  // the fused pass's last CTA wrote the new bins
-        if (!s->ps.scanned) MPM_TRY(ensure_scanned(s, st));
+        MPM_TRY(enqueue_grid_half(s, st));
+        MPM_TRY(enqueue_particle_half(s, st));
     }
     return MPM_OK;
 }
@@ -665,6 +684,7 @@ mpm_status mpm_set_particles_batch(mpm_sim* s, const int* counts, const float* x
     MPM_CUDA(cudaMemsetAsync(s->ws + z0, 0, z1 - z0, st), "cudaMemsetAsync");
     s->N = (int)total;
     s->ps = PipeState{};
+    s->sur_pending = false;
     if (total == 0) {
         s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;
         return MPM_OK;
@@ -805,7 +825,7 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
 }
 
 mpm_status mpm_substep(mpm_sim* s, int n_substeps, void* stream) {
-    if (!s || n_substeps < 0) return MPM_ERR_INVALID_ARG;
+    if (!s || n_substeps < 0 || s->sur_pending) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_substeps == 0) return MPM_OK;
     if (s->N == 0) {
@@ -932,6 +952,114 @@ mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
         off += (size_t)d.geo.n * d.geo.n * d.geo.n * 4;
     }
     return MPM_OK;
+}
+
+mpm_status mpm_surrogate_box(mpm_sim* s, int margin, mpm_box* box, void* stream) {
+    if (!s || !box || margin < 0 || s->nenv != 1 || s->sur_pending) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    *box = mpm_box{0, 0, 0, 0, 0, 0};
+    if (s->N == 0) return MPM_OK;
+    MPM_TRY(ensure_grid(s, st));
+    static const int init[6] = {1 << 30, 1 << 30, 1 << 30, -1, -1, -1};
+    int* d_box = s->sur_box();
+    MPM_CUDA(cudaMemcpyAsync(d_box, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy box init");
+    const Geometry& g = s->envs[0].geo;
+    MPM_CUDA(launch_sur_box(s->list(s->ps.g), s->list_count(s->ps.g), g.nb, (int)s->T.bins, d_box, st), "sur_box");
+    int b[6];
+    MPM_CUDA(cudaMemcpyAsync(b, d_box, sizeof(b), cudaMemcpyDeviceToHost, st), "copy box");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (b[3] < 0) return MPM_OK;  // no active bins
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = std::max(0, 4 * b[a] - margin);
+        hi[a] = std::min(g.n, 4 * b[3 + a] + 4 + margin);
+    }
+    *box = mpm_box{lo[0], lo[1], lo[2], hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    return MPM_OK;
+}
+
+static bool valid_box(const mpm_box* b) {
+    return b && b->D > 0 && b->H > 0 && b->W > 0 && (size_t)b->D * b->H * b->W < ((size_t)1 << 31);
+}
+
+static SurBox to_sur_box(const mpm_box* b) { return SurBox{b->i0, b->j0, b->k0, b->D, b->H, b->W}; }
+
+mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale, float v_scale, float* d_feat,
+                                  uint8_t* d_mask, void* stream) {
+    if (!s || s->nenv != 1 || s->sur_pending || !valid_box(box) || !d_feat || !d_mask || s->N == 0)
+        return MPM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_feat) % 16) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MPM_TRY(ensure_scanned(s, st));
+    MPM_TRY(ensure_grid(s, st));
+    double* sums = s->sur_sums();
+    MPM_CUDA(cudaMemsetAsync(sums, 0, 16 * sizeof(double), st), "cudaMemsetAsync");
+    MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
+                                (int)s->T.bins, sums, st),
+             "sur_moments");
+    if (s->ncol > 0)
+        MPM_CUDA(cudaMemcpyAsync(s->sur_wrench(), s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy wrench");
+    MPM_TRY(enqueue_grid_half(s, st));
+    const Geometry& g = s->envs[0].geo;
+    MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, to_sur_box(box), m_scale, v_scale,
+                                 d_feat, d_mask, sums + 4, st),
+             "sur_features");
+    s->sur_pending = true;
+    return MPM_OK;
+}
+
+mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv, float dv_unit, int k,
+                               double v_ref, double* out, void* stream) {
+    if (!s || !s->sur_pending || !valid_box(box) || !d_dv || !out || k < 1 || !(v_ref > 0.0))
+        return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* sums = s->sur_sums();
+    MPM_CUDA(cudaMemsetAsync(sums + 7, 0, 3 * sizeof(double), st), "cudaMemsetAsync");
+    const Geometry& g = s->envs[0].geo;
+    MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box), d_dv,
+                                dv_unit, 0, sums + 7, st),
+             "sur_check");
+    double h[10];
+    MPM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st), "copy sums");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    const double M = h[0];
+    const double Mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double pexp = h[1 + a] + 0.5 * (k + 1) * (h[4 + a] - h[1 + a]);
+        d2 += (h[7 + a] - pexp) * (h[7 + a] - pexp);
+    }
+    out[0] = Mp > 0.0 ? std::fabs(M - Mp) / Mp : 0.0;
+    out[1] = M > 0.0 ? std::sqrt(d2) / (M * v_ref) : 0.0;
+    out[2] = M;
+    out[3] = std::sqrt(d2);
+    return MPM_OK;
+}
+
+mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_dv, float dv_unit, int k,
+                                 void* stream) {
+    if (!s || !s->sur_pending || k < 1 || (d_dv && !valid_box(box))) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s->sur_pending = false;
+    if (d_dv) {
+        const Geometry& g = s->envs[0].geo;
+        MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box),
+                                    d_dv, dv_unit, 1, s->sur_sums() + 10, st),
+                 "sur_apply");
+        MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt));
+        if (k > 1) {
+            MPM_TRY(launch(s, MPM_K_COLLIDERS, st,
+                           [&] { return launch_advance_counter(s->substep_counter(), k - 1, st); }, "advance"));
+            MPM_CUDA(launch_wrench_extrapolate(s->at<double>(s->L.wrench), s->sur_wrench(), s->ncol * 6,
+                                               (double)(k - 1), st),
+                     "wrench_extrapolate");
+        }
+        return MPM_OK;
+    }
+    MPM_TRY(enqueue_particle_half(s, st));
+    return k > 1 ? enqueue_substeps(s, k - 1, st) : MPM_OK;
 }
 
 mpm_status mpm_set_timing(mpm_sim* s, unsigned kernel_mask) {

@@ -180,6 +180,20 @@ cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* po
                                  uint32_t* counter, float dt, cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s);
 
+// surrogate window (surrogate_kernels.cu): a box of grid nodes [i0, i0 + D) x [j0, j0 + H) x [k0, k0 + W)
+struct SurBox {
+    int i0, j0, k0, D, H, W;
+};
+cudaError_t launch_sur_box(const uint32_t* list, const uint32_t* count, int nb, int nbins_cap, int* box,
+                           cudaStream_t s);
+cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
+                               double* sums, cudaStream_t s);
+cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
+                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s);
+cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                               float unit, int apply, double* sums, cudaStream_t s);
+cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s);
+
 // occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
 int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env);
 

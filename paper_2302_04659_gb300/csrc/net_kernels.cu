@@ -36,11 +36,6 @@ __host__ __device__ __forceinline__ int x_stride(int cin) { return cin % 16 == 0
 __host__ __device__ __forceinline__ int k_pad(int cin) { return ceil_to(27 * cin, 16); }
 __host__ __device__ __forceinline__ int w_stride(int cin) { return k_pad(cin) + 8; }
 
-__device__ __forceinline__ int tap_offset(int t) {  // halo-index offset of tap t
-    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-    return (dz * HY + dy) * HX + dx;
-}
-
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -99,6 +94,38 @@ __device__ void stage_halo(__nv_bfloat16* Xs, const __nv_bfloat16* __restrict__ 
 }
 
 // ------------------------------------------------------------------------ BF16 forward / input gradient
+//
+// Forward tiles are 4 x 8 x 8 voxels (256 GEMM rows, 8 warps x 32 rows) with a 6 x 10 x 10 halo. Fragments
+// come from shared memory with ldmatrix: the A rows of an m16 tile are 16 voxels whose halo rows (one
+// voxel's channels, 16-byte aligned, padded to 80 bytes for 32 channels) fall on distinct banks; B rows are
+// output channels with k contiguous. With a tile flag array, a tile whose flag is 0 is written as zeros
+// instead of computed (the surrogate needs outputs only near the material).
+
+constexpr int FZ = 4, FY = 8, FX = 8, FM = FZ * FY * FX;                // 256 output voxels per tile
+constexpr int GZ = FZ + 2, GY = FY + 2, GX = FX + 2, GV = GZ * GY * GX;  // 600 halo voxels
+constexpr int kFwdThreads = 256;
+
+__host__ __device__ __forceinline__ int fwd_tiles(const Box& b, int& tx, int& ty) {
+    tx = (b.W + FX - 1) / FX;
+    ty = (b.H + FY - 1) / FY;
+    return tx * ty * ((b.D + FZ - 1) / FZ);
+}
+
+__device__ __forceinline__ int fwd_tap_offset(int t) {
+    return ((t / 9) * GY + (t / 3) % 3) * GX + t % 3;
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const __nv_bfloat16* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
 
 struct ConvMma {
     Box box;
@@ -112,14 +139,41 @@ struct ConvMma {
     const __nv_bfloat16* mask;      // [vox][cout] or null: output *= (mask > 0)
     void* y;                        // [vox][cout], bf16 or f32
     int y_f32;
+    const uint8_t* tile_need;       // per forward tile, or null: compute every tile
 };
 
+template <int HZ_, int HY_, int HX_>
+__device__ void stage_halo_t(__nv_bfloat16* Xs, const __nv_bfloat16* __restrict__ x, const Box& b, int cin, int xs,
+                             int z0, int y0, int x0) {
+    constexpr int HV_ = HZ_ * HY_ * HX_;
+    if (cin % 8 == 0) {
+        const int vec = cin / 8;  // 16-byte pieces per voxel
+        for (int i = threadIdx.x; i < HV_ * vec; i += blockDim.x) {
+            const int h = i / vec, q = i % vec;
+            const int z = z0 - 1 + h / (HY_ * HX_), y = y0 - 1 + (h / HX_) % HY_, xx = x0 - 1 + h % HX_;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (z >= 0 && z < b.D && y >= 0 && y < b.H && xx >= 0 && xx < b.W)
+                v = reinterpret_cast<const uint4*>(x + (((size_t)z * b.H + y) * b.W + xx) * cin)[q];
+            *reinterpret_cast<uint4*>(Xs + h * xs + q * 8) = v;
+        }
+    } else {
+        for (int i = threadIdx.x; i < HV_ * cin; i += blockDim.x) {
+            const int h = i / cin, c = i % cin;
+            const int z = z0 - 1 + h / (HY_ * HX_), y = y0 - 1 + (h / HX_) % HY_, xx = x0 - 1 + h % HX_;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (z >= 0 && z < b.D && y >= 0 && y < b.H && xx >= 0 && xx < b.W)
+                v = x[(((size_t)z * b.H + y) * b.W + xx) * cin + c];
+            Xs[h * xs + c] = v;
+        }
+    }
+}
+
 template <int NT>  // n8 tiles: cout <= 8 * NT
-__global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
+__global__ void __launch_bounds__(kFwdThreads, 2) k_conv_mma(ConvMma a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cin = a.cin, xs = x_stride(cin), K = 27 * cin, KP = k_pad(cin), ws = w_stride(cin);
     __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem_raw);                 // [NT*8][ws]
-    __nv_bfloat16* Xs = Ws + NT * 8 * ws;                                            // [HV][xs]
+    __nv_bfloat16* Xs = Ws + NT * 8 * ws;                                            // [GV][xs]
     // weights: Ws[n][k], k = t * cin + c; zero for n >= cout or k >= K
     for (int i = threadIdx.x; i < NT * 8 * KP; i += blockDim.x) {
         const int n = i / KP, k = i % KP;
@@ -133,22 +187,38 @@ __global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, kk = (lane & 3) * 2;
-    // this thread's 4 A-fragment rows (2 m16 tiles x {g, g + 8}) as halo indices of the centre tap
-    int hb[2][2];
+    const int lq = lane >> 3, lr = lane & 7;
+    // halo index (centre tap) of the rows this lane addresses for ldmatrix (A) and holds in the mma layout
+    int hA[2], hb[2][2];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < 2; ++mt) {
+        const int m = warp * 32 + mt * 16 + lr + (lq & 1) * 8;
+        hA[mt] = ((m / (FY * FX)) * GY + (m / FX) % FY) * GX + m % FX;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const int m = warp * 32 + mt * 16 + g + r * 8;
-            const int z = m / (TY * TX), y = (m / TX) % TY, xx = m % TX;
-            hb[mt][r] = (z * HY + y) * HX + xx;  // + tap_offset(t) gives the input voxel of tap t
+            const int mm = warp * 32 + mt * 16 + g + r * 8;
+            hb[mt][r] = ((mm / (FY * FX)) * GY + (mm / FX) % FY) * GX + mm % FX;
         }
+    }
+    const int a_koff = (lq >> 1) * 8;
     const bool fast = cin % 16 == 0;
-    for (int tile = blockIdx.x; tile < a.box.tiles(); tile += gridDim.x) {
-        int z0, y0, x0;
-        tile_origin(a.box, tile, z0, y0, x0);
+    int tx, ty;
+    const int tiles = fwd_tiles(a.box, tx, ty);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int x0 = (tile % tx) * FX, y0 = ((tile / tx) % ty) * FY, z0 = (tile / (tx * ty)) * FZ;
+        if (a.tile_need && !a.tile_need[tile]) {  // not needed: zeros (uniform across the CTA)
+            for (int i = threadIdx.x; i < FM * a.cout; i += blockDim.x) {
+                const int m = i / a.cout, n = i % a.cout;
+                const int z = z0 + m / (FY * FX), y = y0 + (m / FX) % FY, xx = x0 + m % FX;
+                if (z >= a.box.D || y >= a.box.H || xx >= a.box.W) continue;
+                const size_t o = (((size_t)z * a.box.H + y) * a.box.W + xx) * a.cout + n;
+                if (a.y_f32) static_cast<float*>(a.y)[o] = 0.0f;
+                else static_cast<__nv_bfloat16*>(a.y)[o] = __float2bfloat16(0.0f);
+            }
+            continue;
+        }
         __syncthreads();  // previous tile's reads of Xs done (and, first time, Ws written)
-        stage_halo(Xs, a.x, a.box, cin, xs, z0, y0, x0);
+        stage_halo_t<GZ, GY, GX>(Xs, a.x, a.box, cin, xs, z0, y0, x0);
         __syncthreads();
         float acc[2][NT][4];
 #pragma unroll
@@ -160,16 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
         for (int k0 = 0; k0 < KP; k0 += 16) {
             uint32_t af[2][4];
             if (fast) {  // the 16 k of this step are channels c0..c0+15 of one tap
-                const int t = k0 / cin, c0 = k0 % cin, off = tap_offset(t);
+                const int t = k0 / cin, c0 = k0 % cin, off = fwd_tap_offset(t);
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const __nv_bfloat16* r0 = Xs + (hb[mt][0] + off) * xs + c0 + kk;
-                    const __nv_bfloat16* r1 = Xs + (hb[mt][1] + off) * xs + c0 + kk;
-                    af[mt][0] = lds32(r0);
-                    af[mt][1] = lds32(r1);
-                    af[mt][2] = lds32(r0 + 8);
-                    af[mt][3] = lds32(r1 + 8);
-                }
+                for (int mt = 0; mt < 2; ++mt) ldsm_x4(af[mt], Xs + (hA[mt] + off) * xs + c0 + a_koff);
             } else {  // gather element by element (few input channels)
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
@@ -177,17 +240,26 @@ __global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
                     for (int q = 0; q < 4; ++q) {
                         const int r = q & 1, kq = k0 + kk + (q >> 1) * 8;
                         __nv_bfloat16 e0 = __float2bfloat16(0.0f), e1 = e0;
-                        if (kq < K) e0 = Xs[(hb[mt][r] + tap_offset(kq / cin)) * xs + kq % cin];
-                        if (kq + 1 < K) e1 = Xs[(hb[mt][r] + tap_offset((kq + 1) / cin)) * xs + (kq + 1) % cin];
+                        if (kq < K) e0 = Xs[(hb[mt][r] + fwd_tap_offset(kq / cin)) * xs + kq % cin];
+                        if (kq + 1 < K) e1 = Xs[(hb[mt][r] + fwd_tap_offset((kq + 1) / cin)) * xs + (kq + 1) % cin];
                         af[mt][q] = pack2(e0, e1);
                     }
             }
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const __nv_bfloat16* br = Ws + (nt * 8 + g) * ws + k0 + kk;
-                const uint32_t b0 = lds32(br), b1 = lds32(br + 8);
-                mma16816(acc[0][nt], af[0], b0, b1);
-                mma16816(acc[1][nt], af[1], b0, b1);
+            for (int np = 0; np < NT / 2; ++np) {  // two n8 tiles per ldmatrix.x4
+                uint32_t b[4];
+                ldsm_x4(b, Ws + ((np * 2 + (lq >> 1)) * 8 + lr) * ws + k0 + (lq & 1) * 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma16816(acc[mt][2 * np], af[mt], b[0], b[1]);
+                    mma16816(acc[mt][2 * np + 1], af[mt], b[2], b[3]);
+                }
+            }
+            if constexpr (NT % 2 == 1) {
+                uint32_t b0, b1;
+                ldsm_x2(b0, b1, Ws + ((NT - 1) * 8 + lr) * ws + k0 + (lq & 1) * 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][NT - 1], af[mt], b0, b1);
             }
         }
         // epilogue: bias, ReLU, mask, store (rows g / g + 8, columns kk / kk + 1 of each n8 tile)
@@ -196,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const int m = warp * 32 + mt * 16 + g + r * 8;
-                const int z = z0 + m / (TY * TX), y = y0 + (m / TX) % TY, xx = x0 + m % TX;
+                const int z = z0 + m / (FY * FX), y = y0 + (m / FX) % FY, xx = x0 + m % FX;
                 if (z >= a.box.D || y >= a.box.H || xx >= a.box.W) continue;
                 const size_t vox = ((size_t)z * a.box.H + y) * a.box.W + xx;
 #pragma unroll
@@ -218,8 +290,33 @@ __global__ void __launch_bounds__(kThreads) k_conv_mma(ConvMma a) {
     }
 }
 
+// Per forward tile: 1 if any voxel of the tile (dilate = 0), or of the tile and its 26 neighbours
+// (dilate = 1), has a nonzero mask byte.
+__global__ void k_tile_flags(Box b, const uint8_t* __restrict__ mask, int dilate, uint8_t* __restrict__ flags) {
+    int tx, ty;
+    const int tiles = fwd_tiles(b, tx, ty);
+    const int tz = tiles / (tx * ty);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int cx = tile % tx, cy = (tile / tx) % ty, cz = tile / (tx * ty);
+        const int r = dilate ? 1 : 0;
+        int any = 0;
+        for (int dz = -r; dz <= r && !any; ++dz)
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+                    if (nx < 0 || ny < 0 || nz < 0 || nx >= tx || ny >= ty || nz >= tz) continue;
+                    for (int i = threadIdx.x; i < FM; i += blockDim.x) {
+                        const int z = nz * FZ + i / (FY * FX), y = ny * FY + (i / FX) % FY, xx = nx * FX + i % FX;
+                        if (z < b.D && y < b.H && xx < b.W && mask[((size_t)z * b.H + y) * b.W + xx]) any = 1;
+                    }
+                }
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) flags[tile] = any ? 1 : 0;
+    }
+}
+
 size_t conv_mma_smem(int cin, int nt) {
-    return (size_t)(nt * 8 * w_stride(cin) + HV * x_stride(cin)) * sizeof(__nv_bfloat16);
+    return (size_t)(nt * 8 * w_stride(cin) + GV * x_stride(cin)) * sizeof(__nv_bfloat16);
 }
 
 // ------------------------------------------------------------------------ BF16 weight gradient
@@ -477,11 +574,11 @@ __global__ void k_cast_to_f32(int n, const __nv_bfloat16* __restrict__ s, float*
 
 unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-int persistent_ctas(int tiles, const void* kernel, size_t smem) {
+int persistent_ctas(int tiles, const void* kernel, size_t smem, int threads = kThreads) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     return std::max(1, std::min(tiles, std::max(per_sm, 1) * std::max(sms, 1)));
 }
 
@@ -490,8 +587,10 @@ cudaError_t launch_conv_mma(const ConvMma& a, cudaStream_t s) {
     const size_t smem = conv_mma_smem(a.cin, NT);
     cudaError_t e = cudaFuncSetAttribute(k_conv_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_ctas(a.box.tiles(), (const void*)k_conv_mma<NT>, smem);
-    k_conv_mma<NT><<<grid, kThreads, smem, s>>>(a);
+    int tx, ty;
+    const int tiles = fwd_tiles(a.box, tx, ty);
+    const int grid = persistent_ctas(tiles, (const void*)k_conv_mma<NT>, smem, kFwdThreads);
+    k_conv_mma<NT><<<grid, kFwdThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -565,12 +664,40 @@ mpm_status mpm_conv3d_forward(int dtype, int D, int H, int W, int cin, int cout,
         e = cudaGetLastError();
     } else if (dtype == MPM_NET_BF16) {
         ConvMma a{b, cin, cout, static_cast<const __nv_bfloat16*>(x), static_cast<const __nv_bfloat16*>(w), 0, cin,
-                  bias, relu, nullptr, y, y_f32};
+                  bias, relu, nullptr, y, y_f32, nullptr};
         e = conv_mma(a, st);
     } else {
         return MPM_ERR_INVALID_ARG;
     }
     return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_forward");
+}
+
+mpm_status mpm_conv3d_forward_tiled(int D, int H, int W, int cin, int cout, const void* x, const void* w,
+                                    const float* bias, int relu, int y_f32, void* y, const uint8_t* tile_flags,
+                                    void* stream) {
+    if (!valid_dims(D, H, W, cin, cout) || !x || !w || !y || !tile_flags) return MPM_ERR_INVALID_ARG;
+    ConvMma a{make_box(D, H, W), cin, cout, static_cast<const __nv_bfloat16*>(x), static_cast<const __nv_bfloat16*>(w),
+              0, cin, bias, relu, nullptr, y, y_f32, tile_flags};
+    cudaError_t e = conv_mma(a, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_forward_tiled");
+}
+
+int mpm_conv3d_tile_count(int D, int H, int W) {
+    if (D <= 0 || H <= 0 || W <= 0) return 0;
+    int tx, ty;
+    return fwd_tiles(make_box(D, H, W), tx, ty);
+}
+
+mpm_status mpm_conv3d_tile_flags(int D, int H, int W, const uint8_t* mask, int dilate, uint8_t* flags,
+                                 void* stream) {
+    if (D <= 0 || H <= 0 || W <= 0 || !mask || !flags) return MPM_ERR_INVALID_ARG;
+    const Box b = make_box(D, H, W);
+    int tx, ty;
+    const int tiles = fwd_tiles(b, tx, ty);
+    k_tile_flags<<<std::min(tiles, 4096), 256, 0, static_cast<cudaStream_t>(stream)>>>(b, mask, dilate ? 1 : 0,
+                                                                                      flags);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_tile_flags");
 }
 
 mpm_status mpm_conv3d_backward_data(int dtype, int D, int H, int W, int cin, int cout, const void* dy,
@@ -589,7 +716,7 @@ mpm_status mpm_conv3d_backward_data(int dtype, int D, int H, int W, int cin, int
     } else if (dtype == MPM_NET_BF16) {
         // a forward pass over dy (cout channels in) to cin channels out with flipped, transposed weights
         ConvMma a{b, cout, cin, static_cast<const __nv_bfloat16*>(dy), static_cast<const __nv_bfloat16*>(w), 1, cin,
-                  nullptr, 0, static_cast<const __nv_bfloat16*>(act_in), dx, 0};
+                  nullptr, 0, static_cast<const __nv_bfloat16*>(act_in), dx, 0, nullptr};
         e = conv_mma(a, st);
     } else {
         return MPM_ERR_INVALID_ARG;

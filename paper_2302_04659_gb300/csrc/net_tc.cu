@@ -1,0 +1,421 @@
+// net_tc.cu -- the surrogate network's forward convolution on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), behind mpm_conv3d_forward_tc (include/mpm_net.h).
+//
+// Implicit GEMM per tile of 1 x 16 x 8 output voxels (M = 128 rows, N = the output channels padded to 16
+// or 32, K = 27 taps x input channels). The input halo (3 x 18 x 10 voxels) is staged in shared memory
+// as planes of 8 channels, one 16-byte row per voxel, so the 8 voxels of a row of the tile form one
+// 8 x 16-byte core matrix and the next row of the tile sits 10 voxels (160 bytes) further: the A
+// operand of a tap is the plane shifted by the tap's voxel offset, described with no swizzle (leading
+// byte offset = the next 8 channels, stride byte offset = 160 bytes). The weights, packed once per update
+// in the same canonical K-major layout (one block per K step), arrive in each CTA by one bulk copy
+// (cp.async.bulk, completion on an mbarrier). One thread issues the MMAs of a tile
+// into a 32-column FP32 accumulator in tensor memory and commits them to an mbarrier; the four warps then
+// read their 32 rows back (tcgen05.ld 32x32b), add the bias, apply ReLU and store. Every wait on the
+// mbarrier is bounded: past the limit the kernel records an error word and leaves, freeing its tensor
+// memory. Input channels: 4 (padded to 8: the two dx taps of a row pair up in one K step) or a multiple
+// of 16 up to 32; output channels up to 32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mpm_internal.h"
+#include "mpm_net.h"
+
+namespace mpm {
+namespace net_tc {
+namespace {
+
+constexpr int TY = 16, TX = 8, TM = TY * TX;          // 128 rows per tile (one z plane)
+constexpr int HZ = 3, HY = TY + 2, HX = TX + 2, HV = HZ * HY * HX;  // 540 halo voxels
+constexpr int kPlanePad = 16;                          // zero voxels after each plane (dx over-read)
+constexpr int kPlaneVox = HV + kPlanePad;
+constexpr int kPlaneBytes = kPlaneVox * 16;            // 8896
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 32;
+constexpr uint32_t kWaitLimit = 1u << 22;              // mbarrier polls before giving up
+
+__device__ uint32_t g_tc_error;  // nonzero after a bounded wait ran out (mpm_net_tc_status)
+
+struct Args {
+    int D, H, W;
+    int cin, cout;
+    const __nv_bfloat16* x;  // [vox][cin]
+    const unsigned char* wp; // weights packed in the kernel's shared-memory layout (mpm_conv3d_pack_tc)
+    const float* bias;
+    int relu;
+    int y_f32;
+    void* y;
+    const uint8_t* tile_dist;  // per tile: distance to the nearest mask voxel (capped), or null
+    int radius;                // with tile_dist: compute tiles within this distance
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major, N x M.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// K steps: CG = input channel groups of 8 (1 for 4 channels, 2 or 4 for 16 or 32).
+__host__ __device__ constexpr int k_steps(int cg) { return cg == 1 ? 18 : 27 * cg / 2; }
+
+template <int NPAD, int CG>
+__global__ void __launch_bounds__(kThreads, 2) k_conv_tc(Args a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int S = k_steps(CG);
+    constexpr int kBBlock = NPAD * 32;  // bytes of one K step of B: 2 k-groups x NPAD/8 n-groups x 128
+    unsigned char* planes = smem;                                   // CG planes of kPlaneBytes
+    unsigned char* bsm = smem + CG * kPlaneBytes;                   // S blocks of kBBlock
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);  // [0]: MMAs done, [1]: weights landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights: one bulk copy of the packed blocks (issued below, once the barrier exists)
+    // zero padding voxels after each plane (read by the dx over-reach of the 4-channel steps)
+    for (int i = tid; i < CG * kPlanePad; i += kThreads)
+        *reinterpret_cast<uint4*>(planes + (i / kPlanePad) * kPlaneBytes + (HV + i % kPlanePad) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + 1)),
+                     "r"((uint32_t)(S * kBBlock))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(bsm)),
+            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(smem_u32(bar + 1))
+            : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = instr_desc(TM, NPAD);
+    const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm), bar_addr = smem_u32(bar);
+    const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
+    uint32_t phase = 0;
+    bool failed = !mbar_wait(smem_u32(bar + 1), 0);  // the weights
+    if (failed && tid == 0) atomicExch(&g_tc_error, 2u);
+    failed = __syncthreads_or(failed) != 0;
+    for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+        const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
+        const bool need = !a.tile_dist || a.tile_dist[tile] <= a.radius;
+        const int m = warp * 32 + lane;
+        const int y = y0 + m / TX, xx = x0 + m % TX;
+        const bool in_box = y < a.H && xx < a.W;
+        const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
+        if (!need) {
+            if (in_box)
+                for (int n = 0; n < a.cout; ++n) {
+                    if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = 0.0f;
+                    else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(0.0f);
+                }
+            continue;
+        }
+        // stage the halo planes (16 bytes per voxel and plane)
+        for (int i = tid; i < HV * CG; i += kThreads) {
+            const int h = i / CG, q = i % CG;
+            const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - 1 + h % HX;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W) {
+                const __nv_bfloat16* src = a.x + (((size_t)z * a.H + yy) * a.W + xq) * a.cin;
+                if constexpr (CG == 1) {
+                    const uint2 u = *reinterpret_cast<const uint2*>(src);  // 4 channels
+                    v = make_uint4(u.x, u.y, 0u, 0u);
+                } else {
+                    v = reinterpret_cast<const uint4*>(src)[q];
+                }
+            }
+            *reinterpret_cast<uint4*>(planes + q * kPlaneBytes + h * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int s = 0; s < S; ++s) {
+                int off, q;
+                uint32_t lbo;
+                if constexpr (CG == 1) {
+                    const int pair = s >> 1, half = s & 1;
+                    off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
+                    q = 0;
+                    lbo = 16;  // the second k-group is the next voxel along x (dx + 1)
+                } else {
+                    const int tap = s / (CG / 2);
+                    off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
+                    q = (s % (CG / 2)) * 2;
+                    lbo = kPlaneBytes;  // the second k-group is the next plane of 8 channels
+                }
+                const uint64_t ad = smem_desc(planes_addr + q * kPlaneBytes + off * 16, lbo, HX * 16);
+                const uint64_t bd = smem_desc(b_addr + s * kBBlock, (NPAD / 8) * 128, 128);
+                mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+            }
+            mma_commit(bar_addr);
+        }
+        __syncwarp();
+        if (!mbar_wait(bar_addr, phase)) {
+            failed = true;
+            if (lane == 0) atomicExch(&g_tc_error, 1u);
+        }
+        phase ^= 1u;
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc[NPAD];
+        tmem_load<NPAD>(tmem + ((uint32_t)(warp * 32) << 16), acc);
+        if (in_box) {
+            if (!a.y_f32 && a.cout == 32) {
+                uint32_t packed[16];
+#pragma unroll
+                for (int n = 0; n < 32; n += 2) {
+                    float v0 = acc[n] + (a.bias ? a.bias[n] : 0.0f), v1 = acc[n + 1] + (a.bias ? a.bias[n + 1] : 0.0f);
+                    if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(v0, v1);
+                    packed[n / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vox * 32);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int n = 0; n < NPAD; ++n) {
+                    if (n >= a.cout) break;
+                    float v = acc[n] + (a.bias ? a.bias[n] : 0.0f);
+                    if (a.relu) v = fmaxf(v, 0.0f);
+                    if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = v;
+                    else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(v);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // accumulator read and planes consumed before the next tile reuses them
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+size_t smem_bytes(int npad, int cg) {
+    return (size_t)cg * kPlaneBytes + (size_t)k_steps(cg) * npad * 32 + 32 + 16;
+}
+
+int npad_of(int cout) { return cout <= 16 ? 16 : 32; }
+int cg_of(int cin) { return cin == 4 ? 1 : cin / 8; }
+size_t packed_bytes(int cin, int cout) { return (size_t)k_steps(cg_of(cin)) * npad_of(cout) * 32; }
+
+// The weights in the kernel's canonical K-major layout: block s (K step), k-group kg, n-group ng,
+// row r (output channel), column c (k), zero where the step has no tap or channel.
+__global__ void k_pack(const __nv_bfloat16* __restrict__ w, int cin, int cout, int npad, int cg,
+                       __nv_bfloat16* __restrict__ out) {
+    const int S = k_steps(cg);
+    const int total = S * 16 * npad;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i & 7, r = (i >> 3) & 7, ng = (i >> 6) % (npad / 8), kg = (i / (8 * npad)) & 1;
+        const int s = i / (16 * npad);
+        const int n = ng * 8 + r;
+        int tap, ci;
+        bool zero = false;
+        if (cg == 1) {  // a step pairs the dx = 0, 1 taps of a row, then dx = 2 with an empty half
+            const int pair = s >> 1, half = s & 1;
+            zero = half && kg;
+            tap = pair * 3 + (half ? 2 : kg);
+            ci = c;
+        } else {
+            tap = s / (cg / 2);
+            ci = (s % (cg / 2)) * 16 + kg * 8 + c;
+        }
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (!zero && n < cout && ci < cin) v = w[((size_t)tap * cout + n) * cin + ci];
+        out[i] = v;
+    }
+}
+
+// Per tile: the Chebyshev distance (in voxels, capped at kDistCap) from the tile to the nearest voxel
+// whose mask byte is set.
+constexpr int kDistCap = 4;
+__global__ void k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mask, uint8_t* __restrict__ dist) {
+    const int tx = (W + TX - 1) / TX, ty = (H + TY - 1) / TY, tiles = tx * ty * D;
+    constexpr int R = kDistCap;
+    constexpr int EZ = 1 + 2 * R, EY = TY + 2 * R, EX = TX + 2 * R;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
+        int best = R + 1;
+        for (int i = threadIdx.x; i < EZ * EY * EX; i += blockDim.x) {
+            const int z = z0 - R + i / (EY * EX), y = y0 - R + (i / EX) % EY, xx = x0 - R + i % EX;
+            if (z < 0 || z >= D || y < 0 || y >= H || xx < 0 || xx >= W || !mask[((size_t)z * H + y) * W + xx]) continue;
+            const int dz = z < z0 ? z0 - z : (z > z0 ? z - z0 : 0);
+            const int dy = y < y0 ? y0 - y : (y >= y0 + TY ? y - (y0 + TY - 1) : 0);
+            const int dx = xx < x0 ? x0 - xx : (xx >= x0 + TX ? xx - (x0 + TX - 1) : 0);
+            best = min(best, max(dz, max(dy, dx)));
+        }
+        for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+        __shared__ int wmin[8];
+        if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int b = R + 1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = min(b, wmin[w]);
+            dist[tile] = (uint8_t)b;
+        }
+        __syncthreads();
+    }
+}
+
+template <int NPAD, int CG>
+cudaError_t launch(const Args& a, cudaStream_t s) {
+    const size_t smem = smem_bytes(NPAD, CG);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<NPAD, CG>, kThreads, smem);
+    const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
+    const int grid = std::max(1, std::min(tiles, std::max(per_sm, 1) * std::max(sms, 1)));
+    k_conv_tc<NPAD, CG><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace net_tc
+}  // namespace mpm
+
+using namespace mpm::net_tc;
+
+extern "C" {
+
+int mpm_conv3d_tc_packed_bytes(int cin, int cout) {
+    if ((cin != 4 && cin != 16 && cin != 32) || cout < 1 || cout > 32) return 0;
+    return (int)packed_bytes(cin, cout);
+}
+
+mpm_status mpm_conv3d_pack_tc(int cin, int cout, const void* w, void* packed, void* stream) {
+    if ((cin != 4 && cin != 16 && cin != 32) || cout < 1 || cout > 32 || !w || !packed) return MPM_ERR_INVALID_ARG;
+    const int total = (int)(packed_bytes(cin, cout) / 2);
+    k_pack<<<(total + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16*>(w), cin, cout, npad_of(cout), cg_of(cin), static_cast<__nv_bfloat16*>(packed));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_pack_tc");
+}
+
+int mpm_conv3d_tc_tile_count(int D, int H, int W) {
+    if (D <= 0 || H <= 0 || W <= 0) return 0;
+    return ((W + TX - 1) / TX) * ((H + TY - 1) / TY) * D;
+}
+
+mpm_status mpm_conv3d_tc_tile_dist(int D, int H, int W, const uint8_t* mask, uint8_t* dist, void* stream) {
+    if (D <= 0 || H <= 0 || W <= 0 || !mask || !dist) return MPM_ERR_INVALID_ARG;
+    const int tiles = mpm_conv3d_tc_tile_count(D, H, W);
+    k_tile_dist<<<std::min(tiles, 8192), 256, 0, static_cast<cudaStream_t>(stream)>>>(D, H, W, mask, dist);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_tc_tile_dist");
+}
+
+mpm_status mpm_conv3d_forward_tc(int D, int H, int W, int cin, int cout, const void* x, const void* w_packed,
+                                 const float* bias, int relu, int y_f32, void* y, const uint8_t* tile_dist,
+                                 int radius, void* stream) {
+    if (D <= 0 || H <= 0 || W <= 0 || !x || !w_packed || !y || cout < 1 || cout > 32 || radius < 0 ||
+        (size_t)D * H * W >= ((size_t)1 << 31))
+        return MPM_ERR_INVALID_ARG;
+    if (cin != 4 && cin != 16 && cin != 32) return MPM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(w_packed) % 16 || reinterpret_cast<uintptr_t>(x) % 16) return MPM_ERR_INVALID_ARG;
+    Args a{D, H, W, cin, cout, static_cast<const __nv_bfloat16*>(x), static_cast<const unsigned char*>(w_packed), bias,
+           relu, y_f32, y, tile_dist, radius};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const bool n16 = cout <= 16;
+    if (cin == 4) e = n16 ? launch<16, 1>(a, st) : launch<32, 1>(a, st);
+    else if (cin == 16) e = n16 ? launch<16, 2>(a, st) : launch<32, 2>(a, st);
+    else e = n16 ? launch<16, 4>(a, st) : launch<32, 4>(a, st);
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_forward_tc");
+}
+
+mpm_status mpm_net_tc_status(unsigned* flags, int clear, void* stream) {
+    if (!flags) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_tc_error, sizeof(v), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && clear) {
+        static const unsigned zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return mpm::record_cuda_error(e, "mpm_net_tc_status");
+    *flags = v;
+    return MPM_OK;
+}
+
+}  // extern "C"

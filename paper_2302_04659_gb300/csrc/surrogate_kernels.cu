@@ -1,0 +1,182 @@
+// surrogate_kernels.cu -- grid-side kernels of the learned surrogate window (an extension of the method:
+// the paper's simulator has no learned component). A window replaces k substeps by one plain grid update,
+// a network correction of the updated node velocities, and one grid-to-particle transfer with time step
+// k*dt. These kernels read the network input off the updated grid, add the network's correction back,
+// and sum the mass and momentum the fallback gate compares.
+#include <cuda_runtime.h>
+
+#include "mpm_internal.h"
+
+namespace mpm {
+namespace {
+
+constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
+
+// Block-wide sum of NV doubles (blockDim a multiple of 32, at most 1024), added atomically to out.
+template <int NV>
+__device__ __forceinline__ void block_sum_add(double (&v)[NV], double* out) {
+    __shared__ double part[32][NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part[warp][q] = v[q];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < nw ? part[lane][q] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0 && s != 0.0) atomicAdd(&out[q], s);
+        }
+    }
+}
+
+// Bin bounds of the active bins (the grid's bin list): box[0..2] = min bin per axis, box[3..5] = max.
+__global__ void k_sur_box(const uint32_t* __restrict__ list, const uint32_t* __restrict__ count, int nb, int* box) {
+    const uint32_t n = *count;
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = (int)(list[i] & kLocalMask);
+        const int c[3] = {b / (nb * nb), (b / nb) % nb, b % nb};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = min(lo[a], c[a]);
+            hi[a] = max(hi[a], c[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&box[a], lo[a]);
+            atomicMax(&box[3 + a], hi[a]);
+        }
+    }
+}
+
+// Mass and momentum of the transfer, before the grid update (nodes hold (m, m v)).
+__global__ void k_sur_moments(const float4* __restrict__ grid, const uint32_t* __restrict__ list,
+                              const uint32_t* __restrict__ count, double* sums) {
+    const uint32_t n = *count;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kBlkNodes; i += gridDim.x * blockDim.x) {
+        const uint32_t b = list[i / kBlkNodes] & kLocalMask;
+        const float4 g = grid[(size_t)b * kBlkNodes + i % kBlkNodes];
+        v[0] += g.x;
+        v[1] += g.y;
+        v[2] += g.z;
+        v[3] += g.w;
+    }
+    block_sum_add<4>(v, sums);
+}
+
+__device__ __forceinline__ bool box_node(const SurBox& b, size_t t, int& i, int& j, int& k) {
+    k = b.k0 + (int)(t % b.W);
+    j = b.j0 + (int)((t / b.W) % b.H);
+    i = b.i0 + (int)(t / ((size_t)b.W * b.H));
+    return true;
+}
+
+// Network input over the box from the updated grid (nodes hold (v, m)): (m * m_scale, v * v_scale),
+// the mass mask, and the momentum sum of the updated grid.
+__global__ void k_sur_features(const float4* __restrict__ grid, int n, int nb, SurBox box, float m_scale,
+                               float v_scale, float* __restrict__ feat, uint8_t* __restrict__ mask, double* sums) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    double p[3] = {0.0, 0.0, 0.0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(box, t, i, j, k);
+        float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n) g = grid[node_index(i, j, k, nb)];
+        const float m = g.w;
+        reinterpret_cast<float4*>(feat)[t] = make_float4(m * m_scale, g.x * v_scale, g.y * v_scale, g.z * v_scale);
+        mask[t] = m > 0.0f ? 1 : 0;
+        p[0] += (double)m * g.x;
+        p[1] += (double)m * g.y;
+        p[2] += (double)m * g.z;
+    }
+    block_sum_add<3>(p, sums);
+}
+
+__device__ __forceinline__ bool in_wall(int i, int j, int k, int n, int bound) {
+    const int hi = n - bound;
+    return i < bound || j < bound || k < bound || i >= hi || j >= hi || k >= hi;
+}
+
+// The corrected velocity of a node: v + dv * unit where it has mass, zero in the sticky wall band.
+// apply != 0 writes it back; the momentum of the corrected grid is summed either way.
+__global__ void k_sur_correct(float4* __restrict__ grid, int n, int nb, int bound, SurBox box,
+                              const float* __restrict__ dv, float unit, int apply, double* sums) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    double p[3] = {0.0, 0.0, 0.0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(box, t, i, j, k);
+        if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n) continue;
+        float4* node = &grid[node_index(i, j, k, nb)];
+        float4 g = *node;
+        if (!(g.w > 0.0f)) continue;
+        const float* d = dv + t * 3;
+        float v[3] = {g.x + d[0] * unit, g.y + d[1] * unit, g.z + d[2] * unit};
+        if (in_wall(i, j, k, n, bound)) v[0] = v[1] = v[2] = 0.0f;
+        p[0] += (double)g.w * v[0];
+        p[1] += (double)g.w * v[1];
+        p[2] += (double)g.w * v[2];
+        if (apply) *node = make_float4(v[0], v[1], v[2], g.w);
+    }
+    block_sum_add<3>(p, sums);
+}
+
+// Body impulses over a window: the first substep's share, counted k times in all.
+__global__ void k_wrench_extrapolate(double* wrench, const double* before, int n6, double extra) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n6) wrench[i] += extra * (wrench[i] - before[i]);
+}
+
+unsigned grid_for(size_t n, int threads, unsigned cap) {
+    size_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+cudaError_t launch_sur_box(const uint32_t* list, const uint32_t* count, int nb, int nbins_cap, int* box,
+                           cudaStream_t s) {
+    k_sur_box<<<grid_for((size_t)nbins_cap, 256, 512), 256, 0, s>>>(list, count, nb, box);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
+                               double* sums, cudaStream_t s) {
+    k_sur_moments<<<grid_for((size_t)nbins_cap * kBlkNodes, 256, 1024), 256, 0, s>>>(grid, list, count, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
+                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    k_sur_features<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, box, m_scale, v_scale, feat, mask, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                               float unit, int apply, double* sums, cudaStream_t s) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    k_sur_correct<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, bound, box, dv, unit, apply, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s) {
+    if (n6 <= 0) return cudaSuccess;
+    k_wrench_extrapolate<<<(n6 + 255) / 256, 256, 0, s>>>(wrench, before, n6, extra);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

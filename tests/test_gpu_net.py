@@ -205,3 +205,27 @@ def test_adam_matches_oracle(mpm):
     torch.cuda.synchronize()
     assert np.abs(P.cpu().numpy() - rp).max() <= 1e-6
     assert torch.equal(Pb, P.to(torch.bfloat16))
+
+
+def test_tiled_forward_matches_full_on_the_mask(mpm):
+    """The tiled forward (only tiles near the mask computed) gives the full network's output on the mask."""
+    from paper_2302_04659_gb300 import surrogate as sur
+    rng = np.random.default_rng(21)
+    net = sur.Network(seed=3)
+    box = (13, 18, 21)
+    x = dev(rng.normal(size=box + (4,)), torch.bfloat16)
+    mask = np.zeros(box, np.uint8)
+    mask[3:7, 9:12, 2:9] = 1  # a blob in one corner region
+    mask[11, 17, 20] = 1
+    md = torch.from_numpy(mask).cuda()
+    full = net.forward(x).clone()
+    tiled = net.forward(x, md).clone()
+    torch.cuda.synchronize()
+    on = md.bool()
+    assert torch.equal(full[on], tiled[on])
+    nflags = mpm.mpm_conv3d_tile_count(*box)
+    assert nflags == 4 * 3 * 3  # ceil(13/4) * ceil(18/8) * ceil(21/8)
+    flags = torch.zeros(nflags, dtype=torch.uint8, device="cuda")
+    mpm.mpm_conv3d_tile_flags(*box, md.data_ptr(), 0, flags.data_ptr())
+    torch.cuda.synchronize()
+    assert 0 < int(flags.sum()) < nflags

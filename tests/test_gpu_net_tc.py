@@ -1,0 +1,91 @@
+"""GPU parity of the tensor-core (tcgen05) forward convolution with the FP64 network oracle, on the
+surrogate's layer shapes and ragged boxes; masked (tiled) outputs against unmasked ones; the kernel's
+bounded-wait error word stays clear."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import net_oracle as no
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(303)
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    from paper_2302_04659_gb300 import _native, build
+    build.build()
+    return _native
+
+
+def packed(mpm, w, cin, cout):
+    out = torch.zeros(mpm.mpm_conv3d_tc_packed_bytes(cin, cout), dtype=torch.uint8, device="cuda")
+    mpm.mpm_conv3d_pack_tc(cin, cout, w.data_ptr(), out.data_ptr())
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [((1, 16, 8), 32, 32), ((2, 19, 11), 32, 32), ((3, 17, 9), 4, 32), ((5, 21, 13), 32, 3),
+         ((2, 18, 10), 16, 16), ((4, 5, 3), 32, 32), ((1, 1, 1), 4, 32)]
+
+
+@pytest.mark.parametrize("box,cin,cout", CASES)
+@pytest.mark.parametrize("relu,y_f32", [(0, 1), (1, 0)])
+def test_tc_forward_matches_oracle(mpm, box, cin, cout, relu, y_f32):
+    x = torch.from_numpy(RNG.normal(size=box + (cin,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    w = torch.from_numpy((0.2 * RNG.normal(size=(27, cout, cin))).astype(np.float32)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(RNG.normal(size=cout).astype(np.float32)).cuda()
+    y = torch.zeros(box + (cout,), dtype=torch.float32 if y_f32 else torch.bfloat16, device="cuda")
+    wp = packed(mpm, w, cin, cout)
+    mpm.mpm_conv3d_forward_tc(*box, cin, cout, x.data_ptr(), wp.data_ptr(), b.data_ptr(), relu, y_f32, y.data_ptr())
+    assert mpm.mpm_net_tc_status(clear=1) == 0
+    ref = no.conv3d_forward(x.float().cpu().numpy(), w.float().cpu().numpy(), b.cpu().numpy())
+    if relu:
+        ref = no.relu(ref)
+    got = y.float().cpu().numpy()
+    # FP32 output: BF16 products are exact, only the FP32 accumulation order differs
+    assert rel(got, ref) <= (1e-5 if y_f32 else 1e-2)
+
+
+def test_tc_masked_tiles_match_unmasked_on_the_mask(mpm):
+    box, cin, cout = (6, 40, 24), 32, 32
+    x = torch.from_numpy(RNG.normal(size=box + (cin,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    w = torch.from_numpy((0.2 * RNG.normal(size=(27, cout, cin))).astype(np.float32)).to(torch.bfloat16).cuda()
+    wp = packed(mpm, w, cin, cout)
+    mask = np.zeros(box, np.uint8)
+    mask[2:4, 5:9, 3:6] = 1
+    md = torch.from_numpy(mask).cuda()
+    ntiles = mpm.mpm_conv3d_tc_tile_count(*box)
+    assert ntiles == 6 * 3 * 3
+    dist = torch.zeros(ntiles, dtype=torch.uint8, device="cuda")
+    mpm.mpm_conv3d_tc_tile_dist(*box, md.data_ptr(), dist.data_ptr())
+    full = torch.zeros(box + (cout,), dtype=torch.float32, device="cuda")
+    part = torch.full(box + (cout,), 7.0, dtype=torch.float32, device="cuda")
+    mpm.mpm_conv3d_forward_tc(*box, cin, cout, x.data_ptr(), wp.data_ptr(), 0, 0, 1, full.data_ptr())
+    mpm.mpm_conv3d_forward_tc(*box, cin, cout, x.data_ptr(), wp.data_ptr(), 0, 0, 1, part.data_ptr(), dist.data_ptr(), 2)
+    assert mpm.mpm_net_tc_status(clear=1) == 0
+    f, p = full.cpu().numpy(), part.cpu().numpy()
+    # the distance map against a brute-force one
+    d = dist.cpu().numpy()
+    pts = np.argwhere(mask)
+    for t in range(ntiles):
+        x0, y0, z0 = (t % 3) * 8, ((t // 3) % 3) * 16, t // 9
+        zs, ys, xs = [z0], range(y0, min(y0 + 16, box[1])), range(x0, min(x0 + 8, box[2]))
+        best = 5
+        for z in zs:
+            for yy in ys:
+                for xx in xs:
+                    best = min(best, int(np.abs(pts - [z, yy, xx]).max(axis=1).min()))
+        assert d[t] == min(best, 5), (t, d[t], best)
+    # every voxel within distance 2 of the mask is computed exactly as without the mask
+    near = np.zeros(box, bool)
+    for z, yy, xx in pts:
+        near[max(z - 2, 0):z + 3, max(yy - 2, 0):yy + 3, max(xx - 2, 0):xx + 3] = True
+    np.testing.assert_array_equal(p[near], f[near])
+    # tiles far from the mask are zero-filled, not left stale
+    assert not (p == 7.0).any()
+    assert (p == 0.0).any()

@@ -1,0 +1,168 @@
+"""GPU tests of the learned-surrogate window (an extension of the method).
+
+Parity: a corrected window (plain grid update, a seeded correction field, one grid-to-particle pass with
+k*dt) against the oracle's window, element-wise at the parity tolerances, plus the gate's sums; the
+fallback path against plain substeps. Function: the box covers the material; a short training run lowers
+the loss; the trained network (committed weights) beats the same window without it on held-out scenes and
+stays within the 1e-3 relative position error after one environment step."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import TOL_C, TOL_F, TOL_V, TOL_X, make_sim, oracle_colliders, oracle_params, oracle_state, rel, rel_C
+from paper_2302_04659_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2302_04659_gb300 import _native, build, surrogate
+    build.build()
+    return _native, surrogate
+
+
+def test_box_covers_material(mods):
+    mpm, sur = mods
+    sc = scenes.pinch_scene(seed=1000, N=50_000)
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    box = mpm.mpm_surrogate_box(sim.handle, 3)
+    g = sim.read_grid().cpu().numpy()
+    idx = np.argwhere(g[..., 0] > 0)
+    lo, hi = idx.min(0), idx.max(0)
+    assert np.all(np.array([box.i0, box.j0, box.k0]) <= np.maximum(lo - 3, 0))
+    assert np.all(np.array([box.i0 + box.D, box.j0 + box.H, box.k0 + box.W]) >= np.minimum(hi + 4, sc.n))
+    sim.close()
+
+
+@pytest.mark.parametrize("variant", ["rand", "pinch"])
+def test_corrected_window_matches_oracle(mods, variant):
+    mpm, sur = mods
+    if variant == "rand":
+        sc = scenes.cube_scene("rand")
+        cols = None
+    else:
+        sc = scenes.pinch_scene(seed=1003, N=30_000)
+        cols = scenes.finger_state(sc, 0.15)
+    k = 5
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    if cols is not None:
+        sim.set_shapes(sc.shapes)
+        sim.set_colliders(*cols)
+    box = mpm.mpm_surrogate_box(sim.handle, 4)
+    dims = box.dims()
+    rng = np.random.default_rng(9)
+    dv = (0.5 * rng.normal(size=dims + (3,))).astype(np.float32)
+    feat = torch.empty(dims + (4,), dtype=torch.float32, device="cuda")
+    mask = torch.empty(dims, dtype=torch.uint8, device="cuda")
+    dvd = torch.from_numpy(dv).cuda()
+    m_scale = sur.mass_scale(sc.material.rho, sc.n)
+    mpm.mpm_surrogate_features(sim.handle, box, m_scale, sur.V_SCALE, feat.data_ptr(), mask.data_ptr())
+    r = mpm.mpm_surrogate_check(sim.handle, box, dvd.data_ptr(), sur.DV_UNIT, k, 1.0)
+    mpm.mpm_surrogate_advance(sim.handle, box, dvd.data_ptr(), sur.DV_UNIT, k)
+    out = sim.read_state(on_device=False)
+    flags = sim.status()
+    n_sub = sim.read_wrench()[1] if cols is not None else None
+    sim.close()
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    ocols = oracle_colliders(sc, *cols) if cols is not None else ()
+    keep = np.ones(sc.N, bool)
+    if cols is not None:  # particles near a node whose contact branch FP32 and FP64 may take differently
+        _, _, amb = oracle.grid_update(P, oracle.p2g(P, ref), ocols, 0.0, want_ambiguous=True)
+        base = np.floor(sc.x.astype(np.float64) * sc.n - 0.5).astype(int)
+        for node in np.argwhere(amb):
+            keep &= ~np.all((node[:, None] >= base) & (node[:, None] <= base + 2), axis=0)
+        assert (~keep).sum() <= 1e-3 * sc.N
+    sums = oracle.surrogate_window(P, ref, dv, (box.i0, box.j0, box.k0, *dims), sur.DV_UNIT, k, ocols, 0.0)
+    dx = 1.0 / sc.n
+    m = keep
+    assert rel(out["x"][:, m], ref.x[:, m]) <= TOL_X
+    assert rel(out["v"][:, m], ref.v[:, m]) <= TOL_V
+    assert rel_C(out["C"][:, m], ref.C[:, m], ref.v[:, m], dx) <= TOL_C
+    assert rel(out["F"][:, m], ref.F[:, m]) <= TOL_F
+    # the gate's sums: grid mass exactly the particles', momenta as the oracle's
+    M = sums["M"]
+    assert abs(r[2] - M) <= 1e-6 * M
+    assert r[0] <= 1e-6
+    pexp = sums["P0"] + 0.5 * (k + 1) * (sums["P1"] - sums["P0"])
+    dref = np.linalg.norm(sums["P_hat"] - pexp)
+    assert abs(r[3] - dref) <= 1e-4 * max(dref, 1e-6) + 1e-6 * M
+    # the features hold the updated grid over the box
+    g1 = feat.cpu().numpy()
+    assert np.all((g1[..., 0] > 0) == (mask.cpu().numpy() > 0))
+    if n_sub is not None:
+        assert n_sub == k  # the substep counter moved by the whole window
+
+
+def test_fallback_window_equals_plain_substeps(mods):
+    mpm, sur = mods
+    sc = scenes.pinch_scene(seed=1004, N=40_000)
+    cols = scenes.finger_state(sc, 0.12)
+    res = []
+    for mode in ("plain", "fallback"):
+        sim = make_sim(sc)
+        sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+        sim.set_shapes(sc.shapes)
+        sim.set_colliders(*cols)
+        if mode == "plain":
+            sim.substep(10)
+        else:
+            runner = sur.Runner(sim, None, sc.material.rho, threshold=-1.0)  # the gate always refuses
+            box = runner.box()
+            for _ in range(2):
+                assert not runner.window(box)
+            assert runner.fallbacks == 2
+        res.append((sim.read_state(on_device=False)["x"], sim.read_wrench()))
+        sim.close()
+    assert rel(res[1][0], res[0][0]) <= 1e-6
+    assert res[1][1][1] == res[0][1][1] == 10
+    assert rel(res[1][1][0], res[0][1][0]) <= 1e-5
+
+
+def test_substep_refused_inside_a_window(mods):
+    mpm, sur = mods
+    sc = scenes.cube_scene("floor")
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    runner = sur.Runner(sim, None, sc.material.rho)
+    box = runner.box()
+    runner.start(box)
+    with pytest.raises(mpm.MpmError):
+        sim.substep(1)
+    mpm.mpm_surrogate_advance(sim.handle, box, 0, sur.DV_UNIT, sur.K)
+    sim.substep(1)
+    sim.close()
+
+
+def test_training_lowers_the_loss(mods):
+    mpm, sur = mods
+    samples = sur.generate([10000, 10001], particles=20_000, env_steps=3, sample_steps=(1, 2),
+                           windows_per_step=(0, 1, 2, 3, 4))
+    assert len(samples) == 20
+    net = sur.Network(seed=1)
+    hist = sur.train(net, samples, epochs=8, lr=2e-3, lr_end=2e-4)
+    assert hist[-1] < 0.7 * hist[0], hist
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                    "paper_2302_04659_gb300", "weights", "surrogate_pinch64.npz")),
+                    reason="trained weights not present")
+def test_trained_network_gains_over_the_window_without_it(mods):
+    """On held-out pinch scenes: the trained network's windows stay within 1e-3 relative position error
+    of the plain method after one environment step, and are more accurate than the same windows with a
+    zero correction (one big grid-to-particle step after one grid update)."""
+    mpm, sur = mods
+    net = sur.Network.load(sur.WEIGHTS)
+    seeds = range(20000, 20004)
+    with_net = sur.summarize(sur.evaluate(net, seeds, gate=False))
+    without = sur.summarize(sur.evaluate(None, seeds, gate=False))
+    gated = sur.summarize(sur.evaluate(net, seeds, gate=True))
+    assert with_net["rel_x_max"] <= 1e-3
+    assert gated["rel_x_max"] <= 1e-3
+    assert with_net["rel_to_displacement_mean"] < without["rel_to_displacement_mean"]

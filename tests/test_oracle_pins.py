@@ -511,3 +511,40 @@ def test_clamp_keeps_stencils_inside():
     ncl, _, _ = oracle.substep(P, s)
     assert ncl == 2
     assert s.x[0, 0] == 2 * dx and s.x[0, 2] == 1 - 2 * dx
+
+
+# ---------------------------------------------------------------------------- surrogate window (extension)
+
+def test_surrogate_window_reduces_to_a_substep_and_scales_with_k():
+    """With no correction and k = 1 the window is exactly one substep; with k > 1 the grid-to-particle
+    pass moves by k times the one-substep displacement with the same v and C (the gathered velocity does
+    not depend on the step), and F takes (I + k dt C)."""
+    sc = scenes.cube_scene("rand")
+    m = sc.material
+    P = oracle.Params(n=sc.n, dt=sc.dt, kind=m.kind, E=m.E, nu=m.nu, yield_stress=1e9, rho=m.rho, p_vol=m.p_vol)
+    base = oracle.State.from_arrays(sc.x, sc.v, sc.C, sc.F)
+    dv = np.zeros((sc.n, sc.n, sc.n, 3))
+    box = (0, 0, 0, sc.n, sc.n, sc.n)
+    a = oracle.State.from_arrays(sc.x, sc.v, sc.C, sc.F)
+    oracle.substep(P, a)
+    b = oracle.State.from_arrays(sc.x, sc.v, sc.C, sc.F)
+    oracle.surrogate_window(P, b, dv, box, 0.01, 1)
+    for f in ("x", "v", "C", "F"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+    c = oracle.State.from_arrays(sc.x, sc.v, sc.C, sc.F)
+    sums = oracle.surrogate_window(P, c, dv, box, 0.01, 4)
+    free = (b.x > 2.0 / sc.n + 1e-9) & (b.x < 1 - 2.0 / sc.n - 1e-9)  # not clamped
+    np.testing.assert_allclose((c.x - base.x)[free], 4 * (b.x - base.x)[free], rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(c.v, b.v, rtol=0, atol=0)
+    np.testing.assert_allclose(c.C, b.C, rtol=0, atol=0)
+    C = b.C.T.reshape(-1, 3, 3)
+    F0 = base.F.T.reshape(-1, 3, 3)
+    Fk = np.einsum("pab,pbc->pac", np.eye(3) + 4 * sc.dt * C, F0)  # no yielding at this yield stress
+    np.testing.assert_allclose(c.F.T.reshape(-1, 3, 3), Fk, rtol=1e-12, atol=1e-14)
+    # a uniform correction shifts the corrected momentum by M * unit * dv at nodes off the wall band
+    d = oracle.State.from_arrays(sc.x, sc.v, sc.C, sc.F)
+    dv1 = np.zeros_like(dv)
+    dv1[..., 1] = 1.0
+    s1 = oracle.surrogate_window(P, d, dv1, box, 0.01, 4)
+    assert s1["P_hat"][1] > sums["P_hat"][1]
+    np.testing.assert_allclose(s1["P_hat"][[0, 2]], sums["P_hat"][[0, 2]], rtol=1e-12, atol=1e-15)
