@@ -261,6 +261,40 @@ mpm_status mpm_surrogate_check(mpm_sim* sim, const mpm_box* box, const float* d_
 mpm_status mpm_surrogate_advance(mpm_sim* sim, const mpm_box* box, const float* d_dv, float dv_unit, int k,
                                  void* stream);
 
+/* The surrogate network attached to a handle, so that whole environment steps of windows run inside
+ * the library (graph-replayed, the gate decided on the device, no host synchronization per window).
+ * Network: four 3x3x3 convolutions 4 -> 32 -> 32 -> 32 -> 3 (ReLU between), weights packed for the
+ * tensor-core forward (mpm_conv3d_pack_tc in mpm_net.h), biases FP32, all device memory the caller owns
+ * and keeps alive while attached. */
+typedef struct {
+    const void* w_packed[4];
+    const float* bias[4];
+    float m_scale, v_scale;  /* network input: (m * m_scale, v * v_scale) */
+    float dv_unit;           /* m/s per network output unit */
+    double v_ref;            /* velocity scale of the momentum residual */
+    double threshold;        /* fallback when the mass or momentum residual exceeds this */
+    int k;                   /* substeps per window, odd */
+    int margin;              /* nodes added around the material's bins for the box */
+} mpm_surrogate_net;
+
+/* Device workspace for the network's buffers over boxes of up to max_voxels nodes. */
+size_t mpm_surrogate_workspace_size(int max_voxels);
+
+/* Attach (net != NULL) or detach the network. One-env handles whose bins fit the fused scan only. */
+mpm_status mpm_surrogate_attach(mpm_sim* sim, const mpm_surrogate_net* net, void* d_workspace, size_t bytes,
+                                int max_voxels);
+
+/* n_substeps (a multiple of k) as windows of the attached network, from one box computed for the call
+ * (one host synchronization). gate != 0: each window whose residuals exceed the threshold runs as k
+ * plain substeps instead, decided on the device; gate == 0: every window uses the network. A box larger
+ * than max_voxels runs plain substeps. Enqueued as one graph launch per call. */
+mpm_status mpm_surrogate_step(mpm_sim* sim, int n_substeps, int gate, void* stream);
+
+/* Device counters of gated windows: windows run, fallbacks taken, and the last window's (mass,
+ * momentum) residuals; reset != 0 zeroes the counters. Synchronizes `stream`. */
+mpm_status mpm_surrogate_stats(mpm_sim* sim, long long* windows, long long* fallbacks, double* residuals, int reset,
+                               void* stream);
+
 /* Release the host handle (the workspace stays the caller's). Safe on NULL. Does not synchronize:
  * the caller must not free the workspace before work enqueued on it has finished. */
 void mpm_destroy(mpm_sim* sim);

@@ -58,6 +58,12 @@ class mpm_box(ctypes.Structure):
         return (self.D, self.H, self.W)
 
 
+class mpm_surrogate_net(ctypes.Structure):
+    _fields_ = [("w_packed", ctypes.c_void_p * 4), ("bias", ctypes.c_void_p * 4), ("m_scale", ctypes.c_float),
+                ("v_scale", ctypes.c_float), ("dv_unit", ctypes.c_float), ("v_ref", ctypes.c_double),
+                ("threshold", ctypes.c_double), ("k", ctypes.c_int), ("margin", ctypes.c_int)]
+
+
 class MpmError(RuntimeError):
     def __init__(self, fn, status, detail=""):
         self.status = status
@@ -130,6 +136,11 @@ def _load():
         "mpm_surrogate_check": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_double), _vp]),
         "mpm_surrogate_advance": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, _vp]),
+        "mpm_surrogate_workspace_size": (ctypes.c_size_t, [ctypes.c_int]),
+        "mpm_surrogate_attach": (st, [_vp, ctypes.POINTER(mpm_surrogate_net), _vp, ctypes.c_size_t, ctypes.c_int]),
+        "mpm_surrogate_step": (st, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+        "mpm_surrogate_stats": (st, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int, _vp]),
         "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mpm_last_error": (ctypes.c_char_p, []),
     }
@@ -391,3 +402,24 @@ def mpm_surrogate_check(sim, box: mpm_box, dv, dv_unit, k, v_ref, stream=0):
 def mpm_surrogate_advance(sim, box: mpm_box, dv, dv_unit, k, stream=0):
     _check("mpm_surrogate_advance", _load().mpm_surrogate_advance(sim, ctypes.byref(box) if box is not None else None,
                                                                   dv or None, dv_unit, k, stream))
+
+
+def mpm_surrogate_workspace_size(max_voxels) -> int:
+    return _load().mpm_surrogate_workspace_size(max_voxels)
+
+
+def mpm_surrogate_attach(sim, net, d_workspace, nbytes, max_voxels):
+    _check("mpm_surrogate_attach", _load().mpm_surrogate_attach(sim, ctypes.byref(net) if net is not None else None,
+                                                                d_workspace, nbytes, max_voxels))
+
+
+def mpm_surrogate_step(sim, n_substeps, gate=1, stream=0):
+    _check("mpm_surrogate_step", _load().mpm_surrogate_step(sim, n_substeps, gate, stream))
+
+
+def mpm_surrogate_stats(sim, reset=0, stream=0):
+    """Returns (windows, fallbacks, (mass residual, momentum residual) of the last window)."""
+    w, f = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    r = (ctypes.c_double * 2)()
+    _check("mpm_surrogate_stats", _load().mpm_surrogate_stats(sim, ctypes.byref(w), ctypes.byref(f), r, reset, stream))
+    return w.value, f.value, (r[0], r[1])

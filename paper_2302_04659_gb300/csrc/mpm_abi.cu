@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 
 #include "mpm.h"
 #include "mpm_internal.h"
+#include "mpm_net.h"
 
 using namespace mpm;
 
@@ -94,7 +96,8 @@ Layout make_layout(const Totals& T, int nenv) {
     L.poses = take((kcap > (size_t)kSharedPoses ? (size_t)kPoseSteps * kcap : 1) * sizeof(ColliderNow));
     L.wrench = take(kcap * 6 * sizeof(double));
     L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
-    L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + kcap * 6 * sizeof(double));  // surrogate window
+    // surrogate window: sums, box, gate word, stats, the wrench before the window
+    L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double) + kcap * 6 * sizeof(double));
     L.total = off;
     return L;
 }
@@ -186,6 +189,13 @@ struct mpm_sim {
     std::vector<int> shape_counts;  // shapes per env
     int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
     bool sur_pending = false;  // a surrogate window was started and not yet ended
+    // attached surrogate network (mpm_surrogate_attach)
+    bool net_attached = false;
+    mpm_surrogate_net net{};
+    char* net_ws = nullptr;
+    int net_max_voxels = 0;
+    std::vector<GraphEntry> sur_graphs;
+    std::vector<std::array<int, 8>> sur_keys;  // box (6), substeps, gate of each cached graph
     ColliderSet* stage = nullptr;  // pinned staging for collider uploads
     cudaEvent_t stage_done = nullptr;
     int sms = 0;
@@ -221,7 +231,9 @@ struct mpm_sim {
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
     double* sur_sums() { return at<double>(L.sur); }  // M, P0[3], P1[3], P_hat[3]
     int* sur_box() { return reinterpret_cast<int*>(at<char>(L.sur) + 16 * sizeof(double)); }
-    double* sur_wrench() { return at<double>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
+    uint32_t* sur_gate() { return at<uint32_t>(L.sur + 16 * sizeof(double) + 6 * sizeof(int)); }
+    unsigned long long* sur_stats() { return at<unsigned long long>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
+    double* sur_wrench() { return at<double>(L.sur + 16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double)); }
     const EnvDesc* envs_dev() { return at<EnvDesc>(L.envs); }
     bool tail_scan() const { return T.bins <= (size_t)kTailScanMaxBins; }
     StateView view(int which) {
@@ -246,11 +258,14 @@ struct mpm_sim {
         return e;
     }
     void drop_graphs() {
-        for (auto& ge : graphs) {
-            cudaGraphExecDestroy(ge.exec);
-            cudaGraphDestroy(ge.graph);
-        }
+        for (auto* list : {&graphs, &sur_graphs})
+            for (auto& ge : *list) {
+                cudaGraphExecDestroy(ge.exec);
+                cudaGraphDestroy(ge.graph);
+            }
         graphs.clear();
+        sur_graphs.clear();
+        sur_keys.clear();
     }
 };
 
@@ -403,10 +418,12 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
 }
 
 // First half of a substep: the sort-assign of the current state and the grid update of its transfer.
-mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st) {
+mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate = nullptr, uint32_t gate_run = 1) {
     MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
     AssignGridParams ap{};
+    ap.gate = gate;
+    ap.gate_run = gate_run;
     ap.grid = grid_params(s);
     ap.N = s->N;
     ap.keyrank = s->at<uint2>(s->L.key);
@@ -420,8 +437,11 @@ mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st) {
 
 // Second half: the fused G2P -> P2G pass from the updated grid (advecting by advect_dt, the substep's dt
 // unless a surrogate window overrides it for a one-env handle), then the bin scan if it is separate.
-mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 0.0f) {
+mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 0.0f, const uint32_t* gate = nullptr,
+                                 uint32_t gate_run = 1) {
     TransferParams p = transfer_params(s);
+    p.gate = gate;
+    p.gate_run = gate_run;
     p.grid_in = s->at<float4>(s->L.grid[s->ps.g]);
     p.grid_out = s->at<float4>(s->L.grid[1 - s->ps.g]);
     p.flags_out = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
@@ -1060,6 +1080,205 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
     }
     MPM_TRY(enqueue_particle_half(s, st));
     return k > 1 ? enqueue_substeps(s, k - 1, st) : MPM_OK;
+}
+
+// ---- attached network: the whole surrogate environment step inside the library (graph-replayed)
+
+namespace {
+
+struct NetLayout {
+    size_t feat, xbf, act[3], out, mask, dist, total;
+};
+
+NetLayout net_layout(int max_voxels) {
+    NetLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t v = (size_t)std::max(max_voxels, 1);
+    L.feat = take(v * 16);
+    L.xbf = take(v * 8);
+    for (int i = 0; i < 3; ++i) L.act[i] = take(v * 64);
+    L.out = take(v * 12);
+    L.mask = take(v);
+    L.dist = take(v);  // at least one byte per tile
+    L.total = off;
+    return L;
+}
+
+constexpr int kNetChannels[5] = {4, 32, 32, 32, 3};
+
+// One window (k substeps) from the current pipeline state: plain grid update, network, device-side gate,
+// then both branches enqueued, each running only on its side of the gate.
+mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, bool gate_on, cudaStream_t st) {
+    const mpm_surrogate_net& net = s->net;
+    const int k = net.k;
+    const NetLayout NL = net_layout(s->net_max_voxels);
+    char* ws = s->net_ws;
+    const SurBox box = to_sur_box(&b);
+    const Geometry& g = s->envs[0].geo;
+    double* sums = s->sur_sums();
+    MPM_TRY(ensure_scanned(s, st));
+    MPM_TRY(ensure_grid(s, st));
+    if (gate_on) {  // the gate's sums: mass and momentum before the grid update
+        MPM_CUDA(cudaMemsetAsync(sums, 0, 16 * sizeof(double), st), "cudaMemsetAsync");
+        MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
+                                    (int)s->T.bins, sums, st),
+                 "sur_moments");
+    }
+    if (s->ncol > 0)
+        MPM_CUDA(cudaMemcpyAsync(s->sur_wrench(), s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy wrench");
+    MPM_TRY(enqueue_grid_half(s, st));
+    uint8_t* mask = reinterpret_cast<uint8_t*>(ws + NL.mask);
+    uint8_t* dist = reinterpret_cast<uint8_t*>(ws + NL.dist);
+    float* dv = reinterpret_cast<float*>(ws + NL.out);
+    MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, box, net.m_scale, net.v_scale,
+                                 nullptr, mask, gate_on ? sums + 4 : nullptr, st, ws + NL.xbf),
+             "sur_features");
+    MPM_TRY(mpm_conv3d_tc_tile_dist(b.D, b.H, b.W, mask, dist, st));
+    const void* in = ws + NL.xbf;
+    for (int i = 0; i < 4; ++i) {
+        const bool last = i == 3;
+        void* out = last ? static_cast<void*>(dv) : static_cast<void*>(ws + NL.act[i]);
+        MPM_TRY(mpm_conv3d_forward_tc(b.D, b.H, b.W, kNetChannels[i], kNetChannels[i + 1], in, net.w_packed[i],
+                                      net.bias[i], last ? 0 : 1, last ? 1 : 0, out, dist, 3 - i, st));
+        in = out;
+    }
+    if (gate_on) {
+        MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv, net.dv_unit,
+                                    0, sums + 7, st),
+                 "sur_check");
+        const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
+        MPM_CUDA(launch_sur_gate(sums, mp, k, net.v_ref, net.threshold, s->sur_gate(), s->sur_stats(), st),
+                 "sur_gate");
+    }
+    // without the gate every window takes the surrogate branch and the plain one is not enqueued
+    uint32_t* gate = gate_on ? s->sur_gate() : nullptr;
+    const PipeState before = s->ps;
+    // the surrogate branch: correction (with the counter and impulse bookkeeping), then the k*dt pass
+    MPM_CUDA(launch_sur_apply(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv, net.dv_unit, gate,
+                              s->substep_counter(), k, s->at<double>(s->L.wrench), s->sur_wrench(), s->ncol * 6, st),
+             "sur_apply");
+    MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt, gate, 1u));
+    const PipeState after = s->ps;
+    if (!gate_on) return MPM_OK;
+    // the plain branch, from the same state; with k odd it ends in the same buffers
+    s->ps = before;
+    MPM_TRY(enqueue_particle_half(s, st, 0.0f, gate, 0u));
+    for (int it = 1; it < k; ++it) {
+        MPM_TRY(enqueue_grid_half(s, st, gate, 0u));
+        MPM_TRY(enqueue_particle_half(s, st, 0.0f, gate, 0u));
+    }
+    if (!(s->ps == after)) return MPM_ERR_INVALID_ARG;
+    return MPM_OK;
+}
+
+}  // namespace
+
+size_t mpm_surrogate_workspace_size(int max_voxels) { return max_voxels > 0 ? net_layout(max_voxels).total : 0; }
+
+mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* d_workspace, size_t bytes,
+                                int max_voxels) {
+    if (!s || s->nenv != 1 || !s->tail_scan()) return MPM_ERR_INVALID_ARG;
+    if (!net) {
+        s->net_attached = false;
+        s->drop_graphs();
+        return MPM_OK;
+    }
+    if (net->k < 1 || net->k % 2 == 0 || net->margin < 0 || !(net->dv_unit > 0.0f) || !(net->v_ref > 0.0) ||
+        max_voxels < 1)
+        return MPM_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (!net->w_packed[i] || reinterpret_cast<uintptr_t>(net->w_packed[i]) % 16) return MPM_ERR_INVALID_ARG;
+    if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % kAlign || bytes < net_layout(max_voxels).total)
+        return MPM_ERR_WORKSPACE;
+    s->net = *net;
+    s->net_ws = static_cast<char*>(d_workspace);
+    s->net_max_voxels = max_voxels;
+    s->net_attached = true;
+    s->drop_graphs();
+    return MPM_OK;
+}
+
+mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream) {
+    if (!s || !s->net_attached || s->sur_pending || n_substeps < 0 || n_substeps % s->net.k) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_substeps == 0) return MPM_OK;
+    mpm_box b{};
+    MPM_TRY(mpm_surrogate_box(s, s->net.margin, &b, stream));
+    if (b.D == 0 || (size_t)b.D * b.H * b.W > (size_t)s->net_max_voxels) return mpm_substep(s, n_substeps, stream);
+    const std::array<int, 8> key{b.i0, b.j0, b.k0, b.D, b.H, b.W, n_substeps, gate ? 1 : 0};
+    GraphEntry* ge = nullptr;
+    for (size_t i = 0; i < s->sur_graphs.size(); ++i)
+        if (s->sur_keys[i] == key && s->sur_graphs[i].before == s->ps && s->sur_graphs[i].ncol == s->ncol)
+            ge = &s->sur_graphs[i];
+    if (!ge) {
+        if (s->sur_graphs.size() >= 16) {  // keep a bounded cache
+            cudaGraphExecDestroy(s->sur_graphs.front().exec);
+            cudaGraphDestroy(s->sur_graphs.front().graph);
+            s->sur_graphs.erase(s->sur_graphs.begin());
+            s->sur_keys.erase(s->sur_keys.begin());
+        }
+        if (!s->cap_stream)
+            MPM_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        GraphEntry fresh{};
+        fresh.n_substeps = n_substeps;
+        fresh.N = s->N;
+        fresh.ncol = s->ncol;
+        fresh.before = s->ps;
+        const long long l0 = s->launches;
+        const unsigned mask_saved = s->timing_mask;
+        s->timing_mask = 0;  // no timing events inside these graphs
+        MPM_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        s->capturing = true;
+        mpm_status r = MPM_OK;
+        for (int w = 0; w < n_substeps / s->net.k && r == MPM_OK; ++w) r = enqueue_window(s, b, gate != 0, s->cap_stream);
+        s->capturing = false;
+        s->timing_mask = mask_saved;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+        fresh.after = s->ps;
+        fresh.launches = s->launches - l0;
+        s->ps = fresh.before;
+        s->launches = l0;
+        if (r != MPM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&fresh.exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        fresh.graph = graph;
+        s->sur_graphs.push_back(fresh);
+        s->sur_keys.push_back(key);
+        ge = &s->sur_graphs.back();
+    }
+    MPM_CUDA(cudaGraphLaunch(ge->exec, st), "cudaGraphLaunch");
+    s->ps = ge->after;
+    s->launches += ge->launches;
+    return MPM_OK;
+}
+
+mpm_status mpm_surrogate_stats(mpm_sim* s, long long* windows, long long* fallbacks, double* residuals, int reset,
+                               void* stream) {
+    if (!s) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long h[4];
+    MPM_CUDA(cudaMemcpyAsync(h, s->sur_stats(), sizeof(h), cudaMemcpyDeviceToHost, st), "copy stats");
+    if (reset) MPM_CUDA(cudaMemsetAsync(s->sur_stats(), 0, 2 * sizeof(unsigned long long), st), "cudaMemsetAsync");
+    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (windows) *windows = (long long)h[0];
+    if (fallbacks) *fallbacks = (long long)h[1];
+    if (residuals) std::memcpy(residuals, &h[2], 2 * sizeof(double));
+    return MPM_OK;
 }
 
 mpm_status mpm_set_timing(mpm_sim* s, unsigned kernel_mask) {

@@ -89,6 +89,8 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     int tail_scan;
     int total_bins;
     int chunk;              // most particles per chunk (<= kChunk)
+    const uint32_t* gate;   // if set, the launch runs only when *gate == gate_run (read after the wait)
+    uint32_t gate_run;
     const uint32_t* bin_env;  // env of every global bin (for the chunk list)
     uint32_t* cursor;
     int4* chunks_next;
@@ -137,6 +139,8 @@ struct AssignGridParams {  // the sort-assign of the new state and the grid upda
     const uint32_t* cursor;
     uint32_t* perm;
     int assign_ctas;          // the first assign_ctas CTAs assign sorted slots (0: no assign)
+    const uint32_t* gate;     // if set, the launch runs only when *gate == gate_run (read after the wait)
+    uint32_t gate_run;
 };
 
 struct LoadParams {  // mpm_set_particles*: copy in, clamp, bin keys and ranks
@@ -189,10 +193,25 @@ cudaError_t launch_sur_box(const uint32_t* list, const uint32_t* count, int nb, 
 cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
                                double* sums, cudaStream_t s);
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
-                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s);
+                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s,
+                                void* feat_bf16 = nullptr);
 cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
                                float unit, int apply, double* sums, cudaStream_t s);
-cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s);
+cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s,
+                                      const uint32_t* gate = nullptr, uint32_t gate_run = 1);
+// The device-side gate of a window: from the sums (M, P0, P1, P_hat) the mass and momentum residuals;
+// gate = 1 if both are within threshold, else 0; stats[0..1] += (windows, fallbacks), stats[2..3] the
+// residuals (doubles after the two 64-bit counters).
+cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
+                            uint32_t* gate, unsigned long long* stats, cudaStream_t s);
+// The correction written back (only if *gate == 1 when gate is set), with the window's substep-counter and
+// body-impulse bookkeeping.
+cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv, float unit,
+                             const uint32_t* gate, uint32_t* counter, int k, double* wrench,
+                             const double* wrench_before, int n6, cudaStream_t s);
+cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run,
+                                         cudaStream_t s);
+cudaError_t launch_cast_to_bf16(int n, const float* src, void* dst, cudaStream_t s);
 
 // occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
 int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env);

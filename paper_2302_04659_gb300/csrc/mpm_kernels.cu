@@ -637,6 +637,10 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
     const int N = p.N;
     uint32_t flags = 0;
     wait_for_predecessor();
+    if (p.gate && *p.gate != p.gate_run) {  // the other branch of a gated window runs instead
+        release_successor();
+        return;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
     const uint32_t nchunks = *p.num_chunks;
     int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
@@ -940,6 +944,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
 template <bool ONE_ENV, bool SHARED_POSES>
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
     wait_for_predecessor();  // (a CTA's exit releases the successor)
+    if (p.gate && *p.gate != p.gate_run) return;  // the other branch of a gated window runs instead
     if ((int)blockIdx.x < p.assign_ctas) {
         assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
         return;
@@ -1004,7 +1009,8 @@ __global__ void k_set_colliders(const ColliderSet* cols, int k, ColliderNow* pos
     }
 }
 
-__global__ void k_advance_counter(uint32_t* counter, int n) {
+__global__ void k_advance_counter(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run) {
+    if (gate && *gate != gate_run) return;
     if (threadIdx.x == 0) *counter += (uint32_t)n;
 }
 
@@ -1112,7 +1118,13 @@ cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* po
 }
 
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s) {
-    k_advance_counter<<<1, 32, 0, s>>>(counter, n);
+    k_advance_counter<<<1, 32, 0, s>>>(counter, n, nullptr, 0u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run,
+                                         cudaStream_t s) {
+    k_advance_counter<<<1, 32, 0, s>>>(counter, n, gate, gate_run);
     return cudaGetLastError();
 }
 

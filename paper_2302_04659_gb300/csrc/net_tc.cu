@@ -123,38 +123,104 @@ __device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
 // K steps: CG = input channel groups of 8 (1 for 4 channels, 2 or 4 for 16 or 32).
 __host__ __device__ constexpr int k_steps(int cg) { return cg == 1 ? 18 : 27 * cg / 2; }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// Stage the halo of tile (z0, y0, x0) into one plane buffer with asynchronous copies (zero-filled
+// outside the box).
+template <int CG>
+__device__ __forceinline__ void stage_async(const Args& a, uint32_t buf, int z0, int y0, int x0) {
+    for (int i = threadIdx.x; i < HV * CG; i += kThreads) {
+        const int h = i / CG, q = i % CG;
+        const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - 1 + h % HX;
+        const bool in = z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W;
+        const __nv_bfloat16* src = in ? a.x + (((size_t)z * a.H + yy) * a.W + xq) * a.cin + q * 8 : a.x;
+        const uint32_t dst = buf + q * kPlaneBytes + h * 16;
+        if constexpr (CG == 1)
+            cp_async8(dst, src, in ? 8u : 0u);  // 4 channels; the row's other 8 bytes stay zero
+        else
+            cp_async16(dst, src, in ? 16u : 0u);
+    }
+}
+
+template <int NPAD>
+__device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z0, int y0, int x0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = warp * 32 + lane;
+    const int y = y0 + m / TX, xx = x0 + m % TX;
+    float acc[NPAD];
+    tmem_load<NPAD>(tmem_acc + ((uint32_t)(warp * 32) << 16), acc);
+    if (y >= a.H || xx >= a.W) return;
+    const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
+    if (!a.y_f32 && a.cout == 32) {
+        uint32_t packed[16];
+#pragma unroll
+        for (int n = 0; n < 32; n += 2) {
+            float v0 = acc[n] + (a.bias ? a.bias[n] : 0.0f), v1 = acc[n + 1] + (a.bias ? a.bias[n + 1] : 0.0f);
+            if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(v0, v1);
+            packed[n / 2] = *reinterpret_cast<const uint32_t*>(&p2);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vox * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < NPAD; ++n) {
+            if (n >= a.cout) break;
+            float v = acc[n] + (a.bias ? a.bias[n] : 0.0f);
+            if (a.relu) v = fmaxf(v, 0.0f);
+            if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = v;
+            else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(v);
+        }
+    }
+}
+
+// Persistent, software-pipelined: while the tensor core runs the MMAs of tile j (accumulator j % 2), the
+// threads stage tile j + 1's halo into the other plane buffer and store tile j - 1 from the other
+// accumulator.
 template <int NPAD, int CG>
-__global__ void __launch_bounds__(kThreads, 2) k_conv_tc(Args a) {
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int S = k_steps(CG);
     constexpr int kBBlock = NPAD * 32;  // bytes of one K step of B: 2 k-groups x NPAD/8 n-groups x 128
-    unsigned char* planes = smem;                                   // CG planes of kPlaneBytes
-    unsigned char* bsm = smem + CG * kPlaneBytes;                   // S blocks of kBBlock
-    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);  // [0]: MMAs done, [1]: weights landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kBuf = CG * kPlaneBytes;
+    unsigned char* planes = smem;                                   // 2 buffers of CG planes
+    unsigned char* bsm = smem + 2 * kBuf;                           // S blocks of kBBlock
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);  // [0], [1]: MMAs of a buffer, [2]: weights
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 3);
+    const int tid = threadIdx.x, warp = tid >> 5;
 
-    // weights: one bulk copy of the packed blocks (issued below, once the barrier exists)
-    // zero padding voxels after each plane (read by the dx over-reach of the 4-channel steps)
-    for (int i = tid; i < CG * kPlanePad; i += kThreads)
-        *reinterpret_cast<uint4*>(planes + (i / kPlanePad) * kPlaneBytes + (HV + i % kPlanePad) * 16) =
-            make_uint4(0u, 0u, 0u, 0u);
+    // zero the plane padding (and, for 4 channels, every row's upper 8 bytes) of both buffers
+    for (int i = tid; i < 2 * kBuf / 16; i += kThreads) {
+        const int h = (i % (kBuf / 16)) % kPlaneVox;
+        if (CG == 1 || h >= HV) *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)));
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + b)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + 1)),
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + 2)),
                      "r"((uint32_t)(S * kBBlock))
                      : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(bsm)),
-            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(smem_u32(bar + 1))
+            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(smem_u32(bar + 2))
             : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols));
+                     "r"(2 * kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -162,46 +228,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(Args a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = instr_desc(TM, NPAD);
-    const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm), bar_addr = smem_u32(bar);
+    const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm);
     const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
-    uint32_t phase = 0;
-    bool failed = !mbar_wait(smem_u32(bar + 1), 0);  // the weights
-    if (failed && tid == 0) atomicExch(&g_tc_error, 2u);
-    failed = __syncthreads_or(failed) != 0;
-    for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
-        const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
-        const bool need = !a.tile_dist || a.tile_dist[tile] <= a.radius;
-        const int m = warp * 32 + lane;
-        const int y = y0 + m / TX, xx = x0 + m % TX;
-        const bool in_box = y < a.H && xx < a.W;
-        const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
-        if (!need) {
-            if (in_box)
+
+    // this CTA's tiles; the ones far from the mask are zero-filled here and dropped from the pipeline
+    auto origin = [&](int tile, int& z0, int& y0, int& x0) {
+        x0 = (tile % tx) * TX;
+        y0 = ((tile / tx) % ty) * TY;
+        z0 = tile / (tx * ty);
+    };
+    auto next_needed = [&](int tile) {  // the first needed tile >= tile on this CTA's stride, or tiles
+        for (; tile < tiles; tile += gridDim.x) {
+            if (!a.tile_dist || a.tile_dist[tile] <= a.radius) return tile;
+            int z0, y0, x0;
+            origin(tile, z0, y0, x0);
+            const int m = tid, y = y0 + m / TX, xx = x0 + m % TX;
+            if (y < a.H && xx < a.W) {
+                const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
                 for (int n = 0; n < a.cout; ++n) {
                     if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = 0.0f;
                     else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(0.0f);
                 }
-            continue;
-        }
-        // stage the halo planes (16 bytes per voxel and plane)
-        for (int i = tid; i < HV * CG; i += kThreads) {
-            const int h = i / CG, q = i % CG;
-            const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - 1 + h % HX;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W) {
-                const __nv_bfloat16* src = a.x + (((size_t)z * a.H + yy) * a.W + xq) * a.cin;
-                if constexpr (CG == 1) {
-                    const uint2 u = *reinterpret_cast<const uint2*>(src);  // 4 channels
-                    v = make_uint4(u.x, u.y, 0u, 0u);
-                } else {
-                    v = reinterpret_cast<const uint4*>(src)[q];
-                }
             }
-            *reinterpret_cast<uint4*>(planes + q * kPlaneBytes + h * 16) = v;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+        return tiles;
+    };
+
+    bool failed = !mbar_wait(smem_u32(bar + 2), 0);  // the weights
+    failed = __syncthreads_or(failed) != 0;
+    uint32_t phase[2] = {0u, 0u};
+    int cur = failed ? tiles : next_needed(blockIdx.x);
+    int prev = -1;  // tile whose accumulator awaits its epilogue
+    int j = 0;
+    if (cur < tiles) {
+        int z0, y0, x0;
+        origin(cur, z0, y0, x0);
+        stage_async<CG>(a, planes_addr, z0, y0, x0);
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+    }
+    while (cur < tiles) {
+        const int b = j & 1;
+        if (tid == 0) {  // the MMAs of tile `cur` from plane buffer b into accumulator b
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int s = 0; s < S; ++s) {
                 int off, q;
@@ -217,59 +286,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tc(Args a) {
                     q = (s % (CG / 2)) * 2;
                     lbo = kPlaneBytes;  // the second k-group is the next plane of 8 channels
                 }
-                const uint64_t ad = smem_desc(planes_addr + q * kPlaneBytes + off * 16, lbo, HX * 16);
+                const uint64_t ad = smem_desc(planes_addr + b * kBuf + q * kPlaneBytes + off * 16, lbo, HX * 16);
                 const uint64_t bd = smem_desc(b_addr + s * kBBlock, (NPAD / 8) * 128, 128);
-                mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+                mma_bf16(tmem + b * kTmemCols, ad, bd, idesc, s > 0 ? 1u : 0u);
             }
-            mma_commit(bar_addr);
+            mma_commit(smem_u32(bar + b));
         }
         __syncwarp();
-        if (!mbar_wait(bar_addr, phase)) {
-            failed = true;
-            if (lane == 0) atomicExch(&g_tc_error, 1u);
+        const int nxt = next_needed(cur + gridDim.x);
+        if (prev >= 0) {  // tile prev's MMAs (buffer and accumulator 1 - b) must be done
+            if (!mbar_wait(smem_u32(bar + (1 - b)), phase[1 - b])) failed = true;
+            phase[1 - b] ^= 1u;
         }
-        phase ^= 1u;
         failed = __syncthreads_or(failed) != 0;
         if (failed) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc[NPAD];
-        tmem_load<NPAD>(tmem + ((uint32_t)(warp * 32) << 16), acc);
-        if (in_box) {
-            if (!a.y_f32 && a.cout == 32) {
-                uint32_t packed[16];
-#pragma unroll
-                for (int n = 0; n < 32; n += 2) {
-                    float v0 = acc[n] + (a.bias ? a.bias[n] : 0.0f), v1 = acc[n + 1] + (a.bias ? a.bias[n + 1] : 0.0f);
-                    if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(v0, v1);
-                    packed[n / 2] = *reinterpret_cast<const uint32_t*>(&p2);
-                }
-                uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + vox * 32);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
-            } else {
-#pragma unroll
-                for (int n = 0; n < NPAD; ++n) {
-                    if (n >= a.cout) break;
-                    float v = acc[n] + (a.bias ? a.bias[n] : 0.0f);
-                    if (a.relu) v = fmaxf(v, 0.0f);
-                    if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = v;
-                    else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(v);
-                }
-            }
+        if (nxt < tiles) {  // overlaps the MMAs of `cur`
+            int z0, y0, x0;
+            origin(nxt, z0, y0, x0);
+            stage_async<CG>(a, planes_addr + (1 - b) * kBuf, z0, y0, x0);
         }
+        if (prev >= 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int z0, y0, x0;
+            origin(prev, z0, y0, x0);
+            epilogue<NPAD>(a, tmem + (1 - b) * kTmemCols, z0, y0, x0);
+        }
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // accumulator read and planes consumed before the next tile reuses them
+        __syncthreads();
+        prev = cur;
+        cur = nxt;
+        ++j;
     }
+    if (prev >= 0 && !failed) {  // the last tile
+        const int b = (j - 1) & 1;
+        if (!mbar_wait(smem_u32(bar + b), phase[b])) failed = true;
+        failed = __syncthreads_or(failed) != 0;
+        if (!failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int z0, y0, x0;
+            origin(prev, z0, y0, x0);
+            epilogue<NPAD>(a, tmem + b * kTmemCols, z0, y0, x0);
+        }
+    }
+    if (failed && tid == 0) atomicExch(&g_tc_error, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols));
 }
 
 size_t smem_bytes(int npad, int cg) {
-    return (size_t)cg * kPlaneBytes + (size_t)k_steps(cg) * npad * 32 + 32 + 16;
+    return 2 * (size_t)cg * kPlaneBytes + (size_t)k_steps(cg) * npad * 32 + 32 + 16;
 }
 
 int npad_of(int cout) { return cout <= 16 ? 16 : 32; }
@@ -337,14 +407,20 @@ __global__ void k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mas
 template <int NPAD, int CG>
 cudaError_t launch(const Args& a, cudaStream_t s) {
     const size_t smem = smem_bytes(NPAD, CG);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<NPAD, CG>, kThreads, smem);
+    // resident CTAs, set up once per process (the kernels of one library run on GPUs of one kind)
+    static int slots = 0;
+    if (slots == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<NPAD, CG>, kThreads, smem);
+        slots = std::max(per_sm, 1) * std::max(sms, 1);
+    }
     const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
-    const int grid = std::max(1, std::min(tiles, std::max(per_sm, 1) * std::max(sms, 1)));
+    const int grid = std::max(1, std::min(tiles, slots));
     k_conv_tc<NPAD, CG><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 // a network correction of the updated node velocities, and one grid-to-particle transfer with time step
 // k*dt. These kernels read the network input off the updated grid, add the network's correction back,
 // and sum the mass and momentum the fallback gate compares.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "mpm_internal.h"
@@ -87,7 +88,8 @@ __device__ __forceinline__ bool box_node(const SurBox& b, size_t t, int& i, int&
 // Network input over the box from the updated grid (nodes hold (v, m)): (m * m_scale, v * v_scale),
 // the mass mask, and the momentum sum of the updated grid.
 __global__ void k_sur_features(const float4* __restrict__ grid, int n, int nb, SurBox box, float m_scale,
-                               float v_scale, float* __restrict__ feat, uint8_t* __restrict__ mask, double* sums) {
+                               float v_scale, float* __restrict__ feat, __nv_bfloat16* __restrict__ feat_bf16,
+                               uint8_t* __restrict__ mask, double* sums) {
     const size_t nv = (size_t)box.D * box.H * box.W;
     double p[3] = {0.0, 0.0, 0.0};
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
@@ -96,13 +98,19 @@ __global__ void k_sur_features(const float4* __restrict__ grid, int n, int nb, S
         float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n) g = grid[node_index(i, j, k, nb)];
         const float m = g.w;
-        reinterpret_cast<float4*>(feat)[t] = make_float4(m * m_scale, g.x * v_scale, g.y * v_scale, g.z * v_scale);
+        const float4 f = make_float4(m * m_scale, g.x * v_scale, g.y * v_scale, g.z * v_scale);
+        if (feat) reinterpret_cast<float4*>(feat)[t] = f;
+        if (feat_bf16) {  // the network input, 8 bytes per node
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(f.x, f.y), hi = __floats2bfloat162_rn(f.z, f.w);
+            reinterpret_cast<uint2*>(feat_bf16)[t] = make_uint2(*reinterpret_cast<const uint32_t*>(&lo),
+                                                                *reinterpret_cast<const uint32_t*>(&hi));
+        }
         mask[t] = m > 0.0f ? 1 : 0;
         p[0] += (double)m * g.x;
         p[1] += (double)m * g.y;
         p[2] += (double)m * g.z;
     }
-    block_sum_add<3>(p, sums);
+    if (sums) block_sum_add<3>(p, sums);
 }
 
 __device__ __forceinline__ bool in_wall(int i, int j, int k, int n, int bound) {
@@ -135,9 +143,61 @@ __global__ void k_sur_correct(float4* __restrict__ grid, int n, int nb, int boun
 }
 
 // Body impulses over a window: the first substep's share, counted k times in all.
-__global__ void k_wrench_extrapolate(double* wrench, const double* before, int n6, double extra) {
+__global__ void k_wrench_extrapolate(double* wrench, const double* before, int n6, double extra,
+                                     const uint32_t* gate, uint32_t gate_run) {
+    if (gate && *gate != gate_run) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n6) wrench[i] += extra * (wrench[i] - before[i]);
+}
+
+// The fallback gate of a window, on the device (one thread).
+__global__ void k_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
+                           uint32_t* gate, unsigned long long* stats) {
+    const double M = sums[0];
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double pexp = sums[1 + a] + 0.5 * (k + 1) * (sums[4 + a] - sums[1 + a]);
+        d2 += (sums[7 + a] - pexp) * (sums[7 + a] - pexp);
+    }
+    const double r_mass = m_particles > 0.0 ? fabs(M - m_particles) / m_particles : 0.0;
+    const double r_mom = M > 0.0 ? sqrt(d2) / (M * v_ref) : 0.0;
+    const bool ok = r_mass <= threshold && r_mom <= threshold;  // a NaN residual fails
+    *gate = ok ? 1u : 0u;
+    stats[0] += 1ull;
+    if (!ok) stats[1] += 1ull;
+    reinterpret_cast<double*>(stats)[2] = r_mass;
+    reinterpret_cast<double*>(stats)[3] = r_mom;
+}
+
+// The corrected velocities written back (when the gate passed, if there is one); block 0 also advances
+// the substep counter by k - 1 (the pass that follows adds the last one) and counts the first substep's
+// body impulses k times.
+__global__ void k_sur_apply_gated(float4* __restrict__ grid, int n, int nb, int bound, SurBox box,
+                                  const float* __restrict__ dv, float unit, const uint32_t* gate, uint32_t* counter,
+                                  int k, double* wrench, const double* wrench_before, int n6) {
+    if (gate && *gate != 1u) return;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *counter += (uint32_t)(k - 1);
+        for (int i = threadIdx.x; i < n6; i += blockDim.x) wrench[i] += (double)(k - 1) * (wrench[i] - wrench_before[i]);
+    }
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(box, t, i, j, k);
+        if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n) continue;
+        float4* node = &grid[node_index(i, j, k, nb)];
+        const float4 g = *node;
+        if (!(g.w > 0.0f)) continue;
+        const float* d = dv + t * 3;
+        float v[3] = {g.x + d[0] * unit, g.y + d[1] * unit, g.z + d[2] * unit};
+        if (in_wall(i, j, k, n, bound)) v[0] = v[1] = v[2] = 0.0f;
+        *node = make_float4(v[0], v[1], v[2], g.w);
+    }
+}
+
+__global__ void k_cast_bf16(int n, const float* __restrict__ s, __nv_bfloat16* __restrict__ d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = __float2bfloat16(s[i]);
 }
 
 unsigned grid_for(size_t n, int threads, unsigned cap) {
@@ -160,9 +220,11 @@ cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const u
 }
 
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
-                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s) {
+                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s,
+                                void* feat_bf16) {
     const size_t nv = (size_t)box.D * box.H * box.W;
-    k_sur_features<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, box, m_scale, v_scale, feat, mask, sums);
+    k_sur_features<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, box, m_scale, v_scale, feat,
+                                                           static_cast<__nv_bfloat16*>(feat_bf16), mask, sums);
     return cudaGetLastError();
 }
 
@@ -173,9 +235,31 @@ cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const Sur
     return cudaGetLastError();
 }
 
-cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s) {
+cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s,
+                                      const uint32_t* gate, uint32_t gate_run) {
     if (n6 <= 0) return cudaSuccess;
-    k_wrench_extrapolate<<<(n6 + 255) / 256, 256, 0, s>>>(wrench, before, n6, extra);
+    k_wrench_extrapolate<<<(n6 + 255) / 256, 256, 0, s>>>(wrench, before, n6, extra, gate, gate_run);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
+                            uint32_t* gate, unsigned long long* stats, cudaStream_t s) {
+    k_sur_gate<<<1, 1, 0, s>>>(sums, m_particles, k, v_ref, threshold, gate, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv, float unit,
+                             const uint32_t* gate, uint32_t* counter, int k, double* wrench,
+                             const double* wrench_before, int n6, cudaStream_t s) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    k_sur_apply_gated<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, bound, box, dv, unit, gate, counter, k,
+                                                              wrench, wrench_before, n6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_to_bf16(int n, const float* src, void* dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_cast_bf16<<<(n + 255) / 256, 256, 0, s>>>(n, src, static_cast<__nv_bfloat16*>(dst));
     return cudaGetLastError();
 }
 

@@ -166,3 +166,36 @@ def test_trained_network_gains_over_the_window_without_it(mods):
     assert with_net["rel_x_max"] <= 1e-3
     assert gated["rel_x_max"] <= 1e-3
     assert with_net["rel_to_displacement_mean"] < without["rel_to_displacement_mean"]
+
+
+def test_attached_step_matches_host_driven_windows(mods):
+    """The library's graph-replayed environment step (gate on the device) gives the same state as the same
+    windows driven from the host, with the gate open and with it forcing the fallback."""
+    mpm, sur = mods
+    sc = scenes.pinch_scene(seed=1005, N=40_000)
+    cols = scenes.finger_state(sc, 0.12)
+    net = sur.Network(seed=7)
+    outs = {}
+    for mode in ("host", "attached", "attached_fallback", "plain"):
+        sim = make_sim(sc)
+        sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+        sim.set_shapes(sc.shapes)
+        if mode == "host":
+            runner = sur.Runner(sim, net, sc.material.rho, threshold=float("inf"))
+            runner.env_step(*cols, substeps=10)
+        elif mode == "plain":
+            sim.set_colliders(*cols)
+            sim.substep(10)
+        else:
+            thr = -1.0 if mode == "attached_fallback" else float("inf")
+            att = sur.Attached(sim, net, sc.material.rho, threshold=thr)
+            att.env_step(*cols, substeps=10)
+            w, f, _ = att.stats(reset=True)
+            assert w == 2 and f == (2 if thr < 0 else 0)
+            att.detach()
+        outs[mode] = (sim.read_state(on_device=False)["x"], sim.read_wrench())
+        sim.close()
+    assert rel(outs["attached"][0], outs["host"][0]) <= 1e-6
+    assert outs["attached"][1][1] == outs["host"][1][1] == 10
+    assert rel(outs["attached_fallback"][0], outs["plain"][0]) <= 1e-6
+    assert rel(outs["attached_fallback"][1][0], outs["plain"][1][0]) <= 1e-5
