@@ -277,21 +277,28 @@ typedef struct {
     int margin;              /* nodes added around the material's bins for the box */
 } mpm_surrogate_net;
 
-/* Device workspace for the network's buffers over boxes of up to max_voxels nodes. */
-size_t mpm_surrogate_workspace_size(int max_voxels);
+/* Device workspace for the network's buffers over boxes of up to max_voxels nodes and the start-of-step
+ * snapshot of up to max_particles particles (the per-step fallback). */
+size_t mpm_surrogate_workspace_size(int max_voxels, int max_particles);
 
 /* Attach (net != NULL) or detach the network. One-env handles whose bins fit the fused scan only. */
 mpm_status mpm_surrogate_attach(mpm_sim* sim, const mpm_surrogate_net* net, void* d_workspace, size_t bytes,
                                 int max_voxels);
 
 /* n_substeps (a multiple of k) as windows of the attached network, from one box computed for the call
- * (one host synchronization). gate != 0: each window whose residuals exceed the threshold runs as k
- * plain substeps instead, decided on the device; gate == 0: every window uses the network. A box larger
- * than max_voxels runs plain substeps. Enqueued as one graph launch per call. */
+ * (one host synchronization), enqueued as one graph launch. The gate:
+ *   0  off: every window uses the network;
+ *   1  per step: every window uses the network while the gate records its residuals on the device; one
+ *      readback at the end of the call, and if any window exceeded the threshold the step is redone
+ *      from a snapshot of its start (state, body impulses, substep count) with n_substeps plain substeps;
+ *   2  per window: each window whose residuals exceed the threshold runs as k plain substeps instead,
+ *      both branches enqueued and decided on the device.
+ * A box larger than max_voxels runs plain substeps. */
 mpm_status mpm_surrogate_step(mpm_sim* sim, int n_substeps, int gate, void* stream);
 
-/* Device counters of gated windows: windows run, fallbacks taken, and the last window's (mass,
- * momentum) residuals; reset != 0 zeroes the counters. Synchronizes `stream`. */
+/* Counters of gated windows: windows run, windows that ran as plain substeps (failed windows with gate 2,
+ * every window of a redone step with gate 1), and the last window's (mass, momentum) residuals;
+ * reset != 0 zeroes the counters. Synchronizes `stream`. */
 mpm_status mpm_surrogate_stats(mpm_sim* sim, long long* windows, long long* fallbacks, double* residuals, int reset,
                                void* stream);
 

@@ -136,7 +136,7 @@ def _load():
         "mpm_surrogate_check": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_double), _vp]),
         "mpm_surrogate_advance": (st, [_vp, ctypes.POINTER(mpm_box), _vp, ctypes.c_float, ctypes.c_int, _vp]),
-        "mpm_surrogate_workspace_size": (ctypes.c_size_t, [ctypes.c_int]),
+        "mpm_surrogate_workspace_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
         "mpm_surrogate_attach": (st, [_vp, ctypes.POINTER(mpm_surrogate_net), _vp, ctypes.c_size_t, ctypes.c_int]),
         "mpm_surrogate_step": (st, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
         "mpm_surrogate_stats": (st, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -404,8 +404,8 @@ def mpm_surrogate_advance(sim, box: mpm_box, dv, dv_unit, k, stream=0):
                                                                   dv or None, dv_unit, k, stream))
 
 
-def mpm_surrogate_workspace_size(max_voxels) -> int:
-    return _load().mpm_surrogate_workspace_size(max_voxels)
+def mpm_surrogate_workspace_size(max_voxels, max_particles) -> int:
+    return _load().mpm_surrogate_workspace_size(max_voxels, max_particles)
 
 
 def mpm_surrogate_attach(sim, net, d_workspace, nbytes, max_voxels):

@@ -191,6 +191,23 @@ struct mpm_sim {
     bool sur_pending = false;  // a surrogate window was started and not yet ended
     // attached surrogate network (mpm_surrogate_attach)
     bool net_attached = false;
+    long long sur_steps_redone = 0, sur_windows_redone = 0;
+    // the box of the next surrogate step, computed with the previous step's readback
+    bool box_cached = false;
+    mpm_box box_cache{};
+    PipeState box_cache_ps;
+    long long box_cache_version = 0;
+    int box_cache_n = 0;
+    long long particles_version = 0;  // bumped by every particle upload
+    // a gated surrogate step awaiting its verdict (resolved by the next call that depends on the state)
+    bool verify_pending = false;
+    cudaEvent_t verify_event = nullptr;
+    uint32_t* verify_host = nullptr;   // pinned: the gate's word, then the next box (6 ints)
+    int verify_substeps = 0;
+    cudaStream_t verify_stream = nullptr;
+    PipeState verify_ps;               // the state the step ended in (for the next box)
+    long long upload_seq = 0, verify_upload_seq = 0;
+    ColliderUpload last_upload{};      // the latest collider upload (at most kSharedPoses bodies)
     mpm_surrogate_net net{};
     char* net_ws = nullptr;
     int net_max_voxels = 0;
@@ -619,6 +636,8 @@ mpm_status create_impl(const mpm_config* cfg, int nenv, const mpm_env* envs, voi
 
 extern "C" {
 
+static mpm_status resolve_pending(mpm_sim* s);
+
 const char* mpm_status_string(mpm_status s) {
     switch (s) {
         case MPM_OK: return "ok";
@@ -660,6 +679,11 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mat, void* d_wo
 
 void mpm_destroy(mpm_sim* s) {
     if (!s) return;
+    if (s->verify_event) {
+        cudaEventSynchronize(s->verify_event);
+        cudaEventDestroy(s->verify_event);
+    }
+    if (s->verify_host) cudaFreeHost(s->verify_host);
     s->drop_graphs();
     for (auto& ev : s->pending) {
         cudaEventDestroy(ev.a);
@@ -684,6 +708,7 @@ long long mpm_launch_count(const mpm_sim* s) { return s ? s->launches : 0; }
 mpm_status mpm_set_particles_batch(mpm_sim* s, const int* counts, const float* x, const float* v, const float* C,
                                    const float* F, int src_on_device, void* stream) {
     if (!s || !counts) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     size_t total = 0;
     for (int e = 0; e < s->nenv; ++e) {
         if (counts[e] < 0) return MPM_ERR_INVALID_ARG;
@@ -705,6 +730,7 @@ mpm_status mpm_set_particles_batch(mpm_sim* s, const int* counts, const float* x
     s->N = (int)total;
     s->ps = PipeState{};
     s->sur_pending = false;
+    s->particles_version += 1;
     if (total == 0) {
         s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;
         return MPM_OK;
@@ -824,6 +850,7 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
         MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
             return launch_set_colliders_small(u, table, s->at<double>(s->L.wrench), s->substep_counter(), st);
         }, "set_colliders"));
+        s->last_upload = u;  // replayed if a pending surrogate step is redone after this upload
     } else {
         MPM_CUDA(cudaMemcpyAsync(table, s->stage, sizeof(ColliderSet) * k, cudaMemcpyHostToDevice, st),
                  "copy colliders");
@@ -841,11 +868,13 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
     }
     if (changed) MPM_TRY(upload_envs(s, st));
     s->ncol = k;
+    s->upload_seq += 1;
     return MPM_OK;
 }
 
 mpm_status mpm_substep(mpm_sim* s, int n_substeps, void* stream) {
     if (!s || n_substeps < 0 || s->sur_pending) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_substeps == 0) return MPM_OK;
     if (s->N == 0) {
@@ -892,6 +921,7 @@ mpm_status mpm_set_graphs(mpm_sim* s, int enable) {
 
 mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid_ctas_per_sm) {
     if (!s) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     if (chunk && (chunk < 32 || chunk > kChunk || chunk % 32)) return MPM_ERR_INVALID_ARG;
     if (fused_ctas_per_sm && (fused_ctas_per_sm < 1 || fused_ctas_per_sm > s->max_fused_cps)) return MPM_ERR_INVALID_ARG;
     if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
@@ -912,6 +942,7 @@ mpm_status mpm_get_launch(const mpm_sim* s, int* chunk, int* fused_ctas_per_sm, 
 
 mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, int dst_on_device, void* stream) {
     if (!s) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->N == 0) return MPM_OK;
     const size_t N = (size_t)s->N;
@@ -936,6 +967,7 @@ mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, in
 
 mpm_status mpm_read_wrench(mpm_sim* s, double* out, int* n_substeps, void* stream) {
     if (!s || (s->ncol > 0 && !out)) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->ncol > 0)
         MPM_CUDA(cudaMemcpyAsync(out, s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -950,6 +982,7 @@ mpm_status mpm_read_wrench(mpm_sim* s, double* out, int* n_substeps, void* strea
 
 mpm_status mpm_get_status(mpm_sim* s, unsigned* flags, int clear, void* stream) {
     if (!s || !flags) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t f = 0;
     MPM_CUDA(cudaMemcpyAsync(&f, s->status(), 4, cudaMemcpyDeviceToHost, st), "copy status");
@@ -961,6 +994,7 @@ mpm_status mpm_get_status(mpm_sim* s, unsigned* flags, int clear, void* stream) 
 
 mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
     if (!s || !d_out) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->N > 0) MPM_TRY(ensure_grid(s, st));
     const float4* grid = s->at<float4>(s->L.grid[s->ps.g]);
@@ -974,27 +1008,30 @@ mpm_status mpm_read_grid(mpm_sim* s, float* d_out, void* stream) {
     return MPM_OK;
 }
 
+static mpm_box box_from_bins(const int b[6], int margin, int n) {
+    if (b[3] < 0) return mpm_box{0, 0, 0, 0, 0, 0};  // no active bins
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = std::max(0, 4 * b[a] - margin);
+        hi[a] = std::min(n, 4 * b[3 + a] + 4 + margin);
+    }
+    return mpm_box{lo[0], lo[1], lo[2], hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+}
+
 mpm_status mpm_surrogate_box(mpm_sim* s, int margin, mpm_box* box, void* stream) {
     if (!s || !box || margin < 0 || s->nenv != 1 || s->sur_pending) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     *box = mpm_box{0, 0, 0, 0, 0, 0};
     if (s->N == 0) return MPM_OK;
     MPM_TRY(ensure_grid(s, st));
-    static const int init[6] = {1 << 30, 1 << 30, 1 << 30, -1, -1, -1};
     int* d_box = s->sur_box();
-    MPM_CUDA(cudaMemcpyAsync(d_box, init, sizeof(init), cudaMemcpyHostToDevice, st), "copy box init");
     const Geometry& g = s->envs[0].geo;
     MPM_CUDA(launch_sur_box(s->list(s->ps.g), s->list_count(s->ps.g), g.nb, (int)s->T.bins, d_box, st), "sur_box");
     int b[6];
     MPM_CUDA(cudaMemcpyAsync(b, d_box, sizeof(b), cudaMemcpyDeviceToHost, st), "copy box");
     MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-    if (b[3] < 0) return MPM_OK;  // no active bins
-    int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = std::max(0, 4 * b[a] - margin);
-        hi[a] = std::min(g.n, 4 * b[3 + a] + 4 + margin);
-    }
-    *box = mpm_box{lo[0], lo[1], lo[2], hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    *box = box_from_bins(b, margin, g.n);
     return MPM_OK;
 }
 
@@ -1008,6 +1045,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
                                   uint8_t* d_mask, void* stream) {
     if (!s || s->nenv != 1 || s->sur_pending || !valid_box(box) || !d_feat || !d_mask || s->N == 0)
         return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     if (reinterpret_cast<uintptr_t>(d_feat) % 16) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MPM_TRY(ensure_scanned(s, st));
@@ -1087,10 +1125,10 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
 namespace {
 
 struct NetLayout {
-    size_t feat, xbf, act[3], out, mask, dist, total;
+    size_t feat, xbf, act[3], out, mask, dist, snap, wrench, cols, words, total;
 };
 
-NetLayout net_layout(int max_voxels) {
+NetLayout net_layout(int max_voxels, int max_particles = 0) {
     NetLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -1105,6 +1143,12 @@ NetLayout net_layout(int max_voxels) {
     L.out = take(v * 12);
     L.mask = take(v);
     L.dist = take(v);  // at least one byte per tile
+    // the state at the start of a step (x, v, C, F in the caller's order), its body impulses, substep
+    // count and the "a window failed" word, for the per-step fallback
+    L.snap = take((size_t)std::max(max_particles, 1) * 49 * sizeof(float));  // raw state + caller-order scratch
+    L.wrench = take(MPM_MAX_COLLIDERS * 6 * sizeof(double));
+    L.cols = take(MPM_MAX_COLLIDERS * sizeof(ColliderSet));
+    L.words = take(4 * sizeof(uint32_t));
     L.total = off;
     return L;
 }
@@ -1113,18 +1157,21 @@ constexpr int kNetChannels[5] = {4, 32, 32, 32, 3};
 
 // One window (k substeps) from the current pipeline state: plain grid update, network, device-side gate,
 // then both branches enqueued, each running only on its side of the gate.
-mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, bool gate_on, cudaStream_t st) {
+// gate_mode: 0 no gate; 1 the gate only records (residuals, stats, the step's "a window failed" word) and
+// the surrogate branch always runs; 2 both branches, each running on its side of the gate.
+mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStream_t st) {
     const mpm_surrogate_net& net = s->net;
     const int k = net.k;
-    const NetLayout NL = net_layout(s->net_max_voxels);
+    const bool gate_on = gate_mode != 0;
+    const NetLayout NL = net_layout(s->net_max_voxels, s->env_cfg[0].max_particles);
     char* ws = s->net_ws;
     const SurBox box = to_sur_box(&b);
     const Geometry& g = s->envs[0].geo;
     double* sums = s->sur_sums();
     MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
-    if (gate_on) {  // the gate's sums: mass and momentum before the grid update
-        MPM_CUDA(cudaMemsetAsync(sums, 0, 16 * sizeof(double), st), "cudaMemsetAsync");
+    if (gate_on) {  // the gate's sums (zero: cleared at attach and by every gate): mass and momentum before
+        // the grid update
         MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
                                     (int)s->T.bins, sums, st),
                  "sur_moments");
@@ -1150,15 +1197,15 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, bool gate_on, cudaStream
         in = out;
     }
     if (gate_on) {
-        MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv, net.dv_unit,
-                                    0, sums + 7, st),
-                 "sur_check");
         const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
-        MPM_CUDA(launch_sur_gate(sums, mp, k, net.v_ref, net.threshold, s->sur_gate(), s->sur_stats(), st),
-                 "sur_gate");
+        uint32_t* words = reinterpret_cast<uint32_t*>(ws + NL.words);
+        MPM_CUDA(launch_sur_check_gate(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv,
+                                       net.dv_unit, sums, mp, k, net.v_ref, net.threshold, s->sur_gate(),
+                                       s->sur_stats(), gate_mode == 1 ? words : nullptr, words + 2, st),
+                 "sur_check_gate");
     }
-    // without the gate every window takes the surrogate branch and the plain one is not enqueued
-    uint32_t* gate = gate_on ? s->sur_gate() : nullptr;
+    // without per-window branches every window takes the surrogate branch and the plain one is not enqueued
+    uint32_t* gate = gate_mode == 2 ? s->sur_gate() : nullptr;
     const PipeState before = s->ps;
     // the surrogate branch: correction (with the counter and impulse bookkeeping), then the k*dt pass
     MPM_CUDA(launch_sur_apply(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv, net.dv_unit, gate,
@@ -1166,7 +1213,7 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, bool gate_on, cudaStream
              "sur_apply");
     MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt, gate, 1u));
     const PipeState after = s->ps;
-    if (!gate_on) return MPM_OK;
+    if (gate_mode != 2) return MPM_OK;
     // the plain branch, from the same state; with k odd it ends in the same buffers
     s->ps = before;
     MPM_TRY(enqueue_particle_half(s, st, 0.0f, gate, 0u));
@@ -1180,39 +1227,126 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, bool gate_on, cudaStream
 
 }  // namespace
 
-size_t mpm_surrogate_workspace_size(int max_voxels) { return max_voxels > 0 ? net_layout(max_voxels).total : 0; }
+// The verdict of a gated surrogate step that returned without waiting for it: wait for it now; if a window
+// failed the gate, redo the step from its snapshot with plain substeps (then replay a collider upload made
+// after the step, which the caller meant for the next one); otherwise keep the next step's box.
+static mpm_status resolve_pending(mpm_sim* s) {
+    if (!s->verify_pending) return MPM_OK;
+    s->verify_pending = false;
+    MPM_CUDA(cudaEventSynchronize(s->verify_event), "cudaEventSynchronize");
+    cudaStream_t st = s->verify_stream;
+    if (!s->verify_host[0]) {
+        s->box_cache = box_from_bins(reinterpret_cast<const int*>(s->verify_host + 1), s->net.margin, s->envs[0].geo.n);
+        s->box_cache_ps = s->verify_ps;
+        s->box_cache_version = s->particles_version;
+        s->box_cache_n = s->N;
+        s->box_cached = true;
+        return MPM_OK;
+    }
+    const NetLayout NL = net_layout(s->net_max_voxels, s->env_cfg[0].max_particles);
+    float* snap = reinterpret_cast<float*>(s->net_ws + NL.snap);
+    const size_t N = (size_t)s->N, cap = std::max<size_t>(s->T.particles, 1);
+    float* order = snap + cap * 25;  // the snapshot in the caller's order
+    StateView sv;
+    sv.x = snap;
+    sv.v = snap + 3 * N;
+    sv.C = snap + 6 * N;
+    sv.F = snap + 15 * N;
+    sv.pid = reinterpret_cast<uint32_t*>(snap + 24 * cap);
+    MPM_CUDA(launch_read_state(s->N, s->envs_dev(), 1, sv, order, order + 3 * N, order + 6 * N, order + 15 * N, st),
+             "snapshot order");
+    MPM_TRY(mpm_set_particles(s, s->N, order, order + 3 * N, order + 6 * N, order + 15 * N, 1, st));
+    if (s->ncol > 0)
+        MPM_CUDA(cudaMemcpyAsync(s->at<ColliderSet>(s->L.colliders), s->net_ws + NL.cols, s->ncol * sizeof(ColliderSet),
+                                 cudaMemcpyDeviceToDevice, st),
+                 "restore colliders");
+    uint32_t* words = reinterpret_cast<uint32_t*>(s->net_ws + NL.words);
+    MPM_CUDA(launch_sur_step_restore(s->at<double>(s->L.wrench), reinterpret_cast<const double*>(s->net_ws + NL.wrench),
+                                     s->ncol * 6, s->substep_counter(), words, st),
+             "step_restore");
+    MPM_TRY(mpm_substep(s, s->verify_substeps, st));
+    s->sur_steps_redone += 1;
+    s->sur_windows_redone += s->verify_substeps / s->net.k;
+    if (s->upload_seq != s->verify_upload_seq && s->last_upload.k > 0)
+        MPM_TRY(launch(s, MPM_K_COLLIDERS, st, [&] {
+            return launch_set_colliders_small(s->last_upload, s->at<ColliderSet>(s->L.colliders),
+                                              s->at<double>(s->L.wrench), s->substep_counter(), st);
+        }, "set_colliders"));
+    return MPM_OK;
+}
+
+size_t mpm_surrogate_workspace_size(int max_voxels, int max_particles) {
+    return max_voxels > 0 && max_particles >= 0 ? net_layout(max_voxels, max_particles).total : 0;
+}
 
 mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* d_workspace, size_t bytes,
                                 int max_voxels) {
     if (!s || s->nenv != 1 || !s->tail_scan()) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     if (!net) {
         s->net_attached = false;
         s->drop_graphs();
         return MPM_OK;
     }
     if (net->k < 1 || net->k % 2 == 0 || net->margin < 0 || !(net->dv_unit > 0.0f) || !(net->v_ref > 0.0) ||
-        max_voxels < 1)
+        max_voxels < 1 || s->env_cfg[0].max_colliders > kSharedPoses)
         return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
+    if (!s->verify_event) {
+        MPM_CUDA(cudaEventCreateWithFlags(&s->verify_event, cudaEventDisableTiming), "cudaEventCreate");
+        MPM_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&s->verify_host), 8 * sizeof(uint32_t), cudaHostAllocDefault),
+                 "cudaHostAlloc");
+    }
     for (int i = 0; i < 4; ++i)
         if (!net->w_packed[i] || reinterpret_cast<uintptr_t>(net->w_packed[i]) % 16) return MPM_ERR_INVALID_ARG;
-    if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % kAlign || bytes < net_layout(max_voxels).total)
+    if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % kAlign ||
+        bytes < net_layout(max_voxels, s->env_cfg[0].max_particles).total)
         return MPM_ERR_WORKSPACE;
     s->net = *net;
     s->net_ws = static_cast<char*>(d_workspace);
     s->net_max_voxels = max_voxels;
     s->net_attached = true;
     s->drop_graphs();
+    // the gate's sums and ticket start at zero (each gate leaves them so)
+    const NetLayout NL = net_layout(max_voxels, s->env_cfg[0].max_particles);
+    MPM_CUDA(cudaMemset(s->sur_sums(), 0, 16 * sizeof(double)), "cudaMemset");
+    MPM_CUDA(cudaMemset(s->net_ws + NL.words, 0, 4 * sizeof(uint32_t)), "cudaMemset");
     return MPM_OK;
 }
 
 mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream) {
-    if (!s || !s->net_attached || s->sur_pending || n_substeps < 0 || n_substeps % s->net.k) return MPM_ERR_INVALID_ARG;
+    if (!s || !s->net_attached || s->sur_pending || n_substeps < 0 || n_substeps % s->net.k || gate < 0 || gate > 2)
+        return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MPM_TRY(resolve_pending(s));
     if (n_substeps == 0) return MPM_OK;
     mpm_box b{};
-    MPM_TRY(mpm_surrogate_box(s, s->net.margin, &b, stream));
+    if (s->box_cached && s->box_cache_ps == s->ps && s->box_cache_version == s->particles_version &&
+        s->box_cache_n == s->N)
+        b = s->box_cache;  // computed at the end of the previous step, from this state
+    else
+        MPM_TRY(mpm_surrogate_box(s, s->net.margin, &b, stream));
+    s->box_cached = false;
     if (b.D == 0 || (size_t)b.D * b.H * b.W > (size_t)s->net_max_voxels) return mpm_substep(s, n_substeps, stream);
-    const std::array<int, 8> key{b.i0, b.j0, b.k0, b.D, b.H, b.W, n_substeps, gate ? 1 : 0};
+    const std::array<int, 8> key{b.i0, b.j0, b.k0, b.D, b.H, b.W, n_substeps, gate};
+    const NetLayout NL = net_layout(s->net_max_voxels, s->env_cfg[0].max_particles);
+    uint32_t* any_failed = reinterpret_cast<uint32_t*>(s->net_ws + NL.words);
+    if (gate) MPM_CUDA(cudaMemsetAsync(s->sur_sums(), 0, 16 * sizeof(double), st), "cudaMemsetAsync");
+    float* snap = reinterpret_cast<float*>(s->net_ws + NL.snap);
+    const size_t cap = std::max<size_t>(s->T.particles, 1);
+    const int snap_buf = s->ps.cur;  // the state buffer at the start of the step
+    if (gate == 1) {  // the step's starting point (the raw state buffer), for a plain redo
+        MPM_CUDA(cudaMemcpyAsync(snap, s->at<float>(s->L.state[snap_buf]), cap * 25 * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st),
+                 "snapshot");
+        MPM_CUDA(launch_sur_step_begin(s->at<double>(s->L.wrench), reinterpret_cast<double*>(s->net_ws + NL.wrench),
+                                       s->ncol * 6, s->substep_counter(), any_failed, st),
+                 "step_begin");
+        if (s->ncol > 0)
+            MPM_CUDA(cudaMemcpyAsync(s->net_ws + NL.cols, s->at<ColliderSet>(s->L.colliders),
+                                     s->ncol * sizeof(ColliderSet), cudaMemcpyDeviceToDevice, st),
+                     "snapshot colliders");
+    }
     GraphEntry* ge = nullptr;
     for (size_t i = 0; i < s->sur_graphs.size(); ++i)
         if (s->sur_keys[i] == key && s->sur_graphs[i].before == s->ps && s->sur_graphs[i].ncol == s->ncol)
@@ -1237,7 +1371,7 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
         MPM_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         s->capturing = true;
         mpm_status r = MPM_OK;
-        for (int w = 0; w < n_substeps / s->net.k && r == MPM_OK; ++w) r = enqueue_window(s, b, gate != 0, s->cap_stream);
+        for (int w = 0; w < n_substeps / s->net.k && r == MPM_OK; ++w) r = enqueue_window(s, b, gate, s->cap_stream);
         s->capturing = false;
         s->timing_mask = mask_saved;
         cudaGraph_t graph = nullptr;
@@ -1264,19 +1398,36 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
     MPM_CUDA(cudaGraphLaunch(ge->exec, st), "cudaGraphLaunch");
     s->ps = ge->after;
     s->launches += ge->launches;
+    if (gate == 1) {  // the verdict and the next step's box, read back without waiting (resolve_pending)
+        int* d_box = s->sur_box();
+        const Geometry& g = s->envs[0].geo;
+        MPM_CUDA(launch_sur_box(s->list(s->ps.g), s->list_count(s->ps.g), g.nb, (int)s->T.bins, d_box, st), "sur_box");
+        MPM_CUDA(cudaMemcpyAsync(s->verify_host, any_failed, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                 "copy flag");
+        MPM_CUDA(cudaMemcpyAsync(s->verify_host + 1, d_box, 6 * sizeof(int), cudaMemcpyDeviceToHost, st), "copy box");
+        MPM_CUDA(cudaEventRecord(s->verify_event, st), "cudaEventRecord");
+        s->verify_pending = true;
+        s->verify_substeps = n_substeps;
+        s->verify_stream = st;
+        s->verify_ps = s->ps;
+        s->verify_upload_seq = s->upload_seq;
+    }
     return MPM_OK;
 }
 
 mpm_status mpm_surrogate_stats(mpm_sim* s, long long* windows, long long* fallbacks, double* residuals, int reset,
                                void* stream) {
     if (!s) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned long long h[4];
     MPM_CUDA(cudaMemcpyAsync(h, s->sur_stats(), sizeof(h), cudaMemcpyDeviceToHost, st), "copy stats");
     if (reset) MPM_CUDA(cudaMemsetAsync(s->sur_stats(), 0, 2 * sizeof(unsigned long long), st), "cudaMemsetAsync");
     MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     if (windows) *windows = (long long)h[0];
-    if (fallbacks) *fallbacks = (long long)h[1];
+    // per-window branches: the windows that failed the gate; per-step fallback: the windows of redone steps
+    if (fallbacks) *fallbacks = (long long)h[1] + s->sur_windows_redone;
+    if (reset) s->sur_steps_redone = s->sur_windows_redone = 0;
     if (residuals) std::memcpy(residuals, &h[2], 2 * sizeof(double));
     return MPM_OK;
 }

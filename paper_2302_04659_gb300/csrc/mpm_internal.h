@@ -190,6 +190,10 @@ struct SurBox {
 };
 cudaError_t launch_sur_box(const uint32_t* list, const uint32_t* count, int nb, int nbins_cap, int* box,
                            cudaStream_t s);
+cudaError_t launch_sur_step_begin(const double* wrench, double* saved, int n6, const uint32_t* counter, uint32_t* words,
+                                  cudaStream_t s);
+cudaError_t launch_sur_step_restore(double* wrench, const double* saved, int n6, uint32_t* counter,
+                                    const uint32_t* words, cudaStream_t s);
 cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
                                double* sums, cudaStream_t s);
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
@@ -203,7 +207,12 @@ cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int 
 // gate = 1 if both are within threshold, else 0; stats[0..1] += (windows, fallbacks), stats[2..3] the
 // residuals (doubles after the two 64-bit counters).
 cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
-                            uint32_t* gate, unsigned long long* stats, cudaStream_t s);
+                            uint32_t* gate, unsigned long long* stats, cudaStream_t s, uint32_t* any_failed = nullptr);
+// The corrected grid's momentum and the gate in one launch (last block decides; sums re-zeroed).
+cudaError_t launch_sur_check_gate(const float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                                  float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
+                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, uint32_t* ticket,
+                                  cudaStream_t s);
 // The correction written back (only if *gate == 1 when gate is set), with the window's substep-counter and
 // body-impulse bookkeeping.
 cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv, float unit,

@@ -2,8 +2,8 @@
 // (tcgen05.mma, accumulators in tensor memory), behind mpm_conv3d_forward_tc (include/mpm_net.h).
 //
 // Implicit GEMM per tile of 1 x 16 x 8 output voxels (M = 128 rows, N = the output channels padded to 16
-// or 32, K = 27 taps x input channels). The input halo (3 x 18 x 10 voxels) is staged in shared memory
-// as planes of 8 channels, one 16-byte row per voxel, so the 8 voxels of a row of the tile form one
+// or 32, K = 27 taps x input channels). The input halo (3 x 18 x 10 voxels) lands in shared memory by
+// tensor-map bulk copies (TMA, zero fill outside the box) as planes of 8 channels, one 16-byte row per voxel, so the 8 voxels of a row of the tile form one
 // 8 x 16-byte core matrix and the next row of the tile sits 10 voxels (160 bytes) further: the A
 // operand of a tap is the plane shifted by the tap's voxel offset, described with no swizzle (leading
 // byte offset = the next 8 channels, stride byte offset = 160 bytes). The weights, packed once per update
@@ -14,7 +14,9 @@
 // mbarrier is bounded: past the limit the kernel records an error word and leaves, freeing its tensor
 // memory. Input channels: 4 (padded to 8: the two dx taps of a row pair up in one K step) or a multiple
 // of 16 up to 32; output channels up to 32.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,9 +30,9 @@ namespace {
 
 constexpr int TY = 16, TX = 8, TM = TY * TX;          // 128 rows per tile (one z plane)
 constexpr int HZ = 3, HY = TY + 2, HX = TX + 2, HV = HZ * HY * HX;  // 540 halo voxels
-constexpr int kPlanePad = 16;                          // zero voxels after each plane (dx over-read)
+constexpr int kPlanePad = 20;                          // zero voxels after each plane (dx over-read)
 constexpr int kPlaneVox = HV + kPlanePad;
-constexpr int kPlaneBytes = kPlaneVox * 16;            // 8896
+constexpr int kPlaneBytes = kPlaneVox * 16;            // 8960: planes start on 128-byte boundaries (TMA)
 constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 32;
 constexpr uint32_t kWaitLimit = 1u << 22;              // mbarrier polls before giving up
@@ -123,8 +125,14 @@ __device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
 // K steps: CG = input channel groups of 8 (1 for 4 channels, 2 or 4 for 16 or 32).
 __host__ __device__ constexpr int k_steps(int cg) { return cg == 1 ? 18 : 27 * cg / 2; }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+// One tile of the tensor map (channels 8 q .. 8 q + 7 of a 10 x 18 x 3 voxel box) into shared memory.
+__device__ __forceinline__ void tma_plane(uint32_t dst, const CUtensorMap* map, int c, int x, int y, int z,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
@@ -135,20 +143,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-// Stage the halo of tile (z0, y0, x0) into one plane buffer with asynchronous copies (zero-filled
-// outside the box).
+// Stage the halo of tile (z0, y0, x0) into one plane buffer with asynchronous copies (4 input channels:
+// 8 bytes per voxel, zero-filled outside the box; the rows' other 8 bytes stay zero).
 template <int CG>
 __device__ __forceinline__ void stage_async(const Args& a, uint32_t buf, int z0, int y0, int x0) {
-    for (int i = threadIdx.x; i < HV * CG; i += kThreads) {
-        const int h = i / CG, q = i % CG;
+    static_assert(CG == 1, "wider inputs arrive by tensor-map copies");
+    for (int h = threadIdx.x; h < HV; h += kThreads) {
         const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - 1 + h % HX;
         const bool in = z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W;
-        const __nv_bfloat16* src = in ? a.x + (((size_t)z * a.H + yy) * a.W + xq) * a.cin + q * 8 : a.x;
-        const uint32_t dst = buf + q * kPlaneBytes + h * 16;
-        if constexpr (CG == 1)
-            cp_async8(dst, src, in ? 8u : 0u);  // 4 channels; the row's other 8 bytes stay zero
-        else
-            cp_async16(dst, src, in ? 16u : 0u);
+        const __nv_bfloat16* src = in ? a.x + (((size_t)z * a.H + yy) * a.W + xq) * a.cin : a.x;
+        cp_async8(buf + h * 16, src, in ? 8u : 0u);
     }
 }
 
@@ -187,18 +191,21 @@ __device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z
 }
 
 // Persistent, software-pipelined: while the tensor core runs the MMAs of tile j (accumulator j % 2), the
-// threads stage tile j + 1's halo into the other plane buffer and store tile j - 1 from the other
-// accumulator.
+// next tile's halo lands in the other plane buffer (tensor-map bulk copies issued by the MMA thread for 16
+// or 32 input channels; asynchronous 8-byte copies by all threads for 4) and the threads store tile j - 1
+// from the other accumulator.
 template <int NPAD, int CG>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int S = k_steps(CG);
     constexpr int kBBlock = NPAD * 32;  // bytes of one K step of B: 2 k-groups x NPAD/8 n-groups x 128
     constexpr int kBuf = CG * kPlaneBytes;
+    constexpr bool kTma = CG >= 2;
     unsigned char* planes = smem;                                   // 2 buffers of CG planes
     unsigned char* bsm = smem + 2 * kBuf;                           // S blocks of kBBlock
-    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);  // [0], [1]: MMAs of a buffer, [2]: weights
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 3);
+    // [0], [1]: MMAs of a buffer done; [2]: weights landed; [3], [4]: a buffer's halo landed
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 5);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     // zero the plane padding (and, for 4 channels, every row's upper 8 bytes) of both buffers
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
         if (CG == 1 || h >= HV) *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid == 0) {
-        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + b)));
+        for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + b)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + 2)),
                      "r"((uint32_t)(S * kBBlock))
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
                      "r"(2 * kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeroed padding, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -231,13 +239,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
     const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm);
     const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
 
-    // this CTA's tiles; the ones far from the mask are zero-filled here and dropped from the pipeline
     auto origin = [&](int tile, int& z0, int& y0, int& x0) {
         x0 = (tile % tx) * TX;
         y0 = ((tile / tx) % ty) * TY;
         z0 = tile / (tx * ty);
     };
-    auto next_needed = [&](int tile) {  // the first needed tile >= tile on this CTA's stride, or tiles
+    // the first needed tile >= tile on this CTA's stride (or tiles); tiles passed over are zero-filled
+    auto next_needed = [&](int tile) {
         for (; tile < tiles; tile += gridDim.x) {
             if (!a.tile_dist || a.tile_dist[tile] <= a.radius) return tile;
             int z0, y0, x0;
@@ -253,66 +261,89 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
         }
         return tiles;
     };
+    // load a tile's halo into buffer b (TMA: by thread 0 only; otherwise by all threads, then waited)
+    auto load_halo = [&](int tile, int b) {
+        int z0, y0, x0;
+        origin(tile, z0, y0, x0);
+        if constexpr (kTma) {
+            if (tid == 0) {
+                const uint32_t full = smem_u32(bar + 3 + b);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full),
+                             "r"((uint32_t)(CG * HV * 16))
+                             : "memory");
+                for (int q = 0; q < CG; ++q)
+                    tma_plane(planes_addr + b * kBuf + q * kPlaneBytes, &tmap, q * 8, x0 - 1, y0 - 1, z0 - 1, full);
+            }
+        } else {
+            stage_async<CG>(a, planes_addr + b * kBuf, z0, y0, x0);
+        }
+    };
 
     bool failed = !mbar_wait(smem_u32(bar + 2), 0);  // the weights
     failed = __syncthreads_or(failed) != 0;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t ph_mma0 = 0u, ph_mma1 = 0u, ph_full0 = 0u, ph_full1 = 0u;
     int cur = failed ? tiles : next_needed(blockIdx.x);
     int prev = -1;  // tile whose accumulator awaits its epilogue
     int j = 0;
     if (cur < tiles) {
-        int z0, y0, x0;
-        origin(cur, z0, y0, x0);
-        stage_async<CG>(a, planes_addr, z0, y0, x0);
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        load_halo(cur, 0);
+        if constexpr (!kTma) {
+            cp_async_wait_all();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
     }
     while (cur < tiles) {
         const int b = j & 1;
+        const int nxt = next_needed(cur + gridDim.x);
         if (tid == 0) {  // the MMAs of tile `cur` from plane buffer b into accumulator b
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int s = 0; s < S; ++s) {
-                int off, q;
-                uint32_t lbo;
-                if constexpr (CG == 1) {
-                    const int pair = s >> 1, half = s & 1;
-                    off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
-                    q = 0;
-                    lbo = 16;  // the second k-group is the next voxel along x (dx + 1)
-                } else {
-                    const int tap = s / (CG / 2);
-                    off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
-                    q = (s % (CG / 2)) * 2;
-                    lbo = kPlaneBytes;  // the second k-group is the next plane of 8 channels
-                }
-                const uint64_t ad = smem_desc(planes_addr + b * kBuf + q * kPlaneBytes + off * 16, lbo, HX * 16);
-                const uint64_t bd = smem_desc(b_addr + s * kBBlock, (NPAD / 8) * 128, 128);
-                mma_bf16(tmem + b * kTmemCols, ad, bd, idesc, s > 0 ? 1u : 0u);
+            if constexpr (kTma) {
+                uint32_t& ph = b ? ph_full1 : ph_full0;
+                if (!mbar_wait(smem_u32(bar + 3 + b), ph)) failed = true;
+                ph ^= 1u;
             }
-            mma_commit(smem_u32(bar + b));
+            if (!failed) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int s = 0; s < S; ++s) {
+                    int off, q;
+                    uint32_t lbo;
+                    if constexpr (CG == 1) {
+                        const int pair = s >> 1, half = s & 1;
+                        off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
+                        q = 0;
+                        lbo = 16;  // the second k-group is the next voxel along x (dx + 1)
+                    } else {
+                        const int tap = s / (CG / 2);
+                        off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
+                        q = (s % (CG / 2)) * 2;
+                        lbo = kPlaneBytes;  // the second k-group is the next plane of 8 channels
+                    }
+                    const uint64_t ad = smem_desc(planes_addr + b * kBuf + q * kPlaneBytes + off * 16, lbo, HX * 16);
+                    const uint64_t bd = smem_desc(b_addr + s * kBBlock, (NPAD / 8) * 128, 128);
+                    mma_bf16(tmem + b * kTmemCols, ad, bd, idesc, s > 0 ? 1u : 0u);
+                }
+                mma_commit(smem_u32(bar + b));
+            }
         }
         __syncwarp();
-        const int nxt = next_needed(cur + gridDim.x);
         if (prev >= 0) {  // tile prev's MMAs (buffer and accumulator 1 - b) must be done
-            if (!mbar_wait(smem_u32(bar + (1 - b)), phase[1 - b])) failed = true;
-            phase[1 - b] ^= 1u;
+            uint32_t& ph = b ? ph_mma0 : ph_mma1;
+            if (!mbar_wait(smem_u32(bar + (1 - b)), ph)) failed = true;
+            ph ^= 1u;
         }
         failed = __syncthreads_or(failed) != 0;
         if (failed) break;
-        if (nxt < tiles) {  // overlaps the MMAs of `cur`
-            int z0, y0, x0;
-            origin(nxt, z0, y0, x0);
-            stage_async<CG>(a, planes_addr + (1 - b) * kBuf, z0, y0, x0);
-        }
+        if (nxt < tiles) load_halo(nxt, 1 - b);  // overlaps the MMAs of `cur`
         if (prev >= 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             int z0, y0, x0;
             origin(prev, z0, y0, x0);
             epilogue<NPAD>(a, tmem + (1 - b) * kTmemCols, z0, y0, x0);
         }
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if constexpr (!kTma) {
+            cp_async_wait_all();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         prev = cur;
@@ -321,7 +352,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
     }
     if (prev >= 0 && !failed) {  // the last tile
         const int b = (j - 1) & 1;
-        if (!mbar_wait(smem_u32(bar + b), phase[b])) failed = true;
+        uint32_t& ph = b ? ph_mma1 : ph_mma0;
+        if (!mbar_wait(smem_u32(bar + b), ph)) failed = true;
         failed = __syncthreads_or(failed) != 0;
         if (!failed) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -339,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a) {
 }
 
 size_t smem_bytes(int npad, int cg) {
-    return 2 * (size_t)cg * kPlaneBytes + (size_t)k_steps(cg) * npad * 32 + 32 + 16;
+    return 2 * (size_t)cg * kPlaneBytes + (size_t)k_steps(cg) * npad * 32 + 5 * 8 + 16;
 }
 
 int npad_of(int cout) { return cout <= 16 ? 16 : 32; }
@@ -421,7 +453,27 @@ cudaError_t launch(const Args& a, cudaStream_t s) {
     }
     const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
     const int grid = std::max(1, std::min(tiles, slots));
-    k_conv_tc<NPAD, CG><<<grid, kThreads, smem, s>>>(a);
+    CUtensorMap map{};
+    if (CG >= 2) {  // the activations as a 4-D tensor (channels, W, H, D); boxes of 8 x 10 x 18 x 3
+        static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+        if (!encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+        const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D};
+        const cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.W * a.cin * 2,
+                                       (cuuint64_t)a.H * a.W * a.cin * 2};
+        const cuuint32_t box[4] = {8, HX, HY, HZ};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.x), dims,
+                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    k_conv_tc<NPAD, CG><<<grid, kThreads, smem, s>>>(a, map);
     return cudaGetLastError();
 }
 

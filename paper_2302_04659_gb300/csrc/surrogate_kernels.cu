@@ -36,11 +36,12 @@ __device__ __forceinline__ void block_sum_add(double (&v)[NV], double* out) {
     }
 }
 
-// Bin bounds of the active bins (the grid's bin list): box[0..2] = min bin per axis, box[3..5] = max.
+// Bin bounds of the active bins (the grid's bin list), one block: box[0..2] = min bin per axis,
+// box[3..5] = max (box[3] = -1 when there are none).
 __global__ void k_sur_box(const uint32_t* __restrict__ list, const uint32_t* __restrict__ count, int nb, int* box) {
     const uint32_t n = *count;
     int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const int b = (int)(list[i] & kLocalMask);
         const int c[3] = {b / (nb * nb), (b / nb) % nb, b % nb};
 #pragma unroll
@@ -49,17 +50,43 @@ __global__ void k_sur_box(const uint32_t* __restrict__ list, const uint32_t* __r
             hi[a] = max(hi[a], c[a]);
         }
     }
+    __shared__ int red[6][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         for (int off = 16; off > 0; off >>= 1) {
             lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
             hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&box[a], lo[a]);
-            atomicMax(&box[3 + a], hi[a]);
+        if (lane == 0) {
+            red[a][warp] = lo[a];
+            red[3 + a][warp] = hi[a];
         }
     }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        int v = q < 3 ? (1 << 30) : -1;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = q < 3 ? min(v, red[q][w]) : max(v, red[q][w]);
+        box[q] = v;
+    }
+}
+
+// The start of a gated step: save the body impulses and the substep count, clear the step's flag.
+__global__ void k_sur_step_begin(const double* wrench, double* wrench_saved, int n6, const uint32_t* counter,
+                                 uint32_t* words) {
+    for (int i = threadIdx.x; i < n6; i += blockDim.x) wrench_saved[i] = wrench[i];
+    if (threadIdx.x == 0) {
+        words[0] = 0u;        // a window failed the gate
+        words[1] = *counter;  // the substep count at the start
+    }
+}
+
+// Undo a step's bookkeeping: the impulses and the substep count as they were at its start.
+__global__ void k_sur_step_restore(double* wrench, const double* wrench_saved, int n6, uint32_t* counter,
+                                   const uint32_t* words) {
+    for (int i = threadIdx.x; i < n6; i += blockDim.x) wrench[i] = wrench_saved[i];
+    if (threadIdx.x == 0) *counter = words[1];
 }
 
 // Mass and momentum of the transfer, before the grid update (nodes hold (m, m v)).
@@ -142,6 +169,68 @@ __global__ void k_sur_correct(float4* __restrict__ grid, int n, int nb, int boun
     block_sum_add<3>(p, sums);
 }
 
+// The gate in one launch: the corrected grid's momentum summed like k_sur_correct (without writing it
+// back), then the last block to finish computes the residuals, sets the gate, records the stats, and
+// zeroes the sums for the next window (so no separate clearing is needed).
+struct GateArgs {
+    const float4* grid;
+    int n, nb, bound;
+    SurBox box;
+    const float* dv;
+    float unit;
+    double* sums;            // M, P0[3] (k_sur_moments), P1[3] (k_sur_features), P_hat[3] (here)
+    double m_particles, v_ref, threshold;
+    int k;
+    uint32_t* gate;
+    unsigned long long* stats;
+    uint32_t* any_failed;    // per-step mode, or null
+    uint32_t* ticket;
+};
+
+__global__ void k_sur_check_gate(GateArgs g) {
+    const size_t nv = (size_t)g.box.D * g.box.H * g.box.W;
+    double p[3] = {0.0, 0.0, 0.0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(g.box, t, i, j, k);
+        if (i < 0 || i >= g.n || j < 0 || j >= g.n || k < 0 || k >= g.n) continue;
+        const float4 gv = g.grid[node_index(i, j, k, g.nb)];
+        if (!(gv.w > 0.0f)) continue;
+        const float* d = g.dv + t * 3;
+        float v[3] = {gv.x + d[0] * g.unit, gv.y + d[1] * g.unit, gv.z + d[2] * g.unit};
+        if (in_wall(i, j, k, g.n, g.bound)) v[0] = v[1] = v[2] = 0.0f;
+        p[0] += (double)gv.w * v[0];
+        p[1] += (double)gv.w * v[1];
+        p[2] += (double)gv.w * v[2];
+    }
+    block_sum_add<3>(p, g.sums + 7);
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    volatile double* S = g.sums;
+    const double M = S[0];
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double pexp = S[1 + a] + 0.5 * (g.k + 1) * (S[4 + a] - S[1 + a]);
+        d2 += (S[7 + a] - pexp) * (S[7 + a] - pexp);
+    }
+    const double r_mass = g.m_particles > 0.0 ? fabs(M - g.m_particles) / g.m_particles : 0.0;
+    const double r_mom = M > 0.0 ? sqrt(d2) / (M * g.v_ref) : 0.0;
+    const bool ok = r_mass <= g.threshold && r_mom <= g.threshold;  // a NaN residual fails
+    *g.gate = ok ? 1u : 0u;
+    if (!ok && g.any_failed) *g.any_failed = 1u;
+    g.stats[0] += 1ull;
+    if (!ok && !g.any_failed) g.stats[1] += 1ull;
+    reinterpret_cast<double*>(g.stats)[2] = r_mass;
+    reinterpret_cast<double*>(g.stats)[3] = r_mom;
+    for (int q = 0; q < 10; ++q) S[q] = 0.0;
+    *g.ticket = 0u;
+}
+
 // Body impulses over a window: the first substep's share, counted k times in all.
 __global__ void k_wrench_extrapolate(double* wrench, const double* before, int n6, double extra,
                                      const uint32_t* gate, uint32_t gate_run) {
@@ -152,7 +241,7 @@ __global__ void k_wrench_extrapolate(double* wrench, const double* before, int n
 
 // The fallback gate of a window, on the device (one thread).
 __global__ void k_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
-                           uint32_t* gate, unsigned long long* stats) {
+                           uint32_t* gate, unsigned long long* stats, uint32_t* any_failed) {
     const double M = sums[0];
     double d2 = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -163,8 +252,9 @@ __global__ void k_sur_gate(const double* sums, double m_particles, int k, double
     const double r_mom = M > 0.0 ? sqrt(d2) / (M * v_ref) : 0.0;
     const bool ok = r_mass <= threshold && r_mom <= threshold;  // a NaN residual fails
     *gate = ok ? 1u : 0u;
+    if (!ok && any_failed) *any_failed = 1u;  // per-step fallback: the host counts the redone windows
     stats[0] += 1ull;
-    if (!ok) stats[1] += 1ull;
+    if (!ok && !any_failed) stats[1] += 1ull;
     reinterpret_cast<double*>(stats)[2] = r_mass;
     reinterpret_cast<double*>(stats)[3] = r_mom;
 }
@@ -209,7 +299,20 @@ unsigned grid_for(size_t n, int threads, unsigned cap) {
 
 cudaError_t launch_sur_box(const uint32_t* list, const uint32_t* count, int nb, int nbins_cap, int* box,
                            cudaStream_t s) {
-    k_sur_box<<<grid_for((size_t)nbins_cap, 256, 512), 256, 0, s>>>(list, count, nb, box);
+    (void)nbins_cap;
+    k_sur_box<<<1, 1024, 0, s>>>(list, count, nb, box);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_step_begin(const double* wrench, double* saved, int n6, const uint32_t* counter, uint32_t* words,
+                                  cudaStream_t s) {
+    k_sur_step_begin<<<1, 256, 0, s>>>(wrench, saved, n6, counter, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_step_restore(double* wrench, const double* saved, int n6, uint32_t* counter,
+                                    const uint32_t* words, cudaStream_t s) {
+    k_sur_step_restore<<<1, 256, 0, s>>>(wrench, saved, n6, counter, words);
     return cudaGetLastError();
 }
 
@@ -243,8 +346,19 @@ cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int 
 }
 
 cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, double v_ref, double threshold,
-                            uint32_t* gate, unsigned long long* stats, cudaStream_t s) {
-    k_sur_gate<<<1, 1, 0, s>>>(sums, m_particles, k, v_ref, threshold, gate, stats);
+                            uint32_t* gate, unsigned long long* stats, cudaStream_t s, uint32_t* any_failed) {
+    k_sur_gate<<<1, 1, 0, s>>>(sums, m_particles, k, v_ref, threshold, gate, stats, any_failed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_check_gate(const float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                                  float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
+                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, uint32_t* ticket,
+                                  cudaStream_t s) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    GateArgs g{grid, n, nb, bound, box, dv, unit, sums, m_particles, v_ref, threshold, k, gate, stats, any_failed,
+               ticket};
+    k_sur_check_gate<<<grid_for(nv, 256, 1024), 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 

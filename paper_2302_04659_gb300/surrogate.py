@@ -38,7 +38,7 @@ V_SCALE = 10.0        # network input units per m/s
 DV_UNIT = 0.01        # m/s per network output unit
 V_REF = 1.0           # m/s: velocity scale of the momentum residual
 THRESHOLD = 1e-3      # fallback when the mass or momentum residual exceeds this
-MARGIN = 6            # nodes around the material: 4 for the receptive field, 2 for motion in an env step
+MARGIN = 5            # nodes around the material's bins: 4 for the receptive field, 1 for motion in a step
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "surrogate_pinch64.npz")
 
 
@@ -219,11 +219,12 @@ class Attached:
         cfg.m_scale, cfg.v_scale, cfg.dv_unit = mass_scale(rho, sim.n), V_SCALE, DV_UNIT
         cfg.v_ref, cfg.threshold, cfg.k, cfg.margin = V_REF, threshold, k, MARGIN
         self.cfg = cfg
-        nbytes = mpm.mpm_surrogate_workspace_size(max_voxels)
+        nbytes = mpm.mpm_surrogate_workspace_size(max_voxels, sim.cfg.max_particles)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=sim.device)
         mpm.mpm_surrogate_attach(sim.handle, cfg, self.ws.data_ptr(), nbytes, max_voxels)
 
-    def env_step(self, pose, lin, ang, com, substeps: int = 25, gate: bool = True, stream=None):
+    def env_step(self, pose, lin, ang, com, substeps: int = 25, gate=True, stream=None):
+        # gate: False/0 off, True/1 per-step fallback, 2 per-window branches (mpm_surrogate_step)
         self.sim.set_colliders(pose, lin, ang, com, stream=stream)
         mpm.mpm_surrogate_step(self.sim.handle, substeps, int(gate), _stream(stream))
 
@@ -431,12 +432,15 @@ def zero_net(device):
     return _ZERO[device]
 
 
-def evaluate(net: Network | None, seeds, particles=200_000, warm_steps=2, device="cuda", gate=True, warmup=True):
-    """Per held-out scene: after ``warm_steps`` plain env steps, one env step by the plain method and one by
-    windows (with ``net``, or with a zero correction when None) from the same state. Returns per-scene
-    relative position errors, mean absolute errors, fallbacks and the timings of both forms."""
-    out = {"rel_x": [], "mean_abs": [], "rel_disp": [], "windows": 0, "fallbacks": 0, "ms_plain": [],
-           "ms_surrogate": []}
+def evaluate(net: Network | None, seeds, particles=200_000, warm_steps=2, device="cuda", gate=True, warmup=True,
+             steps=4):
+    """Per held-out scene: after ``warm_steps`` plain env steps, ``steps`` env steps by the plain method and
+    the same by windows (with ``net``, or with a zero correction when None) from the same state, the fingers
+    following their scripts. Errors compare the positions after the first env step; the timings are the
+    mean time per env step over the ``steps`` consecutive steps (graphs captured beforehand, off the
+    clock)."""
+    out = {"rel_x": [], "mean_abs": [], "rel_disp": [], "rel_x_last": [], "windows": 0, "fallbacks": 0,
+           "ms_plain": [], "ms_surrogate": []}
     sim = None
     for seed in seeds:
         sc = scenes.pinch_scene(seed=seed, N=particles)
@@ -447,41 +451,66 @@ def evaluate(net: Network | None, seeds, particles=200_000, warm_steps=2, device
             sim.set_colliders(*scenes.finger_state(sc, step * 25 * sc.dt))
             sim.substep(25)
         snap = sim.read_state(on_device=True)
-        cols = scenes.finger_state(sc, warm_steps * 25 * sc.dt)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        # plain (its graph captured once off the clock)
-        if warmup:
-            sim.set_colliders(*cols)
+        cols = [scenes.finger_state(sc, (warm_steps + i) * 25 * sc.dt) for i in range(steps)]
+
+        def restore():
+            sim.set_particles(snap["x"], snap["v"], snap["C"], snap["F"])
+
+        def run(step_fn, n):
+            for i in range(n):
+                step_fn(cols[i])
+
+        def timed(step_fn):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run(step_fn, steps)
+            b.record()
+            b.synchronize()
+            return a.elapsed_time(b) / steps
+
+        def plain_step(c):
+            sim.set_colliders(*c)
             sim.substep(25)
-            sim.set_particles(snap["x"], snap["v"], snap["C"], snap["F"])
-        ev[0].record()
-        sim.set_colliders(*cols)
-        sim.substep(25)
-        ev[1].record()
-        x_plain = _read_x(sim).double()
-        # surrogate from the same state (attached: graph-replayed windows, gate on the device)
-        sim.set_particles(snap["x"], snap["v"], snap["C"], snap["F"])
+
         runner = Attached(sim, net if net is not None else zero_net(sim.device), sc.material.rho)
-        if warmup:  # capture the step's graph once, off the clock, then restore the state
-            runner.env_step(*cols, gate=gate)
-            runner.stats(reset=True)
-            sim.set_particles(snap["x"], snap["v"], snap["C"], snap["F"])
-        ev[2].record()
-        runner.env_step(*cols, gate=gate)
-        ev[3].record()
+
+        def sur_step(c):
+            runner.env_step(*c, gate=gate)
+
+        # accuracy: positions after the first env step and after all of them (this also captures the
+        # graphs of both state parities, so the timed runs below replay only)
+        run(plain_step, 1)
+        x_plain = _read_x(sim).double()
+        restore()
+        run(plain_step, steps)
+        x_plain_last = _read_x(sim).double()
+        restore()
+        run(sur_step, 1)
         x_sur = _read_x(sim).double()
+        restore()
+        run(sur_step, steps)
+        x_sur_last = _read_x(sim).double()
+        runner.stats(reset=True)
+        # timing: consecutive env steps, nothing read back in between
+        if warmup:
+            restore()
+            run(plain_step, 2)
+        restore()
+        ms_p = timed(plain_step)
+        restore()
+        ms_s = timed(sur_step)
         w_, f_, _ = runner.stats(reset=True)
         runner.detach()
-        torch.cuda.synchronize()
         d = x_sur - x_plain
         out["rel_x"].append(float(d.norm() / x_plain.norm()))
         out["mean_abs"].append(float(d.norm(dim=0).mean()))
         disp = x_plain - snap["x"].double()
         out["rel_disp"].append(float(d.norm() / disp.norm().clamp_min(1e-30)))
-        out["windows"] += w_ if gate else 5
+        out["rel_x_last"].append(float((x_sur_last - x_plain_last).norm() / x_plain_last.norm()))
+        out["windows"] += w_ if gate else 5 * steps
         out["fallbacks"] += f_ if gate else 0
-        out["ms_plain"].append(ev[0].elapsed_time(ev[1]))
-        out["ms_surrogate"].append(ev[2].elapsed_time(ev[3]))
+        out["ms_plain"].append(ms_p)
+        out["ms_surrogate"].append(ms_s)
     if sim is not None:
         sim.close()
     return out
@@ -494,6 +523,7 @@ def summarize(res):
         "rel_x_max": float(np.max(res["rel_x"])),
         "mean_abs_dx": float(np.mean(res["mean_abs"])),
         "rel_to_displacement_mean": float(np.mean(res["rel_disp"])),
+        "rel_x_after_all_steps_mean": float(np.mean(res["rel_x_last"])),
         "fallback_rate": res["fallbacks"] / max(res["windows"], 1),
         "ms_per_env_step_plain": float(np.median(res["ms_plain"])),
         "ms_per_env_step_surrogate": float(np.median(res["ms_surrogate"])),

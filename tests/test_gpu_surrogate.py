@@ -176,7 +176,7 @@ def test_attached_step_matches_host_driven_windows(mods):
     cols = scenes.finger_state(sc, 0.12)
     net = sur.Network(seed=7)
     outs = {}
-    for mode in ("host", "attached", "attached_fallback", "plain"):
+    for mode in ("host", "attached", "attached_fallback", "attached_window_fallback", "plain"):
         sim = make_sim(sc)
         sim.set_particles(sc.x, sc.v, sc.C, sc.F)
         sim.set_shapes(sc.shapes)
@@ -186,10 +186,10 @@ def test_attached_step_matches_host_driven_windows(mods):
         elif mode == "plain":
             sim.set_colliders(*cols)
             sim.substep(10)
-        else:
-            thr = -1.0 if mode == "attached_fallback" else float("inf")
+        else:  # the per-step fallback (gate 1) and the per-window one (gate 2), forced with threshold -1
+            thr = -1.0 if mode.endswith("fallback") else float("inf")
             att = sur.Attached(sim, net, sc.material.rho, threshold=thr)
-            att.env_step(*cols, substeps=10)
+            att.env_step(*cols, substeps=10, gate=2 if mode == "attached_window_fallback" else 1)
             w, f, _ = att.stats(reset=True)
             assert w == 2 and f == (2 if thr < 0 else 0)
             att.detach()
@@ -197,5 +197,7 @@ def test_attached_step_matches_host_driven_windows(mods):
         sim.close()
     assert rel(outs["attached"][0], outs["host"][0]) <= 1e-6
     assert outs["attached"][1][1] == outs["host"][1][1] == 10
-    assert rel(outs["attached_fallback"][0], outs["plain"][0]) <= 1e-6
-    assert rel(outs["attached_fallback"][1][0], outs["plain"][1][0]) <= 1e-5
+    for m in ("attached_fallback", "attached_window_fallback"):
+        assert rel(outs[m][0], outs["plain"][0]) <= 1e-6
+        assert outs[m][1][1] == 10
+        assert rel(outs[m][1][0], outs["plain"][1][0]) <= 1e-5
