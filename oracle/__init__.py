@@ -29,6 +29,7 @@ PLASTICINE = 0
 FLUID = 1
 BOX = 0
 CAPSULE = 1
+SDF_VOLUME = 2
 
 
 def build(force: bool = False) -> str:
@@ -72,7 +73,15 @@ class _Collider(ctypes.Structure):
         ("lin_vel", ctypes.c_double * 3),
         ("ang_vel", ctypes.c_double * 3),
         ("com", ctypes.c_double * 3),
+        ("sdf", ctypes.POINTER(ctypes.c_double)),
+        ("res", ctypes.c_int * 3),
+        ("sdf_origin", ctypes.c_double * 3),
+        ("sdf_h", ctypes.c_double),
     ]
+
+
+class _Penalty(ctypes.Structure):
+    _fields_ = [("stiffness", ctypes.c_double), ("damping", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -105,6 +114,16 @@ def lib():
         L.orc_substep.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
                                   ctypes.c_int, ctypes.POINTER(_Collider), ctypes.c_double, _dp, _dp, _u8p]
         L.orc_substep.restype = ctypes.c_int
+        L.orc_p2g_forces.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_sdf_volume.argtypes = [ctypes.POINTER(_Collider), _dp, _dp, _dp, _ip]
+        L.orc_sdf_volume.restype = ctypes.c_int
+        L.orc_penalty_accel.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Penalty), ctypes.c_int, _dp, _dp,
+                                        ctypes.c_int, ctypes.POINTER(_Collider), ctypes.c_double, _dp, _dp, _u8p]
+        L.orc_penalty_accel.restype = ctypes.c_int
+        L.orc_substep_penalty.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Penalty), ctypes.c_int, _dp, _dp,
+                                          _dp, _dp, _dp, ctypes.c_int, ctypes.POINTER(_Collider), ctypes.c_double,
+                                          _dp, _dp, _dp, _u8p]
+        L.orc_substep_penalty.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -154,7 +173,10 @@ class Params:
 
 @dataclass
 class Collider:
-    """One kinematic collider (see ``orc_collider``); pose and velocities as set at t = 0."""
+    """One kinematic collider (see ``orc_collider``); pose and velocities as set at t = 0.
+
+    An SDF volume (type SDF_VOLUME) carries ``sdf`` of shape (nx, ny, nz), sample [i, j, k] at the
+    shape-frame point ``sdf_origin + sdf_h * (i, j, k)``."""
 
     type: int
     half: tuple
@@ -164,12 +186,34 @@ class Collider:
     lin_vel: tuple = (0.0, 0.0, 0.0)
     ang_vel: tuple = (0.0, 0.0, 0.0)
     com: tuple | None = None
+    sdf: np.ndarray | None = None
+    sdf_origin: tuple = (0.0, 0.0, 0.0)
+    sdf_h: float = 1.0
 
     def c(self) -> _Collider:
         com = self.pos if self.com is None else self.com
         d3 = ctypes.c_double * 3
-        return _Collider(self.type, d3(*self.half), self.friction, d3(*self.pos),
-                         (ctypes.c_double * 4)(*self.quat), d3(*self.lin_vel), d3(*self.ang_vel), d3(*com))
+        col = _Collider(self.type, d3(*self.half), self.friction, d3(*self.pos),
+                        (ctypes.c_double * 4)(*self.quat), d3(*self.lin_vel), d3(*self.ang_vel), d3(*com))
+        if self.sdf is not None:
+            # i fastest: element (i, j, k) at i + nx * (j + ny * k); kept alive on the object
+            self._flat = np.ascontiguousarray(np.asarray(self.sdf, np.float64).transpose(2, 1, 0))
+            col.sdf = self._flat.ctypes.data_as(_dp)
+            col.res = (ctypes.c_int * 3)(*self.sdf.shape)
+            col.sdf_origin = d3(*self.sdf_origin)
+            col.sdf_h = self.sdf_h
+        return col
+
+
+@dataclass
+class Penalty:
+    """Constants of the particle contact (see ``orc_penalty``): stiffness 1/s^2, damping 1/s."""
+
+    stiffness: float
+    damping: float
+
+    def c(self) -> _Penalty:
+        return _Penalty(self.stiffness, self.damping)
 
 
 def _cols(colliders):
@@ -347,3 +391,74 @@ def surrogate_window(params: Params, s: State, dv, box, unit: float, k: int, col
     return {"M": g0[..., 0].sum(), "P0": g0[..., 1:].reshape(-1, 3).sum(axis=0),
             "P1": (g1[..., :1] * g1[..., 1:]).reshape(-1, 3).sum(axis=0),
             "P_hat": (g2[..., :1] * g2[..., 1:]).reshape(-1, 3).sum(axis=0)}
+
+
+# ------------------------------------------------------------------ particle contact (Sec. 3's default form)
+
+def sdf_volume(col: Collider, l):
+    """Trilinear value and gradient of ``col``'s SDF volume at the shape-frame point l, or None outside
+    the lattice: (phi, grad (3,), ambiguous)."""
+    c = col.c()
+    l = _f64(l)
+    phi = ctypes.c_double(0.0)
+    g = np.zeros(3)
+    amb = ctypes.c_int(0)
+    inside = lib().orc_sdf_volume(ctypes.byref(c), _ptr(l), ctypes.byref(phi), _ptr(g), ctypes.byref(amb))
+    return (phi.value, g, bool(amb.value)) if inside else None
+
+
+def penalty_accel(params: Params, pen: Penalty, s: State, colliders=(), t: float = 0.0):
+    """Penalty accelerations (3, N), the wrench (k, 6) they put on the bodies, the ambiguous-particle mask
+    and the number of contacts."""
+    k = len(colliders)
+    acc = np.zeros((3, s.n))
+    w = np.zeros(6 * max(k, 1))
+    amb = np.zeros(s.n, dtype=np.uint8)
+    P, Pe = params.c(), pen.c()
+    cols = _cols(colliders)
+    nc = lib().orc_penalty_accel(ctypes.byref(P), ctypes.byref(Pe), s.n, _ptr(s.x), _ptr(s.v), k, cols, t,
+                                 _ptr(acc), _ptr(w), amb.ctypes.data_as(_u8p))
+    return acc, w[: 6 * k].reshape(k, 6), amb.astype(bool), nc
+
+
+def p2g_forces(params: Params, s: State, accel) -> np.ndarray:
+    """P2G with external particle accelerations (3, N): the dense grid (n,n,n,4)."""
+    n = params.n
+    grid = np.zeros(n * n * n * 4)
+    a = _f64(accel)
+    P = params.c()
+    lib().orc_p2g_forces(ctypes.byref(P), s.n, _ptr(s.x), _ptr(s.v), _ptr(s.C), _ptr(s.F), _ptr(s.J), _ptr(a),
+                         _ptr(grid))
+    return grid.reshape(n, n, n, 4)
+
+
+def substep_penalty(params: Params, pen: Penalty, s: State, colliders=(), t: float = 0.0, wrench=None):
+    """One substep with the particle contact, in place on ``s`` at collider time t.
+
+    Returns (clamped coordinate count, wrench (k,6) accumulated onto ``wrench`` if given, ambiguous
+    particle mask)."""
+    n = params.n
+    grid = np.zeros(n ** 3 * 4)
+    acc = np.zeros(3 * s.n)
+    k = len(colliders)
+    w = np.zeros(6 * max(k, 1)) if wrench is None else wrench.reshape(-1)
+    amb = np.zeros(s.n, dtype=np.uint8)
+    P, Pe = params.c(), pen.c()
+    cols = _cols(colliders)
+    ncl = lib().orc_substep_penalty(ctypes.byref(P), ctypes.byref(Pe), s.n, _ptr(s.x), _ptr(s.v), _ptr(s.C),
+                                    _ptr(s.F), _ptr(s.J), k, cols, t, _ptr(w), _ptr(grid), _ptr(acc),
+                                    amb.ctypes.data_as(_u8p))
+    return ncl, w[: 6 * k].reshape(k, 6), amb.astype(bool)
+
+
+def rollout_penalty(params: Params, pen: Penalty, s: State, nsub: int, colliders=(), t0: float = 0.0,
+                    wrench=None):
+    """``nsub`` particle-contact substeps in place; collider time advances by dt per substep from t0.
+    Returns (clamped count, wrench, mask of particles that were ambiguous in any substep)."""
+    total = 0
+    amb_any = np.zeros(s.n, dtype=bool)
+    for k in range(nsub):
+        ncl, wrench, amb = substep_penalty(params, pen, s, colliders, t0 + k * params.dt, wrench)
+        total += ncl
+        amb_any |= amb
+    return total, wrench, amb_any

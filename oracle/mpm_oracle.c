@@ -271,7 +271,55 @@ void orc_collider_pose(const orc_collider* c, double t, double R[9], double p[3]
     for (int i = 0; i < 3; ++i) p[i] = com[i] + Q[i * 3] * d[0] + Q[i * 3 + 1] * d[1] + Q[i * 3 + 2] * d[2];
 }
 
-/* Analytic signed distances of the primitive shapes of Sec. 3 (box, capsule), in the shape frame. */
+/* SDF volume of a mesh (Sec. 3 stores one per mesh as a 3-D texture): the trilinear interpolant of the
+ * lattice samples. In lattice units u = (l - origin) / h the point lies in cell c = floor(u) (the last
+ * cell on the upper faces) at fraction f = u - c; the value is the sum over the cell's 8 corners of
+ * prod_a (f_a or 1 - f_a) times the sample, and the gradient is the interpolant's derivative: along
+ * axis a, the blend by the other two axes' weights of the four edge differences along a, divided by h. */
+int orc_sdf_volume(const orc_collider* c, const double l[3], double* phi, double grad[3], int* ambiguous) {
+    int cell[3];
+    double f[3];
+    int amb = 0;
+    for (int a = 0; a < 3; ++a) {
+        double u = (l[a] - c->sdf_origin[a]) / c->sdf_h;
+        if (!(u >= 0.0) || u > (double)(c->res[a] - 1)) return 0;
+        int ci = (int)floor(u);
+        if (ci > c->res[a] - 2) ci = c->res[a] - 2;
+        cell[a] = ci;
+        f[a] = u - (double)ci;
+        if (f[a] < 1e-5 || f[a] > 1.0 - 1e-5) amb = 1;
+    }
+    double smp[2][2][2]; /* [di][dj][dk] */
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int dk = 0; dk < 2; ++dk)
+                smp[di][dj][dk] = c->sdf[(cell[0] + di) +
+                                         (size_t)c->res[0] * ((cell[1] + dj) + (size_t)c->res[1] * (cell[2] + dk))];
+    double val = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int dk = 0; dk < 2; ++dk) {
+                double wi = di ? f[0] : 1.0 - f[0], wj = dj ? f[1] : 1.0 - f[1], wk = dk ? f[2] : 1.0 - f[2];
+                val += wi * wj * wk * smp[di][dj][dk];
+            }
+    /* the derivative along each axis: the bilinear blend of the cell's four edge differences */
+    for (int e = 0; e < 2; ++e)
+        for (int o = 0; o < 2; ++o) {
+            double w1 = e ? f[1] : 1.0 - f[1], w2 = o ? f[2] : 1.0 - f[2];
+            g[0] += w1 * w2 * (smp[1][e][o] - smp[0][e][o]);
+            double w0 = e ? f[0] : 1.0 - f[0];
+            g[1] += w0 * w2 * (smp[e][1][o] - smp[e][0][o]);
+            double w1b = o ? f[1] : 1.0 - f[1];
+            g[2] += w0 * w1b * (smp[e][o][1] - smp[e][o][0]);
+        }
+    *phi = val;
+    for (int a = 0; a < 3; ++a) grad[a] = g[a] / c->sdf_h;
+    if (ambiguous) *ambiguous = amb;
+    return 1;
+}
+
+/* Analytic signed distances of the primitive shapes of Sec. 3 (box, capsule) and SDF volumes, in the
+ * shape frame. A point outside an SDF volume's lattice is outside the body (phi = +1e30, no normal). */
 double orc_collider_sdf(const orc_collider* c, double t, const double x[3], double normal[3], int* ambiguous) {
     double R[9], p[3], com[3];
     orc_collider_pose(c, t, R, p, com);
@@ -302,6 +350,15 @@ double orc_collider_sdf(const orc_collider* c, double t, const double x[3], doub
                 if (i != am && fabs(q[i] - qmax) < 1e-6) amb = 1;
             if (fabs(l[am]) < 1e-6) amb = 1;
         }
+    } else if (c->type == ORC_SDF_VOLUME) {
+        double g[3];
+        if (!orc_sdf_volume(c, l, &phi, g, &amb)) {
+            phi = 1e30;
+        } else {
+            double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            if (gl > 0.0)
+                for (int i = 0; i < 3; ++i) nl[i] = g[i] / gl;
+        }
     } else {
         double r = c->half[0], h = c->half[1];
         double cz = l[2] < -h ? -h : (l[2] > h ? h : l[2]);
@@ -329,6 +386,13 @@ double orc_collider_sdf(const orc_collider* c, double t, const double x[3], doub
  *   mv_i += w_ip (m_p v_p + A_p (x_i - x_p)),   A_p = m_p C_p - dt V0 (4/dx^2) tau_p. */
 void orc_p2g(const orc_params* P, int np, const double* x, const double* v, const double* C,
              const double* F, const double* J, double* grid) {
+    orc_p2g_forces(P, np, x, v, C, F, J, 0, grid);
+}
+
+/* The same transfer with Algorithm 1's "forces": an external acceleration a_p adds the impulse
+ * dt m_p a_p to the momentum the particle scatters. */
+void orc_p2g_forces(const orc_params* P, int np, const double* x, const double* v, const double* C,
+                    const double* F, const double* J, const double* accel, double* grid) {
     int n = P->n;
     double dx = 1.0 / n;
     size_t nn = (size_t)n * n * n;
@@ -337,6 +401,8 @@ void orc_p2g(const orc_params* P, int np, const double* x, const double* v, cons
     for (int p = 0; p < np; ++p) {
         double xp[3] = {x[p], x[np + p], x[2 * np + p]};
         double vp[3] = {v[p], v[np + p], v[2 * np + p]};
+        if (accel)
+            for (int a = 0; a < 3; ++a) vp[a] += P->dt * accel[(size_t)a * np + p];
         double Cp[9], tau[9], A[9];
         for (int i = 0; i < 9; ++i) Cp[i] = C[(size_t)i * np + p];
         if (P->kind == ORC_PLASTICINE) {
@@ -496,5 +562,77 @@ int orc_substep(const orc_params* P, int np, double* x, double* v, double* C, do
                 unsigned char* ambiguous) {
     orc_p2g(P, np, x, v, C, F, J, grid);
     orc_grid_update(P, grid, ncol, cols, t, wrench, ambiguous);
+    return orc_g2p(P, np, grid, x, v, C, F, J, 0);
+}
+
+/* ---------------------------------------------------------------- particle contact (Sec. 3) */
+
+/* Algorithm 1 "compute penalty forces" and "accumulate equivalent rigid-body forces and torques".
+ * For a particle inside body c (phi < 0), with the body's velocity at the particle
+ * v_c = v_lin + w x (x_p - com), relative velocity v_r = v_p - v_c, its normal part v_n = v_r . n and
+ * tangential part v_t = v_r - v_n n, the penalty acceleration is
+ *   a = a_n n - min(damping |v_t|, friction a_n) v_t / |v_t|,
+ *   a_n = stiffness (-phi) + damping max(-v_n, 0)  (>= 0: a spring on the depth, a damper on approach).
+ * The body receives the opposite impulse, -dt m_p a, and its moment about the centre of mass. */
+int orc_penalty_accel(const orc_params* P, const orc_penalty* pen, int np, const double* x, const double* v,
+                      int ncol, const orc_collider* cols, double t, double* accel, double* wrench,
+                      unsigned char* ambiguous) {
+    int contacts = 0;
+    for (int p = 0; p < np; ++p) {
+        double xp[3] = {x[p], x[np + p], x[2 * np + p]};
+        double vp[3] = {v[p], v[np + p], v[2 * np + p]};
+        double acc[3] = {0.0, 0.0, 0.0};
+        if (ambiguous) ambiguous[p] = 0;
+        for (int c = 0; c < ncol; ++c) {
+            double nrm[3];
+            int amb = 0;
+            double phi = orc_collider_sdf(&cols[c], t, xp, nrm, &amb);
+            if (amb && ambiguous) ambiguous[p] = 1;
+            if (!(phi < 0.0)) continue;
+            ++contacts;
+            double R[9], org[3], com[3];
+            orc_collider_pose(&cols[c], t, R, org, com);
+            double rel[3] = {xp[0] - com[0], xp[1] - com[1], xp[2] - com[2]};
+            double wxr[3];
+            cross3(cols[c].ang_vel, rel, wxr);
+            double vr[3];
+            for (int a = 0; a < 3; ++a) vr[a] = vp[a] - (cols[c].lin_vel[a] + wxr[a]);
+            double vn = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
+            double an = pen->stiffness * (-phi) + pen->damping * (vn < 0.0 ? -vn : 0.0);
+            double vt[3];
+            for (int a = 0; a < 3; ++a) vt[a] = vr[a] - vn * nrm[a];
+            double tn = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+            double ft = 0.0; /* tangential acceleration per unit sliding speed */
+            if (tn > 0.0) {
+                double cap = cols[c].friction * an;
+                double visc = pen->damping * tn;
+                ft = (visc < cap ? visc : cap) / tn;
+            }
+            double a_c[3];
+            for (int a = 0; a < 3; ++a) {
+                a_c[a] = an * nrm[a] - ft * vt[a];
+                acc[a] += a_c[a];
+            }
+            if (wrench) {
+                double imp[3], tq[3];
+                for (int a = 0; a < 3; ++a) imp[a] = -P->dt * P->p_mass * a_c[a];
+                cross3(rel, imp, tq);
+                for (int a = 0; a < 3; ++a) {
+                    wrench[c * 6 + a] += imp[a];
+                    wrench[c * 6 + 3 + a] += tq[a];
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) accel[(size_t)a * np + p] = acc[a];
+    }
+    return contacts;
+}
+
+int orc_substep_penalty(const orc_params* P, const orc_penalty* pen, int np, double* x, double* v, double* C,
+                        double* F, double* J, int ncol, const orc_collider* cols, double t, double* wrench,
+                        double* grid, double* accel, unsigned char* ambiguous) {
+    orc_penalty_accel(P, pen, np, x, v, ncol, cols, t, accel, wrench, ambiguous);
+    orc_p2g_forces(P, np, x, v, C, F, J, accel, grid);
+    orc_grid_update(P, grid, 0, cols, t, 0, 0);
     return orc_g2p(P, np, grid, x, v, C, F, J, 0);
 }

@@ -24,7 +24,13 @@
  *   - grid-node contact against analytic box / capsule signed distances with
  *     Coulomb friction (the grid form of Sec. 3's coupling), the impulse taken
  *     from each node summed per body with its moment about the body's centre of
- *     mass (Algorithm 1, force-torque buffers).
+ *     mass (Algorithm 1, force-torque buffers);
+ *   - the particle form of the coupling (Sec. 3's default; Algorithm 1 "compute
+ *     penalty forces"): a spring-damper penalty acceleration at every particle
+ *     inside a body, with viscous friction capped by Coulomb's law, entering
+ *     P2G as a momentum source, its reaction summed per body;
+ *   - signed distances of meshes as SDF volumes (Sec. 3), read by trilinear
+ *     interpolation with the interpolant's own gradient as the normal.
  *
  * Layout. Particle state is structure-of-arrays in FP64: x[3][np], v[3][np],
  * C[9][np], F[9][np] (3x3 matrices row-major: component r*3+c of particle p at
@@ -44,7 +50,7 @@ extern "C" {
 #endif
 
 enum { ORC_PLASTICINE = 0, ORC_FLUID = 1 };
-enum { ORC_BOX = 0, ORC_CAPSULE = 1 };
+enum { ORC_BOX = 0, ORC_CAPSULE = 1, ORC_SDF_VOLUME = 2 };
 
 typedef struct {
     int n;               /* grid nodes per axis, dx = 1/n */
@@ -59,7 +65,7 @@ typedef struct {
 } orc_params;
 
 typedef struct {
-    int type;            /* ORC_BOX or ORC_CAPSULE */
+    int type;            /* ORC_BOX, ORC_CAPSULE or ORC_SDF_VOLUME */
     double half[3];      /* box half extents | capsule (radius, half length along local z, unused) */
     double friction;     /* Coulomb coefficient */
     double pos[3];       /* shape-frame origin at t = 0 (world) */
@@ -67,7 +73,21 @@ typedef struct {
     double lin_vel[3];   /* velocity of the centre of mass (world) */
     double ang_vel[3];   /* angular velocity (world) */
     double com[3];       /* centre of mass at t = 0 (world) */
+    /* ORC_SDF_VOLUME only: signed distances sampled on a lattice in the shape frame, sample (i,j,k) at
+     * sdf_origin + sdf_h * (i,j,k), stored at sdf[i + res[0] * (j + res[1] * k)]; res[a] >= 2 */
+    const double* sdf;
+    int res[3];
+    double sdf_origin[3];
+    double sdf_h;
 } orc_collider;
+
+/* Penalty contact at the particles (Sec. 3's default coupling): per unit of particle mass, a normal
+ * acceleration stiffness * depth + damping * (approach speed), and a tangential one that opposes the
+ * sliding velocity, damping * |v_t| capped by friction * (normal acceleration). */
+typedef struct {
+    double stiffness;    /* 1/s^2 */
+    double damping;      /* 1/s */
+} orc_penalty;
 
 /* Lame parameters from Young's modulus and Poisson ratio (Table 4 gives E, nu). */
 void orc_lame(double E, double nu, double* mu, double* lambda);
@@ -101,6 +121,26 @@ double orc_collider_sdf(const orc_collider* c, double t, const double x[3], doub
 void orc_p2g(const orc_params* P, int np, const double* x, const double* v, const double* C,
              const double* F, const double* J, double* grid);
 
+/* Step A1+A2 with external particle accelerations accel[3][np] (SoA; NULL = none): the momentum each
+ * particle scatters is m_p (v_p + dt a_p) + A_p (x_i - x_p). */
+void orc_p2g_forces(const orc_params* P, int np, const double* x, const double* v, const double* C,
+                    const double* F, const double* J, const double* accel, double* grid);
+
+/* Trilinear interpolation of a collider's SDF volume at the shape-frame point l: the value and its
+ * gradient (shape frame). Returns 0 (and leaves phi, grad untouched) when l lies outside the lattice.
+ * *ambiguous is set when l is within 1e-5 cells of a cell face (where the gradient is discontinuous). */
+int orc_sdf_volume(const orc_collider* c, const double l[3], double* phi, double grad[3], int* ambiguous);
+
+/* Algorithm 1 "compute penalty forces" and "accumulate equivalent rigid-body forces and torques" at
+ * collider time t: accel[3][np] (SoA) receives each particle's penalty acceleration summed over the
+ * colliders (index order, each from the particle's velocity at the start of the substep); wrench[6*k]
+ * (may be NULL) accumulates per collider the impulse -dt m_p a and its moment about the centre of mass.
+ * ambiguous[np] (may be NULL) marks particles whose inside test or normal branch is within 1e-6 of
+ * flipping. Returns the number of particle-collider contacts. */
+int orc_penalty_accel(const orc_params* P, const orc_penalty* pen, int np, const double* x, const double* v,
+                      int ncol, const orc_collider* cols, double t, double* accel, double* wrench,
+                      unsigned char* ambiguous);
+
 /* Step A3: v = mv/m + dt g on nodes with m > 0, colliders in index order, then sticky walls.
  * wrench[6*k] accumulates (impulse, angular impulse about the com) per collider; may be NULL.
  * ambiguous (n^3 bytes, may be NULL) marks nodes whose inside test or normal branch is within 1e-6
@@ -118,6 +158,14 @@ int orc_g2p(const orc_params* P, int np, const double* grid, double* x, double* 
 int orc_substep(const orc_params* P, int np, double* x, double* v, double* C, double* F, double* J,
                 int ncol, const orc_collider* cols, double t, double* wrench, double* grid,
                 unsigned char* ambiguous);
+
+/* One full substep with the particle form of the contact (Algorithm 1 in order): penalty
+ * accelerations and body impulses at collider time t, P2G with those forces, the grid update without
+ * colliders (gravity, sticky walls), G2P. accel is caller scratch of 3*np doubles; ambiguous (np bytes,
+ * may be NULL) as orc_penalty_accel. Returns the number of clamped coordinates. */
+int orc_substep_penalty(const orc_params* P, const orc_penalty* pen, int np, double* x, double* v, double* C,
+                        double* F, double* J, int ncol, const orc_collider* cols, double t, double* wrench,
+                        double* grid, double* accel, unsigned char* ambiguous);
 
 #ifdef __cplusplus
 }
