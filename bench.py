@@ -55,11 +55,11 @@ def env_rank():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the fused substep kernel (k_g2p2g) is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in ("mpm_device.cuh", "mpm_internal.h", "mpm_kernels.cu"):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -324,6 +324,8 @@ def run_native(args):
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(dev, "batch256", args.batched_steps, 3, per_scene=True, tune=True)
         line["serving"] = run_batched(dev, "serve1024", args.batched_steps, 3, per_scene=False, tune=True)
+    if world == 1 and args.surrogate_scenes > 0:
+        line["surrogate"] = run_surrogate(dev, args.surrogate_scenes)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)
@@ -495,6 +497,42 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
     return out
 
 
+def run_surrogate(dev, n_scenes: int):
+    """The learned grid surrogate (the committed trained weights) against the plain method on held-out
+    pinch scenes (seeds 20000 + i, 200,000 particles, 64^3 grid, two capsule fingers; none of them among the
+    training seeds 10000-11999). Per scene, from the state after two plain env steps: four env steps by
+    each form from the same state; errors compare positions after the first env step; times are the mean
+    of four back-to-back env steps (median over scenes), graphs captured beforehand. The surrogate runs
+    with the per-step gate (a step whose windows fail the mass or momentum check is redone by plain
+    substeps) and without a gate."""
+    from paper_2302_04659_gb300 import surrogate as sur
+
+    if not os.path.exists(sur.WEIGHTS):
+        return {"unavailable": "trained weights not present"}
+    t0 = time.perf_counter()
+    net = sur.Network.load(sur.WEIGHTS, device=dev)
+    seeds = range(20000, 20000 + n_scenes)
+    gated = sur.summarize(sur.evaluate(net, seeds, device=dev, gate=True))
+    ungated = sur.summarize(sur.evaluate(net, seeds, device=dev, gate=False))
+    meta = net.meta
+    return {
+        "workload": "pinch scenes, held out",
+        "seeds": [seeds[0], seeds[-1]],
+        "particles": 200_000,
+        "window_substeps": sur.K,
+        "gate": {"threshold": sur.THRESHOLD, "v_ref": sur.V_REF, "what": "mass and momentum residuals"},
+        "training": {k: meta.get(k) for k in ("rollouts", "seeds", "windows", "epochs")},
+        "gated": gated,
+        "ungated": ungated,
+        "env_steps_per_s_plain": 1e3 / gated["ms_per_env_step_plain"],
+        "env_steps_per_s_surrogate_gated": 1e3 / gated["ms_per_env_step_surrogate"],
+        "env_steps_per_s_surrogate_ungated": 1e3 / ungated["ms_per_env_step_surrogate"],
+        "speedup_gated": gated["ms_per_env_step_plain"] / gated["ms_per_env_step_surrogate"],
+        "speedup_ungated": ungated["ms_per_env_step_plain"] / ungated["ms_per_env_step_surrogate"],
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
 def oracle_setup(sc, sample=None):
     import oracle
     m = sc.material
@@ -598,7 +636,9 @@ def main():
     ap.add_argument("--particles", type=int, default=200_000, help="particles of the pinch scene")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving workloads")
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
-    ap.add_argument("--only", choices=["batched", "serving"], default=None,
+    ap.add_argument("--surrogate-scenes", type=int, default=256,
+                    help="held-out scenes of the surrogate evaluation (0 skips it)")
+    ap.add_argument("--only", choices=["batched", "serving", "surrogate"], default=None,
                     help="run one batched workload alone and print its section (profiling runs)")
     ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
     ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
@@ -613,8 +653,11 @@ def main():
         b.build()
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps, 3,
-                          per_scene=False, tune=not args.no_tune, nenv=args.envs)
+        if args.only == "surrogate":
+            out = run_surrogate(dev, args.surrogate_scenes)
+        else:
+            out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps,
+                              3, per_scene=False, tune=not args.no_tune, nenv=args.envs)
         print(json.dumps(out), flush=True)
     else:
         run_native(args)

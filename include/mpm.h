@@ -11,9 +11,12 @@
  *   - accumulated body forces / torques are read back              -> mpm_read_wrench
  *   - particles are handed to a consumer by one GPU-GPU copy       -> mpm_read_state
  *     (App. D.2), or to the host.
- * Contact uses the grid form the paper names as the alternative it also
- * supports (Sec. 3: signed distances evaluated on grid nodes, as in
- * PlasticineLab), with Coulomb friction.
+ * Contact comes in the two forms Sec. 3 describes (mpm_set_contact): the grid
+ * form (signed distances evaluated on grid nodes, as in PlasticineLab, with a
+ * Coulomb friction projection; the default) and the particle form the paper
+ * prefers (signed distances evaluated at the particles, penalty forces entering
+ * the particle-to-grid transfer). Bodies are boxes, capsules or SDF volumes
+ * (Sec. 3: meshes become signed-distance volumes).
  *
  * Conventions
  *   - Everything is FP32 except the wrench accumulators (FP64).
@@ -65,7 +68,8 @@ typedef enum {
 #define MPM_FLAG_FAR_MOVE 0x8u   /* a particle moved >= 1 cell in one substep (served by a slower path) */
 
 enum { MPM_PLASTICINE = 0, MPM_FLUID = 1 };
-enum { MPM_BOX = 0, MPM_CAPSULE = 1 };
+enum { MPM_BOX = 0, MPM_CAPSULE = 1, MPM_SDF_VOLUME = 2 };
+enum { MPM_CONTACT_GRID = 0, MPM_CONTACT_PARTICLE = 1 };
 
 typedef struct {
     int n;              /* grid nodes per axis: a multiple of 4 in [8, 256]; dx = 1/n */
@@ -86,9 +90,19 @@ typedef struct {
 } mpm_material;
 
 typedef struct {
-    int type;           /* MPM_BOX or MPM_CAPSULE */
+    int type;           /* MPM_BOX, MPM_CAPSULE or MPM_SDF_VOLUME */
     float half[3];      /* box half extents | capsule (radius, half length along local z, ignored) */
     float friction;     /* Coulomb coefficient >= 0 */
+    /* MPM_SDF_VOLUME only (Sec. 3: a mesh's signed distances as a volume): samples on a lattice in the
+     * shape frame, sample (i,j,k) at sdf_origin + sdf_h * (i,j,k) stored at
+     * sdf[i + res[0] * (j + res[1] * k)], FP32, in DEVICE memory owned by the caller, which keeps it
+     * alive and unchanged while the shape is in use. res[a] >= 2, sdf_h > 0. The library interpolates
+     * trilinearly (in FP32, not with texture filtering) and takes the interpolant's gradient as the
+     * normal; a point outside the lattice is outside the body. */
+    const float* sdf;
+    int res[3];
+    float sdf_origin[3];
+    float sdf_h;
 } mpm_shape;
 
 /* Bytes of device workspace a handle with this configuration needs. */
@@ -160,6 +174,22 @@ mpm_status mpm_set_colliders(mpm_sim* sim, int k, const float* pose, const float
  * colliders and sticky walls, G2P with F update and return mapping). Asynchronous: no host sync. */
 mpm_status mpm_substep(mpm_sim* sim, int n_substeps, void* stream);
 
+/* Contact form (Sec. 3), for all envs of the handle; takes effect at the next substep.
+ *   MPM_CONTACT_GRID (default): colliders act on grid nodes in the grid update; stiffness and damping
+ *     are ignored.
+ *   MPM_CONTACT_PARTICLE: Algorithm 1 "compute penalty forces": at the start of every substep each
+ *     particle inside a body (phi < 0) gets, per unit mass and per body (index order), the acceleration
+ *       a = a_n n - min(damping |v_t|, friction a_n) v_t / |v_t|,
+ *       a_n = stiffness (-phi) + damping max(-v_n, 0),
+ *     from its velocity relative to the body's surface velocity (v_n along the outward normal n, v_t
+ *     the tangential rest); the particle-to-grid transfer adds dt m_p a to its momentum and the body's
+ *     force-torque buffer receives -dt m_p a and its moment. The grid update then applies gravity and
+ *     the walls only. stiffness >= 0 in 1/s^2 with stiffness dt^2 <= 1, damping >= 0 in 1/s with
+ *     damping dt <= 1 (explicit stability). Each mpm_substep call then ends on a grid-to-particle pass alone, so that the next call's first
+ *     transfer sees the poses of the mpm_set_colliders in between.
+ * Not available while a surrogate network is attached (mpm_surrogate_attach). */
+mpm_status mpm_set_contact(mpm_sim* sim, int mode, float stiffness, float damping);
+
 /* Particle state in the caller's original order. Any pointer may be NULL (skipped). Arrays SoA with
  * stride n. dst_on_device = 1: written on `stream` (the paper's single GPU-GPU copy), no sync.
  * dst_on_device = 0: host memory, the call synchronizes `stream`. A fluid reports F = J^(1/3) I. */
@@ -167,8 +197,8 @@ mpm_status mpm_read_state(mpm_sim* sim, float* x, float* v, float* C, float* F, 
                           void* stream);
 
 /* Force-torque buffers (Algorithm 1 "apply accumulated forces and torques"): for each collider the
- * impulse (3) and angular impulse about its centre of mass (3) that the soft body received from it
- * since the last mpm_set_colliders, as k x 6 doubles in host memory; *n_substeps (may be NULL) gets
+ * impulse (3) and angular impulse about its centre of mass (3) that the body received from the soft
+ * material since the last mpm_set_colliders, as k x 6 doubles in host memory; *n_substeps (may be NULL) gets
  * the substeps accumulated, so the mean force is impulse / (n_substeps * dt). Synchronizes `stream`. */
 mpm_status mpm_read_wrench(mpm_sim* sim, double* impulse_torque, int* n_substeps, void* stream);
 

@@ -42,7 +42,9 @@ class mpm_material(ctypes.Structure):
 
 
 class mpm_shape(ctypes.Structure):
-    _fields_ = [("type", ctypes.c_int), ("half", ctypes.c_float * 3), ("friction", ctypes.c_float)]
+    _fields_ = [("type", ctypes.c_int), ("half", ctypes.c_float * 3), ("friction", ctypes.c_float),
+                ("sdf", ctypes.c_void_p), ("res", ctypes.c_int * 3), ("sdf_origin", ctypes.c_float * 3),
+                ("sdf_h", ctypes.c_float)]
 
 
 class mpm_env(ctypes.Structure):
@@ -94,6 +96,7 @@ def _load():
         "mpm_set_shapes_batch": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(mpm_shape)]),
         "mpm_num_envs": (ctypes.c_int, [_vp]),
         "mpm_set_launch": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "mpm_set_contact": (st, [_vp, ctypes.c_int, ctypes.c_float, ctypes.c_float]),
         "mpm_get_launch": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)]),
         "mpm_set_particles": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
@@ -216,6 +219,15 @@ def mpm_num_envs(sim: int) -> int:
 
 def mpm_set_launch(sim: int, chunk: int = 0, fused_ctas_per_sm: int = 0, grid_ctas_per_sm: int = 0) -> None:
     _check("mpm_set_launch", _load().mpm_set_launch(sim, chunk, fused_ctas_per_sm, grid_ctas_per_sm))
+
+
+MPM_CONTACT_GRID = 0
+MPM_CONTACT_PARTICLE = 1
+MPM_SDF_VOLUME = 2
+
+
+def mpm_set_contact(sim: int, mode: int, stiffness: float = 0.0, damping: float = 0.0) -> None:
+    _check("mpm_set_contact", _load().mpm_set_contact(sim, mode, stiffness, damping))
 
 
 def mpm_get_launch(sim: int):

@@ -188,6 +188,8 @@ struct mpm_sim {
     std::vector<mpm_shape> shapes;
     std::vector<int> shape_counts;  // shapes per env
     int ncol = 0;  // colliders uploaded by the last mpm_set_colliders
+    int contact = MPM_CONTACT_GRID;  // mpm_set_contact
+    float stiffness = 0.0f, damping = 0.0f;
     bool sur_pending = false;  // a surrogate window was started and not yet ended
     // attached surrogate network (mpm_surrogate_attach)
     bool net_attached = false;
@@ -348,6 +350,14 @@ TransferParams transfer_params(mpm_sim* s) {
     p.chunks_next = s->at<int4>(s->L.chunks);
     p.num_chunks_next = s->num_chunks();
     p.done = s->done();
+    p.contact = s->contact == MPM_CONTACT_PARTICLE ? 1 : 0;
+    p.stiffness = s->stiffness;
+    p.damping = s->damping;
+    p.cols = s->at<ColliderSet>(s->L.colliders);
+    p.poses = s->at<ColliderNow>(s->L.poses);
+    p.k_total = s->ncol;
+    p.wrench = s->at<double>(s->L.wrench);
+    p.scatter = 1;
     return p;
 }
 
@@ -373,6 +383,7 @@ GridParams grid_params(mpm_sim* s) {
     gp.substep_counter = s->substep_counter();
     gp.wrench = s->at<double>(s->L.wrench);
     gp.ctas = (int)std::max<size_t>(1, std::min<size_t>((size_t)s->sms * s->grid_cps, (s->T.bins + 3) / 4));
+    gp.grid_colliders = s->contact == MPM_CONTACT_GRID ? 1 : 0;
     return gp;
 }
 
@@ -455,8 +466,9 @@ mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate =
 // Second half: the fused G2P -> P2G pass from the updated grid (advecting by advect_dt, the substep's dt
 // unless a surrogate window overrides it for a one-env handle), then the bin scan if it is separate.
 mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 0.0f, const uint32_t* gate = nullptr,
-                                 uint32_t gate_run = 1) {
+                                 uint32_t gate_run = 1, bool scatter = true) {
     TransferParams p = transfer_params(s);
+    p.scatter = scatter ? 1 : 0;
     p.gate = gate;
     p.gate_run = gate_run;
     p.grid_in = s->at<float4>(s->L.grid[s->ps.g]);
@@ -469,7 +481,7 @@ mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 
     s->ps.cur = 1 - s->ps.cur;
     s->ps.g = 1 - s->ps.g;
     s->ps.order_valid = false;  // assigned by the next launch
-    s->ps.grid_valid = true;
+    s->ps.grid_valid = scatter;
     s->ps.scanned = s->tail_scan();  // the fused pass's last CTA wrote the new bins
     if (!s->ps.scanned) MPM_TRY(ensure_scanned(s, st));
     return MPM_OK;
@@ -477,11 +489,13 @@ mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 
 
 // The launches of n substeps: per substep one sort-assign + grid-update launch and one fused
 // G2P->P2G launch (whose last CTA sorts the new positions into bins; with many bins two scan launches
-// follow instead).
+// follow instead). With the particle form of the contact the last fused launch stops after G2P: the
+// next call's first transfer then takes its penalties at the poses set in between.
 mpm_status enqueue_substeps(mpm_sim* s, int n, cudaStream_t st) {
+    const bool particle_contact = s->contact == MPM_CONTACT_PARTICLE;
     for (int it = 0; it < n; ++it) {
         MPM_TRY(enqueue_grid_half(s, st));
-        MPM_TRY(enqueue_particle_half(s, st));
+        MPM_TRY(enqueue_particle_half(s, st, 0.0f, nullptr, 1, !(particle_contact && it == n - 1)));
     }
     return MPM_OK;
 }
@@ -789,8 +803,15 @@ mpm_status mpm_set_shapes_batch(mpm_sim* s, const int* counts, const mpm_shape* 
     if (total > 0 && !shapes) return MPM_ERR_INVALID_ARG;
     for (int i = 0; i < total; ++i) {
         const mpm_shape& sh = shapes[i];
-        if (sh.type != MPM_BOX && sh.type != MPM_CAPSULE) return MPM_ERR_INVALID_ARG;
+        if (sh.type != MPM_BOX && sh.type != MPM_CAPSULE && sh.type != MPM_SDF_VOLUME) return MPM_ERR_INVALID_ARG;
         if (!(sh.friction >= 0.0f) || !std::isfinite(sh.friction)) return MPM_ERR_INVALID_ARG;
+        if (sh.type == MPM_SDF_VOLUME) {
+            if (!sh.sdf || !(sh.sdf_h > 0.0f) || !std::isfinite(sh.sdf_h)) return MPM_ERR_INVALID_ARG;
+            if (reinterpret_cast<uintptr_t>(sh.sdf) % alignof(float)) return MPM_ERR_INVALID_ARG;
+            for (int a = 0; a < 3; ++a)
+                if (sh.res[a] < 2 || sh.res[a] > 4096 || !std::isfinite(sh.sdf_origin[a])) return MPM_ERR_INVALID_ARG;
+            continue;
+        }
         const int dims = sh.type == MPM_BOX ? 3 : 2;
         for (int a = 0; a < dims; ++a)
             if (!(sh.half[a] >= 0.0f) || !std::isfinite(sh.half[a])) return MPM_ERR_INVALID_ARG;
@@ -824,6 +845,15 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
         c.type = sh.type;
         for (int a = 0; a < 3; ++a) c.half[a] = sh.half[a];
         c.friction = sh.friction;
+        c.vol = SdfVolume{};
+        if (sh.type == MPM_SDF_VOLUME) {
+            c.vol.data = sh.sdf;
+            for (int a = 0; a < 3; ++a) {
+                c.vol.res[a] = sh.res[a];
+                c.vol.origin[a] = sh.sdf_origin[a];
+            }
+            c.vol.inv_h = 1.0f / sh.sdf_h;
+        }
         float qn = 0.0f;
         for (int a = 0; a < 3; ++a) {
             c.pos[a] = pose[i * 7 + a];
@@ -932,6 +962,24 @@ mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid
     return MPM_OK;
 }
 
+mpm_status mpm_set_contact(mpm_sim* s, int mode, float stiffness, float damping) {
+    if (!s || (mode != MPM_CONTACT_GRID && mode != MPM_CONTACT_PARTICLE)) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
+    if (s->net_attached || s->sur_pending) return MPM_ERR_INVALID_ARG;
+    if (mode == MPM_CONTACT_PARTICLE) {
+        const double dt = s->cfg.dt;
+        if (!(stiffness >= 0.0f) || !std::isfinite(stiffness) || (double)stiffness * dt * dt > 1.0) return MPM_ERR_INVALID_ARG;
+        if (!(damping >= 0.0f) || !std::isfinite(damping) || (double)damping * dt > 1.0) return MPM_ERR_INVALID_ARG;
+    }
+    s->contact = mode;
+    s->stiffness = mode == MPM_CONTACT_PARTICLE ? stiffness : 0.0f;
+    s->damping = mode == MPM_CONTACT_PARTICLE ? damping : 0.0f;
+    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, s->nenv == 1, mode == MPM_CONTACT_PARTICLE);
+    s->fused_cps = std::min(s->fused_cps, s->max_fused_cps);
+    s->drop_graphs();
+    return MPM_OK;
+}
+
 mpm_status mpm_get_launch(const mpm_sim* s, int* chunk, int* fused_ctas_per_sm, int* grid_ctas_per_sm) {
     if (!s) return MPM_ERR_INVALID_ARG;
     if (chunk) *chunk = s->chunk;
@@ -1019,7 +1067,8 @@ static mpm_box box_from_bins(const int b[6], int margin, int n) {
 }
 
 mpm_status mpm_surrogate_box(mpm_sim* s, int margin, mpm_box* box, void* stream) {
-    if (!s || !box || margin < 0 || s->nenv != 1 || s->sur_pending) return MPM_ERR_INVALID_ARG;
+    if (!s || !box || margin < 0 || s->nenv != 1 || s->sur_pending || s->contact != MPM_CONTACT_GRID)
+        return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     *box = mpm_box{0, 0, 0, 0, 0, 0};
@@ -1283,6 +1332,7 @@ mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* 
                                 int max_voxels) {
     if (!s || s->nenv != 1 || !s->tail_scan()) return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
+    if (net && s->contact != MPM_CONTACT_GRID) return MPM_ERR_INVALID_ARG;  // windows use the grid form
     if (!net) {
         s->net_attached = false;
         s->drop_graphs();

@@ -228,6 +228,13 @@ __device__ __forceinline__ void fixed_corotated_stress(const float (&F)[3][3], c
 // rigidly with those velocities: com(t) = com0 + t v, orientation Rot(w t) R0 (Rodrigues), frame
 // origin carried about the centre of mass.
 
+struct SdfVolume {  // a mesh's signed distances on a lattice in the shape frame (type 2)
+    const float* data;  // sample (i,j,k) at origin + h (i,j,k), index i + res[0] (j + res[1] k)
+    int res[3];
+    float origin[3];
+    float inv_h;
+};
+
 struct ColliderSet {  // as set by the host (one entry per body)
     int type;
     float half[3];
@@ -237,6 +244,7 @@ struct ColliderSet {  // as set by the host (one entry per body)
     float lin[3];
     float ang[3];
     float com[3];
+    SdfVolume vol;
 };
 
 struct ColliderNow {  // pose at the current substep
@@ -248,6 +256,7 @@ struct ColliderNow {  // pose at the current substep
     float half[3];
     float friction;
     int type;
+    SdfVolume vol;
 };
 
 __device__ __forceinline__ void collider_at(const ColliderSet& c, float t, ColliderNow& o) {
@@ -290,9 +299,57 @@ __device__ __forceinline__ void collider_at(const ColliderSet& c, float t, Colli
     }
     o.friction = c.friction;
     o.type = c.type;
+    o.vol = c.vol;
 }
 
-// Signed distance and world-space outward normal of point xw (analytic box / capsule, Sec. 3).
+// Trilinear interpolation of an SDF volume at the shape-frame point l (Sec. 3 keeps one per mesh as a
+// 3-D texture; here plain loads and FP32 weights, since texture filtering quantises the weights):
+// the value, and the interpolant's gradient along each axis as the blend of the cell's four edge
+// differences. Returns false outside the lattice.
+__device__ __forceinline__ bool sdf_volume(const SdfVolume& V, const float l[3], float& phi, float g[3]) {
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = (l[a] - V.origin[a]) * V.inv_h;
+        if (!(u >= 0.0f) || u > (float)(V.res[a] - 1)) return false;
+        c[a] = min((int)floorf(u), V.res[a] - 2);
+        f[a] = u - (float)c[a];
+    }
+    const size_t sx = 1, sy = (size_t)V.res[0], sz = (size_t)V.res[0] * V.res[1];
+    const float* b = V.data + c[0] + sy * c[1] + sz * c[2];
+    float s[2][2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) s[i][j][k] = __ldg(b + i * sx + j * sy + k * sz);
+    float val = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                val += (i ? f[0] : 1.0f - f[0]) * (j ? f[1] : 1.0f - f[1]) * (k ? f[2] : 1.0f - f[2]) * s[i][j][k];
+    g[0] = g[1] = g[2] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            g[0] += (e ? f[1] : 1.0f - f[1]) * (o ? f[2] : 1.0f - f[2]) * (s[1][e][o] - s[0][e][o]);
+            g[1] += (e ? f[0] : 1.0f - f[0]) * (o ? f[2] : 1.0f - f[2]) * (s[e][1][o] - s[e][0][o]);
+            g[2] += (e ? f[0] : 1.0f - f[0]) * (o ? f[1] : 1.0f - f[1]) * (s[e][o][1] - s[e][o][0]);
+        }
+    phi = val;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] *= V.inv_h;
+    return true;
+}
+
+// Signed distance and world-space outward normal of point xw (analytic box / capsule, SDF volume;
+// Sec. 3). A point outside a volume's lattice is outside the body: phi = 1e30, no normal.
 __device__ __forceinline__ float collider_sdf(const ColliderNow& c, const float xw[3], float n[3]) {
     float d[3] = {xw[0] - c.p[0], xw[1] - c.p[1], xw[2] - c.p[2]};
     float l[3];
@@ -322,6 +379,17 @@ __device__ __forceinline__ float collider_sdf(const ColliderNow& c, const float 
             const bool on[3] = {!a1 && !a2, a1 && !a2, a2};
 #pragma unroll
             for (int i = 0; i < 3; ++i) nl[i] = on[i] ? (l[i] >= 0.0f ? 1.0f : -1.0f) : 0.0f;
+        }
+    } else if (c.type == 2) {
+        float g[3];
+        if (!sdf_volume(c.vol, l, phi, g)) {
+            phi = 1e30f;
+        } else {
+            const float gl = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            if (gl > 0.0f) {
+                const float r = 1.0f / gl;
+                nl[0] = g[0] * r; nl[1] = g[1] * r; nl[2] = g[2] * r;
+            }
         }
     } else {
         float r = c.half[0], h = c.half[1];

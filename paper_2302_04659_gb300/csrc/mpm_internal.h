@@ -96,6 +96,15 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     int4* chunks_next;
     uint32_t* num_chunks_next;
     uint32_t* done;         // CTAs finished, reset by the last one
+    // the particle form of the contact (mpm_set_contact): penalty accelerations added to the momentum
+    // each particle transfers, at the collider poses of substep *substep_counter
+    int contact;            // 1: particle penalty contact
+    float stiffness, damping;
+    const ColliderSet* cols;
+    const ColliderNow* poses;  // pose table (k_total > kSharedPoses), rows of k_total per substep
+    int k_total;
+    double* wrench;
+    int scatter;            // fused pass: 0 = grid-to-particle only, no transfer into the next grid
 };
 
 struct ScanParams {  // grid-wide scan of the bin counts (many bins)
@@ -127,9 +136,10 @@ struct GridParams {
     const ColliderSet* cols;  // all envs' colliders, as set
     const ColliderNow* poses; // [kPoseSteps][k_total] poses after each substep count (k_total > kSharedPoses)
     int k_total;              // colliders of all envs
-    const uint32_t* substep_counter;
+    uint32_t* substep_counter;  // read at the start, advanced by the last CTA
     double* wrench;           // k_total x 6
     int ctas;                 // CTAs of the (persistent) grid update
+    int grid_colliders;       // 1: the grid form of the contact acts here (0: particle form, no colliders)
 };
 
 struct AssignGridParams {  // the sort-assign of the new state and the grid update, one launch
@@ -223,6 +233,6 @@ cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_
 cudaError_t launch_cast_to_bf16(int n, const float* src, void* dst, cudaStream_t s);
 
 // occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
-int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env);
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen = false);
 
 }  // namespace mpm

@@ -560,12 +560,116 @@ __global__ void __launch_bounds__(256) k_assign(int N, const uint2* __restrict__
 
 // ------------------------------------------------------------------------ standalone P2G
 
+// ------------------------------------------------------------------------ particle contact
+
+// Penalty acceleration of a particle at x with velocity v against one body (Sec. 3's particle form of
+// the coupling, Algorithm 1 "compute penalty forces"): inside the body (phi < 0),
+//   a = a_n n - min(damping |v_t|, friction a_n) v_t / |v_t|,  a_n = stiffness (-phi) + damping max(-v_n, 0),
+// with v_n, v_t the normal and tangential parts of the velocity relative to the body's surface
+// velocity there. rel receives x - com, the lever arm of the reaction.
+__device__ __forceinline__ bool penalty_one(const ColliderNow& cn, const float x[3], const float v[3], float stiffness,
+                                            float damping, float a[3], float rel[3]) {
+    float nrm[3];
+    const float phi = collider_sdf(cn, x, nrm);
+    if (!(phi < 0.0f)) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rel[i] = x[i] - cn.com[i];
+    const float vr[3] = {v[0] - (cn.lin[0] + cn.ang[1] * rel[2] - cn.ang[2] * rel[1]),
+                         v[1] - (cn.lin[1] + cn.ang[2] * rel[0] - cn.ang[0] * rel[2]),
+                         v[2] - (cn.lin[2] + cn.ang[0] * rel[1] - cn.ang[1] * rel[0])};
+    const float vn = vr[0] * nrm[0] + vr[1] * nrm[1] + vr[2] * nrm[2];
+    const float an = stiffness * (-phi) + damping * fmaxf(-vn, 0.0f);
+    const float vt[3] = {vr[0] - vn * nrm[0], vr[1] - vn * nrm[1], vr[2] - vn * nrm[2]};
+    const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+    const float ft = tn > 0.0f ? fminf(damping * tn, cn.friction * an) / tn : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a[i] = an * nrm[i] - ft * vt[i];
+    return true;
+}
+
+// Pose of collider c at substep `step` for the penalty: this CTA's shared copy (few colliders), the
+// table mpm_set_colliders filled (first kPoseSteps substeps), else evaluated here.
+__device__ __forceinline__ void penalty_pose(const TransferParams& p, const ColliderNow* cs, bool shared_poses, int c,
+                                             uint32_t step, float dt, ColliderNow& cn) {
+    if (shared_poses)
+        cn = cs[c];
+    else if (step < (uint32_t)kPoseSteps)
+        cn = p.poses[(size_t)step * p.k_total + c];
+    else
+        collider_at(p.cols[c], (float)step * dt, cn);
+}
+
+// A particle's penalty acceleration summed over its env's bodies (index order), and the reactions
+// (Algorithm 1 "accumulate equivalent rigid-body forces and torques"): -dt m a and its moment about
+// the centre of mass, summed over the warp, then into this CTA's shared sums (few colliders) or the
+// FP64 buffers. All threads of the CTA call it (the loop bound is the chunk's env).
+__device__ __forceinline__ void penalty_accel(const TransferParams& p, const EnvDesc& E, const ColliderNow* cs,
+                                              float* cw, bool shared_poses, uint32_t step, bool active,
+                                              const float x[3], const float v[3], float acc[3]) {
+    const float dt = E.geo.dt, m = E.mat.p_mass;
+    acc[0] = acc[1] = acc[2] = 0.0f;
+    const int c1 = E.col_first + E.col_count;
+    for (int c = E.col_first; c < c1; ++c) {
+        ColliderNow cn;
+        penalty_pose(p, cs, shared_poses, c, step, dt, cn);
+        float a[3], rel[3];
+        const bool hit = active && penalty_one(cn, x, v, p.stiffness, p.damping, a, rel);
+        float w6[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (hit) {
+            const float imp[3] = {-dt * m * a[0], -dt * m * a[1], -dt * m * a[2]};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                acc[i] += a[i];
+                w6[i] = imp[i];
+            }
+            w6[3] = rel[1] * imp[2] - rel[2] * imp[1];
+            w6[4] = rel[2] * imp[0] - rel[0] * imp[2];
+            w6[5] = rel[0] * imp[1] - rel[1] * imp[0];
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) w6[q] += __shfl_xor_sync(0xffffffffu, w6[q], off);
+            if ((threadIdx.x & 31) == 0) {
+                if (shared_poses) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) atomicAdd(&cw[c * 6 + q], w6[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) atomicAdd(&p.wrench[(size_t)c * 6 + q], (double)w6[q]);
+                }
+            }
+        }
+    }
+}
+
+// Shared poses and reaction sums of a CTA that applies penalties (few colliders): poses at `step`.
+__device__ __forceinline__ void penalty_begin(const TransferParams& p, ColliderNow* cs, float* cw, uint32_t step,
+                                              float dt) {
+    if ((int)threadIdx.x < p.k_total) collider_at(p.cols[threadIdx.x], (float)step * dt, cs[threadIdx.x]);
+    for (int t = threadIdx.x; t < p.k_total * 6; t += blockDim.x) cw[t] = 0.0f;
+}
+
+__device__ __forceinline__ void penalty_end(const TransferParams& p, const float* cw) {
+    for (int t = threadIdx.x; t < p.k_total * 6; t += blockDim.x)
+        if (cw[t] != 0.0f) atomicAdd(&p.wrench[t], (double)cw[t]);
+}
+
 __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
     __shared__ ScatterTile T;
     __shared__ EnvDesc E;
+    __shared__ ColliderNow cs[kSharedPoses];
+    __shared__ float cw[kSharedPoses * 6];
     const int N = p.N;
     uint32_t flags = 0;
     const uint32_t nchunks = *p.num_chunks;
+    const bool shared_poses = p.k_total <= kSharedPoses;
+    const uint32_t step = p.contact ? *p.substep_counter : 0u;
+    if (p.contact && shared_poses) {
+        penalty_begin(p, cs, cw, step, p.env0.geo.dt);
+        __syncthreads();
+    }
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
         const int4 ch = p.chunks[w];
         const int env = ch.w;
@@ -600,8 +704,14 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
                     for (int c = 0; c < 3; ++c) tau[r][c] = r == c ? s : 0.0f;
             }
             affine(E.mat, C, tau, A);
-            bp = particle_bound(E.mat.p_mass, v, A, E.geo.dx);
         }
+        if (p.contact) {  // the penalty impulse joins the momentum this particle transfers
+            float acc[3];
+            penalty_accel(p, E, cs, cw, shared_poses, step, active, x, v, acc);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] += E.geo.dt * acc[a];
+        }
+        if (active) bp = particle_bound(E.mat.p_mass, v, A, E.geo.dx);
         tile_bound(T, bp);
         __syncthreads();
         const int k = momentum_scale_exp(T.bound_bits);
@@ -610,6 +720,7 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
         tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
         __syncthreads();
     }
+    if (p.contact && shared_poses) penalty_end(p, cw);
     if (flags) atomicOr(p.status, flags);
 }
 
@@ -627,13 +738,17 @@ __device__ __forceinline__ const EnvDesc& chunk_env(const TransferParams& p, con
 // than from shared memory, which keeps the single-scene kernel's register budget.
 // 7 resident CTAs per SM (72 registers): measured faster than 8, 9 or 10 CTAs with the spills a tighter
 // register budget forces, on both the 200k and the 600k pinch scene.
-template <int KIND, bool ONE_ENV>
-__global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
+// PEN: the particle form of the contact (penalty accelerations join the transfer; the grid update
+// applies no colliders then).
+template <int KIND, bool ONE_ENV, bool PEN>
+__global__ void __launch_bounds__(kChunk, PEN ? 6 : 7) k_g2p2g(TransferParams p) {
     // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots
     // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
     __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
     __shared__ ScatterTile T;
     __shared__ EnvDesc Es[2];  // several envs: the current chunk's env and the next one's
+    __shared__ ColliderNow cs[PEN ? kSharedPoses : 1];
+    __shared__ float cw[PEN ? kSharedPoses * 6 : 1];
     const int N = p.N;
     uint32_t flags = 0;
     wait_for_predecessor();
@@ -641,7 +756,11 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
         release_successor();
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(p.substep_counter, 1u);
+    // the substep the transfer belongs to (the grid update before this launch counted the last one)
+    const bool pen = PEN && p.scatter;
+    const bool shared_poses = p.k_total <= kSharedPoses;
+    const uint32_t step = pen ? *p.substep_counter : 0u;
+    if (pen && shared_poses) penalty_begin(p, cs, cw, step, p.env0.geo.dt);
     const uint32_t nchunks = *p.num_chunks;
     int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
     if constexpr (!ONE_ENV) {
@@ -774,22 +893,36 @@ __global__ void __launch_bounds__(kChunk, 7) k_g2p2g(TransferParams p) {
             p.out.pid[slot] = p.in.pid[src];
             newkey = E.bin_base + local_bin_of(xn, g);
             affine(E.mat, Cn, tau, A);
-            bp = particle_bound(E.mat.p_mass, vn, A, g.dx);
         }
+        if constexpr (PEN) {
+            if (pen) {  // the penalty impulse joins the momentum the new state transfers
+                float acc[3];
+                penalty_accel(p, E, cs, cw, shared_poses, step, active, xn, vn, acc);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vn[a] += dt * acc[a];
+            }
+        }
+        if (active) bp = particle_bound(E.mat.p_mass, vn, A, g.dx);
         // rank within the new bin: the atomic's result is only stored after the scatter, so its round
         // trip overlaps the work in between
         const uint32_t rank = warp_hist_add(p.hist, newkey, true);
-        tile_bound(T, bp);
-        __syncthreads();
-        // ---- P2G of the new state into the next grid
-        const int k = momentum_scale_exp(T.bound_bits);
-        const int o[3] = {ox - 1, oy - 1, oz - 1};
-        if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, pow2f(k));
-        if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
-        __syncthreads();
-        tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
+        if (p.scatter) {
+            tile_bound(T, bp);
+            __syncthreads();
+            // ---- P2G of the new state into the next grid
+            const int k = momentum_scale_exp(T.bound_bits);
+            const int o[3] = {ox - 1, oy - 1, oz - 1};
+            if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, pow2f(k));
+            if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
+            __syncthreads();
+            tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
+        } else if (active) {
+            p.keyrank_out[slot] = make_uint2(newkey, rank);
+        }
         __syncthreads();
     }
+    if constexpr (PEN)
+        if (pen && shared_poses) penalty_end(p, cw);
     if (flags) atomicOr(p.status, flags);
     release_successor();
     if (!p.tail_scan) return;
@@ -834,7 +967,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
     const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63, lane = threadIdx.x & 31;
     const uint32_t step = *p.substep_counter;
     constexpr bool shared_poses = SHARED_POSES;
-    if (shared_poses) {
+    if (shared_poses && p.grid_colliders) {
         if ((int)threadIdx.x < p.k_total) collider_at(p.cols[threadIdx.x], (float)step * p.dt, cs[threadIdx.x]);
         if ((int)threadIdx.x < p.k_total * 6) cw[threadIdx.x] = 0.0f;
         __syncthreads();
@@ -865,7 +998,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         decode_bin((int)lb, g.nb, bx, by, bz);
         const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
         const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
-        const int c_end = __any_sync(0xffffffffu, has_mass) ? E.col_first + E.col_count : 0;
+        const int c_end = p.grid_colliders && __any_sync(0xffffffffu, has_mass) ? E.col_first + E.col_count : 0;
         for (int c = E.col_first; c < c_end; ++c) {
             ColliderNow cn;
             if (shared_poses)
@@ -927,14 +1060,16 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         *node = make_float4(v[0], v[1], v[2], m);
     }
     __syncthreads();
-    if (shared_poses && (int)threadIdx.x < p.k_total * 6 && cw[threadIdx.x] != 0.0f)
+    if (shared_poses && p.grid_colliders && (int)threadIdx.x < p.k_total * 6 && cw[threadIdx.x] != 0.0f)
         atomicAdd(&p.wrench[threadIdx.x], (double)cw[threadIdx.x]);
-    // the last CTA to finish empties the previous grid's bin list (every CTA has read its count)
+    // the last CTA to finish empties the previous grid's bin list (every CTA has read its count) and
+    // counts the substep (every CTA has read the count)
     __shared__ bool last;
     if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == (uint32_t)p.ctas - 1u;
     __syncthreads();
     if (last && threadIdx.x == 0) {
         *p.list_count_old = 0u;
+        *p.substep_counter = step + 1u;
         *p.done = 0u;
     }
 }
@@ -1073,15 +1208,19 @@ cudaError_t launch_p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
 
 using TransferKernel = void (*)(TransferParams);
 
-static TransferKernel g2p2g_variant(int kind_all, bool one_env) {
-    if (one_env) return kind_all == 1 ? k_g2p2g<1, true> : k_g2p2g<0, true>;
-    if (kind_all == 0) return k_g2p2g<0, false>;
-    if (kind_all == 1) return k_g2p2g<1, false>;
-    return k_g2p2g<-1, false>;
+static TransferKernel g2p2g_variant(int kind_all, bool one_env, bool pen) {
+    if (pen) {  // the particle contact: one-env variants per material, one for every batch
+        if (one_env) return kind_all == 1 ? k_g2p2g<1, true, true> : k_g2p2g<0, true, true>;
+        return k_g2p2g<-1, false, true>;
+    }
+    if (one_env) return kind_all == 1 ? k_g2p2g<1, true, false> : k_g2p2g<0, true, false>;
+    if (kind_all == 0) return k_g2p2g<0, false, false>;
+    if (kind_all == 1) return k_g2p2g<1, false, false>;
+    return k_g2p2g<-1, false, false>;
 }
 
 cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
-    return launch_dependent(g2p2g_variant(p.kind_all, p.one_env != 0), grid_ctas, kChunk, s, p);
+    return launch_dependent(g2p2g_variant(p.kind_all, p.one_env != 0, p.contact != 0), grid_ctas, kChunk, s, p);
 }
 
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
@@ -1128,9 +1267,9 @@ cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_
     return cudaGetLastError();
 }
 
-int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env) {
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen) {
     int n = 0;
-    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, g2p2g_variant(kind_all, one_env), kChunk, 0)
+    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, g2p2g_variant(kind_all, one_env, pen), kChunk, 0)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g, kChunk, 0);
     if (e != cudaSuccess || n < 1) n = 1;
     return n;

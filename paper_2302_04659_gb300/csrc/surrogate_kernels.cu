@@ -260,7 +260,7 @@ __global__ void k_sur_gate(const double* sums, double m_particles, int k, double
 }
 
 // The corrected velocities written back (when the gate passed, if there is one); block 0 also advances
-// the substep counter by k - 1 (the pass that follows adds the last one) and counts the first substep's
+// the substep counter by k - 1 (the grid update before it counted the first) and counts the first substep's
 // body impulses k times.
 __global__ void k_sur_apply_gated(float4* __restrict__ grid, int n, int nb, int bound, SurBox box,
                                   const float* __restrict__ dv, float unit, const uint32_t* gate, uint32_t* counter,

@@ -34,6 +34,7 @@ PLASTICINE = 0
 FLUID = 1
 BOX = 0
 CAPSULE = 1
+SDF_VOLUME = 2
 
 
 def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
@@ -73,11 +74,16 @@ class Material:
 
 @dataclass
 class Shape:
-    """Collider shape: box half extents, or capsule (radius, half length along local z, 0)."""
+    """Collider shape: box half extents, or capsule (radius, half length along local z, 0), or an SDF
+    volume: ``sdf`` (nx, ny, nz) FP32 samples, [i, j, k] at ``sdf_origin + sdf_h * (i, j, k)`` in the
+    shape frame."""
 
     type: int
     half: tuple
     friction: float
+    sdf: np.ndarray | None = None
+    sdf_origin: tuple = (0.0, 0.0, 0.0)
+    sdf_h: float = 1.0
 
 
 @dataclass
@@ -220,14 +226,73 @@ def finger_state(scene: Scene, t: float):
     k = len(sc["c0"])
     pose = np.zeros((k, 7))
     lin = np.zeros((k, 3))
+    ang = np.zeros((k, 3)) if "ang" not in sc else np.asarray(sc["ang"], np.float64)
     for i in range(k):
         A, f = sc["amp"][i], sc["freq"][i]
         axis = np.asarray(sc["axis"][i], np.float64) if "axis" in sc else np.array([sc["dir"][i], 0.0, 0.0])
         pose[i, :3] = sc["c0"][i] + axis * A * (1.0 - math.cos(2 * math.pi * f * t)) / 2.0
-        pose[i, 3:] = sc["quat"][i]
+        pose[i, 3:] = _quat_mul(_quat_of_rotvec(ang[i] * t), np.asarray(sc["quat"][i], np.float64))
         lin[i] = axis * A * math.pi * f * math.sin(2 * math.pi * f * t)
-    return (pose.astype(np.float32), lin.astype(np.float32), np.zeros((k, 3), np.float32),
+    return (pose.astype(np.float32), lin.astype(np.float32), ang.astype(np.float32),
             pose[:, :3].astype(np.float32))
+
+
+def _quat_of_rotvec(r) -> np.ndarray:
+    """Unit quaternion (w, x, y, z) of the rotation by |r| about r."""
+    a = float(np.linalg.norm(r))
+    if a == 0.0:
+        return np.array([1.0, 0.0, 0.0, 0.0])
+    return np.concatenate([[math.cos(a / 2)], math.sin(a / 2) * np.asarray(r) / a])
+
+
+def _quat_mul(p, q) -> np.ndarray:
+    """Hamilton product p q (apply q, then p)."""
+    w1, v1 = p[0], np.asarray(p[1:])
+    w2, v2 = q[0], np.asarray(q[1:])
+    return np.concatenate([[w1 * w2 - v1 @ v2], w1 * v2 + w2 * v1 + np.cross(v1, v2)])
+
+
+# ---------------------------------------------------------------------------- SDF volumes
+
+def torus_volume(R: float, r: float, h: float, pad: int = 2):
+    """Signed distances of a torus about local z (ring radius R, tube radius r) sampled on a lattice
+    of spacing h covering it with ``pad`` samples to spare: (samples (nx, ny, nz) FP32, origin).
+    A stand-in for a mesh's SDF volume (Sec. 3): a shape no primitive describes."""
+    ext = np.array([R + r, R + r, r]) + pad * h
+    res = tuple(int(math.ceil(2 * e / h)) + 1 for e in ext)
+    origin = tuple(-(res[a] - 1) * h / 2 for a in range(3))
+    ii = np.indices(res).astype(np.float64)
+    x, y, z = (origin[a] + h * ii[a] for a in range(3))
+    d = np.sqrt((np.sqrt(x * x + y * y) - R) ** 2 + z * z) - r
+    return d.astype(np.float32), origin
+
+
+def ring_press_scene(seed: int = 4000, N: int = 50_000, n: int = 64) -> Scene:
+    """A plasticine ellipsoid (as the pinch scene's) pressed by a spinning ring tool held as an SDF
+    volume: a torus with R ~ U[0.06, 0.09], r ~ U[0.02, 0.03], sampled at half the grid spacing, its axis
+    tilted by up to 0.4 rad from vertical, starting 0.01 above the body and pressing down along -y as
+    c0 - y A (1 - cos 2 pi f t) / 2 (A ~ U[0.05, 0.1], f ~ U[1, 3] Hz) while it spins about world y at
+    w ~ U[-4, 4] rad/s; friction 0.5."""
+    dx = 1.0 / n
+    u = uniform(seed, 12, offset=0)
+    semi = 0.16 + 0.06 * u[0:3]
+    center = (0.5, 3 * dx + semi[1], 0.5)
+    x = ellipsoid_particles(N, center, semi, seed=seed + 1)
+    vol = 4.0 / 3.0 * math.pi * semi[0] * semi[1] * semi[2]
+    mat = Material(PLASTICINE, rho=1e3, E=5e3, nu=0.3, yield_stress=50.0, p_vol=vol / N)
+    R = 0.06 + 0.03 * u[3]
+    r = 0.02 + 0.01 * u[4]
+    samples, origin = torus_volume(R, r, 0.5 * dx)
+    tilt = 0.4 * (u[5:7] - 0.5) * 2
+    q0 = _quat_mul(_quat_of_rotvec([tilt[0], 0.0, tilt[1]]), _quat_of_rotvec([-math.pi / 2, 0.0, 0.0]))
+    shapes = [Shape(SDF_VOLUME, (0.0, 0.0, 0.0), 0.5, sdf=samples, sdf_origin=origin, sdf_h=0.5 * dx)]
+    c0 = [(0.5 + 0.02 * (u[7] - 0.5), center[1] + semi[1] + 0.01 + r, 0.5 + 0.02 * (u[8] - 0.5))]
+    script = {"c0": np.array(c0), "axis": np.array([[0.0, -1.0, 0.0]]), "amp": np.array([0.05 + 0.05 * u[9]]),
+              "freq": np.array([1.0 + 2.0 * u[10]]), "quat": np.array([q0]),
+              "ang": np.array([[0.0, 8.0 * (u[11] - 0.5), 0.0]])}
+    return Scene(n=n, dt=2e-4, material=mat, x=x, v=np.zeros((3, N), np.float32),
+                 C=np.zeros((9, N), np.float32), F=_identity_F(N), shapes=shapes, script=script,
+                 substeps_per_env_step=25)
 
 
 # ---------------------------------------------------------------------------- batched workloads

@@ -117,6 +117,30 @@ class _Handle:
         """(chunk, fused CTAs per SM, grid-update CTAs per SM)."""
         return mpm.mpm_get_launch(self.handle)
 
+    def set_contact(self, mode: str = "grid", stiffness: float = 0.0, damping: float = 0.0):
+        """Contact form: "grid" (colliders act on grid nodes) or "particle" (penalty accelerations at
+        the particles: stiffness in 1/s^2, damping in 1/s); drops cached graphs."""
+        m = {"grid": mpm.MPM_CONTACT_GRID, "particle": mpm.MPM_CONTACT_PARTICLE}[mode]
+        mpm.mpm_set_contact(self.handle, m, stiffness, damping)
+
+    def _shape_structs(self, shapes):
+        """ABI shape structs; SDF volumes are copied to device buffers that live with the handle."""
+        arr = []
+        bufs = []
+        for sh in shapes:
+            st = mpm.mpm_shape(sh.type, (ctypes.c_float * 3)(*sh.half), sh.friction)
+            if getattr(sh, "sdf", None) is not None:
+                vol = np.asarray(sh.sdf, np.float32)
+                buf = torch.from_numpy(np.ascontiguousarray(vol.transpose(2, 1, 0))).to(self.device)
+                bufs.append(buf)
+                st.sdf = buf.data_ptr()
+                st.res = (ctypes.c_int * 3)(*vol.shape)
+                st.sdf_origin = (ctypes.c_float * 3)(*sh.sdf_origin)
+                st.sdf_h = sh.sdf_h
+            arr.append(st)
+        self._sdf_bufs = bufs
+        return arr
+
 
 class Sim(_Handle):
     """One scene: an n^3 grid of one material."""
@@ -151,7 +175,7 @@ class Sim(_Handle):
         return g
 
     def set_shapes(self, shapes):
-        arr = [mpm.mpm_shape(s.type, (ctypes.c_float * 3)(*s.half), s.friction) for s in shapes]
+        arr = self._shape_structs(shapes)
         mpm.mpm_set_shapes(self.handle, arr)
         self.k = len(arr)
 
@@ -213,7 +237,7 @@ class BatchSim(_Handle):
     def set_shapes(self, shapes_per_env):
         """shapes_per_env[e]: the collider shapes of env e."""
         counts = [len(s) for s in shapes_per_env]
-        arr = [mpm.mpm_shape(s.type, (ctypes.c_float * 3)(*s.half), s.friction) for env in shapes_per_env for s in env]
+        arr = self._shape_structs([s for env in shapes_per_env for s in env])
         mpm.mpm_set_shapes_batch(self.handle, counts, arr)
         self.shape_counts = counts
         self.k = len(arr)

@@ -54,11 +54,25 @@ def oracle_state(sc: scenes.Scene, x=None, v=None, C=None, F=None) -> oracle.Sta
 def oracle_colliders(sc: scenes.Scene, pose, lin, ang, com):
     cols = []
     for i, sh in enumerate(sc.shapes):
+        vol = {}
+        if getattr(sh, "sdf", None) is not None:  # the same FP32 samples, widened
+            vol = dict(sdf=np.asarray(sh.sdf, np.float32).astype(np.float64),
+                       sdf_origin=tuple(float(np.float32(a)) for a in sh.sdf_origin),
+                       sdf_h=float(np.float32(sh.sdf_h)))
         cols.append(oracle.Collider(sh.type, tuple(float(h) for h in sh.half), float(sh.friction),
                                     tuple(float(a) for a in pose[i, :3]), tuple(float(a) for a in pose[i, 3:]),
                                     tuple(float(a) for a in lin[i]), tuple(float(a) for a in ang[i]),
-                                    tuple(float(a) for a in com[i])))
+                                    tuple(float(a) for a in com[i]), **vol))
     return cols
+
+
+def stencil_neighbours(x, n, bad):
+    """Particles whose 27-node stencil shares a node with the stencil of a particle in ``bad``."""
+    base = np.floor(np.asarray(x, np.float64) * n - 0.5).astype(np.int64)  # (3, N)
+    out = np.zeros(base.shape[1], bool)
+    for q in np.flatnonzero(bad):
+        out |= np.all(np.abs(base - base[:, q:q + 1]) <= 2, axis=0)
+    return out
 
 
 def make_sim(sc: scenes.Scene, max_particles=None):

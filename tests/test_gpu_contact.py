@@ -1,0 +1,201 @@
+"""GPU parity of the particle form of the contact (Sec. 3's default coupling: penalty forces at the
+particles entering the particle-to-grid transfer, reactions summed per body; Algorithm 1 "compute
+penalty forces") and of SDF-volume colliders (Sec. 3: meshes as signed-distance volumes), against the
+FP64 oracle on the same FP32 inputs.
+
+Particles whose penalty branch the oracle marks ambiguous (inside test or normal within 1e-6 of
+flipping), and the particles sharing a grid node with them, are excluded; there must be very few."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (TOL_C, TOL_F, TOL_V, TOL_X, make_sim, oracle_colliders, oracle_params, oracle_state, rel,
+                         rel_C, stencil_neighbours)
+from paper_2302_04659_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+DT = 2e-4
+KAPPA, BETA = 0.2 / DT ** 2, 0.5 / DT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2302_04659_gb300 import build
+    build.build()
+    yield
+
+
+def _check_state(out, ref, keep, n, tol_scale=1.0):
+    ex = rel(out["x"][:, keep], ref.x[:, keep])
+    ev = rel(out["v"][:, keep], ref.v[:, keep])
+    ec = rel_C(out["C"][:, keep], ref.C[:, keep], ref.v[:, keep], 1.0 / n)
+    ef = rel(out["F"][:, keep], ref.F[:, keep])
+    assert ex <= TOL_X * tol_scale, f"e_x = {ex:.3e}"
+    assert ev <= TOL_V * tol_scale, f"e_v = {ev:.3e}"
+    assert ec <= TOL_C * tol_scale, f"e_C = {ec:.3e}"
+    assert ef <= TOL_F * tol_scale, f"e_F = {ef:.3e}"
+    return ex, ev, ec, ef
+
+
+def _check_wrench(wr, wref):
+    scale = max(np.abs(wref).max(), 1e-12)
+    assert np.abs(wref).max() > 0, "the bodies should touch the material"
+    assert rel(wr[:, :3], wref[:, :3]) < 1e-4 or np.abs(wr[:, :3] - wref[:, :3]).max() < 1e-4 * scale
+    assert rel(wr[:, 3:], wref[:, 3:]) < 1e-4 or np.abs(wr[:, 3:] - wref[:, 3:]).max() < 1e-4 * scale
+
+
+def _run(sc, cols, nsub, mode, steps=1):
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.set_shapes(sc.shapes)
+    if mode == "particle":
+        sim.set_contact("particle", KAPPA, BETA)
+    for c in cols[:steps]:
+        sim.set_colliders(*c)
+        sim.substep(nsub)
+    out = sim.read_state(on_device=False)
+    wr = sim.read_wrench()
+    flags = sim.status()
+    sim.close()
+    return out, wr, flags
+
+
+def test_particle_contact_one_substep_pinch():
+    """Both fingers pressed into the ellipsoid, one substep with penalty contact."""
+    sc = scenes.pinch_scene(seed=1003, N=60_000)
+    cols = scenes.finger_state(sc, 0.15)
+    out, (wr, nsub), flags = _run(sc, [cols], 1, "particle")
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    _, wref, amb = oracle.substep_penalty(P, oracle.Penalty(KAPPA, BETA), ref, oracle_colliders(sc, *cols), 0.0)
+    keep = ~stencil_neighbours(sc.x, sc.n, amb)
+    assert (~keep).sum() <= 1e-3 * sc.N
+    _check_state(out, ref, keep, sc.n)
+    assert nsub == 1
+    _check_wrench(wr, wref)
+
+
+def test_particle_contact_across_env_steps():
+    """Three env steps of 4 substeps, the fingers' poses set before each: every step's first transfer
+    takes its penalties at the new poses and books them to the new force-torque buffers."""
+    sc = scenes.pinch_scene(seed=1006, N=20_000)
+    steps = [scenes.finger_state(sc, 0.12 + 4 * i * sc.dt) for i in range(3)]
+    out, (wr, nsub), flags = _run(sc, steps, 4, "particle", steps=3)
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    pen = oracle.Penalty(KAPPA, BETA)
+    amb_any = np.zeros(sc.N, bool)
+    for c in steps:
+        _, wref, amb = oracle.rollout_penalty(P, pen, ref, 4, oracle_colliders(sc, *c), 0.0)
+        amb_any |= amb
+    keep = ~stencil_neighbours(sc.x, sc.n, amb_any)
+    assert (~keep).sum() <= 2e-3 * sc.N
+    _check_state(out, ref, keep, sc.n, tol_scale=4.0)
+    assert nsub == 4
+    _check_wrench(wr, wref)
+
+
+def _ring_at_press(seed=4000, N=40_000):
+    sc = scenes.ring_press_scene(seed=seed, N=N)
+    t = 1.0 / (4.0 * sc.script["freq"][0])  # half the stroke
+    return sc, scenes.finger_state(sc, t)
+
+
+@pytest.mark.parametrize("mode", ["grid", "particle"])
+def test_sdf_volume_collider_one_substep(mode):
+    """A spinning ring tool held as an SDF volume pressed into plasticine: one substep in either
+    contact form."""
+    sc, cols = _ring_at_press()
+    out, (wr, nsub), flags = _run(sc, [cols], 1, mode)
+    P = oracle_params(sc)
+    ref = oracle_state(sc)
+    ocols = oracle_colliders(sc, *cols)
+    if mode == "grid":
+        _, wref, amb_nodes = oracle.substep(P, ref, ocols, 0.0, want_ambiguous=True)
+        base = np.floor(sc.x.astype(np.float64) * sc.n - 0.5).astype(int)
+        keep = np.ones(sc.N, bool)
+        for node in np.argwhere(amb_nodes):
+            keep &= ~np.all((node[:, None] >= base) & (node[:, None] <= base + 2), axis=0)
+    else:
+        _, wref, amb = oracle.substep_penalty(P, oracle.Penalty(KAPPA, BETA), ref, ocols, 0.0)
+        keep = ~stencil_neighbours(sc.x, sc.n, amb)
+    assert (~keep).sum() <= 2e-3 * sc.N
+    _check_state(out, ref, keep, sc.n)
+    _check_wrench(wr, wref)
+
+
+def test_particle_contact_batched_with_pose_table():
+    """18 envs (box tools plus capsule fingers, plasticine and fluid; 36 bodies, beyond the shared
+    poses, so the penalty reads the pose table) in one handle: one env step of 3 substeps, each env
+    against its own oracle."""
+    from paper_2302_04659_gb300.sim import BatchSim
+    import torch
+
+    envs = [scenes.tool_scene(5000 + e, scenes.PLASTICINE if e % 2 == 0 else scenes.FLUID, 3000, n=32,
+                              extra_capsule=True) for e in range(18)]
+    t = 0.12
+    counts, (x, v, C, F) = scenes.concat_states(envs)
+    sim = BatchSim([(sc.n, sc.material, sc.N, len(sc.shapes)) for sc in envs], envs[0].dt,
+                   gravity=envs[0].gravity, bound=envs[0].bound)
+    sim.set_particles(counts, *(torch.from_numpy(a).cuda() for a in (x, v, C, F)))
+    sim.set_shapes([sc.shapes for sc in envs])
+    sim.set_contact("particle", KAPPA, BETA)
+    states = [scenes.finger_state(sc, t) for sc in envs]
+    cat = [np.concatenate([s[i] for s in states]) for i in range(4)]
+    sim.set_colliders(*cat)
+    sim.substep(3)
+    out = sim.read_state(on_device=False)
+    wr, nsub = sim.read_wrench()
+    sim.close()
+    assert nsub == 3
+    off = np.concatenate([[0], np.cumsum(counts)])
+    pen = oracle.Penalty(KAPPA, BETA)
+    touched = 0
+    for e, sc in enumerate(envs):
+        ref = oracle_state(sc)
+        _, wref, amb = oracle.rollout_penalty(oracle_params(sc), pen, ref, 3, oracle_colliders(sc, *states[e]), 0.0)
+        keep = ~stencil_neighbours(sc.x, sc.n, amb)
+        assert (~keep).sum() <= 5e-3 * sc.N
+        sl = slice(off[e], off[e + 1])
+        ex = rel(out["x"][:, sl][:, keep], ref.x[:, keep])
+        ev = rel(out["v"][:, sl][:, keep], ref.v[:, keep])
+        assert ex <= 3 * TOL_X, (e, ex)
+        assert ev <= 3 * TOL_V, (e, ev)
+        w = wr[2 * e:2 * e + 2]
+        if np.abs(wref).max() > 0:
+            touched += 1
+            assert np.abs(w - wref).max() <= 1e-4 * np.abs(wref).max() + 1e-12, (e, w, wref)
+    assert touched >= 4
+
+
+def test_contact_mode_switch_and_validation():
+    from paper_2302_04659_gb300 import _native as mpm
+    from paper_2302_04659_gb300 import surrogate as sur
+
+    sc = scenes.pinch_scene(seed=1007, N=10_000)
+    cols = scenes.finger_state(sc, 0.15)
+    sim = make_sim(sc)
+    with pytest.raises(mpm.MpmError):
+        sim.set_contact("particle", 2.0 / DT ** 2, BETA)  # stiffness dt^2 > 1
+    with pytest.raises(mpm.MpmError):
+        sim.set_contact("particle", KAPPA, 2.0 / DT)  # damping dt > 1
+    sim.set_contact("particle", KAPPA, BETA)
+    with pytest.raises(mpm.MpmError):
+        sur.Attached(sim, sur.Network(seed=1), sc.material.rho)  # windows use the grid form
+    sim.close()
+    # particle form, then back to the grid form: the grid form's results are unchanged
+    a, _, _ = _run(sc, [cols], 3, "grid")
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.set_shapes(sc.shapes)
+    sim.set_contact("particle", KAPPA, BETA)
+    sim.set_colliders(*cols)
+    sim.substep(1)
+    sim.set_contact("grid")
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.set_colliders(*cols)
+    sim.substep(3)
+    b = sim.read_state(on_device=False)
+    sim.close()
+    assert np.array_equal(a["x"], b["x"])
