@@ -22,6 +22,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "splat_oracle.c")]
+_HDRS = [os.path.join(_HERE, "mpm_oracle.h"), os.path.join(_HERE, "splat_oracle.h")]
 _LIB_PATH = os.path.join(_HERE, "libmpm_oracle.so")
 _lib = None
 
@@ -35,13 +37,13 @@ SDF_VOLUME = 2
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, no FMA contraction, no fast-math)."""
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mpm_oracle.h"))
+        os.path.getmtime(f) for f in _SRCS + _HDRS
     ):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.run(
         ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-         "-Wall", "-o", tmp, _SRC, "-lm"],
+         "-Wall", "-o", tmp, *_SRCS, "-lm"],
         check=True,
     )
     os.replace(tmp, _LIB_PATH)
@@ -78,6 +80,18 @@ class _Collider(ctypes.Structure):
         ("sdf_origin", ctypes.c_double * 3),
         ("sdf_h", ctypes.c_double),
     ]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("eye", ctypes.c_double * 3),
+                ("rot", ctypes.c_double * 9), ("near_z", ctypes.c_double)]
+
+
+class _Render(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_double), ("smooth", ctypes.c_double), ("sigma_depth", ctypes.c_double),
+                ("window", ctypes.c_int), ("light", ctypes.c_double * 3), ("albedo", ctypes.c_double * 3),
+                ("ambient", ctypes.c_double), ("background", ctypes.c_double * 3)]
 
 
 class _Penalty(ctypes.Structure):
@@ -124,6 +138,10 @@ def lib():
                                           _dp, _dp, _dp, ctypes.c_int, ctypes.POINTER(_Collider), ctypes.c_double,
                                           _dp, _dp, _dp, _u8p]
         L.orc_substep_penalty.restype = ctypes.c_int
+        L.orc_splat_depth.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Render), ctypes.c_int, _dp, _dp, _u8p]
+        L.orc_splat_depth.restype = ctypes.c_int
+        L.orc_bilateral.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Render), _dp, _dp]
+        L.orc_shade.argtypes = [ctypes.POINTER(_Camera), ctypes.POINTER(_Render), _dp, _dp, _dp, _u8p]
         _lib = L
     return _lib
 
@@ -462,3 +480,75 @@ def rollout_penalty(params: Params, pen: Penalty, s: State, nsub: int, colliders
         total += ncl
         amb_any |= amb
     return total, wrench, amb_any
+
+
+# ------------------------------------------------------------------ particle renderer (App. D.2)
+
+@dataclass
+class Camera:
+    """Pinhole camera (see ``orc_camera``): rot is world -> camera (x right, y down, z forward)."""
+
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    eye: tuple
+    rot: np.ndarray
+    near_z: float = 1e-3
+
+    def c(self) -> _Camera:
+        return _Camera(self.width, self.height, self.fx, self.fy, self.cx, self.cy, (ctypes.c_double * 3)(*self.eye),
+                       (ctypes.c_double * 9)(*np.asarray(self.rot, np.float64).reshape(9)), self.near_z)
+
+
+@dataclass
+class RenderParams:
+    """Splatting, filter and shading constants (see ``orc_render``)."""
+
+    radius: float
+    smooth: float
+    sigma_depth: float
+    window: int
+    light: tuple = (0.3, -0.6, -0.75)
+    albedo: tuple = (0.85, 0.6, 0.4)
+    ambient: float = 0.25
+    background: tuple = (0.0, 0.0, 0.0)
+
+    def c(self) -> _Render:
+        d3 = ctypes.c_double * 3
+        return _Render(self.radius, self.smooth, self.sigma_depth, self.window, d3(*self.light), d3(*self.albedo),
+                       self.ambient, d3(*self.background))
+
+
+def splat_depth(cam: Camera, rp: RenderParams, x):
+    """Step 1: (depth (H, W), ambiguous mask (H, W), particles drawn)."""
+    x = _f64(x)
+    n = x.shape[1]
+    depth = np.zeros(cam.width * cam.height)
+    amb = np.zeros(cam.width * cam.height, np.uint8)
+    C, Rr = cam.c(), rp.c()
+    drawn = lib().orc_splat_depth(ctypes.byref(C), ctypes.byref(Rr), n, _ptr(x), _ptr(depth), amb.ctypes.data_as(_u8p))
+    return depth.reshape(cam.height, cam.width), amb.reshape(cam.height, cam.width).astype(bool), drawn
+
+
+def bilateral(cam: Camera, rp: RenderParams, depth):
+    """Step 2: the smoothed depth (H, W)."""
+    d = _f64(depth).reshape(-1)
+    out = np.zeros_like(d)
+    C, Rr = cam.c(), rp.c()
+    lib().orc_bilateral(ctypes.byref(C), ctypes.byref(Rr), _ptr(d), _ptr(out))
+    return out.reshape(cam.height, cam.width)
+
+
+def shade(cam: Camera, rp: RenderParams, smoothed):
+    """Steps 3 and 4: (normals (H, W, 3), rgb (H, W, 3), ambiguous mask (H, W))."""
+    z = _f64(smoothed).reshape(-1)
+    nrm = np.zeros(3 * z.size)
+    rgb = np.zeros(3 * z.size)
+    amb = np.zeros(z.size, np.uint8)
+    C, Rr = cam.c(), rp.c()
+    lib().orc_shade(ctypes.byref(C), ctypes.byref(Rr), _ptr(z), _ptr(nrm), _ptr(rgb), amb.ctypes.data_as(_u8p))
+    H, W = cam.height, cam.width
+    return nrm.reshape(H, W, 3), rgb.reshape(H, W, 3), amb.reshape(H, W).astype(bool)
