@@ -324,6 +324,8 @@ def run_native(args):
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(dev, "batch256", args.batched_steps, 3, per_scene=True, tune=True)
         line["serving"] = run_batched(dev, "serve1024", args.batched_steps, 3, per_scene=False, tune=True)
+    if world == 1 and not args.no_batched:
+        line["contact_forms"] = run_contact(dev, args.batched_steps * 4)
     if world == 1 and args.surrogate_scenes > 0:
         line["surrogate"] = run_surrogate(dev, args.surrogate_scenes)
     if not args.no_cpu_baseline:
@@ -497,6 +499,55 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
     return out
 
 
+def run_contact(dev, steps: int, warmup: int = 3):
+    """The two contact forms (Sec. 3) side by side on 200,000-particle plasticine scenes, 64^3 grid:
+    the pinch scene (two capsule fingers) and the ring press (a spinning torus tool held as an SDF
+    volume at half the grid spacing). Per scene and form: `steps` env steps of 25 substeps, graph
+    replay, L2 flushed before each step (outside the events), the mean time per env step. Particle
+    form: penalty stiffness 0.2/dt^2, damping 0.5/dt."""
+    import torch
+
+    from paper_2302_04659_gb300 import scenes
+    from paper_2302_04659_gb300.sim import Sim
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"stiffness_dt2": 0.2, "damping_dt": 0.5, "l2": "flushed before every timed step"}
+    for name, sc in (("pinch_capsules", scenes.pinch_scene(seed=1000, N=200_000)),
+                     ("ring_press_sdf_volume", scenes.ring_press_scene(seed=4000, N=200_000))):
+        res = {}
+        for mode in ("grid", "particle"):
+            sim = Sim(sc.n, sc.dt, sc.material, sc.N, gravity=sc.gravity, bound=sc.bound,
+                      max_colliders=len(sc.shapes), device=dev)
+            sim.set_shapes(sc.shapes)
+            if mode == "particle":
+                sim.set_contact("particle", 0.2 / sc.dt ** 2, 0.5 / sc.dt)
+            sim.set_particles(*(torch.from_numpy(a).to(dev) for a in (sc.x, sc.v, sc.C, sc.F)))
+
+            def env_step(i):
+                sim.set_colliders(*scenes.finger_state(sc, i * SUBSTEPS * sc.dt), stream=stream)
+                sim.substep(SUBSTEPS, stream=stream)
+
+            for i in range(warmup):
+                env_step(i)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize(dev)
+            for i in range(steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                env_step(warmup + i)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            wr, _ = sim.read_wrench()
+            res[mode] = {"ms_per_env_step": ms, "particle_substeps_per_s": sc.N * SUBSTEPS / (ms / 1e3),
+                         "status_flags": sim.status(), "last_impulse_norm": float(np.linalg.norm(wr[:, :3]))}
+            sim.close()
+        res["particle_over_grid_time"] = res["particle"]["ms_per_env_step"] / res["grid"]["ms_per_env_step"]
+        out[name] = res
+    return out
+
+
 def run_surrogate(dev, n_scenes: int):
     """The learned grid surrogate (the committed trained weights) against the plain method on held-out
     pinch scenes (seeds 20000 + i, 200,000 particles, 64^3 grid, two capsule fingers; none of them among the
@@ -638,7 +689,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
     ap.add_argument("--surrogate-scenes", type=int, default=256,
                     help="held-out scenes of the surrogate evaluation (0 skips it)")
-    ap.add_argument("--only", choices=["batched", "serving", "surrogate"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact"], default=None,
                     help="run one batched workload alone and print its section (profiling runs)")
     ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
     ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
@@ -655,6 +706,8 @@ def main():
         torch.cuda.set_device(dev)
         if args.only == "surrogate":
             out = run_surrogate(dev, args.surrogate_scenes)
+        elif args.only == "contact":
+            out = run_contact(dev, args.batched_steps * 4)
         else:
             out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps,
                               3, per_scene=False, tune=not args.no_tune, nenv=args.envs)

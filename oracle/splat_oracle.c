@@ -39,10 +39,34 @@ int orc_splat_depth(const orc_camera* cam, const orc_render* R, int n, const dou
             for (int i = i0; i <= i1; ++i) {
                 double du = ((double)i + 0.5 - up) / rx, dv = ((double)j + 0.5 - vp) / ry;
                 double s2 = du * du + dv * dv;
-                if (ambiguous && fabs(s2 - 1.0) < 1e-5) ambiguous[j * W + i] = 1;
                 if (!(s2 < 1.0)) continue;
                 double z = c[2] - R->radius * sqrt(1.0 - s2);
+                if (z < 0.0) z = 0.0; /* a sphere reaching behind the camera */
                 if (z < depth[j * W + i]) depth[j * W + i] = z;
+            }
+    }
+    if (!ambiguous) return drawn;
+    /* A pixel is ambiguous when a particle's coverage test there is within 1e-4 of flipping (FP32
+     * evaluates s^2 to about that) and the particle, if it covered the pixel, would be at least as
+     * near as what the pixel holds: only then can the flip change the depth. */
+    for (int q = 0; q < n; ++q) {
+        double d[3] = {x[q] - cam->eye[0], x[n + q] - cam->eye[1], x[2 * n + q] - cam->eye[2]};
+        double c[3];
+        for (int a = 0; a < 3; ++a) c[a] = cam->rot[a * 3] * d[0] + cam->rot[a * 3 + 1] * d[1] + cam->rot[a * 3 + 2] * d[2];
+        if (!(c[2] > cam->near_z)) continue;
+        double up = cam->fx * c[0] / c[2] + cam->cx, vp = cam->fy * c[1] / c[2] + cam->cy;
+        double rx = cam->fx * R->radius / c[2], ry = cam->fy * R->radius / c[2];
+        int i0 = (int)floor(up - rx - 0.5) - 1, i1 = (int)ceil(up + rx - 0.5) + 1;
+        int j0 = (int)floor(vp - ry - 0.5) - 1, j1 = (int)ceil(vp + ry - 0.5) + 1;
+        if (i0 < 0) i0 = 0;
+        if (j0 < 0) j0 = 0;
+        if (i1 > W - 1) i1 = W - 1;
+        if (j1 > H - 1) j1 = H - 1;
+        for (int j = j0; j <= j1; ++j)
+            for (int i = i0; i <= i1; ++i) {
+                double du = ((double)i + 0.5 - up) / rx, dv = ((double)j + 0.5 - vp) / ry;
+                double s2 = du * du + dv * dv;
+                if (fabs(s2 - 1.0) < 1e-4 && c[2] - R->radius * 0.01 <= depth[j * W + i]) ambiguous[j * W + i] = 1;
             }
     }
     return drawn;
@@ -55,8 +79,8 @@ void orc_bilateral(const orc_camera* cam, const orc_render* R, const double* dep
     for (int j = 0; j < H; ++j)
         for (int i = 0; i < W; ++i) {
             double d0 = depth[j * W + i];
-            if (!(d0 < inf())) {
-                smoothed[j * W + i] = inf();
+            if (K == 0 || !(d0 < inf())) { /* no filter, or nothing drawn here */
+                smoothed[j * W + i] = d0;
                 continue;
             }
             double ss = cam->fx * R->smooth / d0;
@@ -101,7 +125,7 @@ static int side_difference(const orc_camera* cam, const double* z, int i, int j,
     if (has_f && has_b) {
         double jf = fabs(z[fj * W + fi] - d0), jb = fabs(z[bj * W + bi] - d0);
         use_f = jf <= jb;
-        if (fabs(jf - jb) < 1e-6 * d0) *ambiguous = 1;
+        if (fabs(jf - jb) < 1e-5 * d0) *ambiguous = 1;
     }
     if (use_f) {
         unproject(cam, fi, fj, z[fj * W + fi], P1);

@@ -14,10 +14,11 @@
  * Sainz 2009, "Screen space fluid rendering with curvature flow"):
  *   1. splat: pinhole projection; a particle at camera-space depth z covers the
  *      pixels whose centres fall inside its projected disk (an ellipse when
- *      fx != fy), at depth z - r sqrt(1 - s^2), s the normalised distance from
- *      the disk centre (the point-sprite sphere); the buffer keeps the minimum;
+ *      fx != fy), at depth z - r sqrt(1 - s^2) clamped at 0, s the normalised
+ *      distance from the disk centre (the point-sprite sphere); the buffer keeps
+ *      the minimum;
  *   2. bilateral filter: for each covered pixel with depth d0, over a fixed
- *      (2K+1)^2 window, weights exp(-|offset|^2 / (2 sigma_s^2)) *
+ *      (2K+1)^2 window (K = 0: no filter), weights exp(-|offset|^2 / (2 sigma_s^2)) *
  *      exp(-(d - d0)^2 / (2 sigma_d^2)) on covered pixels, with the spatial
  *      width sigma_s = min(fx * smooth / d0, K / 2) pixels (world width
  *      `smooth` seen at depth d0: the distance scaling of App. D.2);
@@ -60,8 +61,8 @@ typedef struct {
 } orc_render;
 
 /* Step 1: depth[H*W] = min splat depth (+inf where empty). ambiguous[H*W] (may be NULL): pixels where
- * some particle's coverage test is within 1e-5 of flipping (|s^2 - 1| < 1e-5). Returns the number of
- * particles drawn (in front of near_z). */
+ * some particle's coverage test is within 1e-4 of flipping (|s^2 - 1| < 1e-4) and that particle would
+ * be at least as near as the pixel's depth. Returns the number of particles drawn (in front of near_z). */
 int orc_splat_depth(const orc_camera* cam, const orc_render* R, int n, const double* x, double* depth,
                     unsigned char* ambiguous);
 
@@ -69,7 +70,7 @@ int orc_splat_depth(const orc_camera* cam, const orc_render* R, int n, const dou
 void orc_bilateral(const orc_camera* cam, const orc_render* R, const double* depth, double* smoothed);
 
 /* Steps 3 and 4: normal[H*W*3] (camera frame; zero where empty) and rgb[H*W*3] from the smoothed
- * depth. ambiguous[H*W] (may be NULL) marks pixels whose difference side is within 1e-6 * depth of
+ * depth. ambiguous[H*W] (may be NULL) marks pixels whose difference side is within 1e-5 * depth of
  * switching. */
 void orc_shade(const orc_camera* cam, const orc_render* R, const double* smoothed, double* normal, double* rgb,
                unsigned char* ambiguous);

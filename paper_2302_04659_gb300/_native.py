@@ -47,6 +47,18 @@ class mpm_shape(ctypes.Structure):
                 ("sdf_h", ctypes.c_float)]
 
 
+class mpm_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("eye", ctypes.c_float * 3), ("rot", ctypes.c_float * 9),
+                ("near_z", ctypes.c_float)]
+
+
+class mpm_render_params(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_float), ("smooth", ctypes.c_float), ("sigma_depth", ctypes.c_float),
+                ("window", ctypes.c_int), ("light", ctypes.c_float * 3), ("albedo", ctypes.c_float * 3),
+                ("ambient", ctypes.c_float), ("background", ctypes.c_float * 3)]
+
+
 class mpm_env(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("max_particles", ctypes.c_int), ("max_colliders", ctypes.c_int),
                 ("material", mpm_material)]
@@ -97,6 +109,11 @@ def _load():
         "mpm_num_envs": (ctypes.c_int, [_vp]),
         "mpm_set_launch": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "mpm_set_contact": (st, [_vp, ctypes.c_int, ctypes.c_float, ctypes.c_float]),
+        "mpm_render_workspace_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+        "mpm_render": (st, [ctypes.POINTER(mpm_camera), ctypes.POINTER(mpm_render_params), ctypes.c_int, ctypes.c_int,
+                            _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+        "mpm_render_sim": (st, [_vp, ctypes.POINTER(mpm_camera), ctypes.POINTER(mpm_render_params), _vp, _vp, _vp, _vp,
+                                _vp, ctypes.c_size_t, _vp]),
         "mpm_get_launch": (st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)]),
         "mpm_set_particles": (st, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
@@ -228,6 +245,22 @@ MPM_SDF_VOLUME = 2
 
 def mpm_set_contact(sim: int, mode: int, stiffness: float = 0.0, damping: float = 0.0) -> None:
     _check("mpm_set_contact", _load().mpm_set_contact(sim, mode, stiffness, damping))
+
+
+def mpm_render_workspace_size(width: int, height: int) -> int:
+    return _load().mpm_render_workspace_size(width, height)
+
+
+def mpm_render(cam: mpm_camera, params: mpm_render_params, n: int, stride: int, d_x: int, d_depth: int, d_smooth: int,
+               d_normal: int, d_rgb: int, d_ws: int, nbytes: int, stream: int = 0) -> None:
+    _check("mpm_render", _load().mpm_render(ctypes.byref(cam), ctypes.byref(params), n, stride, d_x, d_depth, d_smooth,
+                                            d_normal, d_rgb, d_ws, nbytes, stream))
+
+
+def mpm_render_sim(sim: int, cam: mpm_camera, params: mpm_render_params, d_depth: int, d_smooth: int, d_normal: int,
+                   d_rgb: int, d_ws: int, nbytes: int, stream: int = 0) -> None:
+    _check("mpm_render_sim", _load().mpm_render_sim(sim, ctypes.byref(cam), ctypes.byref(params), d_depth, d_smooth,
+                                                    d_normal, d_rgb, d_ws, nbytes, stream))
 
 
 def mpm_get_launch(sim: int):

@@ -962,6 +962,16 @@ mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid
     return MPM_OK;
 }
 
+mpm_status mpm_render_sim(mpm_sim* s, const mpm_camera* cam, const mpm_render_params* params, float* d_depth,
+                          float* d_smooth, float* d_normal, float* d_rgb, void* d_workspace, size_t bytes,
+                          void* stream) {
+    if (!s || !render_args_valid(cam, params)) return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
+    const StateView v = s->view(s->ps.cur);  // positions in sorted order: the image does not depend on it
+    return render_enqueue(*cam, *params, s->N, s->N, v.x, d_depth, d_smooth, d_normal, d_rgb, d_workspace, bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
 mpm_status mpm_set_contact(mpm_sim* s, int mode, float stiffness, float damping) {
     if (!s || (mode != MPM_CONTACT_GRID && mode != MPM_CONTACT_PARTICLE)) return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));

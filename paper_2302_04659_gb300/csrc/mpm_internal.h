@@ -11,6 +11,7 @@
 
 #include "mpm.h"
 #include "mpm_device.cuh"
+#include "mpm_render.h"
 
 namespace mpm {
 
@@ -231,6 +232,13 @@ cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBo
 cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run,
                                          cudaStream_t s);
 cudaError_t launch_cast_to_bf16(int n, const float* src, void* dst, cudaStream_t s);
+
+// the particle renderer (render_kernels.cu)
+size_t render_workspace_bytes(int width, int height);
+bool render_args_valid(const mpm_camera* cam, const mpm_render_params* rp);
+mpm_status render_enqueue(const mpm_camera& cam, const mpm_render_params& rp, int n, int stride, const float* d_x,
+                          float* d_depth, float* d_smooth, float* d_normal, float* d_rgb, void* ws, size_t bytes,
+                          cudaStream_t st);
 
 // occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
 int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen = false);
