@@ -326,6 +326,7 @@ def run_native(args):
         line["serving"] = run_batched(dev, "serve1024", args.batched_steps, 3, per_scene=False, tune=True)
     if world == 1 and not args.no_batched:
         line["contact_forms"] = run_contact(dev, args.batched_steps * 4)
+        line["render"] = run_render(dev, args.batched_steps * 5)
     if world == 1 and args.surrogate_scenes > 0:
         line["surrogate"] = run_surrogate(dev, args.surrogate_scenes)
     if not args.no_cpu_baseline:
@@ -548,6 +549,49 @@ def run_contact(dev, steps: int, warmup: int = 3):
     return out
 
 
+def run_render(dev, frames: int, warmup: int = 3):
+    """The particle renderer (App. D.2 splatting) on the 200,000-particle pinch scene after one env step,
+    rendered in place from the simulation's buffers (no copy): splat, distance-scaled bilateral filter
+    (half window 4), normals and shading, at 640x480 and 1280x960. Mean time per frame over `frames`
+    frames bracketed by CUDA events, L2 flushed before each (outside the events)."""
+    import torch
+
+    from paper_2302_04659_gb300 import scenes
+    from paper_2302_04659_gb300.render import Camera, Renderer, Style
+    from paper_2302_04659_gb300.sim import Sim
+
+    sc = scenes.pinch_scene(seed=1000, N=200_000)
+    sim = Sim(sc.n, sc.dt, sc.material, sc.N, gravity=sc.gravity, bound=sc.bound, max_colliders=len(sc.shapes),
+              device=dev)
+    sim.set_shapes(sc.shapes)
+    sim.set_particles(*(torch.from_numpy(a).to(dev) for a in (sc.x, sc.v, sc.C, sc.F)))
+    sim.set_colliders(*scenes.finger_state(sc, 0.1))
+    sim.substep(SUBSTEPS)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"particles": sc.N, "style": "radius 0.004, smooth 0.008, sigma_depth 0.01, half window 4",
+           "l2": "flushed before every frame"}
+    for W, H in ((640, 480), (1280, 960)):
+        r = Renderer(Camera.looking(W, H, 40.0, (0.55, 0.55, -0.35), (0.5, 0.2, 0.5)),
+                     Style(radius=0.004, smooth=0.008, sigma_depth=0.01, window=4), device=dev)
+        for _ in range(warmup):
+            r.render_sim(sim, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        torch.cuda.synchronize(dev)
+        for i in range(frames):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            r.render_sim(sim, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / frames
+        drawn = float(torch.isfinite(r.depth).float().mean())
+        out[f"{W}x{H}"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms, "drawn_pixel_fraction": drawn,
+                           "launches_per_frame": 4}
+    sim.close()
+    return out
+
+
 def run_surrogate(dev, n_scenes: int):
     """The learned grid surrogate (the committed trained weights) against the plain method on held-out
     pinch scenes (seeds 20000 + i, 200,000 particles, 64^3 grid, two capsule fingers; none of them among the
@@ -689,7 +733,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
     ap.add_argument("--surrogate-scenes", type=int, default=256,
                     help="held-out scenes of the surrogate evaluation (0 skips it)")
-    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact", "render"], default=None,
                     help="run one batched workload alone and print its section (profiling runs)")
     ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
     ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
@@ -708,6 +752,8 @@ def main():
             out = run_surrogate(dev, args.surrogate_scenes)
         elif args.only == "contact":
             out = run_contact(dev, args.batched_steps * 4)
+        elif args.only == "render":
+            out = run_render(dev, args.batched_steps * 5)
         else:
             out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps,
                               3, per_scene=False, tune=not args.no_tune, nenv=args.envs)

@@ -3,7 +3,8 @@
 // Three launches per frame after the depth plane is cleared:
 //   k_splat      one thread per particle: project, walk the pixels of its projected ellipse, keep the
 //                nearest point-sprite depth per pixel with an integer atomicMin on the FP32 bits
-//                (depths are >= 0, where the bit order is the numeric order)
+//                (depths are >= 0, where the bit order is the numeric order), skipped when the value
+//                already there is nearer
 //   k_bilateral  one thread per pixel over a shared-memory tile with a K-pixel halo: the
 //                distance-scaled bilateral filter of the depth
 //   k_shade      one thread per pixel: normals from one-sided differences of the smoothed depth,
@@ -54,8 +55,11 @@ __global__ void __launch_bounds__(256) k_splat(mpm_camera cam, float r, int n, i
             const float du = ((float)i + 0.5f - up) / rx;
             const float s2 = du * du + dv * dv;
             if (!(s2 < 1.0f)) continue;
-            const float z = fmaxf(c[2] - r * sqrtf(1.0f - s2), 0.0f);
-            atomicMin(&depth[(size_t)j * cam.width + i], __float_as_uint(z));
+            const uint32_t zb = __float_as_uint(fmaxf(c[2] - r * sqrtf(1.0f - s2), 0.0f));
+            uint32_t* px = &depth[(size_t)j * cam.width + i];
+            // the plane only ever decreases, so any value read is an upper bound of the final one: a
+            // particle behind it needs no atomic (most are hidden behind the front surface)
+            if (zb < __ldcg(px)) atomicMin(px, zb);
         }
     }
 }
