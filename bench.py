@@ -592,6 +592,52 @@ def run_render(dev, frames: int, warmup: int = 3):
     return out
 
 
+def run_conv_scan(dev, reps: int = 20):
+    """The surrogate network's tcgen05 convolution alone, per layer shape (4 -> 32, 32 -> 32, 32 -> 3)
+    and box size, from one tile to a 64^3 box: mean time per launch over `reps` launches replayed from a
+    CUDA graph (no host launch cost), and the dense TFLOP/s that implies. Random BF16 inputs."""
+    import torch
+
+    from paper_2302_04659_gb300 import _native as mpm
+
+    torch.manual_seed(0)
+    out = []
+    for cin, cout in ((4, 32), (32, 32), (32, 3)):
+        w = (torch.randn(27, cout, cin, device=dev) * 0.05).to(torch.bfloat16).contiguous()
+        wp = torch.empty(mpm.mpm_conv3d_tc_packed_bytes(cin, cout), dtype=torch.uint8, device=dev)
+        st = torch.cuda.Stream(dev)
+        mpm.mpm_conv3d_pack_tc(cin, cout, w.data_ptr(), wp.data_ptr(), st.cuda_stream)
+        bias = torch.zeros(cout, device=dev)
+        for D, H, W in ((1, 16, 8), (1, 16, 8 * 152), (2, 16, 8 * 152), (4, 16, 8 * 152), (33, 38, 40),
+                        (64, 64, 64)):
+            x = torch.randn(D, H, W, cin, device=dev).to(torch.bfloat16).contiguous()
+            y = torch.empty(D, H, W, cout, device=dev, dtype=torch.bfloat16)
+
+            def conv():
+                mpm.mpm_conv3d_forward_tc(D, H, W, cin, cout, x.data_ptr(), wp.data_ptr(), bias.data_ptr(), 1, 0,
+                                          y.data_ptr(), 0, 0, st.cuda_stream)
+
+            with torch.cuda.stream(st):
+                for _ in range(3):
+                    conv()
+            torch.cuda.synchronize(dev)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                for _ in range(reps):
+                    conv()
+            g.replay()
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            g.replay()
+            b.record(st)
+            b.synchronize()
+            us = a.elapsed_time(b) / reps * 1e3
+            out.append({"cin": cin, "cout": cout, "box": [D, H, W], "tiles": mpm.mpm_conv3d_tc_tile_count(D, H, W),
+                        "us_per_launch": us, "tflops": 2.0 * D * H * W * 27 * cin * cout / us / 1e6})
+    return {"what": "k_conv_tc forward, graph-replayed launches, CUDA events", "rows": out}
+
+
 def run_surrogate(dev, n_scenes: int):
     """The learned grid surrogate (the committed trained weights) against the plain method on held-out
     pinch scenes (seeds 20000 + i, 200,000 particles, 64^3 grid, two capsule fingers; none of them among the
@@ -733,7 +779,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
     ap.add_argument("--surrogate-scenes", type=int, default=256,
                     help="held-out scenes of the surrogate evaluation (0 skips it)")
-    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact", "render"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact", "render", "conv"], default=None,
                     help="run one batched workload alone and print its section (profiling runs)")
     ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
     ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
@@ -754,6 +800,8 @@ def main():
             out = run_contact(dev, args.batched_steps * 4)
         elif args.only == "render":
             out = run_render(dev, args.batched_steps * 5)
+        elif args.only == "conv":
+            out = run_conv_scan(dev)
         else:
             out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps,
                               3, per_scene=False, tune=not args.no_tune, nenv=args.envs)

@@ -304,23 +304,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_co
             }
             if (!failed) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // 4 channels: the second k-group is the next voxel along x (dx + 1); wider inputs: the
+                // next plane of 8 channels. Step descriptors = base + compile-time offsets.
+                constexpr uint32_t lbo = CG == 1 ? 16u : (uint32_t)kPlaneBytes;
+                const uint64_t ad0 = smem_desc(planes_addr + b * kBuf, lbo, HX * 16);
+                const uint64_t bd0 = smem_desc(b_addr, (NPAD / 8) * 128, 128);
+#pragma unroll
                 for (int s = 0; s < S; ++s) {
                     int off, q;
-                    uint32_t lbo;
                     if constexpr (CG == 1) {
                         const int pair = s >> 1, half = s & 1;
                         off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
                         q = 0;
-                        lbo = 16;  // the second k-group is the next voxel along x (dx + 1)
                     } else {
-                        const int tap = s / (CG / 2);
+                        constexpr int h2 = CG / 2;
+                        const int tap = s / h2;
                         off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
-                        q = (s % (CG / 2)) * 2;
-                        lbo = kPlaneBytes;  // the second k-group is the next plane of 8 channels
+                        q = (s % h2) * 2;
                     }
-                    const uint64_t ad = smem_desc(planes_addr + b * kBuf + q * kPlaneBytes + off * 16, lbo, HX * 16);
-                    const uint64_t bd = smem_desc(b_addr + s * kBBlock, (NPAD / 8) * 128, 128);
-                    mma_bf16(tmem + b * kTmemCols, ad, bd, idesc, s > 0 ? 1u : 0u);
+                    mma_bf16(tmem + b * kTmemCols, ad0 + (uint64_t)((q * kPlaneBytes + off * 16) >> 4),
+                             bd0 + (uint64_t)((s * kBBlock) >> 4), idesc, s > 0 ? 1u : 0u);
                 }
                 mma_commit(smem_u32(bar + b));
             }
@@ -363,6 +366,180 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_co
         }
     }
     if (failed && tid == 0) atomicExch(&g_tc_error, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols));
+}
+
+// ---- the tensor-map path (16 or 32 input channels) with a ring of halo buffers
+//
+// Each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (those within reach of the material).
+// Thread 0 issues the weights' bulk copy and the halo copies of the first NB tiles at once, then, for
+// tile i, waits for its halo, issues its MMAs into accumulator i % 2 and commits; after the MMAs of tile
+// i - 1 are done, their halo buffer takes the copy of tile i - 1 + NB and the four warps store tile i - 1
+// from its accumulator while the tensor core runs tile i. Copies are NB - 1 tiles ahead of the MMAs, so
+// their latency is hidden once the ring is full.
+template <int NPAD, int CG>
+__host__ __device__ constexpr int ring_depth() {
+    return (4 * CG * kPlaneBytes + k_steps(CG) * NPAD * 32 + 1024 <= 227 * 1024) ? 4
+           : (3 * CG * kPlaneBytes + k_steps(CG) * NPAD * 32 + 1024 <= 227 * 1024) ? 3 : 2;
+}
+
+template <int NPAD, int CG>
+__host__ __device__ constexpr size_t ring_smem_bytes() {
+    return (size_t)ring_depth<NPAD, CG>() * CG * kPlaneBytes + (size_t)k_steps(CG) * NPAD * 32 +
+           (ring_depth<NPAD, CG>() + 3) * 8 + 16;
+}
+
+template <int NPAD, int CG>
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc_ring(Args a, const __grid_constant__ CUtensorMap tmap) {
+    static_assert(CG >= 2, "the ring path reads its halos through the tensor map");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int S = k_steps(CG), NB = ring_depth<NPAD, CG>();
+    constexpr int kBBlock = NPAD * 32, kBuf = CG * kPlaneBytes;
+    unsigned char* planes = smem;                                    // NB buffers of CG planes
+    unsigned char* bsm = smem + NB * kBuf;                           // S blocks of kBBlock
+    // [0, NB): a buffer's halo landed; NB, NB + 1: MMAs into an accumulator done; NB + 2: weights landed
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + NB + 3);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
+    const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm);
+    auto bar_addr = [&](int k) { return smem_u32(bar + k); };
+    auto needed = [&](int t) { return !a.tile_dist || a.tile_dist[t] <= a.radius; };
+    auto advance = [&](int t) {  // the first needed tile >= t on this CTA's stride (or tiles)
+        for (; t < tiles; t += gridDim.x)
+            if (needed(t)) return t;
+        return tiles;
+    };
+    auto origin = [&](int tile, int& z0, int& y0, int& x0) {
+        x0 = (tile % tx) * TX;
+        y0 = ((tile / tx) % ty) * TY;
+        z0 = tile / (tx * ty);
+    };
+    auto issue_halo = [&](int tile, int b) {  // thread 0
+        int z0, y0, x0;
+        origin(tile, z0, y0, x0);
+        const uint32_t full = bar_addr(b);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"((uint32_t)(CG * HV * 16))
+                     : "memory");
+        for (int q = 0; q < CG; ++q)
+            tma_plane(planes_addr + b * kBuf + q * kPlaneBytes, &tmap, q * 8, x0 - 1, y0 - 1, z0 - 1, full);
+    };
+
+    // the planes' zero padding (the dx over-read) in every buffer; zero outputs of skipped tiles
+    for (int i = tid; i < NB * kBuf / 16; i += kThreads)
+        if ((i % (kBuf / 16)) % kPlaneVox >= HV) *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        if (needed(t)) continue;
+        int z0, y0, x0;
+        origin(t, z0, y0, x0);
+        const int y = y0 + tid / TX, xx = x0 + tid % TX;
+        if (y < a.H && xx < a.W) {
+            const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
+            for (int n = 0; n < a.cout; ++n) {
+                if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = 0.0f;
+                else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(0.0f);
+            }
+        }
+    }
+    int pf = tiles;       // thread 0: the next tile to prefetch
+    int issued = 0;       // thread 0: halo copies issued (copy q went to buffer q % NB, phase (q / NB) & 1)
+    if (tid == 0) {
+        for (int k = 0; k < NB + 3; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_addr(k)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_addr(NB + 2)),
+                     "r"((uint32_t)(S * kBBlock))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(b_addr),
+            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(bar_addr(NB + 2))
+            : "memory");
+        pf = advance(blockIdx.x);
+        for (; issued < NB && pf < tiles; ++issued) {
+            issue_halo(pf, issued);
+            pf = advance(pf + gridDim.x);
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeroed padding, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = instr_desc(TM, NPAD);
+
+    bool failed = false;
+    int commits = 0;  // thread 0: MMA groups committed (group c to barrier NB + c % 2, phase (c / 2) & 1)
+    int cur = advance(blockIdx.x), prev = -1, i = 0;
+    while (cur < tiles) {
+        const int b = i % NB, acc = i & 1;
+        if (tid == 0) {
+            if (i == 0 && !mbar_wait(bar_addr(NB + 2), 0)) failed = true;     // the weights
+            if (!failed && !mbar_wait(bar_addr(b), (i / NB) & 1)) failed = true;  // this tile's halo
+            if (!failed) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // the descriptors of step st are the tile's base descriptors plus compile-time offsets
+                // (addresses stay below 256 KB, so the 14-bit address field never carries)
+                const uint64_t ad0 = smem_desc(planes_addr + b * kBuf, kPlaneBytes, HX * 16);
+                const uint64_t bd0 = smem_desc(b_addr, (NPAD / 8) * 128, 128);
+                const uint32_t d = tmem + acc * kTmemCols;
+#pragma unroll
+                for (int st = 0; st < S; ++st) {
+                    constexpr int half = CG / 2;
+                    const int tap = st / half, q = (st % half) * 2;
+                    const int off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
+                    mma_bf16(d, ad0 + (uint64_t)((q * kPlaneBytes + off * 16) >> 4),
+                             bd0 + (uint64_t)((st * kBBlock) >> 4), idesc, st > 0 ? 1u : 0u);
+                }
+                mma_commit(bar_addr(NB + acc));
+                ++commits;
+            }
+        }
+        __syncwarp();
+        if (prev >= 0 && !mbar_wait(bar_addr(NB + (1 - acc)), ((i - 1) >> 1) & 1)) failed = true;  // tile i - 1
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+        if (prev >= 0) {
+            if (tid == 0 && pf < tiles) {  // tile i - 1's buffer is free: the copy NB tiles ahead
+                issue_halo(pf, issued % NB);
+                ++issued;
+                pf = advance(pf + gridDim.x);
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int z0, y0, x0;
+            origin(prev, z0, y0, x0);
+            epilogue<NPAD>(a, tmem + (1 - acc) * kTmemCols, z0, y0, x0);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        prev = cur;
+        cur = advance(cur + gridDim.x);
+        ++i;
+    }
+    if (prev >= 0 && !failed) {  // the last tile
+        const int acc = (i - 1) & 1;
+        if (!mbar_wait(bar_addr(NB + acc), ((i - 1) >> 1) & 1)) failed = true;
+        failed = __syncthreads_or(failed) != 0;
+        if (!failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int z0, y0, x0;
+            origin(prev, z0, y0, x0);
+            epilogue<NPAD>(a, tmem + acc * kTmemCols, z0, y0, x0);
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(&g_tc_error, 1u);
+        // leave nothing in flight: the copies not yet consumed (from copy i on) and the last MMA group
+        for (int q = i; q < issued; ++q) mbar_wait(bar_addr(q % NB), (q / NB) & 1);
+        if (commits > 0) mbar_wait(bar_addr(NB + ((commits - 1) & 1)), ((commits - 1) >> 1) & 1);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -438,17 +615,19 @@ __global__ void k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mas
 
 template <int NPAD, int CG>
 cudaError_t launch(const Args& a, cudaStream_t s) {
-    const size_t smem = smem_bytes(NPAD, CG);
+    constexpr bool ring = CG >= 2;
+    using Kernel = void (*)(Args, const CUtensorMap);
+    const Kernel kernel = ring ? (Kernel)k_conv_tc_ring<NPAD, (CG >= 2 ? CG : 2)> : (Kernel)k_conv_tc<NPAD, CG>;
+    const size_t smem = ring ? ring_smem_bytes<NPAD, (CG >= 2 ? CG : 2)>() : smem_bytes(NPAD, CG);
     // resident CTAs, set up once per process (the kernels of one library run on GPUs of one kind)
     static int slots = 0;
     if (slots == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NPAD, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<NPAD, CG>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
         slots = std::max(per_sm, 1) * std::max(sms, 1);
     }
     const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
@@ -473,7 +652,7 @@ cudaError_t launch(const Args& a, cudaStream_t s) {
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
-    k_conv_tc<NPAD, CG><<<grid, kThreads, smem, s>>>(a, map);
+    kernel<<<grid, kThreads, smem, s>>>(a, map);
     return cudaGetLastError();
 }
 

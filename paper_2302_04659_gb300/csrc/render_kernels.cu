@@ -3,8 +3,7 @@
 // Three launches per frame after the depth plane is cleared:
 //   k_splat      one thread per particle: project, walk the pixels of its projected ellipse, keep the
 //                nearest point-sprite depth per pixel with an integer atomicMin on the FP32 bits
-//                (depths are >= 0, where the bit order is the numeric order), skipped when the value
-//                already there is nearer
+//                (depths are >= 0, where the bit order is the numeric order)
 //   k_bilateral  one thread per pixel over a shared-memory tile with a K-pixel halo: the
 //                distance-scaled bilateral filter of the depth
 //   k_shade      one thread per pixel: normals from one-sided differences of the smoothed depth,
@@ -29,8 +28,8 @@ __global__ void __launch_bounds__(256) k_depth_clear(uint32_t* __restrict__ d, i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d[i] = kInfBits;
 }
 
-// Step 1. A particle behind near_z draws nothing; the pixel loop covers the ellipse's bounding box with
-// one pixel to spare on each side, clamped to the image before any float -> int conversion.
+// Step 1. A particle behind near_z draws nothing; the pixel loop covers the ellipse's bounding box,
+// clamped to the image before any float -> int conversion.
 __global__ void __launch_bounds__(256) k_splat(mpm_camera cam, float r, int n, int stride,
                                                const float* __restrict__ x, uint32_t* __restrict__ depth) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,23 +42,22 @@ __global__ void __launch_bounds__(256) k_splat(mpm_camera cam, float r, int n, i
     const float up = cam.fx * c[0] / c[2] + cam.cx, vp = cam.fy * c[1] / c[2] + cam.cy;
     const float rx = cam.fx * r / c[2], ry = cam.fy * r / c[2];
     const float W = (float)cam.width, H = (float)cam.height;
-    const float fi0 = fminf(fmaxf(floorf(up - rx - 0.5f) - 1.0f, 0.0f), W);
-    const float fi1 = fminf(fmaxf(ceilf(up + rx - 0.5f) + 1.0f, -1.0f), W - 1.0f);
-    const float fj0 = fminf(fmaxf(floorf(vp - ry - 0.5f) - 1.0f, 0.0f), H);
-    const float fj1 = fminf(fmaxf(ceilf(vp + ry - 0.5f) + 1.0f, -1.0f), H - 1.0f);
+    // pixel centres i + 0.5 inside [up - rx, up + rx]: floor / ceil leave up to a pixel of slack
+    const float fi0 = fminf(fmaxf(floorf(up - rx - 0.5f), 0.0f), W);
+    const float fi1 = fminf(fmaxf(ceilf(up + rx - 0.5f), -1.0f), W - 1.0f);
+    const float fj0 = fminf(fmaxf(floorf(vp - ry - 0.5f), 0.0f), H);
+    const float fj1 = fminf(fmaxf(ceilf(vp + ry - 0.5f), -1.0f), H - 1.0f);
     if (!(fi0 <= fi1) || !(fj0 <= fj1)) return;  // off screen (or NaN)
     const int i0 = (int)fi0, i1 = (int)fi1, j0 = (int)fj0, j1 = (int)fj1;
+    const float irx = 1.0f / rx, iry = 1.0f / ry;
     for (int j = j0; j <= j1; ++j) {
-        const float dv = ((float)j + 0.5f - vp) / ry;
+        const float dv = ((float)j + 0.5f - vp) * iry;
         for (int i = i0; i <= i1; ++i) {
-            const float du = ((float)i + 0.5f - up) / rx;
+            const float du = ((float)i + 0.5f - up) * irx;
             const float s2 = du * du + dv * dv;
             if (!(s2 < 1.0f)) continue;
-            const uint32_t zb = __float_as_uint(fmaxf(c[2] - r * sqrtf(1.0f - s2), 0.0f));
-            uint32_t* px = &depth[(size_t)j * cam.width + i];
-            // the plane only ever decreases, so any value read is an upper bound of the final one: a
-            // particle behind it needs no atomic (most are hidden behind the front surface)
-            if (zb < __ldcg(px)) atomicMin(px, zb);
+            const float z = fmaxf(c[2] - r * sqrtf(1.0f - s2), 0.0f);
+            atomicMin(&depth[(size_t)j * cam.width + i], __float_as_uint(z));
         }
     }
 }
