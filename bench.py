@@ -625,12 +625,14 @@ def run_conv_scan(dev, reps: int = 20):
             with torch.cuda.graph(g, stream=st):
                 for _ in range(reps):
                     conv()
-            g.replay()
+            with torch.cuda.stream(st):
+                g.replay()
             torch.cuda.synchronize(dev)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(st)
-            g.replay()
-            b.record(st)
+            with torch.cuda.stream(st):  # the graph replays on the current stream: time it there
+                a.record()
+                g.replay()
+                b.record()
             b.synchronize()
             us = a.elapsed_time(b) / reps * 1e3
             out.append({"cin": cin, "cout": cout, "box": [D, H, W], "tiles": mpm.mpm_conv3d_tc_tile_count(D, H, W),

@@ -846,6 +846,7 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
         for (int a = 0; a < 3; ++a) c.half[a] = sh.half[a];
         c.friction = sh.friction;
         c.vol = SdfVolume{};
+        double reach = 0.0;  // a ball about the frame origin holding the body: inside points lie in it
         if (sh.type == MPM_SDF_VOLUME) {
             c.vol.data = sh.sdf;
             for (int a = 0; a < 3; ++a) {
@@ -853,7 +854,20 @@ mpm_status mpm_set_colliders(mpm_sim* s, int k, const float* pose, const float* 
                 c.vol.origin[a] = sh.sdf_origin[a];
             }
             c.vol.inv_h = 1.0f / sh.sdf_h;
+            double far2 = 0.0;  // the lattice corner farthest from the origin
+            for (int a = 0; a < 3; ++a) {
+                const double lo = sh.sdf_origin[a], hi = lo + (double)sh.sdf_h * (sh.res[a] - 1);
+                far2 += std::max(lo * lo, hi * hi);
+            }
+            reach = std::sqrt(far2);
+        } else if (sh.type == MPM_BOX) {
+            reach = std::sqrt((double)sh.half[0] * sh.half[0] + (double)sh.half[1] * sh.half[1] +
+                              (double)sh.half[2] * sh.half[2]);
+        } else {
+            reach = (double)sh.half[0] + sh.half[1];
         }
+        reach = reach * (1.0 + 1e-4) + 1e-6;  // FP32 rounding of the distance test stays on the safe side
+        c.reach2 = (float)(reach * reach);
         float qn = 0.0f;
         for (int a = 0; a < 3; ++a) {
             c.pos[a] = pose[i * 7 + a];

@@ -244,6 +244,7 @@ struct ColliderSet {  // as set by the host (one entry per body)
     float lin[3];
     float ang[3];
     float com[3];
+    float reach2;  // squared radius about the frame origin of a ball holding the whole body (padded)
     SdfVolume vol;
 };
 
@@ -256,6 +257,7 @@ struct ColliderNow {  // pose at the current substep
     float half[3];
     float friction;
     int type;
+    float reach2;
     SdfVolume vol;
 };
 
@@ -299,6 +301,7 @@ __device__ __forceinline__ void collider_at(const ColliderSet& c, float t, Colli
     }
     o.friction = c.friction;
     o.type = c.type;
+    o.reach2 = c.reach2;
     o.vol = c.vol;
 }
 

@@ -569,6 +569,8 @@ __global__ void __launch_bounds__(256) k_assign(int N, const uint2* __restrict__
 // velocity there. rel receives x - com, the lever arm of the reaction.
 __device__ __forceinline__ bool penalty_one(const ColliderNow& cn, const float x[3], const float v[3], float stiffness,
                                             float damping, float a[3], float rel[3]) {
+    const float o[3] = {x[0] - cn.p[0], x[1] - cn.p[1], x[2] - cn.p[2]};
+    if (o[0] * o[0] + o[1] * o[1] + o[2] * o[2] > cn.reach2) return false;  // beyond the body's ball
     float nrm[3];
     const float phi = collider_sdf(cn, x, nrm);
     if (!(phi < 0.0f)) return false;
@@ -1007,8 +1009,10 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
                 cn = p.poses[(size_t)step * p.k_total + c];
             else
                 collider_at(p.cols[c], (float)step * p.dt, cn);
-            float nrm[3];
-            const float phi = collider_sdf(cn, xi, nrm);
+            float nrm[3] = {0.0f, 0.0f, 0.0f};
+            const float o[3] = {xi[0] - cn.p[0], xi[1] - cn.p[1], xi[2] - cn.p[2]};
+            const bool near = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] <= cn.reach2;  // else surely outside
+            const float phi = near ? collider_sdf(cn, xi, nrm) : 1e30f;
             const float rel[3] = {xi[0] - cn.com[0], xi[1] - cn.com[1], xi[2] - cn.com[2]};
             const float vc[3] = {cn.lin[0] + cn.ang[1] * rel[2] - cn.ang[2] * rel[1],
                                  cn.lin[1] + cn.ang[2] * rel[0] - cn.ang[0] * rel[2],
