@@ -238,6 +238,10 @@ def run_native(args):
     elapsed_instrumented = timed_pass(args.warmup + args.steps)
     ktime = sim.read_timing(reset=True)
     sim.set_timing(False)
+    # ---------------- the same steps with plain launches (no graph replay), for comparison
+    sim.set_graphs(False)
+    elapsed_plain = timed_pass(args.warmup + 2 * args.steps)
+    sim.set_graphs(True)
     value, elapsed, total_units = job_throughput(N * SUBSTEPS * args.steps, elapsed, dev)
     flags = sim.status()
     g_ms, g_n = ktime["g2p2g"]
@@ -297,6 +301,9 @@ def run_native(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches,
+        "plain_launches": {"value": N * SUBSTEPS * args.steps / elapsed_plain, "unit": UNIT,
+                           "ms_per_step": elapsed_plain / args.steps * 1e3,
+                           "what": "the same env steps launched kernel by kernel instead of replayed from a graph"},
         "roofline": {
             "kernel": "k_g2p2g",
             "bound": "hbm",

@@ -20,10 +20,11 @@ import os
 
 import torch
 
+from . import _native as mpm
 from . import build as _build
 
-CHUNKS = (128, 96, 64)
-FUSED_CTAS = (7, 6, 5, 4)
+CHUNKS = (256, 192, 128, 96, 64)
+FUSED_CTAS = (7, 6, 5, 4, 3, 2)
 GRID_CTAS = (1, 2, 4)
 CACHE_PATH = os.path.join(os.path.dirname(_build.LIB_PATH), "autotune.json")
 
@@ -36,7 +37,8 @@ def signature(sim) -> str:
     ns = sorted(set(getattr(sim, "ns", [getattr(sim, "n", 0)])))
     kinds = sorted(set(getattr(sim, "kinds", [])))
     nenv = getattr(sim, "nenv", 1)
-    return f"{dev}|envs={nenv}|N~2^{bucket / 2:.1f}|n={','.join(map(str, ns))}|kinds={','.join(map(str, kinds))}"
+    return (f"{dev}|envs={nenv}|N~2^{bucket / 2:.1f}|n={','.join(map(str, ns))}|kinds={','.join(map(str, kinds))}"
+            f"|chunks<={CHUNKS[0]}")
 
 
 def _load_cache() -> dict:
@@ -75,6 +77,20 @@ def time_shape(sim, shape, substeps: int, reps: int, prepare=None, stream=None) 
     return best
 
 
+def max_fused_for(sim, chunk: int, cap: int | None = None) -> int:
+    """The most fused-pass CTAs per SM the handle accepts with this chunk size (the fused pass's CTA size,
+    and so its occupancy limit, follows the chunk)."""
+    for f in FUSED_CTAS:
+        if cap is not None and f > cap:
+            continue
+        try:
+            sim.set_launch(chunk, f, 0)
+            return f
+        except mpm.MpmError:
+            continue
+    return FUSED_CTAS[-1]
+
+
 def tune(sim, substeps: int = 10, reps: int = 3, prepare=None, restore=None, use_cache: bool = True,
          max_fused: int | None = None):
     """Choose and apply the fastest launch shape for ``sim``'s current scene. Returns
@@ -86,8 +102,8 @@ def tune(sim, substeps: int = 10, reps: int = 3, prepare=None, restore=None, use
         shape = tuple(cache[key]["shape"])
         sim.set_launch(*shape)
         return shape, cache[key]["ms_per_substep"], {}
-    _, fused_max, _ = sim.get_launch()  # the default is the most the fused kernel fits per SM
-    fused_opts = [c for c in FUSED_CTAS if c <= (max_fused or fused_max)]
+    start_shape = tuple(sim.get_launch())
+    limits = {c: max_fused_for(sim, c, max_fused) for c in CHUNKS}
     trials = {}
 
     def trial(shape):
@@ -95,12 +111,18 @@ def tune(sim, substeps: int = 10, reps: int = 3, prepare=None, restore=None, use
             trials[shape] = time_shape(sim, shape, substeps, reps, prepare)
         return trials[shape]
 
-    best = (CHUNKS[0], fused_opts[0], 2)
+    c0, f0, g0 = start_shape
+    best = (c0, min(f0, limits.get(c0, f0)), g0)
     for _ in range(2):  # coordinate descent, two rounds
         start = best
-        for axis, options in ((1, fused_opts), (0, CHUNKS), (2, GRID_CTAS)):
-            cands = [tuple(o if i == axis else best[i] for i in range(3)) for o in options]
-            best = min(cands, key=trial)
+        c, f, g = best
+        cands = [(c, fo, g) for fo in FUSED_CTAS if fo <= limits.get(c, fo)]
+        best = min(cands, key=trial)
+        c, f, g = best
+        # a chunk of another CTA size takes that size's own most CTAs per SM when f exceeds it
+        best = min([(co, min(f, limits[co]), g) for co in CHUNKS], key=trial)
+        c, f, g = best
+        best = min([(c, f, go) for go in GRID_CTAS], key=trial)
         if best == start:
             break
     sim.set_launch(*best)

@@ -638,7 +638,8 @@ mpm_status create_impl(const mpm_config* cfg, int nenv, const mpm_env* envs, voi
     s->kind_all = envs[0].material.kind;
     for (int e = 1; e < nenv; ++e)
         if (envs[e].material.kind != s->kind_all) s->kind_all = -1;
-    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, nenv == 1);
+    s->chunk = nenv == 1 ? kChunk : 128;  // dense single scenes: 256-particle chunks; batches: 128
+    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, nenv == 1, false, s->chunk);
     s->fused_cps = s->max_fused_cps;
     s->p2g_cps = transfer_ctas_per_sm(false, s->kind_all, nenv == 1);
     s->ps.scanned = s->ps.order_valid = s->ps.grid_valid = true;  // no particles yet
@@ -967,7 +968,15 @@ mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid
     if (!s) return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
     if (chunk && (chunk < 32 || chunk > kChunk || chunk % 32)) return MPM_ERR_INVALID_ARG;
-    if (fused_ctas_per_sm && (fused_ctas_per_sm < 1 || fused_ctas_per_sm > s->max_fused_cps)) return MPM_ERR_INVALID_ARG;
+    // the fused pass's CTA size follows the chunk, and its occupancy limit follows the CTA size
+    const int new_chunk = chunk ? chunk : s->chunk;
+    const bool pen = s->contact == MPM_CONTACT_PARTICLE;
+    const int max_fused = transfer_ctas_per_sm(true, s->kind_all, s->nenv == 1, pen, new_chunk);
+    if (fused_ctas_per_sm && (fused_ctas_per_sm < 1 || fused_ctas_per_sm > max_fused)) return MPM_ERR_INVALID_ARG;
+    if (fused_cta_threads(new_chunk) != fused_cta_threads(s->chunk) && !fused_ctas_per_sm)
+        s->fused_cps = max_fused;  // a new CTA size starts at its own occupancy
+    s->fused_cps = std::min(s->fused_cps, max_fused);
+    s->max_fused_cps = max_fused;
     if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
     if (chunk) s->chunk = chunk;
     if (fused_ctas_per_sm) s->fused_cps = fused_ctas_per_sm;
@@ -998,7 +1007,7 @@ mpm_status mpm_set_contact(mpm_sim* s, int mode, float stiffness, float damping)
     s->contact = mode;
     s->stiffness = mode == MPM_CONTACT_PARTICLE ? stiffness : 0.0f;
     s->damping = mode == MPM_CONTACT_PARTICLE ? damping : 0.0f;
-    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, s->nenv == 1, mode == MPM_CONTACT_PARTICLE);
+    s->max_fused_cps = transfer_ctas_per_sm(true, s->kind_all, s->nenv == 1, mode == MPM_CONTACT_PARTICLE, s->chunk);
     s->fused_cps = std::min(s->fused_cps, s->max_fused_cps);
     s->drop_graphs();
     return MPM_OK;

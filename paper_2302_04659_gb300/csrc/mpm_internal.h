@@ -16,7 +16,7 @@
 namespace mpm {
 
 // Most particles per chunk of a bin = threads per CTA of the particle passes.
-constexpr int kChunk = 128;
+constexpr int kChunk = 256;
 
 // With at most kSharedPoses colliders in a handle, each grid-update CTA evaluates the poses of the
 // substep into shared memory. With more, mpm_set_colliders tabulates them for the next kPoseSteps
@@ -241,6 +241,8 @@ mpm_status render_enqueue(const mpm_camera& cam, const mpm_render_params& rp, in
                           cudaStream_t st);
 
 // occupancy of the particle kernels (CTAs per SM at kChunk threads), for the variant launch_g2p2g picks
-int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen = false);
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen = false, int chunk = kChunk);
+// threads per CTA of the fused pass for a chunk size (128 or 256)
+int fused_cta_threads(int chunk);
 
 }  // namespace mpm

@@ -86,11 +86,11 @@ __device__ __forceinline__ void load_env(EnvDesc& dst, const EnvDesc* envs, int 
 // The particle-to-grid scatter of one chunk (at most kChunk particles of one bin) goes into a shared
 // tile of the 8^3 nodes its particles can reach, accumulated with 32-bit integer atomics: shared-memory
 // integer adds are single native instructions, FP32 ones are not. Values are fixed point:
-//   mass      sum of weights, scaled by 2^22 (a node sums at most kChunk weights <= 0.75^3 each, so the
-//             sum stays below 54 * 2^22 < 2^31);
+//   mass      sum of weights, scaled by 2^22 (a node sums at most kChunk = 256 weights <= 0.75^3 each, so
+//             the sum stays below 108 * 2^22 < 2^31);
 //   momentum  scaled by 2^k with k = 22 - e, where 2^e bounds (from above, within a factor 2) the largest
 //             per-particle magnitude B_p = max_a (m |v_a| + 1.5 dx sum_c |A_ac|) of the chunk, so every node
-//             sum stays below 54 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term,
+//             sum stays below 108 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term,
 //             comparable to an FP32 accumulation of the same terms. Every scaled term is below 2^22, so it
 //             is rounded to an integer by one FP32 add (round_fixed).
 // The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
@@ -738,12 +738,15 @@ __device__ __forceinline__ const EnvDesc& chunk_env(const TransferParams& p, con
 // KIND: the material of every env (0 plasticine, 1 fluid) or -1 for a per-env choice at run time.
 // ONE_ENV: one env whose descriptor comes from the kernel parameters (constant bank operands) rather
 // than from shared memory, which keeps the single-scene kernel's register budget.
-// 7 resident CTAs per SM (72 registers): measured faster than 8, 9 or 10 CTAs with the spills a tighter
-// register budget forces, on both the 200k and the 600k pinch scene.
+// CTA: threads per CTA = the most particles of a chunk it takes (128 or 256). Dense scenes (many
+// particles per bin) run 256-particle chunks at 4 resident CTAs per SM (64 registers): measured 6 % faster
+// per env step than 128-particle chunks at 7 CTAs (72 registers) on the 200k and the 600k pinch scene — a
+// chunk's gather-tile load and scatter-tile flush then serve twice the particles — and faster than 3 or 5
+// CTAs, or chunks of 384 or 512. Sparse batches keep 128-thread CTAs, whose threads chunks fill.
 // PEN: the particle form of the contact (penalty accelerations join the transfer; the grid update
 // applies no colliders then).
-template <int KIND, bool ONE_ENV, bool PEN>
-__global__ void __launch_bounds__(kChunk, PEN ? 6 : 7) k_g2p2g(TransferParams p) {
+template <int KIND, bool ONE_ENV, bool PEN, int CTA>
+__global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7)) k_g2p2g(TransferParams p) {
     // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots
     // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
     __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
@@ -1212,19 +1215,28 @@ cudaError_t launch_p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
 
 using TransferKernel = void (*)(TransferParams);
 
-static TransferKernel g2p2g_variant(int kind_all, bool one_env, bool pen) {
+template <int CTA>
+static TransferKernel g2p2g_variant_cta(int kind_all, bool one_env, bool pen) {
     if (pen) {  // the particle contact: one-env variants per material, one for every batch
-        if (one_env) return kind_all == 1 ? k_g2p2g<1, true, true> : k_g2p2g<0, true, true>;
-        return k_g2p2g<-1, false, true>;
+        if (one_env) return kind_all == 1 ? k_g2p2g<1, true, true, CTA> : k_g2p2g<0, true, true, CTA>;
+        return k_g2p2g<-1, false, true, CTA>;
     }
-    if (one_env) return kind_all == 1 ? k_g2p2g<1, true, false> : k_g2p2g<0, true, false>;
-    if (kind_all == 0) return k_g2p2g<0, false, false>;
-    if (kind_all == 1) return k_g2p2g<1, false, false>;
-    return k_g2p2g<-1, false, false>;
+    if (one_env) return kind_all == 1 ? k_g2p2g<1, true, false, CTA> : k_g2p2g<0, true, false, CTA>;
+    if (kind_all == 0) return k_g2p2g<0, false, false, CTA>;
+    if (kind_all == 1) return k_g2p2g<1, false, false, CTA>;
+    return k_g2p2g<-1, false, false, CTA>;
+}
+
+int fused_cta_threads(int chunk) { return chunk > 128 ? 256 : 128; }
+
+static TransferKernel g2p2g_variant(int kind_all, bool one_env, bool pen, int chunk) {
+    return fused_cta_threads(chunk) == 256 ? g2p2g_variant_cta<256>(kind_all, one_env, pen)
+                                           : g2p2g_variant_cta<128>(kind_all, one_env, pen);
 }
 
 cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s) {
-    return launch_dependent(g2p2g_variant(p.kind_all, p.one_env != 0, p.contact != 0), grid_ctas, kChunk, s, p);
+    return launch_dependent(g2p2g_variant(p.kind_all, p.one_env != 0, p.contact != 0, p.chunk), grid_ctas,
+                            fused_cta_threads(p.chunk), s, p);
 }
 
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
@@ -1271,9 +1283,10 @@ cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_
     return cudaGetLastError();
 }
 
-int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen) {
+int transfer_ctas_per_sm(bool fused, int kind_all, bool one_env, bool pen, int chunk) {
     int n = 0;
-    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, g2p2g_variant(kind_all, one_env, pen), kChunk, 0)
+    cudaError_t e = fused ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, g2p2g_variant(kind_all, one_env, pen, chunk),
+                                                                          fused_cta_threads(chunk), 0)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2g, kChunk, 0);
     if (e != cudaSuccess || n < 1) n = 1;
     return n;

@@ -7,8 +7,12 @@ from paper_2302_04659_gb300 import autotune
 
 
 class FakeSim:
+    """Launch shapes as the library checks them: chunks above 128 run 256-thread CTAs, which fit at
+    most 4 per SM (max_fused caps both CTA sizes further)."""
+
     def __init__(self, max_fused=7):
-        self.shape = (128, max_fused, 2)
+        self.max_fused = max_fused
+        self.shape = (128, min(7, max_fused), 2)
         self.N = 123456
         self.ns = [64]
         self.kinds = [0, 1]
@@ -17,7 +21,11 @@ class FakeSim:
         self.restored = 0
 
     def set_launch(self, c, f, g):
-        self.shape = (c, f, g)
+        c = c or self.shape[0]
+        limit = min(4 if c > 128 else 7, self.max_fused)
+        if f and f > limit:
+            raise autotune.mpm.MpmError("mpm_set_launch", 1)
+        self.shape = (c, f or self.shape[1], g or self.shape[2])
 
     def get_launch(self):
         return self.shape
@@ -25,7 +33,7 @@ class FakeSim:
 
 def cost(shape):
     c, f, g = shape
-    return 1.0 + 0.01 * abs(c - 96) + 0.05 * abs(f - 5) + 0.02 * abs(g - 4)
+    return 1.0 + 0.01 * abs(c - 192) + 0.05 * abs(f - 3) + 0.02 * abs(g - 4)
 
 
 @pytest.fixture
@@ -46,17 +54,17 @@ def fake_env(monkeypatch, tmp_path):
 def test_descent_finds_optimum_and_caches(fake_env):
     sim = FakeSim()
     shape, ms, trials = autotune.tune(sim, restore=lambda: setattr(sim, "restored", sim.restored + 1))
-    assert shape == (96, 5, 4)
-    assert sim.get_launch() == (96, 5, 4)
-    assert ms == pytest.approx(cost((96, 5, 4)))
+    assert shape == (192, 3, 4)
+    assert sim.get_launch() == (192, 3, 4)
+    assert ms == pytest.approx(cost((192, 3, 4)))
     assert sim.restored == 1
     assert len(trials) == len(set(fake_env)) < 4 * 3 * 3  # fewer trials than the full grid
     # second call: served from the cache, no trials, shape applied
     sim2 = FakeSim()
     n_calls = len(fake_env)
     shape2, ms2, trials2 = autotune.tune(sim2)
-    assert shape2 == (96, 5, 4) and trials2 == {} and len(fake_env) == n_calls
-    assert sim2.get_launch() == (96, 5, 4)
+    assert shape2 == (192, 3, 4) and trials2 == {} and len(fake_env) == n_calls
+    assert sim2.get_launch() == (192, 3, 4)
 
 
 def test_signature_separates_workloads(fake_env):
@@ -72,10 +80,10 @@ def test_signature_separates_workloads(fake_env):
 
 
 def test_occupancy_limit_respected(fake_env):
-    sim = FakeSim(max_fused=4)
+    sim = FakeSim(max_fused=2)
     shape, _, _ = autotune.tune(sim, use_cache=False)
-    assert shape[1] <= 4
-    assert all(s[1] <= 4 for s in fake_env)
+    assert shape[1] <= 2
+    assert all(s[1] <= 2 for s in fake_env)
 
 
 @pytest.mark.gpu
@@ -94,6 +102,6 @@ def test_tune_real_batch():
                                       use_cache=False)
     assert sim.get_launch() == shape
     assert shape[0] in autotune.CHUNKS and shape[2] in autotune.GRID_CTAS
-    assert 1 <= shape[1] <= 7
+    assert 1 <= shape[1] <= 4
     assert ms > 0 and len(trials) >= 3
     sim.close()

@@ -191,7 +191,7 @@ def test_launch_shapes_agree():
             for e in range(4)]
     counts, (x, v, C, F) = scenes.concat_states(envs)
     outs = []
-    for shape in [(0, 0, 0), (32, 1, 1), (64, 3, 4), (96, 7, 8)]:
+    for shape in [(0, 0, 0), (32, 1, 1), (96, 3, 4), (256, 4, 8)]:
         sim = make_batch(envs)
         if shape != (0, 0, 0):
             sim.set_launch(*shape)
@@ -201,7 +201,7 @@ def test_launch_shapes_agree():
         sim.set_colliders(*scenes.concat_tool_states(envs, 0.2))
         sim.substep(10)
         outs.append(sim.read_state(on_device=False)["x"])
-        for bad in [(16, 0, 0), (100, 0, 0), (0, 99, 0), (0, 0, 99), (0, -1, 0)]:
+        for bad in [(16, 0, 0), (100, 0, 0), (288, 0, 0), (0, 99, 0), (0, 0, 99), (0, -1, 0)]:
             with pytest.raises(_native.MpmError):
                 sim.set_launch(*bad)
         sim.close()
