@@ -150,9 +150,10 @@ struct PipeState {
     bool scanned = false;      // bin offsets and chunk list match the current keys
     bool order_valid = false;  // perm (sorted slot -> particle) matches them too
     bool grid_valid = false;   // grid g holds the transfer of the current state
+    bool rechunk = false;      // the chunk size changed since the scan: recut the chunk list
     bool operator==(const PipeState& o) const {
         return cur == o.cur && g == o.g && scanned == o.scanned && order_valid == o.order_valid &&
-               grid_valid == o.grid_valid;
+               grid_valid == o.grid_valid && rechunk == o.rechunk;
     }
 };
 
@@ -414,7 +415,14 @@ mpm_status enqueue_scan(mpm_sim* s, cudaStream_t st) {
 }
 
 mpm_status ensure_scanned(mpm_sim* s, cudaStream_t st) {
-    if (s->ps.scanned) return MPM_OK;
+    if (s->ps.scanned && !s->ps.rechunk) return MPM_OK;
+    if (s->ps.rechunk) {  // the bins' counts again, from their offsets, for a scan with the new chunk size
+        MPM_TRY(launch(s, MPM_K_SCAN, st, [&] {
+            return launch_hist_from_cursor(s->at<uint32_t>(s->L.cursor), s->at<uint32_t>(s->L.hist), (int)s->T.bins,
+                                           (uint32_t)s->N, st);
+        }, "hist_from_cursor"));
+        s->ps.rechunk = false;
+    }
     MPM_TRY(enqueue_scan(s, st));
     s->ps.scanned = true;
     return MPM_OK;
@@ -979,6 +987,9 @@ mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid
     s->max_fused_cps = max_fused;
     if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
     if (chunk) s->chunk = chunk;
+    // a chunk list cut for another size must be recut before the fused pass runs with this one (its
+    // CTA may be smaller than the listed chunks)
+    if (chunk && chunk != s->chunk && s->ps.scanned) s->ps.rechunk = true;
     if (fused_ctas_per_sm) s->fused_cps = fused_ctas_per_sm;
     if (grid_ctas_per_sm) s->grid_cps = grid_ctas_per_sm;
     s->drop_graphs();

@@ -194,6 +194,9 @@ cudaError_t launch_set_colliders_small(const ColliderUpload& u, ColliderSet* tab
 cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* poses, double* wrench,
                                  uint32_t* counter, float dt, cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* counter, int n, cudaStream_t s);
+// hist[b] = particles of global bin b, recovered from the exclusive offsets cursor (n particles in all)
+cudaError_t launch_hist_from_cursor(const uint32_t* cursor, uint32_t* hist, int total_bins, uint32_t n,
+                                    cudaStream_t s);
 
 // surrogate window (surrogate_kernels.cu): a box of grid nodes [i0, i0 + D) x [j0, j0 + H) x [k0, k0 + W)
 struct SurBox {

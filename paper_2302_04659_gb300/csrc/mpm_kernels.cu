@@ -784,8 +784,11 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         int bx, by, bz;
         decode_bin(ch.x - (int)E.bin_base, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
-        // this thread's particle: its loads are issued first so they overlap the tile load below
-        const bool active = (int)threadIdx.x < ch.z;
+        // this thread's particle: its loads are issued first so they overlap the tile load below. A chunk
+        // never holds more particles than the CTA has threads (the list is recut when the chunk size
+        // changes); should one, the rest are left alone and the internal-error flag is raised.
+        if (ch.z > CTA && threadIdx.x == 0) flags |= kFlagInternal;
+        const bool active = (int)threadIdx.x < min(ch.z, CTA);
         const uint32_t slot = (uint32_t)(ch.y + threadIdx.x);
         uint32_t src = 0;
         float x[3] = {0.5f, 0.5f, 0.5f};
@@ -1151,6 +1154,13 @@ __global__ void k_set_colliders(const ColliderSet* cols, int k, ColliderNow* pos
     }
 }
 
+__global__ void __launch_bounds__(256) k_hist_from_cursor(const uint32_t* __restrict__ cursor,
+                                                          uint32_t* __restrict__ hist, int total_bins, uint32_t n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= total_bins) return;
+    hist[b] = (b + 1 < total_bins ? cursor[b + 1] : n) - cursor[b];
+}
+
 __global__ void k_advance_counter(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run) {
     if (gate && *gate != gate_run) return;
     if (threadIdx.x == 0) *counter += (uint32_t)n;
@@ -1269,6 +1279,12 @@ cudaError_t launch_set_colliders(const ColliderSet* cols, int k, ColliderNow* po
                                  uint32_t* counter, float dt, cudaStream_t s) {
     const int threads = std::max(k > kSharedPoses ? k * kPoseSteps : k * 6, 1);
     k_set_colliders<<<ceil_div(threads, 256), 256, 0, s>>>(cols, k, poses, wrench, counter, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_from_cursor(const uint32_t* cursor, uint32_t* hist, int total_bins, uint32_t n,
+                                    cudaStream_t s) {
+    k_hist_from_cursor<<<ceil_div((size_t)total_bins, 256), 256, 0, s>>>(cursor, hist, total_bins, n);
     return cudaGetLastError();
 }
 

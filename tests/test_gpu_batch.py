@@ -257,3 +257,27 @@ def test_many_colliders_pose_table_matches_single_handles():
         assert np.abs(wr[e:e + 1] - wref).max() <= 1e-3 * scale
         hit += np.abs(wref).max() > 1e-3
     assert hit >= 5, "several tools should push their bodies"
+
+
+def test_chunk_size_change_mid_run():
+    """A chunk-size change between substeps recuts the chunk list: the fused pass of a smaller CTA never
+    meets a chunk cut for the larger one (every particle still moves, no internal-error flag), and the
+    state equals a run that used the final size throughout."""
+    from paper_2302_04659_gb300.sim import Sim
+    sc = scenes.pinch_scene(seed=1008, N=100_000)
+    cols = scenes.finger_state(sc, 0.1)
+    outs = []
+    for sizes in ((256, 64), (64, 64), (128, 256)):
+        sim = Sim(sc.n, sc.dt, sc.material, sc.N, gravity=sc.gravity, bound=sc.bound, max_colliders=2)
+        sim.set_shapes(sc.shapes)
+        sim.set_launch(sizes[0])
+        sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+        sim.set_colliders(*cols)
+        sim.substep(3)
+        sim.set_launch(sizes[1])
+        sim.substep(3)
+        assert sim.status() & 0x80000000 == 0
+        outs.append(sim.read_state(on_device=False)["x"])
+        sim.close()
+    for o in outs[1:]:
+        assert rel(o, outs[0]) <= 1e-5
