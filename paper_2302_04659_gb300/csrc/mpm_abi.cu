@@ -976,21 +976,23 @@ mpm_status mpm_set_launch(mpm_sim* s, int chunk, int fused_ctas_per_sm, int grid
     if (!s) return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
     if (chunk && (chunk < 32 || chunk > kChunk || chunk % 32)) return MPM_ERR_INVALID_ARG;
+    if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
     // the fused pass's CTA size follows the chunk, and its occupancy limit follows the CTA size
     const int new_chunk = chunk ? chunk : s->chunk;
     const bool pen = s->contact == MPM_CONTACT_PARTICLE;
     const int max_fused = transfer_ctas_per_sm(true, s->kind_all, s->nenv == 1, pen, new_chunk);
     if (fused_ctas_per_sm && (fused_ctas_per_sm < 1 || fused_ctas_per_sm > max_fused)) return MPM_ERR_INVALID_ARG;
-    if (fused_cta_threads(new_chunk) != fused_cta_threads(s->chunk) && !fused_ctas_per_sm)
-        s->fused_cps = max_fused;  // a new CTA size starts at its own occupancy
-    s->fused_cps = std::min(s->fused_cps, max_fused);
-    s->max_fused_cps = max_fused;
-    if (grid_ctas_per_sm && (grid_ctas_per_sm < 1 || grid_ctas_per_sm > 8)) return MPM_ERR_INVALID_ARG;
-    if (chunk) s->chunk = chunk;
     // a chunk list cut for another size must be recut before the fused pass runs with this one (its
     // CTA may be smaller than the listed chunks)
-    if (chunk && chunk != s->chunk && s->ps.scanned) s->ps.rechunk = true;
-    if (fused_ctas_per_sm) s->fused_cps = fused_ctas_per_sm;
+    if (new_chunk != s->chunk && s->ps.scanned) s->ps.rechunk = true;
+    if (fused_ctas_per_sm)
+        s->fused_cps = fused_ctas_per_sm;
+    else if (fused_cta_threads(new_chunk) != fused_cta_threads(s->chunk))
+        s->fused_cps = max_fused;  // a new CTA size starts at its own occupancy
+    else
+        s->fused_cps = std::min(s->fused_cps, max_fused);
+    s->chunk = new_chunk;
+    s->max_fused_cps = max_fused;
     if (grid_ctas_per_sm) s->grid_cps = grid_ctas_per_sm;
     s->drop_graphs();
     return MPM_OK;
