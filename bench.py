@@ -63,6 +63,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+# FP32 flops per particle-substep of the fused kernel (FMA counted as 2): ncu instruction counters of
+# the 600k-particle pinch capture, 8.22e8 flops per launch / 600,000 particles.
+FP32_FLOPS_PER_PARTICLE_SUBSTEP = 1370
+
+
+def fp32_peak_tflops(sm_mhz: float | None) -> float:
+    """Dense FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flops at the given SM clock."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -273,6 +283,7 @@ def run_native(args):
         return None
     peak, peak_kind = measured_peak_gbs()
     src_hash = kernel_source_hash()
+    clk_mhz = (clk.summary() or {}).get("sm_mhz")
     achieved = BYTES_PER_PARTICLE_SUBSTEP * N / g_avg / 1e9 if g_avg > 0 else None
     line = {
         "metric": METRIC,
@@ -322,6 +333,18 @@ def run_native(args):
                        "overlap between kernels)"),
             "kernel_source_hash": src_hash,
             "note": "state (38 MB) fits the 129 MB L2 inside a step; L2 flushed between steps",
+            "fp32": {
+                "bound": "alu",
+                "flops_per_particle_substep": FP32_FLOPS_PER_PARTICLE_SUBSTEP,
+                "achieved": FP32_FLOPS_PER_PARTICLE_SUBSTEP * N / g_avg / 1e12 if g_avg > 0 else None,
+                "peak": fp32_peak_tflops(clk_mhz),
+                "unit": "TFLOP/s",
+                "frac": (FP32_FLOPS_PER_PARTICLE_SUBSTEP * N / g_avg / 1e12 / fp32_peak_tflops(clk_mhz)
+                         if g_avg > 0 else None),
+                "what": ("FP32 flops of k_g2p2g per particle-substep (FMA = 2) counted by ncu on the 600k pinch "
+                         "capture (profiles/g2p2g_pinch200k.md); peak = 152 SMs x 128 FP32 lanes x 2 x the "
+                         "median SM clock sampled during the timed region"),
+            },
         },
         "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in ktime.items() if v[1]},
         "status_flags": flags,
