@@ -190,29 +190,27 @@ __device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z
     }
 }
 
-// Persistent, software-pipelined: while the tensor core runs the MMAs of tile j (accumulator j % 2), the
-// next tile's halo lands in the other plane buffer (tensor-map bulk copies issued by the MMA thread for 16
-// or 32 input channels; asynchronous 8-byte copies by all threads for 4) and the threads store tile j - 1
-// from the other accumulator.
+// 4 input channels (the first layer), persistent, software-pipelined: while the tensor core runs the MMAs
+// of tile j (accumulator j % 2), the next tile's halo lands in the other plane buffer by asynchronous
+// 8-byte copies from all threads (a 4-channel voxel row is too narrow for a tensor-map copy), and the
+// threads store tile j - 1 from the other accumulator. Wider inputs use k_conv_tc_ring.
 template <int NPAD, int CG>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_constant__ CUtensorMap /*tmap*/) {
+    static_assert(CG == 1, "16 or 32 input channels run k_conv_tc_ring");
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int S = k_steps(CG);
     constexpr int kBBlock = NPAD * 32;  // bytes of one K step of B: 2 k-groups x NPAD/8 n-groups x 128
     constexpr int kBuf = CG * kPlaneBytes;
-    constexpr bool kTma = CG >= 2;
     unsigned char* planes = smem;                                   // 2 buffers of CG planes
     unsigned char* bsm = smem + 2 * kBuf;                           // S blocks of kBBlock
-    // [0], [1]: MMAs of a buffer done; [2]: weights landed; [3], [4]: a buffer's halo landed
+    // [0], [1]: MMAs of a buffer done; [2]: weights landed
     uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + S * kBBlock);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 5);
     const int tid = threadIdx.x, warp = tid >> 5;
 
-    // zero the plane padding (and, for 4 channels, every row's upper 8 bytes) of both buffers
-    for (int i = tid; i < 2 * kBuf / 16; i += kThreads) {
-        const int h = (i % (kBuf / 16)) % kPlaneVox;
-        if (CG == 1 || h >= HV) *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
-    }
+    // zero both buffers: every row's upper 8 bytes (channels 4..7) and the plane padding stay zero
+    for (int i = tid; i < 2 * kBuf / 16; i += kThreads)
+        *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + b)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,72 +259,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_co
         }
         return tiles;
     };
-    // load a tile's halo into buffer b (TMA: by thread 0 only; otherwise by all threads, then waited)
+    // load a tile's halo into buffer b (by all threads; waited before the buffer is used)
     auto load_halo = [&](int tile, int b) {
         int z0, y0, x0;
         origin(tile, z0, y0, x0);
-        if constexpr (kTma) {
-            if (tid == 0) {
-                const uint32_t full = smem_u32(bar + 3 + b);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full),
-                             "r"((uint32_t)(CG * HV * 16))
-                             : "memory");
-                for (int q = 0; q < CG; ++q)
-                    tma_plane(planes_addr + b * kBuf + q * kPlaneBytes, &tmap, q * 8, x0 - 1, y0 - 1, z0 - 1, full);
-            }
-        } else {
-            stage_async<CG>(a, planes_addr + b * kBuf, z0, y0, x0);
-        }
+        stage_async<CG>(a, planes_addr + b * kBuf, z0, y0, x0);
     };
 
     bool failed = !mbar_wait(smem_u32(bar + 2), 0);  // the weights
     failed = __syncthreads_or(failed) != 0;
-    uint32_t ph_mma0 = 0u, ph_mma1 = 0u, ph_full0 = 0u, ph_full1 = 0u;
+    uint32_t ph_mma0 = 0u, ph_mma1 = 0u;
     int cur = failed ? tiles : next_needed(blockIdx.x);
     int prev = -1;  // tile whose accumulator awaits its epilogue
     int j = 0;
     if (cur < tiles) {
         load_halo(cur, 0);
-        if constexpr (!kTma) {
-            cp_async_wait_all();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-        }
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
     }
     while (cur < tiles) {
         const int b = j & 1;
         const int nxt = next_needed(cur + gridDim.x);
-        if (tid == 0) {  // the MMAs of tile `cur` from plane buffer b into accumulator b
-            if constexpr (kTma) {
-                uint32_t& ph = b ? ph_full1 : ph_full0;
-                if (!mbar_wait(smem_u32(bar + 3 + b), ph)) failed = true;
-                ph ^= 1u;
-            }
-            if (!failed) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // 4 channels: the second k-group is the next voxel along x (dx + 1); wider inputs: the
-                // next plane of 8 channels. Step descriptors = base + compile-time offsets.
-                constexpr uint32_t lbo = CG == 1 ? 16u : (uint32_t)kPlaneBytes;
-                const uint64_t ad0 = smem_desc(planes_addr + b * kBuf, lbo, HX * 16);
-                const uint64_t bd0 = smem_desc(b_addr, (NPAD / 8) * 128, 128);
+        if (tid == 0 && !failed) {  // the MMAs of tile `cur` from plane buffer b into accumulator b
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // a K step pairs the dx = 0, 1 taps of a row (the second k-group is the next voxel along x,
+            // 16 bytes on), then dx = 2 with an empty half. Step descriptors = base + compile-time offsets.
+            const uint64_t ad0 = smem_desc(planes_addr + b * kBuf, 16u, HX * 16);
+            const uint64_t bd0 = smem_desc(b_addr, (NPAD / 8) * 128, 128);
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    int off, q;
-                    if constexpr (CG == 1) {
-                        const int pair = s >> 1, half = s & 1;
-                        off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
-                        q = 0;
-                    } else {
-                        constexpr int h2 = CG / 2;
-                        const int tap = s / h2;
-                        off = ((tap / 9) * HY + (tap / 3) % 3) * HX + tap % 3;
-                        q = (s % h2) * 2;
-                    }
-                    mma_bf16(tmem + b * kTmemCols, ad0 + (uint64_t)((q * kPlaneBytes + off * 16) >> 4),
-                             bd0 + (uint64_t)((s * kBBlock) >> 4), idesc, s > 0 ? 1u : 0u);
-                }
-                mma_commit(smem_u32(bar + b));
+            for (int s = 0; s < S; ++s) {
+                const int pair = s >> 1, half = s & 1;
+                const int off = ((pair / 3) * HY + pair % 3) * HX + (half ? 2 : 0);
+                mma_bf16(tmem + b * kTmemCols, ad0 + (uint64_t)off, bd0 + (uint64_t)((s * kBBlock) >> 4), idesc,
+                         s > 0 ? 1u : 0u);
             }
+            mma_commit(smem_u32(bar + b));
         }
         __syncwarp();
         if (prev >= 0) {  // tile prev's MMAs (buffer and accumulator 1 - b) must be done
@@ -343,10 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_co
             origin(prev, z0, y0, x0);
             epilogue<NPAD>(a, tmem + (1 - b) * kTmemCols, z0, y0, x0);
         }
-        if constexpr (!kTma) {
-            cp_async_wait_all();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         prev = cur;
@@ -615,10 +581,16 @@ __global__ void k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mas
 
 template <int NPAD, int CG>
 cudaError_t launch(const Args& a, cudaStream_t s) {
-    constexpr bool ring = CG >= 2;
     using Kernel = void (*)(Args, const CUtensorMap);
-    const Kernel kernel = ring ? (Kernel)k_conv_tc_ring<NPAD, (CG >= 2 ? CG : 2)> : (Kernel)k_conv_tc<NPAD, CG>;
-    const size_t smem = ring ? ring_smem_bytes<NPAD, (CG >= 2 ? CG : 2)>() : smem_bytes(NPAD, CG);
+    Kernel kernel;
+    size_t smem;
+    if constexpr (CG >= 2) {
+        kernel = k_conv_tc_ring<NPAD, CG>;
+        smem = ring_smem_bytes<NPAD, CG>();
+    } else {
+        kernel = k_conv_tc<NPAD, CG>;
+        smem = smem_bytes(NPAD, CG);
+    }
     // resident CTAs, set up once per process (the kernels of one library run on GPUs of one kind)
     static int slots = 0;
     if (slots == 0) {
