@@ -281,3 +281,27 @@ def test_chunk_size_change_mid_run():
         sim.close()
     for o in outs[1:]:
         assert rel(o, outs[0]) <= 1e-5
+
+
+def test_chunk_size_change_with_grid_scan():
+    """The recut after a chunk-size change on the grid-wide scan path (more bins than the fused pass's
+    last CTA scans): same state as a batch that used the final size throughout, no internal-error flag."""
+    envs = [scenes.tool_scene(120 + e, scenes.PLASTICINE if e % 2 == 0 else scenes.FLUID, 20_000, n=64)
+            for e in range(6)]
+    assert sum((sc.n // 4) ** 3 for sc in envs) > TAIL_SCAN_MAX_BINS
+    counts, (x, v, C, F) = scenes.concat_states(envs)
+    cols = scenes.concat_tool_states(envs, 0.1)
+    outs = []
+    for sizes in ((256, 64), (64, 64)):
+        sim = make_batch(envs)
+        sim.set_launch(sizes[0])
+        sim.set_particles(counts, x, v, C, F)
+        sim.set_shapes([sc.shapes for sc in envs])
+        sim.set_colliders(*cols)
+        sim.substep(3)
+        sim.set_launch(sizes[1])
+        sim.substep(3)
+        assert sim.status() & 0x80000000 == 0
+        outs.append(sim.read_state(on_device=False)["x"])
+        sim.close()
+    assert rel(outs[0], outs[1]) <= 1e-5
