@@ -66,7 +66,7 @@ Totals totals_of(int nenv, const mpm_env* envs) {
 
 struct Layout {
     size_t state[2], key, perm, grid[2], flags[2], hist, list[2], list_meta, cursor, chunks, tile_sums, envs,
-        bin_env, colliders, poses, wrench, counters, sur, total;
+        bin_env, colliders, poses, wrench, counters, sur, sur_reduce, total;
 };
 
 Layout make_layout(const Totals& T, int nenv) {
@@ -98,6 +98,7 @@ Layout make_layout(const Totals& T, int nenv) {
     L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
     // surrogate window: sums, box, gate word, stats, the wrench before the window
     L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double) + kcap * 6 * sizeof(double));
+    L.sur_reduce = take((size_t)kReduceBlocks * 4 * sizeof(double) + 16);  // per-block totals, ticket
     L.total = off;
     return L;
 }
@@ -254,6 +255,10 @@ struct mpm_sim {
     uint32_t* sur_gate() { return at<uint32_t>(L.sur + 16 * sizeof(double) + 6 * sizeof(int)); }
     unsigned long long* sur_stats() { return at<unsigned long long>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
     double* sur_wrench() { return at<double>(L.sur + 16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double)); }
+    ReduceScratch sur_reduce() {
+        return ReduceScratch{at<double>(L.sur_reduce),
+                             reinterpret_cast<uint32_t*>(at<char>(L.sur_reduce) + (size_t)kReduceBlocks * 4 * sizeof(double))};
+    }
     const EnvDesc* envs_dev() { return at<EnvDesc>(L.envs); }
     bool tail_scan() const { return T.bins <= (size_t)kTailScanMaxBins; }
     StateView view(int which) {
@@ -454,13 +459,15 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
 }
 
 // First half of a substep: the sort-assign of the current state and the grid update of its transfer.
-mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate = nullptr, uint32_t gate_run = 1) {
+mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate = nullptr, uint32_t gate_run = 1,
+                             double* p0_sums = nullptr) {
     MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
     AssignGridParams ap{};
     ap.gate = gate;
     ap.gate_run = gate_run;
     ap.grid = grid_params(s);
+    ap.grid.p0_sums = p0_sums;
     ap.N = s->N;
     ap.keyrank = s->at<uint2>(s->L.key);
     ap.cursor = s->at<uint32_t>(s->L.cursor);
@@ -1148,7 +1155,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
     double* sums = s->sur_sums();
     MPM_CUDA(cudaMemsetAsync(sums, 0, 16 * sizeof(double), st), "cudaMemsetAsync");
     MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
-                                (int)s->T.bins, sums, st),
+                                (int)s->T.bins, sums, s->sur_reduce(), st),
              "sur_moments");
     if (s->ncol > 0)
         MPM_CUDA(cudaMemcpyAsync(s->sur_wrench(), s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
@@ -1157,7 +1164,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
     MPM_TRY(enqueue_grid_half(s, st));
     const Geometry& g = s->envs[0].geo;
     MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, to_sur_box(box), m_scale, v_scale,
-                                 d_feat, d_mask, sums + 4, st),
+                                 d_feat, d_mask, sums + 4, s->sur_reduce(), st),
              "sur_features");
     s->sur_pending = true;
     return MPM_OK;
@@ -1172,7 +1179,7 @@ mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv
     MPM_CUDA(cudaMemsetAsync(sums + 7, 0, 3 * sizeof(double), st), "cudaMemsetAsync");
     const Geometry& g = s->envs[0].geo;
     MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box), d_dv,
-                                dv_unit, 0, sums + 7, st),
+                                dv_unit, 0, sums + 7, s->sur_reduce(), st),
              "sur_check");
     double h[10];
     MPM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st), "copy sums");
@@ -1199,7 +1206,7 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
     if (d_dv) {
         const Geometry& g = s->envs[0].geo;
         MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box),
-                                    d_dv, dv_unit, 1, s->sur_sums() + 10, st),
+                                    d_dv, dv_unit, 1, s->sur_sums() + 10, s->sur_reduce(), st),
                  "sur_apply");
         MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt));
         if (k > 1) {
@@ -1265,22 +1272,18 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStrea
     double* sums = s->sur_sums();
     MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
-    if (gate_on) {  // the gate's sums (zero: cleared at attach and by every gate): mass and momentum before
-        // the grid update
-        MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
-                                    (int)s->T.bins, sums, st),
-                 "sur_moments");
-    }
     if (s->ncol > 0)
         MPM_CUDA(cudaMemcpyAsync(s->sur_wrench(), s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st),
                  "copy wrench");
-    MPM_TRY(enqueue_grid_half(s, st));
+    // with a gate, the grid update also sums the transfer's mass and momentum (the gate's sums are zero:
+    // cleared at attach and by every gate)
+    MPM_TRY(enqueue_grid_half(s, st, nullptr, 1, gate_on ? sums : nullptr));
     uint8_t* mask = reinterpret_cast<uint8_t*>(ws + NL.mask);
     uint8_t* dist = reinterpret_cast<uint8_t*>(ws + NL.dist);
     float* dv = reinterpret_cast<float*>(ws + NL.out);
     MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, box, net.m_scale, net.v_scale,
-                                 nullptr, mask, gate_on ? sums + 4 : nullptr, st, ws + NL.xbf),
+                                 nullptr, mask, gate_on ? sums + 4 : nullptr, s->sur_reduce(), st, ws + NL.xbf),
              "sur_features");
     MPM_TRY(mpm_conv3d_tc_tile_dist(b.D, b.H, b.W, mask, dist, st));
     const void* in = ws + NL.xbf;
@@ -1291,14 +1294,21 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStrea
                                       net.bias[i], last ? 0 : 1, last ? 1 : 0, out, dist, 3 - i, st));
         in = out;
     }
-    if (gate_on) {
-        const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
+    const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
+    if (gate_mode == 1) {  // per-step gate: correction, its sums and the decision in one launch
         uint32_t* words = reinterpret_cast<uint32_t*>(ws + NL.words);
+        MPM_CUDA(launch_sur_apply_check(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv,
+                                        net.dv_unit, sums, mp, k, net.v_ref, net.threshold, s->sur_gate(),
+                                        s->sur_stats(), words, s->sur_reduce(), s->substep_counter(),
+                                        s->at<double>(s->L.wrench), s->sur_wrench(), s->ncol * 6, st),
+                 "sur_apply_check");
+        return enqueue_particle_half(s, st, (float)k * s->cfg.dt);
+    }
+    if (gate_on)
         MPM_CUDA(launch_sur_check_gate(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv,
                                        net.dv_unit, sums, mp, k, net.v_ref, net.threshold, s->sur_gate(),
-                                       s->sur_stats(), gate_mode == 1 ? words : nullptr, words + 2, st),
+                                       s->sur_stats(), nullptr, s->sur_reduce(), st),
                  "sur_check_gate");
-    }
     // without per-window branches every window takes the surrogate branch and the plain one is not enqueued
     uint32_t* gate = gate_mode == 2 ? s->sur_gate() : nullptr;
     const PipeState before = s->ps;
@@ -1427,22 +1437,36 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
     const std::array<int, 8> key{b.i0, b.j0, b.k0, b.D, b.H, b.W, n_substeps, gate};
     const NetLayout NL = net_layout(s->net_max_voxels, s->env_cfg[0].max_particles);
     uint32_t* any_failed = reinterpret_cast<uint32_t*>(s->net_ws + NL.words);
-    if (gate) MPM_CUDA(cudaMemsetAsync(s->sur_sums(), 0, 16 * sizeof(double), st), "cudaMemsetAsync");
     float* snap = reinterpret_cast<float*>(s->net_ws + NL.snap);
     const size_t cap = std::max<size_t>(s->T.particles, 1);
-    const int snap_buf = s->ps.cur;  // the state buffer at the start of the step
-    if (gate == 1) {  // the step's starting point (the raw state buffer), for a plain redo
-        MPM_CUDA(cudaMemcpyAsync(snap, s->at<float>(s->L.state[snap_buf]), cap * 25 * sizeof(float),
-                                 cudaMemcpyDeviceToDevice, st),
+    // the work around the windows, captured with them: one graph launch per step
+    auto step_prologue = [&](cudaStream_t cs) -> mpm_status {
+        if (gate) MPM_CUDA(cudaMemsetAsync(s->sur_sums(), 0, 16 * sizeof(double), cs), "cudaMemsetAsync");
+        if (gate != 1) return MPM_OK;
+        // the step's starting point (the raw state buffer), for a plain redo
+        MPM_CUDA(cudaMemcpyAsync(snap, s->at<float>(s->L.state[s->ps.cur]), cap * 25 * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, cs),
                  "snapshot");
         MPM_CUDA(launch_sur_step_begin(s->at<double>(s->L.wrench), reinterpret_cast<double*>(s->net_ws + NL.wrench),
-                                       s->ncol * 6, s->substep_counter(), any_failed, st),
+                                       s->ncol * 6, s->substep_counter(), any_failed, cs),
                  "step_begin");
         if (s->ncol > 0)
             MPM_CUDA(cudaMemcpyAsync(s->net_ws + NL.cols, s->at<ColliderSet>(s->L.colliders),
-                                     s->ncol * sizeof(ColliderSet), cudaMemcpyDeviceToDevice, st),
+                                     s->ncol * sizeof(ColliderSet), cudaMemcpyDeviceToDevice, cs),
                      "snapshot colliders");
-    }
+        return MPM_OK;
+    };
+    // per-step gate: the verdict and the next step's box, copied to pinned host memory (read lazily)
+    auto step_epilogue = [&](cudaStream_t cs) -> mpm_status {
+        if (gate != 1) return MPM_OK;
+        int* d_box = s->sur_box();
+        const Geometry& g = s->envs[0].geo;
+        MPM_CUDA(launch_sur_box(s->list(s->ps.g), s->list_count(s->ps.g), g.nb, (int)s->T.bins, d_box, cs), "sur_box");
+        MPM_CUDA(cudaMemcpyAsync(s->verify_host, any_failed, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs),
+                 "copy flag");
+        MPM_CUDA(cudaMemcpyAsync(s->verify_host + 1, d_box, 6 * sizeof(int), cudaMemcpyDeviceToHost, cs), "copy box");
+        return MPM_OK;
+    };
     GraphEntry* ge = nullptr;
     for (size_t i = 0; i < s->sur_graphs.size(); ++i)
         if (s->sur_keys[i] == key && s->sur_graphs[i].before == s->ps && s->sur_graphs[i].ncol == s->ncol)
@@ -1466,8 +1490,9 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
         s->timing_mask = 0;  // no timing events inside these graphs
         MPM_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         s->capturing = true;
-        mpm_status r = MPM_OK;
+        mpm_status r = step_prologue(s->cap_stream);
         for (int w = 0; w < n_substeps / s->net.k && r == MPM_OK; ++w) r = enqueue_window(s, b, gate, s->cap_stream);
+        if (r == MPM_OK) r = step_epilogue(s->cap_stream);
         s->capturing = false;
         s->timing_mask = mask_saved;
         cudaGraph_t graph = nullptr;
@@ -1494,13 +1519,7 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
     MPM_CUDA(cudaGraphLaunch(ge->exec, st), "cudaGraphLaunch");
     s->ps = ge->after;
     s->launches += ge->launches;
-    if (gate == 1) {  // the verdict and the next step's box, read back without waiting (resolve_pending)
-        int* d_box = s->sur_box();
-        const Geometry& g = s->envs[0].geo;
-        MPM_CUDA(launch_sur_box(s->list(s->ps.g), s->list_count(s->ps.g), g.nb, (int)s->T.bins, d_box, st), "sur_box");
-        MPM_CUDA(cudaMemcpyAsync(s->verify_host, any_failed, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
-                 "copy flag");
-        MPM_CUDA(cudaMemcpyAsync(s->verify_host + 1, d_box, 6 * sizeof(int), cudaMemcpyDeviceToHost, st), "copy box");
+    if (gate == 1) {  // the verdict and the next step's box were copied by the graph; read them lazily
         MPM_CUDA(cudaEventRecord(s->verify_event, st), "cudaEventRecord");
         s->verify_pending = true;
         s->verify_substeps = n_substeps;

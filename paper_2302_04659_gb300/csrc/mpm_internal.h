@@ -141,6 +141,7 @@ struct GridParams {
     double* wrench;           // k_total x 6
     int ctas;                 // CTAs of the (persistent) grid update
     int grid_colliders;       // 1: the grid form of the contact acts here (0: particle form, no colliders)
+    double* p0_sums;          // if set: mass and momentum of the transfer (before the update) added here (4)
 };
 
 struct AssignGridParams {  // the sort-assign of the new state and the grid update, one launch
@@ -208,13 +209,20 @@ cudaError_t launch_sur_step_begin(const double* wrench, double* saved, int n6, c
                                   cudaStream_t s);
 cudaError_t launch_sur_step_restore(double* wrench, const double* saved, int n6, uint32_t* counter,
                                     const uint32_t* words, cudaStream_t s);
+// Scratch of the surrogate's sums: per-block totals and the last-block ticket (reductions launch at most
+// kReduceBlocks blocks).
+constexpr int kReduceBlocks = 304;
+struct ReduceScratch {
+    double* partials;  // kReduceBlocks x 4
+    uint32_t* ticket;  // zero between launches
+};
 cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
-                               double* sums, cudaStream_t s);
+                               double* sums, const ReduceScratch& r, cudaStream_t s);
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
-                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s,
-                                void* feat_bf16 = nullptr);
+                                float v_scale, float* feat, uint8_t* mask, double* sums, const ReduceScratch& r,
+                                cudaStream_t s, void* feat_bf16 = nullptr);
 cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
-                               float unit, int apply, double* sums, cudaStream_t s);
+                               float unit, int apply, double* sums, const ReduceScratch& r, cudaStream_t s);
 cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s,
                                       const uint32_t* gate = nullptr, uint32_t gate_run = 1);
 // The device-side gate of a window: from the sums (M, P0, P1, P_hat) the mass and momentum residuals;
@@ -225,8 +233,16 @@ cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, doubl
 // The corrected grid's momentum and the gate in one launch (last block decides; sums re-zeroed).
 cudaError_t launch_sur_check_gate(const float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
-                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, uint32_t* ticket,
+                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, const ReduceScratch& r,
                                   cudaStream_t s);
+// Per-step gate mode in one launch: the corrected grid written back, its momentum summed, and the last
+// block deciding the gate (as launch_sur_check_gate) besides the counter and impulse bookkeeping of
+// launch_sur_apply.
+cudaError_t launch_sur_apply_check(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
+                                   uint32_t* gate, unsigned long long* stats, uint32_t* any_failed,
+                                   const ReduceScratch& r, uint32_t* counter, double* wrench,
+                                   const double* wrench_before, int n6, cudaStream_t s);
 // The correction written back (only if *gate == 1 when gate is set), with the window's substep-counter and
 // body-impulse bookkeeping.
 cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv, float unit,

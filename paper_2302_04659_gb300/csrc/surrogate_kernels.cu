@@ -13,10 +13,14 @@ namespace {
 
 constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
 
-// Block-wide sum of NV doubles (blockDim a multiple of 32, at most 1024), added atomically to out.
+// Block-wide sum of NV doubles (blockDim a multiple of 32, at most 1024) added to out[NV] without
+// contended atomics: each block stores its total in partials[block][NV]; the last block to finish
+// (ticket) adds the blocks' totals, in block order, to out and resets the ticket. Returns true in that
+// last block (all of its threads), after out is written.
 template <int NV>
-__device__ __forceinline__ void block_sum_add(double (&v)[NV], double* out) {
+__device__ __forceinline__ bool block_sum_last(double (&v)[NV], double* partials, uint32_t* ticket, double* out) {
     __shared__ double part[32][NV];
+    __shared__ bool last;
 #pragma unroll
     for (int q = 0; q < NV; ++q)
         for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
@@ -31,9 +35,42 @@ __device__ __forceinline__ void block_sum_add(double (&v)[NV], double* out) {
         for (int q = 0; q < NV; ++q) {
             double s = lane < nw ? part[lane][q] : 0.0;
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0 && s != 0.0) atomicAdd(&out[q], s);
+            if (lane == 0) partials[(size_t)blockIdx.x * NV + q] = s;
         }
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    // the blocks' totals, spread over the threads (L2 reads, all in flight), then the same block reduction
+    double t[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) t[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) t[q] += __ldcg(&partials[(size_t)b * NV + q]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int off = 16; off > 0; off >>= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
+    __syncthreads();  // part[] is reused
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part[warp][q] = t[q];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < nw ? part[lane][q] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) out[q] += s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
 }
 
 // Bin bounds of the active bins (the grid's bin list), one block: box[0..2] = min bin per axis,
@@ -91,7 +128,7 @@ __global__ void k_sur_step_restore(double* wrench, const double* wrench_saved, i
 
 // Mass and momentum of the transfer, before the grid update (nodes hold (m, m v)).
 __global__ void k_sur_moments(const float4* __restrict__ grid, const uint32_t* __restrict__ list,
-                              const uint32_t* __restrict__ count, double* sums) {
+                              const uint32_t* __restrict__ count, double* sums, double* partials, uint32_t* ticket) {
     const uint32_t n = *count;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kBlkNodes; i += gridDim.x * blockDim.x) {
@@ -102,7 +139,7 @@ __global__ void k_sur_moments(const float4* __restrict__ grid, const uint32_t* _
         v[2] += g.z;
         v[3] += g.w;
     }
-    block_sum_add<4>(v, sums);
+    block_sum_last<4>(v, partials, ticket, sums);
 }
 
 __device__ __forceinline__ bool box_node(const SurBox& b, size_t t, int& i, int& j, int& k) {
@@ -116,7 +153,7 @@ __device__ __forceinline__ bool box_node(const SurBox& b, size_t t, int& i, int&
 // the mass mask, and the momentum sum of the updated grid.
 __global__ void k_sur_features(const float4* __restrict__ grid, int n, int nb, SurBox box, float m_scale,
                                float v_scale, float* __restrict__ feat, __nv_bfloat16* __restrict__ feat_bf16,
-                               uint8_t* __restrict__ mask, double* sums) {
+                               uint8_t* __restrict__ mask, double* sums, double* partials, uint32_t* ticket) {
     const size_t nv = (size_t)box.D * box.H * box.W;
     double p[3] = {0.0, 0.0, 0.0};
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
@@ -137,7 +174,7 @@ __global__ void k_sur_features(const float4* __restrict__ grid, int n, int nb, S
         p[1] += (double)m * g.y;
         p[2] += (double)m * g.z;
     }
-    if (sums) block_sum_add<3>(p, sums);
+    if (sums) block_sum_last<3>(p, partials, ticket, sums);
 }
 
 __device__ __forceinline__ bool in_wall(int i, int j, int k, int n, int bound) {
@@ -148,7 +185,8 @@ __device__ __forceinline__ bool in_wall(int i, int j, int k, int n, int bound) {
 // The corrected velocity of a node: v + dv * unit where it has mass, zero in the sticky wall band.
 // apply != 0 writes it back; the momentum of the corrected grid is summed either way.
 __global__ void k_sur_correct(float4* __restrict__ grid, int n, int nb, int bound, SurBox box,
-                              const float* __restrict__ dv, float unit, int apply, double* sums) {
+                              const float* __restrict__ dv, float unit, int apply, double* sums, double* partials,
+                              uint32_t* ticket) {
     const size_t nv = (size_t)box.D * box.H * box.W;
     double p[3] = {0.0, 0.0, 0.0};
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
@@ -166,7 +204,7 @@ __global__ void k_sur_correct(float4* __restrict__ grid, int n, int nb, int boun
         p[2] += (double)g.w * v[2];
         if (apply) *node = make_float4(v[0], v[1], v[2], g.w);
     }
-    block_sum_add<3>(p, sums);
+    block_sum_last<3>(p, partials, ticket, sums);
 }
 
 // The gate in one launch: the corrected grid's momentum summed like k_sur_correct (without writing it
@@ -185,32 +223,12 @@ struct GateArgs {
     unsigned long long* stats;
     uint32_t* any_failed;    // per-step mode, or null
     uint32_t* ticket;
+    double* partials;         // per-block totals (kReduceBlocks x 3)
 };
 
-__global__ void k_sur_check_gate(GateArgs g) {
-    const size_t nv = (size_t)g.box.D * g.box.H * g.box.W;
-    double p[3] = {0.0, 0.0, 0.0};
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
-        int i, j, k;
-        box_node(g.box, t, i, j, k);
-        if (i < 0 || i >= g.n || j < 0 || j >= g.n || k < 0 || k >= g.n) continue;
-        const float4 gv = g.grid[node_index(i, j, k, g.nb)];
-        if (!(gv.w > 0.0f)) continue;
-        const float* d = g.dv + t * 3;
-        float v[3] = {gv.x + d[0] * g.unit, gv.y + d[1] * g.unit, gv.z + d[2] * g.unit};
-        if (in_wall(i, j, k, g.n, g.bound)) v[0] = v[1] = v[2] = 0.0f;
-        p[0] += (double)gv.w * v[0];
-        p[1] += (double)gv.w * v[1];
-        p[2] += (double)gv.w * v[2];
-    }
-    block_sum_add<3>(p, g.sums + 7);
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
+// The gate's decision from the complete sums (M, P0, P1, P_hat): residuals, gate word, stats; the sums are
+// zeroed for the next window. One thread.
+__device__ void gate_decide(const GateArgs& g) {
     volatile double* S = g.sums;
     const double M = S[0];
     double d2 = 0.0;
@@ -228,7 +246,57 @@ __global__ void k_sur_check_gate(GateArgs g) {
     reinterpret_cast<double*>(g.stats)[2] = r_mass;
     reinterpret_cast<double*>(g.stats)[3] = r_mom;
     for (int q = 0; q < 10; ++q) S[q] = 0.0;
-    *g.ticket = 0u;
+}
+
+__global__ void k_sur_check_gate(GateArgs g) {
+    const size_t nv = (size_t)g.box.D * g.box.H * g.box.W;
+    double p[3] = {0.0, 0.0, 0.0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(g.box, t, i, j, k);
+        if (i < 0 || i >= g.n || j < 0 || j >= g.n || k < 0 || k >= g.n) continue;
+        const float4 gv = g.grid[node_index(i, j, k, g.nb)];
+        if (!(gv.w > 0.0f)) continue;
+        const float* d = g.dv + t * 3;
+        float v[3] = {gv.x + d[0] * g.unit, gv.y + d[1] * g.unit, gv.z + d[2] * g.unit};
+        if (in_wall(i, j, k, g.n, g.bound)) v[0] = v[1] = v[2] = 0.0f;
+        p[0] += (double)gv.w * v[0];
+        p[1] += (double)gv.w * v[1];
+        p[2] += (double)gv.w * v[2];
+    }
+    if (!block_sum_last<3>(p, g.partials, g.ticket, g.sums + 7) || threadIdx.x != 0) return;
+    gate_decide(g);
+}
+
+// Per-step gate mode: the correction written back while its momentum is summed, the counter and impulse
+// bookkeeping of k_sur_apply_gated (block 0), and the gate decided by the last block (a failure only
+// marks the step for a plain redo, so nothing waits on it here).
+__global__ void k_sur_apply_check(GateArgs g, float4* __restrict__ grid, uint32_t* counter, double* wrench,
+                                  const double* wrench_before, int n6) {
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *counter += (uint32_t)(g.k - 1);
+        for (int i = threadIdx.x; i < n6; i += blockDim.x)
+            wrench[i] += (double)(g.k - 1) * (wrench[i] - wrench_before[i]);
+    }
+    const size_t nv = (size_t)g.box.D * g.box.H * g.box.W;
+    double p[3] = {0.0, 0.0, 0.0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv; t += (size_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        box_node(g.box, t, i, j, k);
+        if (i < 0 || i >= g.n || j < 0 || j >= g.n || k < 0 || k >= g.n) continue;
+        float4* node = &grid[node_index(i, j, k, g.nb)];
+        const float4 gv = *node;
+        if (!(gv.w > 0.0f)) continue;
+        const float* d = g.dv + t * 3;
+        float v[3] = {gv.x + d[0] * g.unit, gv.y + d[1] * g.unit, gv.z + d[2] * g.unit};
+        if (in_wall(i, j, k, g.n, g.bound)) v[0] = v[1] = v[2] = 0.0f;
+        p[0] += (double)gv.w * v[0];
+        p[1] += (double)gv.w * v[1];
+        p[2] += (double)gv.w * v[2];
+        *node = make_float4(v[0], v[1], v[2], gv.w);
+    }
+    if (!block_sum_last<3>(p, g.partials, g.ticket, g.sums + 7) || threadIdx.x != 0) return;
+    gate_decide(g);
 }
 
 // Body impulses over a window: the first substep's share, counted k times in all.
@@ -317,24 +385,27 @@ cudaError_t launch_sur_step_restore(double* wrench, const double* saved, int n6,
 }
 
 cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
-                               double* sums, cudaStream_t s) {
-    k_sur_moments<<<grid_for((size_t)nbins_cap * kBlkNodes, 256, 1024), 256, 0, s>>>(grid, list, count, sums);
+                               double* sums, const ReduceScratch& r, cudaStream_t s) {
+    k_sur_moments<<<grid_for((size_t)nbins_cap * kBlkNodes, 256, kReduceBlocks), 256, 0, s>>>(grid, list, count, sums,
+                                                                                             r.partials, r.ticket);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
-                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s,
-                                void* feat_bf16) {
+                                float v_scale, float* feat, uint8_t* mask, double* sums, const ReduceScratch& r,
+                                cudaStream_t s, void* feat_bf16) {
     const size_t nv = (size_t)box.D * box.H * box.W;
-    k_sur_features<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, box, m_scale, v_scale, feat,
-                                                           static_cast<__nv_bfloat16*>(feat_bf16), mask, sums);
+    k_sur_features<<<grid_for(nv, 256, kReduceBlocks), 256, 0, s>>>(grid, n, nb, box, m_scale, v_scale, feat,
+                                                                    static_cast<__nv_bfloat16*>(feat_bf16), mask, sums,
+                                                                    r.partials, r.ticket);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
-                               float unit, int apply, double* sums, cudaStream_t s) {
+                               float unit, int apply, double* sums, const ReduceScratch& r, cudaStream_t s) {
     const size_t nv = (size_t)box.D * box.H * box.W;
-    k_sur_correct<<<grid_for(nv, 256, 2048), 256, 0, s>>>(grid, n, nb, bound, box, dv, unit, apply, sums);
+    k_sur_correct<<<grid_for(nv, 256, kReduceBlocks), 256, 0, s>>>(grid, n, nb, bound, box, dv, unit, apply, sums,
+                                                                   r.partials, r.ticket);
     return cudaGetLastError();
 }
 
@@ -353,12 +424,24 @@ cudaError_t launch_sur_gate(const double* sums, double m_particles, int k, doubl
 
 cudaError_t launch_sur_check_gate(const float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
-                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, uint32_t* ticket,
-                                  cudaStream_t s) {
+                                  uint32_t* gate, unsigned long long* stats, uint32_t* any_failed,
+                                  const ReduceScratch& r, cudaStream_t s) {
     const size_t nv = (size_t)box.D * box.H * box.W;
     GateArgs g{grid, n, nb, bound, box, dv, unit, sums, m_particles, v_ref, threshold, k, gate, stats, any_failed,
-               ticket};
-    k_sur_check_gate<<<grid_for(nv, 256, 1024), 256, 0, s>>>(g);
+               r.ticket, r.partials};
+    k_sur_check_gate<<<grid_for(nv, 256, kReduceBlocks), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_apply_check(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
+                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
+                                   uint32_t* gate, unsigned long long* stats, uint32_t* any_failed,
+                                   const ReduceScratch& r, uint32_t* counter, double* wrench,
+                                   const double* wrench_before, int n6, cudaStream_t s) {
+    const size_t nv = (size_t)box.D * box.H * box.W;
+    GateArgs g{grid, n, nb, bound, box, dv, unit, sums, m_particles, v_ref, threshold, k, gate, stats, any_failed,
+               r.ticket, r.partials};
+    k_sur_apply_check<<<grid_for(nv, 256, kReduceBlocks), 256, 0, s>>>(g, grid, counter, wrench, wrench_before, n6);
     return cudaGetLastError();
 }
 
