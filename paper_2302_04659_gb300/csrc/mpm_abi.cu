@@ -98,7 +98,7 @@ Layout make_layout(const Totals& T, int nenv) {
     L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
     // surrogate window: sums, box, gate word, stats, the wrench before the window
     L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double) + kcap * 6 * sizeof(double));
-    L.sur_reduce = take((size_t)kReduceBlocks * 4 * sizeof(double) + 16);  // per-block totals, ticket
+    L.sur_reduce = take((size_t)kReduceBlocks * 4 * sizeof(Pair) + 16);  // per-block totals, ticket
     L.total = off;
     return L;
 }
@@ -256,8 +256,8 @@ struct mpm_sim {
     unsigned long long* sur_stats() { return at<unsigned long long>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
     double* sur_wrench() { return at<double>(L.sur + 16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double)); }
     ReduceScratch sur_reduce() {
-        return ReduceScratch{at<double>(L.sur_reduce),
-                             reinterpret_cast<uint32_t*>(at<char>(L.sur_reduce) + (size_t)kReduceBlocks * 4 * sizeof(double))};
+        return ReduceScratch{at<Pair>(L.sur_reduce),
+                             reinterpret_cast<uint32_t*>(at<char>(L.sur_reduce) + (size_t)kReduceBlocks * 4 * sizeof(Pair))};
     }
     const EnvDesc* envs_dev() { return at<EnvDesc>(L.envs); }
     bool tail_scan() const { return T.bins <= (size_t)kTailScanMaxBins; }
@@ -1155,7 +1155,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
     double* sums = s->sur_sums();
     MPM_CUDA(cudaMemsetAsync(sums, 0, 16 * sizeof(double), st), "cudaMemsetAsync");
     MPM_CUDA(launch_sur_moments(s->at<float4>(s->L.grid[s->ps.g]), s->list(s->ps.g), s->list_count(s->ps.g),
-                                (int)s->T.bins, sums, s->sur_reduce(), st),
+                                (int)s->T.bins, sums, st),
              "sur_moments");
     if (s->ncol > 0)
         MPM_CUDA(cudaMemcpyAsync(s->sur_wrench(), s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double),
@@ -1164,7 +1164,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
     MPM_TRY(enqueue_grid_half(s, st));
     const Geometry& g = s->envs[0].geo;
     MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, to_sur_box(box), m_scale, v_scale,
-                                 d_feat, d_mask, sums + 4, s->sur_reduce(), st),
+                                 d_feat, d_mask, sums + 4, st),
              "sur_features");
     s->sur_pending = true;
     return MPM_OK;
@@ -1179,7 +1179,7 @@ mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv
     MPM_CUDA(cudaMemsetAsync(sums + 7, 0, 3 * sizeof(double), st), "cudaMemsetAsync");
     const Geometry& g = s->envs[0].geo;
     MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box), d_dv,
-                                dv_unit, 0, sums + 7, s->sur_reduce(), st),
+                                dv_unit, 0, sums + 7, st),
              "sur_check");
     double h[10];
     MPM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st), "copy sums");
@@ -1206,7 +1206,7 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
     if (d_dv) {
         const Geometry& g = s->envs[0].geo;
         MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box),
-                                    d_dv, dv_unit, 1, s->sur_sums() + 10, s->sur_reduce(), st),
+                                    d_dv, dv_unit, 1, s->sur_sums() + 10, st),
                  "sur_apply");
         MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt));
         if (k > 1) {
@@ -1227,8 +1227,12 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
 namespace {
 
 struct NetLayout {
-    size_t feat, xbf, act[3], out, mask, dist, snap, wrench, cols, words, total;
+    size_t feat, xbf, act[3], out, mask, dist, snap, wrench, cols, words, slots, total;
 };
+
+// Per-step gate: the sums of up to kGateSlots windows wait for one decision (more windows are decided in
+// groups of kGateSlots).
+constexpr int kGateSlots = 64;
 
 NetLayout net_layout(int max_voxels, int max_particles = 0) {
     NetLayout L{};
@@ -1251,6 +1255,7 @@ NetLayout net_layout(int max_voxels, int max_particles = 0) {
     L.wrench = take(MPM_MAX_COLLIDERS * 6 * sizeof(double));
     L.cols = take(MPM_MAX_COLLIDERS * sizeof(ColliderSet));
     L.words = take(4 * sizeof(uint32_t));
+    L.slots = take(kGateSlots * 10 * sizeof(double));
     L.total = off;
     return L;
 }
@@ -1259,9 +1264,9 @@ constexpr int kNetChannels[5] = {4, 32, 32, 32, 3};
 
 // One window (k substeps) from the current pipeline state: plain grid update, network, device-side gate,
 // then both branches enqueued, each running only on its side of the gate.
-// gate_mode: 0 no gate; 1 the gate only records (residuals, stats, the step's "a window failed" word) and
-// the surrogate branch always runs; 2 both branches, each running on its side of the gate.
-mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStream_t st) {
+// gate_mode: 0 no gate; 1 the window's sums go to `slot` (10 doubles, zero) for a decision after the step's
+// windows, and the surrogate branch always runs; 2 both branches, each running on its side of the gate.
+mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStream_t st, double* slot = nullptr) {
     const mpm_surrogate_net& net = s->net;
     const int k = net.k;
     const bool gate_on = gate_mode != 0;
@@ -1269,7 +1274,8 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStrea
     char* ws = s->net_ws;
     const SurBox box = to_sur_box(&b);
     const Geometry& g = s->envs[0].geo;
-    double* sums = s->sur_sums();
+    if (gate_mode == 1 && !slot) return MPM_ERR_INVALID_ARG;
+    double* sums = gate_mode == 1 ? slot : s->sur_sums();
     MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
     if (s->ncol > 0)
@@ -1277,13 +1283,13 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStrea
                                  cudaMemcpyDeviceToDevice, st),
                  "copy wrench");
     // with a gate, the grid update also sums the transfer's mass and momentum (the gate's sums are zero:
-    // cleared at attach and by every gate)
+    // cleared at attach and by every decision)
     MPM_TRY(enqueue_grid_half(s, st, nullptr, 1, gate_on ? sums : nullptr));
     uint8_t* mask = reinterpret_cast<uint8_t*>(ws + NL.mask);
     uint8_t* dist = reinterpret_cast<uint8_t*>(ws + NL.dist);
     float* dv = reinterpret_cast<float*>(ws + NL.out);
     MPM_CUDA(launch_sur_features(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, box, net.m_scale, net.v_scale,
-                                 nullptr, mask, gate_on ? sums + 4 : nullptr, s->sur_reduce(), st, ws + NL.xbf),
+                                 nullptr, mask, gate_on ? sums + 4 : nullptr, st, ws + NL.xbf),
              "sur_features");
     MPM_TRY(mpm_conv3d_tc_tile_dist(b.D, b.H, b.W, mask, dist, st));
     const void* in = ws + NL.xbf;
@@ -1295,13 +1301,11 @@ mpm_status enqueue_window(mpm_sim* s, const mpm_box& b, int gate_mode, cudaStrea
         in = out;
     }
     const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
-    if (gate_mode == 1) {  // per-step gate: correction, its sums and the decision in one launch
-        uint32_t* words = reinterpret_cast<uint32_t*>(ws + NL.words);
-        MPM_CUDA(launch_sur_apply_check(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv,
-                                        net.dv_unit, sums, mp, k, net.v_ref, net.threshold, s->sur_gate(),
-                                        s->sur_stats(), words, s->sur_reduce(), s->substep_counter(),
-                                        s->at<double>(s->L.wrench), s->sur_wrench(), s->ncol * 6, st),
-                 "sur_apply_check");
+    if (gate_mode == 1) {  // per-step gate: the correction and its momentum sum; decided after the windows
+        MPM_CUDA(launch_sur_apply(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, box, dv, net.dv_unit,
+                                  nullptr, s->substep_counter(), k, s->at<double>(s->L.wrench), s->sur_wrench(),
+                                  s->ncol * 6, st, sums + 7),
+                 "sur_apply");
         return enqueue_particle_half(s, st, (float)k * s->cfg.dt);
     }
     if (gate_on)
@@ -1417,6 +1421,7 @@ mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* 
     const NetLayout NL = net_layout(max_voxels, s->env_cfg[0].max_particles);
     MPM_CUDA(cudaMemset(s->sur_sums(), 0, 16 * sizeof(double)), "cudaMemset");
     MPM_CUDA(cudaMemset(s->net_ws + NL.words, 0, 4 * sizeof(uint32_t)), "cudaMemset");
+    MPM_CUDA(cudaMemset(s->net_ws + NL.slots, 0, kGateSlots * 10 * sizeof(double)), "cudaMemset");
     return MPM_OK;
 }
 
@@ -1441,7 +1446,7 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
     const size_t cap = std::max<size_t>(s->T.particles, 1);
     // the work around the windows, captured with them: one graph launch per step
     auto step_prologue = [&](cudaStream_t cs) -> mpm_status {
-        if (gate) MPM_CUDA(cudaMemsetAsync(s->sur_sums(), 0, 16 * sizeof(double), cs), "cudaMemsetAsync");
+        if (gate == 2) MPM_CUDA(cudaMemsetAsync(s->sur_sums(), 0, 16 * sizeof(double), cs), "cudaMemsetAsync");
         if (gate != 1) return MPM_OK;
         // the step's starting point (the raw state buffer), for a plain redo
         MPM_CUDA(cudaMemcpyAsync(snap, s->at<float>(s->L.state[s->ps.cur]), cap * 25 * sizeof(float),
@@ -1491,7 +1496,18 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
         MPM_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
         s->capturing = true;
         mpm_status r = step_prologue(s->cap_stream);
-        for (int w = 0; w < n_substeps / s->net.k && r == MPM_OK; ++w) r = enqueue_window(s, b, gate, s->cap_stream);
+        const int nwin = n_substeps / s->net.k;
+        double* slots = reinterpret_cast<double*>(s->net_ws + NL.slots);
+        const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
+        for (int w = 0; w < nwin && r == MPM_OK; ++w) {
+            r = enqueue_window(s, b, gate, s->cap_stream, slots + (size_t)(w % kGateSlots) * 10);
+            const int done = w % kGateSlots + 1;  // windows waiting in the slots
+            if (r == MPM_OK && gate == 1 && (done == kGateSlots || w + 1 == nwin)) {
+                const cudaError_t e = launch_sur_decide(slots, done, mp, s->net.k, s->net.v_ref, s->net.threshold,
+                                                        s->sur_stats(), any_failed, s->cap_stream);
+                if (e != cudaSuccess) r = cuda_fail(e, "sur_decide");
+            }
+        }
         if (r == MPM_OK) r = step_epilogue(s->cap_stream);
         s->capturing = false;
         s->timing_mask = mask_saved;

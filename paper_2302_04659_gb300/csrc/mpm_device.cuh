@@ -412,4 +412,29 @@ __device__ __forceinline__ float collider_sdf(const ColliderNow& c, const float 
     return phi;
 }
 
+// Sums kept as unevaluated FP32 pairs: hi + lo carries about 48 significant bits. An addition is
+// Knuth's TwoSum of the high parts (s + e equals a.hi + b.hi exactly), the low parts added to that
+// error, then Dekker's Fast2Sum to renormalise. The device-wide mass and momentum sums reduce these
+// instead of FP64 values: this part's FP64 pipe is a small fraction of its FP32 one, and a dependent
+// tree of FP64 adds and shuffles stalls on it.
+struct Pair {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Pair pair_add(Pair a, Pair b) {
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    const float e = ((a.hi - (s - bv)) + (b.hi - bv)) + (a.lo + b.lo);
+    const float hi = s + e;
+    return Pair{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ Pair pair_add(Pair a, float b) { return pair_add(a, Pair{b, 0.0f}); }
+
+__device__ __forceinline__ Pair pair_shfl_xor(Pair a, int off) {
+    return Pair{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
+
+__device__ __forceinline__ double pair_value(Pair a) { return (double)a.hi + (double)a.lo; }
+
 }  // namespace mpm

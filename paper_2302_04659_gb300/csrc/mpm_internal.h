@@ -209,20 +209,23 @@ cudaError_t launch_sur_step_begin(const double* wrench, double* saved, int n6, c
                                   cudaStream_t s);
 cudaError_t launch_sur_step_restore(double* wrench, const double* saved, int n6, uint32_t* counter,
                                     const uint32_t* words, cudaStream_t s);
-// Scratch of the surrogate's sums: per-block totals and the last-block ticket (reductions launch at most
-// kReduceBlocks blocks).
-constexpr int kReduceBlocks = 304;
+// Scratch of the gate's one-launch check: per-block totals and the last-block ticket (reductions launch at
+// most kReduceBlocks blocks: 8 resident 256-thread blocks on each of the 152 SMs).
+constexpr int kReduceBlocks = 152 * 8;
 struct ReduceScratch {
-    double* partials;  // kReduceBlocks x 4
+    Pair* partials;    // kReduceBlocks x 4 per-block totals
     uint32_t* ticket;  // zero between launches
 };
+// The surrogate's sums are added to `sums` (FP64, one atomic per component per block of FP32-pair totals):
+// the transfer's mass and momentum (before the grid update), the updated grid's momentum over the box
+// (with the network input), the corrected grid's momentum.
 cudaError_t launch_sur_moments(const float4* grid, const uint32_t* list, const uint32_t* count, int nbins_cap,
-                               double* sums, const ReduceScratch& r, cudaStream_t s);
+                               double* sums, cudaStream_t s);
 cudaError_t launch_sur_features(const float4* grid, int n, int nb, const SurBox& box, float m_scale,
-                                float v_scale, float* feat, uint8_t* mask, double* sums, const ReduceScratch& r,
-                                cudaStream_t s, void* feat_bf16 = nullptr);
+                                float v_scale, float* feat, uint8_t* mask, double* sums, cudaStream_t s,
+                                void* feat_bf16 = nullptr);
 cudaError_t launch_sur_correct(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
-                               float unit, int apply, double* sums, const ReduceScratch& r, cudaStream_t s);
+                               float unit, int apply, double* sums, cudaStream_t s);
 cudaError_t launch_wrench_extrapolate(double* wrench, const double* before, int n6, double extra, cudaStream_t s,
                                       const uint32_t* gate = nullptr, uint32_t gate_run = 1);
 // The device-side gate of a window: from the sums (M, P0, P1, P_hat) the mass and momentum residuals;
@@ -235,19 +238,15 @@ cudaError_t launch_sur_check_gate(const float4* grid, int n, int nb, int bound, 
                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
                                   uint32_t* gate, unsigned long long* stats, uint32_t* any_failed, const ReduceScratch& r,
                                   cudaStream_t s);
-// Per-step gate mode in one launch: the corrected grid written back, its momentum summed, and the last
-// block deciding the gate (as launch_sur_check_gate) besides the counter and impulse bookkeeping of
-// launch_sur_apply.
-cudaError_t launch_sur_apply_check(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv,
-                                   float unit, double* sums, double m_particles, int k, double v_ref, double threshold,
-                                   uint32_t* gate, unsigned long long* stats, uint32_t* any_failed,
-                                   const ReduceScratch& r, uint32_t* counter, double* wrench,
-                                   const double* wrench_before, int n6, cudaStream_t s);
+// The per-step gate over nwin windows whose sums are slots[10 w .. 10 w + 10): any_failed = 1 if one fails;
+// stats[0] += nwin, stats[2..3] the last window's residuals; the slots are zeroed.
+cudaError_t launch_sur_decide(double* slots, int nwin, double m_particles, int k, double v_ref, double threshold,
+                              unsigned long long* stats, uint32_t* any_failed, cudaStream_t s);
 // The correction written back (only if *gate == 1 when gate is set), with the window's substep-counter and
-// body-impulse bookkeeping.
+// body-impulse bookkeeping; with sums, the corrected grid's momentum is added to sums[0..3).
 cudaError_t launch_sur_apply(float4* grid, int n, int nb, int bound, const SurBox& box, const float* dv, float unit,
                              const uint32_t* gate, uint32_t* counter, int k, double* wrench,
-                             const double* wrench_before, int n6, cudaStream_t s);
+                             const double* wrench_before, int n6, cudaStream_t s, double* sums = nullptr);
 cudaError_t launch_advance_counter_gated(uint32_t* counter, int n, const uint32_t* gate, uint32_t gate_run,
                                          cudaStream_t s);
 cudaError_t launch_cast_to_bf16(int n, const float* src, void* dst, cudaStream_t s);

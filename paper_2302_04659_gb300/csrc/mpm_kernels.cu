@@ -982,7 +982,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
     }
     const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
     constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
-    double p0[4] = {0.0, 0.0, 0.0, 0.0};  // mass and momentum of the transfer (for a surrogate's gate)
+    Pair p0[4] = {};  // mass and momentum of the transfer (for a surrogate's gate)
     for (uint32_t item = (uint32_t)(cta * 4 + grp); item < n_old + n_new; item += (uint32_t)(p.ctas * 4)) {
         // item, and so env and bin, are uniform across each warp
         const bool is_old = item < n_old;
@@ -998,10 +998,12 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         const Geometry& g = E.geo;
         float4* node = &p.grid[E.node_base + (size_t)lb * kBlkNodes + ln];
         const float4 gv = *node;
-        p0[0] += gv.x;
-        p0[1] += gv.y;
-        p0[2] += gv.z;
-        p0[3] += gv.w;
+        if (p.p0_sums) {  // (uniform)
+            p0[0] = pair_add(p0[0], gv.x);
+            p0[1] = pair_add(p0[1], gv.y);
+            p0[2] = pair_add(p0[2], gv.z);
+            p0[3] = pair_add(p0[3], gv.w);
+        }
         const bool has_mass = gv.x > 0.0f;
         const float m = gv.x;
         const float im = has_mass ? 1.0f / m : 0.0f;
@@ -1074,20 +1076,20 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
         *node = make_float4(v[0], v[1], v[2], m);
     }
-    if (p.p0_sums) {  // (uniform) this CTA's sums, one FP64 atomic per component
-        __shared__ double ps[8][4];
+    if (p.p0_sums) {  // (uniform) this CTA's sums as FP32 pairs, one FP64 atomic per component
+        __shared__ Pair ps[8][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) p0[q] += __shfl_xor_sync(0xffffffffu, p0[q], off);
+            for (int off = 16; off > 0; off >>= 1) p0[q] = pair_add(p0[q], pair_shfl_xor(p0[q], off));
         if (lane == 0)
 #pragma unroll
             for (int q = 0; q < 4; ++q) ps[threadIdx.x >> 5][q] = p0[q];
         __syncthreads();
         if (threadIdx.x < 4) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ps[w][threadIdx.x];
-            if (t != 0.0) atomicAdd(&p.p0_sums[threadIdx.x], t);
+            Pair t{0.0f, 0.0f};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = pair_add(t, ps[w][threadIdx.x]);
+            if (t.hi != 0.0f) atomicAdd(&p.p0_sums[threadIdx.x], pair_value(t));
         }
     }
     __syncthreads();
