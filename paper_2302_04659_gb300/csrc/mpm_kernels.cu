@@ -103,6 +103,10 @@ __device__ __forceinline__ int round_fixed(float x) {
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
+// Layers of the class-layered order a chunk gives the particles that stay in its bin: one per particle
+// of a class at most, so as many as a chunk holds particles.
+constexpr int kLayers = kChunk;
+
 struct __align__(16) ScatterTile {
     int m[kScatterNodes];
     int px[kScatterNodes];
@@ -110,6 +114,9 @@ struct __align__(16) ScatterTile {
     int pz[kScatterNodes];
     uint32_t touched[27];
     uint32_t bound_bits;  // max over the chunk of B_p, as FP32 bits (non-negative floats order as integers)
+    uint32_t class_count[32];      // staying particles per bank class so far
+    uint32_t layer_mask[kLayers];  // per layer, its classes
+    uint32_t stay_base;            // the staying group's first rank in the bin
 };
 
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
@@ -230,6 +237,8 @@ __device__ __forceinline__ void tile_clear(ScatterTile& T) {
     for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) q[t] = make_int4(0, 0, 0, 0);
     if (threadIdx.x < 27) T.touched[threadIdx.x] = 0u;
     if (threadIdx.x == 0) T.bound_bits = 0u;
+    if (threadIdx.x < 32) T.class_count[threadIdx.x] = 0u;
+    for (int t = threadIdx.x; t < kLayers; t += blockDim.x) T.layer_mask[t] = 0u;
 }
 
 // CTA-wide max of the particle bounds into T.bound_bits; every thread of the CTA must call it.
@@ -751,6 +760,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
     // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
     __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
     __shared__ ScatterTile T;
+    static_assert(CTA <= kLayers, "a cell's layer index stays below kLayers");
     __shared__ EnvDesc Es[2];  // several envs: the current chunk's env and the next one's
     __shared__ ColliderNow cs[PEN ? kSharedPoses : 1];
     __shared__ float cw[PEN ? kSharedPoses * 6 : 1];
@@ -911,18 +921,43 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
             }
         }
         if (active) bp = particle_bound(E.mat.p_mass, vn, A, g.dx);
-        // rank within the new bin: the atomic's result is only stored after the scatter, so its round
-        // trip overlaps the work in between
-        const uint32_t rank = warp_hist_add(p.hist, newkey, true);
+        // Rank within the new bin. The 64 cells of a bin fall in 32 bank classes (x index mod 2, y, z): for
+        // every stencil offset, tile nodes of cells in different classes lie in different banks (tile_slot).
+        // The particles that stay in the chunk's bin take consecutive ranks in class-layered order: layer r
+        // holds the r-th staying particle (in slot order) of each class, the classes in a fixed order; so
+        // while layers are full, any 32 consecutive ranks -- a warp of the next substep, wherever the group
+        // starts -- hold 32 classes and gather and scatter without bank conflicts. The others take a
+        // warp-aggregated rank. The atomics' results are only stored after the scatter, so their round
+        // trips overlap the work in between.
+        const bool stay = p.scatter && active && newkey == (uint32_t)ch.x;
+        uint32_t class_key = 0;  // layer * 32 + class
+        if (stay) {
+            const int c0 = cell_base(xn[0], g.inv_dx) - ox, c1 = cell_base(xn[1], g.inv_dx) - oy,
+                      c2 = cell_base(xn[2], g.inv_dx) - oz;  // each in 0..3: xn is in this bin
+            const uint32_t cls = (uint32_t)(((c0 & 1) * 4 + c1) * 4 + c2);
+            const uint32_t lay = atomicAdd(&T.class_count[cls], 1u);  // < particles in the chunk
+            atomicOr(&T.layer_mask[lay], 1u << cls);
+            class_key = lay * 32u + cls;
+        }
+        // (a staying particle's rank is its layered position until the group's base is known)
+        uint32_t rank = warp_hist_add(p.hist, stay ? 0xffffffffu : newkey, true);
         if (p.scatter) {
             tile_bound(T, bp);
-            __syncthreads();
+            const int nstay = __syncthreads_count(stay);
+            if (threadIdx.x == 0 && nstay > 0) T.stay_base = atomicAdd(&p.hist[ch.x], (uint32_t)nstay);
+            if (stay) {  // the earlier layers, then this layer's classes before this one
+                const uint32_t lay = class_key >> 5, cls = class_key & 31u;
+                uint32_t pos = 0;
+                for (uint32_t q = 0; q < lay; ++q) pos += __popc(T.layer_mask[q]);
+                rank = pos + __popc(T.layer_mask[lay] & ((1u << cls) - 1u));
+            }
             // ---- P2G of the new state into the next grid
             const int k = momentum_scale_exp(T.bound_bits);
             const int o[3] = {ox - 1, oy - 1, oz - 1};
             if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, pow2f(k));
-            if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
+            if (active && !stay) p.keyrank_out[slot] = make_uint2(newkey, rank);
             __syncthreads();
+            if (stay) p.keyrank_out[slot] = make_uint2(newkey, T.stay_base + rank);
             tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
         } else if (active) {
             p.keyrank_out[slot] = make_uint2(newkey, rank);
