@@ -92,15 +92,16 @@ __device__ __forceinline__ void load_env(EnvDesc& dst, const EnvDesc* envs, int 
 //             per-particle magnitude B_p = max_a (m |v_a| + 1.5 dx sum_c |A_ac|) of the chunk, so every node
 //             sum stays below 108 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term,
 //             comparable to an FP32 accumulation of the same terms. Every scaled term is below 2^22, so it
-//             is rounded to an integer by one FP32 add (round_fixed).
+//             is rounded to an integer by one FP32 fused multiply-add (round_fixed_mul).
 // The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
 
 constexpr int kMassBits = 22;
 
-// round(x) for |x| < 2^22 with one FP32 add: x + 1.5 * 2^23 lands where one unit is one ulp, so the
-// low mantissa bits hold round-to-nearest-even(x), offset by the constant's own bit pattern.
-__device__ __forceinline__ int round_fixed(float x) {
-    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+// round(a b) for |a b| < 2^22 with one FP32 fused multiply-add: a b + 1.5 * 2^23 lands where one unit is
+// one ulp, so the low mantissa bits hold round-to-nearest-even of the exact product, offset by the
+// constant's own bit pattern.
+__device__ __forceinline__ int round_fixed_mul(float a, float b) {
+    return __float_as_int(__fmaf_rn(a, b, 12582912.0f)) - 0x4B400000;
 }
 
 // Layers of the class-layered order a chunk gives the particles that stay in its bin: one per particle
@@ -201,10 +202,10 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
                 for (int k = 0; k < 3; ++k) {
                     const float wk = wij * w[2][k];
                     const int t = tile_slot(l0 + i, l1 + j, l2 + k);
-                    atomicAdd(&T.m[t], round_fixed(wijm * w[2][k]));
-                    atomicAdd(&T.px[t], round_fixed(wk * (mij[0] + k * Ad[2][0])));
-                    atomicAdd(&T.py[t], round_fixed(wk * (mij[1] + k * Ad[2][1])));
-                    atomicAdd(&T.pz[t], round_fixed(wk * (mij[2] + k * Ad[2][2])));
+                    atomicAdd(&T.m[t], round_fixed_mul(wijm, w[2][k]));
+                    atomicAdd(&T.px[t], round_fixed_mul(wk, mij[0] + k * Ad[2][0]));
+                    atomicAdd(&T.py[t], round_fixed_mul(wk, mij[1] + k * Ad[2][1]));
+                    atomicAdd(&T.pz[t], round_fixed_mul(wk, mij[2] + k * Ad[2][2]));
                 }
             }
         return 0;
@@ -842,27 +843,41 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
                 l1 = min(max(l1, 0), 3);
                 l2 = min(max(l2, 0), 3);
             }
-            // 27 independent weighted reads into 12 accumulators: M[a][c] = sum_ijk w (index_c) v_a
+            // 27 weighted reads into 12 sums, M[a][c] = sum_ijk w_i w_j w_k (index_c) v_a and v, contracted
+            // one axis at a time: over k the sums with weights w_k and k w_k, over j with w_j and j w_j,
+            // over i with w_i and i w_i
             float M[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i) {
+                float b0[3] = {0.0f, 0.0f, 0.0f}, bj[3] = {0.0f, 0.0f, 0.0f}, bk[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const float wij = w3[0][i] * w3[1][j];
+                    float a0[3] = {0.0f, 0.0f, 0.0f}, ak[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const float wk = wij * w3[2][k];
                         const int s = tile_slot(l0 + i, l1 + j, l2 + k);
-                        const float wv[3] = {wk * Gx[s], wk * Gy[s], wk * Gz[s]};
+                        const float gv[3] = {Gx[s], Gy[s], Gz[s]};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            vn[a] += wv[a];
-                            if (i) M[a][0] += (float)i * wv[a];
-                            if (j) M[a][1] += (float)j * wv[a];
-                            if (k) M[a][2] += (float)k * wv[a];
+                            a0[a] = fmaf(w3[2][k], gv[a], a0[a]);
+                            if (k) ak[a] = fmaf((float)k * w3[2][k], gv[a], ak[a]);
                         }
                     }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        b0[a] = fmaf(w3[1][j], a0[a], b0[a]);
+                        bk[a] = fmaf(w3[1][j], ak[a], bk[a]);
+                        if (j) bj[a] = fmaf((float)j * w3[1][j], a0[a], bj[a]);
+                    }
                 }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    vn[a] = fmaf(w3[0][i], b0[a], vn[a]);
+                    if (i) M[a][0] = fmaf((float)i * w3[0][i], b0[a], M[a][0]);
+                    M[a][1] = fmaf(w3[0][i], bj[a], M[a][1]);
+                    M[a][2] = fmaf(w3[0][i], bk[a], M[a][2]);
+                }
+            }
             float Cn[3][3];
             const float cs = 4.0f * g.inv_dx;
 #pragma unroll
