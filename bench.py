@@ -64,8 +64,8 @@ def kernel_source_hash() -> str:
 
 
 # FP32 flops per particle-substep of the fused kernel (FMA counted as 2): ncu instruction counters of
-# the 600k-particle pinch capture, 8.22e8 flops per launch / 600,000 particles.
-FP32_FLOPS_PER_PARTICLE_SUBSTEP = 1370
+# the 600k-particle pinch capture, 8.30e8 flops per launch / 600,000 particles.
+FP32_FLOPS_PER_PARTICLE_SUBSTEP = 1383
 
 
 def fp32_peak_tflops(sm_mhz: float | None) -> float:
