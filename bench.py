@@ -31,6 +31,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -55,11 +56,16 @@ def env_rank():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources the fused substep kernel (k_g2p2g) is compiled from."""
+    """Hash of the code of the sources the fused substep kernel (k_g2p2g) is compiled from: comments,
+    blank lines and trailing spaces are left out, so a change of wording alone keeps the hash."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
     for fn in ("mpm_device.cuh", "mpm_internal.h", "mpm_kernels.cu"):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+        src = open(os.path.join(csrc, fn), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

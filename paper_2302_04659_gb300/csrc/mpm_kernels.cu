@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(kScanTile) k_scan_apply(ScanParams p) {
 }
 
 // Sorted slot of particle j: slot = start of its bin + its rank within the bin. The rank was handed out
-// when the particle's bin count was taken (one atomic per warp and bin, lanes ranked in order), so this
-// pass needs no atomics.
+// with the particle's bin count (a chunk's staying particles from one atomic per chunk, in class-layered
+// order; the others one atomic per warp and bin), so this pass needs no atomics.
 __device__ __forceinline__ void assign_slot(int j, int N, const uint2* __restrict__ keyrank,
                                             const uint32_t* __restrict__ cursor, uint32_t* __restrict__ perm) {
     if (j >= N) return;
