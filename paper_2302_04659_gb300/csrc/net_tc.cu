@@ -551,28 +551,40 @@ __global__ void k_pack(const __nv_bfloat16* __restrict__ w, int cin, int cout, i
 // Per tile: the Chebyshev distance (in voxels, capped at kDistCap) from the tile to the nearest voxel
 // whose mask byte is set.
 constexpr int kDistCap = 4;
-__global__ void k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mask, uint8_t* __restrict__ dist) {
+constexpr int kDistThreads = 256;
+__global__ void __launch_bounds__(kDistThreads, 4) k_tile_dist(int D, int H, int W, const uint8_t* __restrict__ mask,
+                                                               uint8_t* __restrict__ dist) {
     const int tx = (W + TX - 1) / TX, ty = (H + TY - 1) / TY, tiles = tx * ty * D;
     constexpr int R = kDistCap;
     constexpr int EZ = 1 + 2 * R, EY = TY + 2 * R, EX = TX + 2 * R;
+    constexpr int NE = EZ * EY * EX, PER = (NE + kDistThreads - 1) / kDistThreads;
+    __shared__ int wmin[kDistThreads / 32];
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
-        int best = R + 1;
-        for (int i = threadIdx.x; i < EZ * EY * EX; i += blockDim.x) {
+        // this thread's voxels of the expanded box: their distances to the tile, and every mask byte
+        // requested before any is used
+        uint8_t dv[PER], m[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = (int)threadIdx.x + k * kDistThreads;
             const int z = z0 - R + i / (EY * EX), y = y0 - R + (i / EX) % EY, xx = x0 - R + i % EX;
-            if (z < 0 || z >= D || y < 0 || y >= H || xx < 0 || xx >= W || !mask[((size_t)z * H + y) * W + xx]) continue;
+            const bool in = i < NE && z >= 0 && z < D && y >= 0 && y < H && xx >= 0 && xx < W;
             const int dz = z < z0 ? z0 - z : (z > z0 ? z - z0 : 0);
             const int dy = y < y0 ? y0 - y : (y >= y0 + TY ? y - (y0 + TY - 1) : 0);
             const int dx = xx < x0 ? x0 - xx : (xx >= x0 + TX ? xx - (x0 + TX - 1) : 0);
-            best = min(best, max(dz, max(dy, dx)));
+            dv[k] = (uint8_t)max(dz, max(dy, dx));  // <= R inside the expanded box
+            m[k] = in ? mask[((size_t)z * H + y) * W + xx] : (uint8_t)0;
         }
+        int best = R + 1;
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (m[k]) best = min(best, (int)dv[k]);
         for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-        __shared__ int wmin[8];
         if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
             int b = R + 1;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = min(b, wmin[w]);
+            for (int w = 0; w < kDistThreads / 32; ++w) b = min(b, wmin[w]);
             dist[tile] = (uint8_t)b;
         }
         __syncthreads();
@@ -658,7 +670,7 @@ int mpm_conv3d_tc_tile_count(int D, int H, int W) {
 mpm_status mpm_conv3d_tc_tile_dist(int D, int H, int W, const uint8_t* mask, uint8_t* dist, void* stream) {
     if (D <= 0 || H <= 0 || W <= 0 || !mask || !dist) return MPM_ERR_INVALID_ARG;
     const int tiles = mpm_conv3d_tc_tile_count(D, H, W);
-    k_tile_dist<<<std::min(tiles, 8192), 256, 0, static_cast<cudaStream_t>(stream)>>>(D, H, W, mask, dist);
+    k_tile_dist<<<std::min(tiles, 8192), kDistThreads, 0, static_cast<cudaStream_t>(stream)>>>(D, H, W, mask, dist);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_tc_tile_dist");
 }
