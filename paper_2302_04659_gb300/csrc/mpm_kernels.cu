@@ -977,7 +977,11 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         } else if (active) {
             p.keyrank_out[slot] = make_uint2(newkey, rank);
         }
-        __syncthreads();
+        // With the scatter, the barriers above already order this chunk's reads of the shared tiles before
+        // the next chunk's writes: the gather tile is last read before the bound barrier, the scatter tile
+        // before the flush's barrier, and a thread clearing T.touched[t] is the one that read it. Without
+        // the scatter, the next gather tile must wait here.
+        if (!p.scatter) __syncthreads();
     }
     if constexpr (PEN)
         if (pen && shared_poses) penalty_end(p, cw);
