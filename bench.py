@@ -262,26 +262,34 @@ def run_native(args):
     flags = sim.status()
     g_ms, g_n = ktime["g2p2g"]
     g_avg = g_ms / max(g_n, 1) / 1e3
-    # ---------------- end-to-end through the C-ABI with host buffers
-    e2e_steps = max(1, min(args.steps, 200)) if not args.no_e2e else 0
+    # ---------------- end-to-end through the C-ABI with host buffers: the same env steps as the device
+    # pass (same warm-up, L2 flushed before each step outside its events), each step's events bracketing
+    # the collider upload from pinned host memory, the substeps, and the read-back of the step's positions,
+    # impulses and substep count into page-locked host memory (asynchronous, in stream order: the host
+    # never waits inside the loop, the closing barrier waits for the last copy)
+    e2e_steps = args.steps if not args.no_e2e else 0
     x_h = torch.empty((3, N), dtype=torch.float32).pin_memory()
     wr_h = torch.empty((k, 6), dtype=torch.float64).pin_memory()
+    cnt_h = torch.empty(1, dtype=torch.int32).pin_memory()
     sim.set_particles(xd, vd, Cd, Fd)
-    for s in range(min(args.warmup, 3)):
+    for s in range(args.warmup):
         env_step(s)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
     for s in range(e2e_steps):
-        env_step(s)
-        mpm.mpm_read_state(sim.handle, x_h.data_ptr(), 0, 0, 0, 0, int(stream.cuda_stream))
-        mpm.mpm_read_wrench(sim.handle, wr_h.data_ptr(), int(stream.cuda_stream))
-    ev1.record(stream)
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        env_step(args.warmup + s)
+        mpm.mpm_read_state(sim.handle, x_h.data_ptr(), 0, 0, 0, 2, int(stream.cuda_stream))
+        mpm.mpm_read_wrench_async(sim.handle, wr_h.data_ptr(), cnt_h.data_ptr(), int(stream.cuda_stream))
+        ev[s][1].record(stream)
     barrier()
-    e2e_value = (job_throughput(N * SUBSTEPS * e2e_steps, ev0.elapsed_time(ev1) / 1e3, dev)[0]
+    e2e_value = (job_throughput(N * SUBSTEPS * e2e_steps, sum(a.elapsed_time(b) for a, b in ev) / 1e3, dev)[0]
                  if e2e_steps else None)
     h2d = k * (7 + 3 + 3 + 3) * 4
     d2h = 3 * N * 4 + k * 6 * 8 + 4
+    if e2e_steps and int(cnt_h[0]) != SUBSTEPS:  # the last step's read arrived: 25 substeps since its upload
+        raise RuntimeError(f"e2e read-back: substep count {int(cnt_h[0])}, expected {SUBSTEPS}")
     sim.close()
     if rank != 0:
         if world > 1:
@@ -316,7 +324,9 @@ def run_native(args):
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e2e_steps,
+                "what": "collider upload from pinned host memory + 25 substeps + positions, impulses and substep "
+                        "count read back to page-locked host memory, per env step, L2 flushed between steps"},
         "gpu_launches": launches,
         "plain_launches": {"value": N * SUBSTEPS * args.steps / elapsed_plain, "unit": UNIT,
                            "ms_per_step": elapsed_plain / args.steps * 1e3,

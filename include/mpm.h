@@ -192,7 +192,10 @@ mpm_status mpm_set_contact(mpm_sim* sim, int mode, float stiffness, float dampin
 
 /* Particle state in the caller's original order. Any pointer may be NULL (skipped). Arrays SoA with
  * stride n. dst_on_device = 1: written on `stream` (the paper's single GPU-GPU copy), no sync.
- * dst_on_device = 0: host memory, the call synchronizes `stream`. A fluid reports F = J^(1/3) I. */
+ * dst_on_device = 0: host memory, the call synchronizes `stream`. dst_on_device = 2: page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister), the copies enqueued on `stream` without waiting: the arrays
+ * hold the state once `stream` reaches this call (MPM_ERR_INVALID_ARG for other memory). A fluid
+ * reports F = J^(1/3) I. */
 mpm_status mpm_read_state(mpm_sim* sim, float* x, float* v, float* C, float* F, int dst_on_device,
                           void* stream);
 
@@ -201,6 +204,12 @@ mpm_status mpm_read_state(mpm_sim* sim, float* x, float* v, float* C, float* F, 
  * material since the last mpm_set_colliders, as k x 6 doubles in host memory; *n_substeps (may be NULL) gets
  * the substeps accumulated, so the mean force is impulse / (n_substeps * dt). Synchronizes `stream`. */
 mpm_status mpm_read_wrench(mpm_sim* sim, double* impulse_torque, int* n_substeps, void* stream);
+
+/* mpm_read_wrench into page-locked host memory, enqueued on `stream` without waiting: impulse_torque
+ * (k x 6 doubles) and *n_substeps (may be NULL) hold the values once `stream` reaches this call. A loop
+ * that reads every step's impulses back can so keep the device busy. MPM_ERR_INVALID_ARG if a destination
+ * is not page-locked. */
+mpm_status mpm_read_wrench_async(mpm_sim* sim, double* impulse_torque, unsigned* n_substeps, void* stream);
 
 /* Sticky device flags (MPM_FLAG_*), ORed since creation or the last clear. Synchronizes `stream`. */
 mpm_status mpm_get_status(mpm_sim* sim, unsigned* flags, int clear, void* stream);

@@ -122,6 +122,7 @@ def _load():
         "mpm_substep": (st, [_vp, ctypes.c_int, _vp]),
         "mpm_read_state": (st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "mpm_read_wrench": (st, [_vp, _vp, ctypes.POINTER(ctypes.c_int), _vp]),
+        "mpm_read_wrench_async": (st, [_vp, _vp, _vp, _vp]),
         "mpm_get_status": (st, [_vp, ctypes.POINTER(ctypes.c_uint), ctypes.c_int, _vp]),
         "mpm_num_particles": (ctypes.c_int, [_vp]),
         "mpm_read_grid": (st, [_vp, _vp, _vp]),
@@ -300,6 +301,11 @@ def mpm_read_wrench(sim: int, out: int, stream: int = 0) -> int:
     n = ctypes.c_int(0)
     _check("mpm_read_wrench", _load().mpm_read_wrench(sim, out or None, ctypes.byref(n), stream))
     return n.value
+
+
+def mpm_read_wrench_async(sim: int, out: int, n_substeps: int, stream: int = 0) -> None:
+    """Enqueue the wrench and substep count into page-locked host memory (pointers), without waiting."""
+    _check("mpm_read_wrench_async", _load().mpm_read_wrench_async(sim, out or None, n_substeps or None, stream))
 
 
 def mpm_get_status(sim: int, clear: int = 0, stream: int = 0) -> int:

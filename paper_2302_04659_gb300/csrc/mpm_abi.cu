@@ -1041,14 +1041,27 @@ mpm_status mpm_get_launch(const mpm_sim* s, int* chunk, int* fused_ctas_per_sm, 
     return MPM_OK;
 }
 
+// Page-locked host memory (a destination the device copies into without the host waiting).
+static bool page_locked(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // (not a pointer the runtime knows: clear the error)
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, int dst_on_device, void* stream) {
-    if (!s) return MPM_ERR_INVALID_ARG;
+    if (!s || dst_on_device < 0 || dst_on_device > 2) return MPM_ERR_INVALID_ARG;
+    if (dst_on_device == 2)
+        for (const float* d : {x, v, C, F})
+            if (d && !page_locked(d)) return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (s->N == 0) return MPM_OK;
     const size_t N = (size_t)s->N;
     StateView src = s->view(s->ps.cur);
-    if (dst_on_device) {
+    if (dst_on_device == 1) {
         return launch(s, MPM_K_READ, st, [&] {
             return launch_read_state(s->N, s->envs_dev(), s->nenv, src, x, v, C, F, st);
         }, "read_state");
@@ -1062,7 +1075,9 @@ mpm_status mpm_read_state(mpm_sim* s, float* x, float* v, float* C, float* F, in
     if (v) MPM_CUDA(cudaMemcpyAsync(v, stage.v, 3 * N * 4, cudaMemcpyDeviceToHost, st), "copy v");
     if (C) MPM_CUDA(cudaMemcpyAsync(C, stage.C, 9 * N * 4, cudaMemcpyDeviceToHost, st), "copy C");
     if (F) MPM_CUDA(cudaMemcpyAsync(F, stage.F, 9 * N * 4, cudaMemcpyDeviceToHost, st), "copy F");
-    MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    // (page-locked destinations: the copies finish in stream order, before the next launch reuses the
+    // staging buffer)
+    if (dst_on_device == 0) MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return MPM_OK;
 }
 
@@ -1078,6 +1093,20 @@ mpm_status mpm_read_wrench(mpm_sim* s, double* out, int* n_substeps, void* strea
     MPM_CUDA(cudaMemcpyAsync(&cnt, s->substep_counter(), 4, cudaMemcpyDeviceToHost, st), "copy counter");
     MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     if (n_substeps) *n_substeps = (int)cnt;
+    return MPM_OK;
+}
+
+mpm_status mpm_read_wrench_async(mpm_sim* s, double* out, unsigned* n_substeps, void* stream) {
+    if (!s || (s->ncol > 0 && (!out || !page_locked(out))) || (n_substeps && !page_locked(n_substeps)))
+        return MPM_ERR_INVALID_ARG;
+    MPM_TRY(resolve_pending(s));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (s->ncol > 0)
+        MPM_CUDA(cudaMemcpyAsync(out, s->at<double>(s->L.wrench), s->ncol * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 st),
+                 "copy wrench");
+    if (n_substeps)
+        MPM_CUDA(cudaMemcpyAsync(n_substeps, s->substep_counter(), 4, cudaMemcpyDeviceToHost, st), "copy counter");
     return MPM_OK;
 }
 

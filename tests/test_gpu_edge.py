@@ -132,6 +132,40 @@ def test_device_io_matches_host_io():
     sim.close()
 
 
+def test_async_host_reads_match_blocking_reads():
+    """Reads into page-locked host memory, enqueued without waiting, hold what the blocking reads return
+    once the stream has reached them -- also when the next substeps are already queued behind them;
+    pageable destinations are refused."""
+    sc = scenes.pinch_scene(seed=1003, N=20000)
+    pose, lin, ang, com = scenes.finger_state(sc, 0.1)
+    sim = make_sim(sc)
+    sim.set_particles(sc.x, sc.v, sc.C, sc.F)
+    sim.set_shapes(sc.shapes)
+    sim.set_colliders(pose, lin, ang, com)
+    sim.substep(7)
+    h = sim.read_state(on_device=False)
+    w, n = sim.read_wrench()
+    st = torch.cuda.current_stream().cuda_stream
+    x_p = torch.empty((3, sc.N), dtype=torch.float32).pin_memory()
+    F_p = torch.empty((9, sc.N), dtype=torch.float32).pin_memory()
+    w_p = torch.empty((len(sc.shapes), 6), dtype=torch.float64).pin_memory()
+    n_p = torch.zeros(1, dtype=torch.int32).pin_memory()
+    mpm.mpm_read_state(sim.handle, x_p.data_ptr(), 0, 0, F_p.data_ptr(), 2, st)
+    mpm.mpm_read_wrench_async(sim.handle, w_p.data_ptr(), n_p.data_ptr(), st)
+    sim.substep(3)  # queued behind the reads: it reuses the staging buffer the reads copy from
+    torch.cuda.synchronize()
+    assert np.array_equal(x_p.numpy(), h["x"]) and np.array_equal(F_p.numpy(), h["F"])
+    assert np.array_equal(w_p.numpy(), w) and int(n_p[0]) == n == 7
+    pageable = np.empty((3, sc.N), np.float32)
+    with pytest.raises(mpm.MpmError):
+        mpm.mpm_read_state(sim.handle, pageable.ctypes.data, 0, 0, 0, 2, st)
+    with pytest.raises(mpm.MpmError):
+        mpm.mpm_read_wrench_async(sim.handle, np.empty((2, 6)).ctypes.data, 0, st)
+    with pytest.raises(mpm.MpmError):
+        mpm.mpm_read_state(sim.handle, x_p.data_ptr(), 0, 0, 0, 3, st)
+    sim.close()
+
+
 def test_wrench_bookkeeping_and_timing():
     sc = scenes.pinch_scene(seed=1002, N=20000)
     pose, lin, ang, com = scenes.finger_state(sc, 0.2)
