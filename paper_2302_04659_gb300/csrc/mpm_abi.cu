@@ -378,6 +378,7 @@ GridParams grid_params(mpm_sim* s) {
     gp.grid = s->at<float4>(s->L.grid[s->ps.g]);
     gp.list = s->list(s->ps.g);
     gp.list_count = s->list_count(s->ps.g);
+    gp.list_cap = (int)s->T.bins;
     gp.grid_old = s->at<float4>(s->L.grid[1 - s->ps.g]);
     gp.flags_old = s->at<uint32_t>(s->L.flags[1 - s->ps.g]);
     gp.list_old = s->list(1 - s->ps.g);

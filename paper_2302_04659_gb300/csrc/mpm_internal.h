@@ -129,6 +129,7 @@ struct GridParams {
     float4* grid;             // (m, mv) in, (v, m) out
     const uint32_t* list;     // active bins of grid (packed) and their count
     const uint32_t* list_count;
+    int list_cap;             // entries either bin list can hold
     float4* grid_old;         // the previous grid, zeroed here (its active bins) for its next use
     uint32_t* flags_old;      // its bin flags, cleared
     const uint32_t* list_old;

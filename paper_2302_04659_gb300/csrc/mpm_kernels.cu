@@ -1027,6 +1027,14 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
     __shared__ ColliderNow cs[SHARED_POSES ? kSharedPoses : 1];
     __shared__ float cw[SHARED_POSES ? kSharedPoses * 6 : 1];  // this CTA's wrench sums (few colliders)
     const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63, lane = threadIdx.x & 31;
+    // The group takes entry `item` of both bin lists per pass. The list counts and the first pass's
+    // entries (their index does not depend on the counts) are requested before the pose evaluation and
+    // its barrier, so the first node load waits for one round trip less.
+    const uint32_t stride = (uint32_t)(p.ctas * 4);
+    uint32_t item = (uint32_t)(cta * 4 + grp);
+    uint32_t e_old = item < (uint32_t)p.list_cap ? p.list_old[item] : 0u;
+    uint32_t e_new = item < (uint32_t)p.list_cap ? p.list[item] : 0u;
+    const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
     const uint32_t step = *p.substep_counter;
     constexpr bool shared_poses = SHARED_POSES;
     if (shared_poses && p.grid_colliders) {
@@ -1034,21 +1042,28 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         if ((int)threadIdx.x < p.k_total * 6) cw[threadIdx.x] = 0.0f;
         __syncthreads();
     }
-    const uint32_t n_old = *p.list_count_old, n_new = *p.list_count;
     constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
     Pair p0[4] = {};  // mass and momentum of the transfer (for a surrogate's gate)
-    for (uint32_t item = (uint32_t)(cta * 4 + grp); item < n_old + n_new; item += (uint32_t)(p.ctas * 4)) {
+    for (; item < max(n_old, n_new); item += stride) {
         // item, and so env and bin, are uniform across each warp
-        const bool is_old = item < n_old;
-        const uint32_t entry = is_old ? p.list_old[item] : p.list[item - n_old];
+        if (item < n_old) {  // a bin of the previous grid: zeroed for its next use
+            const uint32_t lbo = e_old & kLocalMask;
+            const EnvDesc& Eo = bin_env_desc<ONE_ENV>(p, (int)(e_old >> kLocalBinBits));
+            p.grid_old[Eo.node_base + (size_t)lbo * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (ln == 0) p.flags_old[Eo.bin_base + lbo] = 0u;
+        }
+        const uint32_t nx = item + stride;  // the next pass's entries, requested early
+        const uint32_t e_old_next = nx < n_old ? p.list_old[nx] : 0u;
+        if (item >= n_new) {
+            e_old = e_old_next;
+            continue;
+        }
+        const uint32_t entry = e_new;
+        e_new = nx < n_new ? p.list[nx] : 0u;
+        e_old = e_old_next;
         const int env = (int)(entry >> kLocalBinBits);
         const uint32_t lb = entry & kLocalMask;
         const EnvDesc& E = bin_env_desc<ONE_ENV>(p, env);
-        if (is_old) {
-            p.grid_old[E.node_base + (size_t)lb * kBlkNodes + ln] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (ln == 0) p.flags_old[E.bin_base + lb] = 0u;
-            continue;
-        }
         const Geometry& g = E.geo;
         float4* node = &p.grid[E.node_base + (size_t)lb * kBlkNodes + ln];
         const float4 gv = *node;
