@@ -69,6 +69,9 @@ struct Layout {
         bin_env, colliders, poses, wrench, counters, sur, sur_reduce, total;
 };
 
+// Chunk list capacity: chunks of at least 32 particles, plus one partial chunk per bin.
+size_t chunk_entries(const Totals& T) { return std::max<size_t>(T.particles, 1) / 32 + T.bins + 1; }
+
 Layout make_layout(const Totals& T, int nenv) {
     Layout L{};
     size_t off = 0;
@@ -88,7 +91,7 @@ Layout make_layout(const Totals& T, int nenv) {
     L.list_meta = take(4 * sizeof(uint32_t));  // list counts [2], grid-update CTAs done, spare
     // everything from grid[0] up to here restarts from zero on mpm_set_particles
     L.cursor = take(T.bins * 4 + 16);
-    L.chunks = take((cap / 32 + T.bins + 1) * sizeof(int4));
+    L.chunks = take(chunk_entries(T) * sizeof(int4));
     L.tile_sums = take(((T.bins + kScanTile - 1) / kScanTile + 1) * sizeof(uint2));
     L.envs = take((size_t)nenv * sizeof(EnvDesc));
     L.bin_env = take(T.bins * 4 + 16);  // padded to a multiple of 4 bins, like the counts
@@ -346,6 +349,7 @@ TransferParams transfer_params(mpm_sim* s) {
     p.hist = s->at<uint32_t>(s->L.hist);
     p.chunks = s->at<int4>(s->L.chunks);
     p.num_chunks = s->num_chunks();
+    p.chunk_cap = (int)chunk_entries(s->T);
     p.status = s->status();
     p.substep_counter = s->substep_counter();
     p.tail_scan = s->tail_scan() ? 1 : 0;

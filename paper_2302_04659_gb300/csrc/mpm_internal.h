@@ -83,6 +83,7 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     uint32_t* list_count_out;
     const int4* chunks;     // (global bin, first sorted slot, count, env)
     const uint32_t* num_chunks;
+    int chunk_cap;          // entries the chunk list can hold
     uint32_t* status;
     uint32_t* substep_counter;
     // fused pass with few bins: the last CTA to finish scans `hist` into these (the same buffers as

@@ -777,8 +777,11 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
     const bool shared_poses = p.k_total <= kSharedPoses;
     const uint32_t step = pen ? *p.substep_counter : 0u;
     if (pen && shared_poses) penalty_begin(p, cs, cw, step, p.env0.geo.dt);
+    // the first chunk is requested with the count (its index does not depend on it), then dropped if
+    // past the end
+    int4 next = (int)blockIdx.x < p.chunk_cap ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
     const uint32_t nchunks = *p.num_chunks;
-    int4 next = blockIdx.x < nchunks ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
+    if (blockIdx.x >= nchunks) next = make_int4(0, 0, 0, 0);
     if constexpr (!ONE_ENV) {
         load_env(Es[0], p.envs, next.w);
         __syncthreads();
