@@ -55,18 +55,22 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def kernel_source_hash() -> str:
-    """Hash of the code of the sources the fused substep kernel (k_g2p2g) is compiled from: comments,
-    blank lines and trailing spaces are left out, so a change of wording alone keeps the hash."""
+def code_digest(sources) -> str:
+    """Hash of the code of C/CUDA source texts: comments, blank lines and trailing spaces are left out, so
+    a change of wording alone keeps the hash."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
-    for fn in ("mpm_device.cuh", "mpm_internal.h", "mpm_kernels.cu"):
-        src = open(os.path.join(csrc, fn), encoding="utf-8").read()
+    for src in sources:
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
-        h.update(code.encode())
+        h.update("\n".join(line.rstrip() for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash() -> str:
+    """code_digest of the sources the fused substep kernel (k_g2p2g) is compiled from."""
+    csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
+    return code_digest(open(os.path.join(csrc, fn), encoding="utf-8").read()
+                       for fn in ("mpm_device.cuh", "mpm_internal.h", "mpm_kernels.cu"))
 
 
 # FP32 flops per particle-substep of the fused kernel (FMA counted as 2): ncu instruction counters of

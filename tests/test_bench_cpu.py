@@ -1,0 +1,52 @@
+"""Host-side pieces of the benchmark that need no GPU: the code digest that keys the committed DRAM
+traffic figures to the kernel sources."""
+import importlib.util
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+SRC = """// header comment
+__global__ void k(float* a) {  // trailing comment
+    /* block
+       comment */ a[0] = 1.0f;
+}
+"""
+
+
+def test_code_digest_ignores_comments_and_blank_lines():
+    b = _bench()
+    base = b.code_digest([SRC])
+    assert b.code_digest([SRC.replace("// header comment", "// reworded header")]) == base
+    assert b.code_digest([SRC + "\n\n// a note\n/* another */\n"]) == base
+    assert b.code_digest([SRC.replace("trailing comment", "other words")]) == base
+
+
+def test_code_digest_tracks_code():
+    b = _bench()
+    base = b.code_digest([SRC])
+    assert b.code_digest([SRC.replace("1.0f", "2.0f")]) != base
+    assert b.code_digest([SRC + "\nint x;\n"]) != base
+    assert b.code_digest([SRC, ""]) == base  # an empty file adds no code
+    assert b.code_digest(["int a;", "int b;"]) != b.code_digest(["int b;", "int a;"])
+
+
+def test_traffic_record_names_its_kernel():
+    with open(os.path.join(ROOT, "profiles", "g2p2g_traffic.json")) as f:
+        rec = json.load(f)
+    assert rec["kernel"] == "k_g2p2g" and len(rec["kernel_source_hash"]) == 16
+    assert rec["dram_bytes_per_launch_full_size"] == rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
