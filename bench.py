@@ -66,6 +66,16 @@ def code_digest(sources) -> str:
     return h.hexdigest()[:16]
 
 
+FLAG_NAMES = {0x1: "clamped (a particle reached the 2 dx margin of the domain)",
+              0x2: "nonfinite", 0x4: "singular value clamped", 0x8: "far move (slow path)",
+              0x80000000: "internal"}
+
+
+def flag_names(flags: int):
+    """The sticky device flags (MPM_FLAG_*) set, by name."""
+    return [name for bit, name in FLAG_NAMES.items() if flags & bit]
+
+
 def kernel_source_hash() -> str:
     """code_digest of the sources the fused substep kernel (k_g2p2g) is compiled from."""
     csrc = os.path.join(ROOT, "paper_2302_04659_gb300", "csrc")
@@ -368,6 +378,7 @@ def run_native(args):
         },
         "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in ktime.items() if v[1]},
         "status_flags": flags,
+        "status_flags_set": flag_names(flags),
         "wall_s": wall,
     }
     line["clocks"] = clk.summary()
@@ -494,6 +505,7 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
         "launch_shape": {"chunk": shape_now[0], "fused_ctas_per_sm": shape_now[1], "grid_ctas_per_sm": shape_now[2]},
         "autotune": tuned,
         "status_flags": flags,
+        "status_flags_set": flag_names(flags),
         "clocks": clk.summary(),
         "input_generation_s": t_gen,
         "l2": "inputs larger than L2 (not flushed)",

@@ -50,3 +50,13 @@ def test_traffic_record_names_its_kernel():
         rec = json.load(f)
     assert rec["kernel"] == "k_g2p2g" and len(rec["kernel_source_hash"]) == 16
     assert rec["dram_bytes_per_launch_full_size"] == rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+
+
+def test_flag_names_match_the_header():
+    b = _bench()
+    from paper_2302_04659_gb300 import _native as mpm
+    assert b.flag_names(0) == []
+    assert b.flag_names(mpm.MPM_FLAG_CLAMPED)[0].startswith("clamped")
+    every = (mpm.MPM_FLAG_CLAMPED | mpm.MPM_FLAG_NONFINITE | mpm.MPM_FLAG_SV_CLAMPED | mpm.MPM_FLAG_FAR_MOVE
+             | mpm.MPM_FLAG_INTERNAL)
+    assert len(b.flag_names(every)) == 5
