@@ -190,6 +190,10 @@ __device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z
     }
 }
 
+// Programmatic dependent launch: wait for the previous launch's memory, and let the next one start.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void trigger_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // 4 input channels (the first layer), persistent, software-pipelined: while the tensor core runs the MMAs
 // of tile j (accumulator j % 2), the next tile's halo lands in the other plane buffer by asynchronous
 // 8-byte copies from all threads (a 4-channel voxel row is too narrow for a tensor-map copy), and the
@@ -232,6 +236,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(Args a, const __grid_co
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // The setup above touches no data of earlier launches (the weights are static), so with programmatic
+    // dependent launch it overlaps the end of the previous kernel; the input and the tile map are read
+    // only after the wait. The next launch may begin its own setup once every CTA is past this point.
+    grid_dependency_wait();
+    trigger_dependents();
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = instr_desc(TM, NPAD);
     const uint32_t planes_addr = smem_u32(planes), b_addr = smem_u32(bsm);
@@ -395,9 +404,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc_ring(Args a, const __gr
             tma_plane(planes_addr + b * kBuf + q * kPlaneBytes, &tmap, q * 8, x0 - 1, y0 - 1, z0 - 1, full);
     };
 
-    // the planes' zero padding (the dx over-read) in every buffer; zero outputs of skipped tiles
+    // The setup up to the wait touches no data of earlier launches (the weights are static), so with
+    // programmatic dependent launch it overlaps the end of the previous kernel; the tile map, the input
+    // halos and the outputs are touched only after the wait. The next launch may begin its own setup
+    // once every CTA is past the wait.
+    // the planes' zero padding (the dx over-read) in every buffer
     for (int i = tid; i < NB * kBuf / 16; i += kThreads)
         if ((i % (kBuf / 16)) % kPlaneVox >= HV) *reinterpret_cast<uint4*>(planes + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int k = 0; k < NB + 3; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_addr(k)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_addr(NB + 2)),
+                     "r"((uint32_t)(S * kBBlock))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(b_addr),
+            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(bar_addr(NB + 2))
+            : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    grid_dependency_wait();
+    trigger_dependents();
+    // zero outputs of skipped tiles
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
         if (needed(t)) continue;
         int z0, y0, x0;
@@ -414,25 +446,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc_ring(Args a, const __gr
     int pf = tiles;       // thread 0: the next tile to prefetch
     int issued = 0;       // thread 0: halo copies issued (copy q went to buffer q % NB, phase (q / NB) & 1)
     if (tid == 0) {
-        for (int k = 0; k < NB + 3; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_addr(k)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_addr(NB + 2)),
-                     "r"((uint32_t)(S * kBBlock))
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(b_addr),
-            "l"(a.wp), "r"((uint32_t)(S * kBBlock)), "r"(bar_addr(NB + 2))
-            : "memory");
         pf = advance(blockIdx.x);
         for (; issued < NB && pf < tiles; ++issued) {
             issue_halo(pf, issued);
             pf = advance(pf + gridDim.x);
         }
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeroed padding, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -636,8 +654,17 @@ cudaError_t launch(const Args& a, cudaStream_t s) {
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
-    kernel<<<grid, kThreads, smem, s>>>(a, map);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a, static_cast<const CUtensorMap>(map));
 }
 
 }  // namespace
