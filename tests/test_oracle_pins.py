@@ -396,6 +396,103 @@ def test_p2g_brute_force(kind):
     assert np.abs(grid.reshape(-1, 4) - ref).max() < 1e-12 * np.abs(ref).max()
 
 
+def _mls_energy(P, pc, s, node, disp, stencils):
+    """Total elastic energy sum_p V0 psi(F_p(x^)) after moving one grid node by `disp`, with each
+    particle's deformation gradient carried by the MLS-MPM update that the node positions define:
+    F_p(x^) = (I + D^-1 sum_i w_ip (x^_i - x_i)(x_i - x_p)^T) F_p, D^-1 = 4/dx^2 (Hu et al. 2018).
+    Only the moved node contributes to the sum. Plasticine: fixed-corotated psi through numpy's SVD;
+    fluid: psi(J) = lambda/2 (J - 1)^2 with J_p(x^) = J_p det(I + ...)."""
+    dx = 1.0 / P.n
+    Dinv = 4.0 / dx ** 2
+    E = 0.0
+    for p, (idx, w, d) in enumerate(stencils):
+        G = np.eye(3)
+        for q in range(27):
+            if idx[q] == node:
+                G = G + Dinv * w[q] * np.outer(disp, d[q])
+        if P.kind == oracle.PLASTICINE:
+            E += P.p_vol * _psi(pc.mu, pc.lam, G @ s.F[:, p].reshape(3, 3))
+        else:
+            J = s.J[p] * np.linalg.det(G)
+            E += P.p_vol * 0.5 * pc.lam * (J - 1.0) ** 2
+    return E
+
+
+@pytest.mark.parametrize("kind", [oracle.PLASTICINE, oracle.FLUID])
+def test_p2g_stress_momentum_is_minus_dt_energy_gradient(kind):
+    """The stress half of the particle-to-grid momentum (Algorithm 1's "forces"; MLS-MPM, Hu et al.
+    2018) is dt times the grid force f_i = -dE/dx^_i, the derivative of the total elastic energy with
+    respect to the node position taken here by central finite differences of E through the MLS
+    deformation-gradient update and numpy's SVD. With v = 0 and C = 0 the transfer's momentum is that
+    term alone, so this fixes its sign, the D^-1 = 4/dx^2 scale, V0, dt and tau = (dpsi/dF) F^T, none
+    of which the momentum-conservation pins can see."""
+    n, N = 8, 6
+    rng = np.random.default_rng(21)
+    dx = 1.0 / n
+    x = rng.uniform(2.2 * dx, 1 - 2.2 * dx, size=(3, N))
+    F = np.empty((9, N))
+    for p in range(N):
+        while True:
+            Fp = np.eye(3) + 0.15 * rng.normal(size=(3, 3))
+            if np.linalg.det(Fp) > 0.3:
+                break
+        F[:, p] = Fp.reshape(9)
+    J = rng.uniform(0.7, 1.3, size=N)
+    s = oracle.State.from_arrays(x, np.zeros((3, N)), np.zeros((9, N)), F if kind == oracle.PLASTICINE else None,
+                                 J if kind == oracle.FLUID else None)
+    P = oracle.Params(n=n, dt=1e-3, kind=kind, p_vol=2e-3)
+    pc = P.c()
+    mom = oracle.p2g(P, s).reshape(-1, 4)[:, 1:]
+    stencils = []
+    for p in range(N):
+        _, idx, w, d = oracle.stencil(n, s.x[:, p])
+        stencils.append((idx, w, d))
+    nodes = sorted({int(i) for idx, _, _ in stencils for i in idx})
+    h = 1e-7
+    worst = 0.0
+    scale = np.abs(mom).max()
+    assert scale > 0.0
+    for node in nodes:
+        grad = np.zeros(3)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            grad[a] = (_mls_energy(P, pc, s, node, e, stencils) - _mls_energy(P, pc, s, node, -e, stencils)) / (2 * h)
+        worst = max(worst, np.abs(mom[node] - (-P.dt * grad)).max())
+    assert worst < 1e-6 * scale
+    # nodes outside every stencil receive nothing
+    others = np.setdiff1d(np.arange(n ** 3), nodes)
+    assert np.abs(mom[others]).max() == 0.0
+
+
+def test_return_map_singular_value_clamp_branch():
+    """Singular values below 1e-6 are raised to 1e-6 before the logarithm and F is rebuilt from the
+    clamped values, even when the clamped state lies inside the yield surface (closed forms)."""
+    mu, la = oracle.lame(5e3, 0.3)
+    ty = 50.0
+    radius = ty / (2 * mu)
+    rng = np.random.default_rng(5)
+    U, V = rand_rot(rng), rand_rot(rng)
+    # all three below the floor: log sigma = log(1e-6) (1, 1, 1) has no deviatoric part, so no projection;
+    # F comes back as 1e-6 U V^T
+    Ftr = U @ np.diag([3e-8, 1e-9, 5e-7]) @ V.T
+    Fn, proj, cl = oracle.return_map(mu, ty, Ftr)
+    assert cl and not proj
+    assert np.abs(Fn - 1e-6 * U @ V.T).max() < 1e-18
+    # one below the floor: clamped, then projected onto the yield sphere with the trace kept
+    Ftr = U @ np.diag([1e-9, 1.02, 0.99]) @ V.T
+    Fn, proj, cl = oracle.return_map(mu, ty, Ftr)
+    assert cl and proj
+    e = np.log([1e-6, 1.02, 0.99])
+    dev = e - e.mean()
+    e_new = e.mean() + dev * radius / np.linalg.norm(dev)
+    assert np.abs(Fn - U @ np.diag(np.exp(e_new)) @ V.T).max() < 1e-12
+    # just above the floor: no clamp, and inside the yield surface nothing changes
+    Ftr = U @ np.diag([1.001, 1.0, 0.999]) @ V.T
+    Fn, proj, cl = oracle.return_map(mu, ty, Ftr)
+    assert not cl and not proj and np.array_equal(Fn, Ftr)
+
+
 def test_g2p_reproduces_affine_velocity_fields():
     """APIC reproduces affine fields exactly: grid v_i = a + B x_i gives v_p = a + B x_p, C_p = B."""
     n, N = 16, 40
