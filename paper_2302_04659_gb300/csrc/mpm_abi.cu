@@ -27,6 +27,23 @@ mpm_status mpm::record_cuda_error(cudaError_t e, const char* what) {
     return MPM_ERR_CUDA;
 }
 
+namespace mpm {
+
+mpm_status check_material(const mpm_material* m) {
+    if (!m) return MPM_ERR_INVALID_ARG;
+    if (m->kind != MPM_PLASTICINE && m->kind != MPM_FLUID) return MPM_ERR_INVALID_ARG;
+    if (!(m->rho > 0.0f) || !(m->p_vol > 0.0f)) return MPM_ERR_INVALID_ARG;
+    if (m->kind == MPM_PLASTICINE) {
+        if (!(m->E > 0.0f) || !(m->nu >= 0.0f && m->nu < 0.5f) || !(m->yield_stress >= 0.0f))
+            return MPM_ERR_INVALID_ARG;
+    } else {
+        if (!(m->bulk_modulus >= 0.0f)) return MPM_ERR_INVALID_ARG;
+    }
+    return MPM_OK;
+}
+
+}  // namespace mpm
+
 namespace {
 
 mpm_status cuda_fail(cudaError_t e, const char* what) { return record_cuda_error(e, what); }
@@ -98,7 +115,8 @@ Layout make_layout(const Totals& T, int nenv) {
     L.colliders = take(kcap * sizeof(ColliderSet));  // written in stream order by each upload
     L.poses = take((kcap > (size_t)kSharedPoses ? (size_t)kPoseSteps * kcap : 1) * sizeof(ColliderNow));
     L.wrench = take(kcap * 6 * sizeof(double));
-    L.counters = take(4 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done
+    L.counters = take(8 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done,
+                                              // fused-pass chunk counter, spare
     // surrogate window: sums, box, gate word, stats, the wrench before the window
     L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double) + kcap * 6 * sizeof(double));
     L.sur_reduce = take((size_t)kReduceBlocks * 4 * sizeof(Pair) + 16);  // per-block totals, ticket
@@ -106,18 +124,6 @@ Layout make_layout(const Totals& T, int nenv) {
     return L;
 }
 
-mpm_status check_material(const mpm_material* m) {
-    if (!m) return MPM_ERR_INVALID_ARG;
-    if (m->kind != MPM_PLASTICINE && m->kind != MPM_FLUID) return MPM_ERR_INVALID_ARG;
-    if (!(m->rho > 0.0f) || !(m->p_vol > 0.0f)) return MPM_ERR_INVALID_ARG;
-    if (m->kind == MPM_PLASTICINE) {
-        if (!(m->E > 0.0f) || !(m->nu >= 0.0f && m->nu < 0.5f) || !(m->yield_stress >= 0.0f))
-            return MPM_ERR_INVALID_ARG;
-    } else {
-        if (!(m->bulk_modulus >= 0.0f)) return MPM_ERR_INVALID_ARG;
-    }
-    return MPM_OK;
-}
 
 mpm_status check_batch(const mpm_config* c, int nenv, const mpm_env* envs) {
     if (!c || !envs || nenv < 1 || nenv > MPM_MAX_ENVS) return MPM_ERR_INVALID_ARG;
@@ -250,6 +256,7 @@ struct mpm_sim {
     uint32_t* substep_counter() { return at<uint32_t>(L.counters) + 1; }
     uint32_t* num_chunks() { return at<uint32_t>(L.counters) + 2; }
     uint32_t* done() { return at<uint32_t>(L.counters) + 3; }
+    uint32_t* work() { return at<uint32_t>(L.counters) + 4; }
     uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
     uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
@@ -360,6 +367,7 @@ TransferParams transfer_params(mpm_sim* s) {
     p.chunks_next = s->at<int4>(s->L.chunks);
     p.num_chunks_next = s->num_chunks();
     p.done = s->done();
+    p.work = s->work();
     p.contact = s->contact == MPM_CONTACT_PARTICLE ? 1 : 0;
     p.stiffness = s->stiffness;
     p.damping = s->damping;

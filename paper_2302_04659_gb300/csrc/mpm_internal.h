@@ -98,6 +98,7 @@ struct TransferParams {  // particle passes: the fused G2P->P2G substep and the 
     int4* chunks_next;
     uint32_t* num_chunks_next;
     uint32_t* done;         // CTAs finished, reset by the last one
+    uint32_t* work;         // fused pass: chunks handed out after each CTA's first, reset by the last CTA
     // the particle form of the contact (mpm_set_contact): penalty accelerations added to the momentum
     // each particle transfers, at the collider poses of substep *substep_counter
     int contact;            // 1: particle penalty contact
@@ -156,6 +157,9 @@ struct AssignGridParams {  // the sort-assign of the new state and the grid upda
     const uint32_t* gate;     // if set, the launch runs only when *gate == gate_run (read after the wait)
     uint32_t gate_run;
 };
+
+// Argument check of a material (mpm_material rules in mpm.h); shared by the entry points.
+mpm_status check_material(const mpm_material* m);
 
 struct LoadParams {  // mpm_set_particles*: copy in, clamp, bin keys and ranks
     const EnvDesc* envs;

@@ -90,31 +90,47 @@ __device__ __forceinline__ void load_env(EnvDesc& dst, const EnvDesc* envs, int 
 //             the sum stays below 108 * 2^22 < 2^31);
 //   momentum  scaled by 2^k with k = 22 - e, where 2^e bounds (from above, within a factor 2) the largest
 //             per-particle magnitude B_p = max_a (m |v_a| + 1.5 dx sum_c |A_ac|) of the chunk, so every node
-//             sum stays below 108 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term,
-//             comparable to an FP32 accumulation of the same terms. Every scaled term is below 2^22, so it
-//             is rounded to an integer by one FP32 fused multiply-add (round_fixed_mul).
-// The tile is flushed in FP32 with one 16-byte vector atomic per touched node.
+//             sum stays below 108 * 2^22 as well. Rounding is then at most 2^-23 of that bound per term.
+// A chunk has two such tiles. The chunk records which FP32 exponents its particles' bounds B_p take (a
+// 256-bit map); particles whose exponent lies more than kSlowShift below the largest go to the second
+// tile, scaled from the largest exponent among them. A slow particle sharing a chunk with a fast one
+// (material at rest beside a moving tool) is then rounded relative to the slow particles' range, not the
+// fast one's: a term is rounded at most 2^-18 of its particle's bound in the first tile (its bounds lie
+// within 2^5 of the largest), and relative to the largest slow bound in the second.
+// Every scaled term a b is below 2^22, so one FP32 fused multiply-add rounds it to an integer:
+// a b + 1.5 * 2^23 lands where one unit is one ulp, so the low mantissa bits hold round-to-nearest-even
+// of the exact product, offset by the bit pattern 0x4B400000 of the constant, which is subtracted.
+// The tiles are flushed in FP32 with one 16-byte vector atomic per touched node, and zeroed as they are
+// read, so a chunk finds them clear.
 
 constexpr int kMassBits = 22;
-
-// round(a b) for |a b| < 2^22 with one FP32 fused multiply-add: a b + 1.5 * 2^23 lands where one unit is
-// one ulp, so the low mantissa bits hold round-to-nearest-even of the exact product, offset by the
-// constant's own bit pattern.
-__device__ __forceinline__ int round_fixed_mul(float a, float b) {
-    return __float_as_int(__fmaf_rn(a, b, 12582912.0f)) - 0x4B400000;
-}
+constexpr int kSlowShift = 4;  // a bound whose exponent field is this far below the chunk's largest is slow
 
 // Layers of the class-layered order a chunk gives the particles that stay in its bin: one per particle
 // of a class at most, so as many as a chunk holds particles.
 constexpr int kLayers = kChunk;
 
+// Tile storage: node (lx, ly, lz) of a chunk's tile sits at slot lx * kPitchX + ly * kPitchY + lz, with
+// kPitchX = 4 (mod 32). The 64 cells (c0, c1, c2) of a bin then start at bank 4 (c0 + 2 c1) + c2 (mod 32):
+// two cells per bank, so for any one stencil offset the nodes of particles in 32 different bank classes
+// ((c0 + 2 c1) mod 8, c2) fall in 32 different banks. The map is additive, so a particle's 27 nodes are
+// one base register plus compile-time offsets.
+constexpr int kPitchY = 8;
+constexpr int kPitchX = 68;
+constexpr int kScatterSlots = 7 * kPitchX + 7 * kPitchY + 8;  // 540, a multiple of 4 (cleared as int4)
+constexpr int kGatherSlots = 5 * kPitchX + 5 * kPitchY + 6;   // 386: the 6^3 gather tile
+
+__device__ __forceinline__ int tile_slot(int lx, int ly, int lz) { return lx * kPitchX + ly * kPitchY + lz; }
+
+// Bank class of cell (c0, c1, c2) of a bin (each in 0..3).
+__device__ __forceinline__ uint32_t bank_class(int c0, int c1, int c2) {
+    return ((uint32_t)((c0 + 2 * c1) & 7) << 2) | (uint32_t)c2;
+}
+
 struct __align__(16) ScatterTile {
-    int m[kScatterNodes];
-    int px[kScatterNodes];
-    int py[kScatterNodes];
-    int pz[kScatterNodes];
+    int q[2][4][kScatterSlots];  // [fast, slow tile][m, mx, my, mz][slot]
     uint32_t touched[27];
-    uint32_t bound_bits;  // max over the chunk of B_p, as FP32 bits (non-negative floats order as integers)
+    uint32_t expo_map[8];  // bit e set: some particle of the chunk has a bound B_p with FP32 exponent field e
     uint32_t class_count[32];      // staying particles per bank class so far
     uint32_t layer_mask[kLayers];  // per layer, its classes
     uint32_t stay_base;            // the staying group's first rank in the bin
@@ -122,17 +138,10 @@ struct __align__(16) ScatterTile {
 
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
-// Storage slot of tile node (lx, ly, lz): row-major with bit 2 of lz flipped for odd lx. A bin's particles
-// sit in 4 consecutive cells per axis, so for any one stencil offset their nodes then spread over all 32
-// banks (two cells per bank) instead of 16. The map is its own inverse for a fixed lx.
-__device__ __forceinline__ int tile_slot(int lx, int ly, int lz) {
-    return ((lx * kScatterEdge + ly) * kScatterEdge + lz) ^ ((lx & 1) << 2);
-}
-
-// Scale exponent k of a chunk from the FP32 bits of its bound (clamped so 2^k and 2^-k stay normal).
-__device__ __forceinline__ int momentum_scale_exp(uint32_t bound_bits) {
-    int e = (int)((bound_bits >> 23) & 0xffu) - 126;  // bound < 2^e
-    int k = kMassBits - e;
+// Scale exponent k for bounds whose FP32 exponent field is at most `field` (clamped so 2^k and 2^-k stay
+// normal): such a bound is below 2^e with e = field - 126, and k = 22 - e.
+__device__ __forceinline__ int momentum_scale_exp(int field) {
+    const int k = kMassBits - (field - 126);
     return min(max(k, -100), 100);
 }
 
@@ -161,7 +170,7 @@ __device__ __forceinline__ void mark_bin(const TransferParams& p, uint32_t b, ui
 // touches. Returns flag bits.
 __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const TransferParams& p, const EnvDesc& E,
                                                      int env, const int o[3], const float xn[3], const float vn[3],
-                                                     const float (&A)[3][3], float mscale) {
+                                                     const float (&A)[3][3], int tile, float mscale) {
     const Geometry& g = E.geo;
     int bs[3];
     float f[3], w[3][3];
@@ -183,6 +192,9 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
     const int l0 = bs[0] - o[0], l1 = bs[1] - o[1], l2 = bs[2] - o[2];
     const bool in_tile = (unsigned)l0 <= 5u && (unsigned)l1 <= 5u && (unsigned)l2 <= 5u;
     if (in_tile) {
+        // Node (i, j, k) receives round(w 2^22) and round(w m_k) with m_k = bm + i Ad0 + j Ad1 + k Ad2 (scaled).
+        // Packed FP32x2 pairs: (mass, x) with the pair (2^22, m_k.x), and (y, z); each lane is rounded as
+        // a scalar fused multiply-add would round it.
         const float wscale = pow2f(kMassBits);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -190,22 +202,34 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
 #pragma unroll
             for (int c = 0; c < 3; ++c) Ad[c][r] *= mscale;
         }
+        const float2 magic = make_float2(12582912.0f, 12582912.0f);
+        const float2 ad2x = make_float2(0.0f, Ad[2][0]);
+        const float2 ad2yz = make_float2(Ad[2][1], Ad[2][2]);
+        int* tm = T.q[tile][0] + tile_slot(l0, l1, l2);
+        int* tx = T.q[tile][1] + tile_slot(l0, l1, l2);
+        int* ty = T.q[tile][2] + tile_slot(l0, l1, l2);
+        int* tz = T.q[tile][3] + tile_slot(l0, l1, l2);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const float wij = w[0][i] * w[1][j];
-                const float wijm = wij * wscale;
-                const float mij[3] = {bm[0] + i * Ad[0][0] + j * Ad[1][0], bm[1] + i * Ad[0][1] + j * Ad[1][1],
-                                      bm[2] + i * Ad[0][2] + j * Ad[1][2]};
+                const float2 mx = make_float2(wscale, bm[0] + i * Ad[0][0] + j * Ad[1][0]);
+                const float2 myz = make_float2(bm[1] + i * Ad[0][1] + j * Ad[1][1], bm[2] + i * Ad[0][2] + j * Ad[1][2]);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float wk = wij * w[2][k];
-                    const int t = tile_slot(l0 + i, l1 + j, l2 + k);
-                    atomicAdd(&T.m[t], round_fixed_mul(wijm, w[2][k]));
-                    atomicAdd(&T.px[t], round_fixed_mul(wk, mij[0] + k * Ad[2][0]));
-                    atomicAdd(&T.py[t], round_fixed_mul(wk, mij[1] + k * Ad[2][1]));
-                    atomicAdd(&T.pz[t], round_fixed_mul(wk, mij[2] + k * Ad[2][2]));
+                    const float2 wk2 = make_float2(wk, wk);
+                    const float kf = (float)k;
+                    const float2 vx = k ? __ffma2_rn(make_float2(kf, kf), ad2x, mx) : mx;
+                    const float2 vyz = k ? __ffma2_rn(make_float2(kf, kf), ad2yz, myz) : myz;
+                    const float2 qmx = __ffma2_rn(wk2, vx, magic);
+                    const float2 qyz = __ffma2_rn(wk2, vyz, magic);
+                    const int o = i * kPitchX + j * kPitchY + k;
+                    atomicAdd(tm + o, __float_as_int(qmx.x) - 0x4B400000);
+                    atomicAdd(tx + o, __float_as_int(qmx.y) - 0x4B400000);
+                    atomicAdd(ty + o, __float_as_int(qyz.x) - 0x4B400000);
+                    atomicAdd(tz + o, __float_as_int(qyz.y) - 0x4B400000);
                 }
             }
         return 0;
@@ -233,37 +257,101 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
     return 0x8u;
 }
 
+// Zero both tiles (once per launch; afterwards the flush zeroes what it reads).
+__device__ __forceinline__ void tile_zero(ScatterTile& T) {
+    int4* q = reinterpret_cast<int4*>(&T.q[0][0][0]);
+    for (int t = threadIdx.x; t < 2 * kScatterSlots; t += blockDim.x) q[t] = make_int4(0, 0, 0, 0);
+}
+
+// The per-chunk bookkeeping of a tile (the node values are already zero).
 __device__ __forceinline__ void tile_clear(ScatterTile& T) {
-    int4* q = reinterpret_cast<int4*>(T.m);  // m, px, py, pz are contiguous: 4 * 512 ints
-    for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) q[t] = make_int4(0, 0, 0, 0);
     if (threadIdx.x < 27) T.touched[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) T.bound_bits = 0u;
+    if (threadIdx.x < 8) T.expo_map[threadIdx.x] = 0u;
     if (threadIdx.x < 32) T.class_count[threadIdx.x] = 0u;
     for (int t = threadIdx.x; t < kLayers; t += blockDim.x) T.layer_mask[t] = 0u;
 }
 
-// CTA-wide max of the particle bounds into T.bound_bits; every thread of the CTA must call it.
-__device__ __forceinline__ void tile_bound(ScatterTile& T, float bp) {
-    uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(bp));
-    if ((threadIdx.x & 31) == 0) atomicMax(&T.bound_bits, wmax);
+// Record the exponent of this thread's particle bound in the chunk's map; every thread of the CTA must
+// call it. A warp whose bounds share one map word (the usual case) sets its bits with one atomic.
+__device__ __forceinline__ void tile_bound(ScatterTile& T, float bp, bool active) {
+    const uint32_t field = (__float_as_uint(bp) >> 23) & 0xffu;
+    const uint32_t word = field >> 5, bit = 1u << (field & 31u);
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, active ? word : 0xffffu);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, active ? word : 0u);
+    if (lo == hi) {
+        const uint32_t bits = __reduce_or_sync(0xffffffffu, active ? bit : 0u);
+        if ((threadIdx.x & 31) == 0) atomicOr(&T.expo_map[lo], bits);
+    } else if (active) {
+        atomicOr(&T.expo_map[word], bit);
+    }
 }
 
-// Add the tile's nonzero nodes to the env's global grid (FP32, one vector atomic each), then mark the
-// bins that received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
+// The chunk's two scales from its exponent map (read after the barrier that follows tile_bound): the
+// largest exponent field `top` sets the first tile's scale k_fast; the largest field below
+// top - kSlowShift, if any, the second tile's k_slow (slow = false: no particle goes there).
+struct TileScales {
+    int k_fast, k_slow, split;  // a particle with exponent field < split uses the second tile
+    bool slow;
+};
+
+__device__ __forceinline__ TileScales tile_scales(const ScatterTile& T) {
+    // every thread reads the same words (broadcast); the loops are uniform across the CTA
+    int wt = 7;
+    while (wt > 0 && T.expo_map[wt] == 0u) --wt;
+    const uint32_t mt = T.expo_map[wt];
+    const int top = mt ? wt * 32 + 31 - __clz(mt) : 0;
+    TileScales t;
+    t.split = top - kSlowShift;
+    int low = -1;
+    if (t.split > 0) {
+        int ws = (t.split - 1) >> 5;  // word of the highest field below split
+        uint32_t w = T.expo_map[ws] & (0xffffffffu >> (31 - ((t.split - 1) & 31)));
+        while (w == 0u && ws > 0) w = T.expo_map[--ws];
+        if (w) low = ws * 32 + 31 - __clz(w);
+    }
+    t.k_fast = momentum_scale_exp(top);
+    t.slow = low >= 0;
+    t.k_slow = momentum_scale_exp(t.slow ? low : 0);
+    return t;
+}
+
+// The tile a particle scatters into (0 fast, 1 slow) and its momentum scale.
+__device__ __forceinline__ int tile_of(float bp, const TileScales& ts, float& mscale) {
+    const bool slow = (int)((__float_as_uint(bp) >> 23) & 0xffu) < ts.split;
+    mscale = pow2f(slow ? ts.k_slow : ts.k_fast);
+    return slow ? 1 : 0;
+}
+
+// Add the tiles' nonzero nodes to the env's global grid (FP32, one vector atomic each), zero them, then
+// mark the bins that received mass. bin = (bx, by, bz) of the particles; the tile origin is 4 * bin - 1.
+// The slow tile is read only when a particle of the chunk used it (ts.slow, uniform over the CTA).
 __device__ __forceinline__ void tile_flush(ScatterTile& T, const TransferParams& p, const EnvDesc& E, int env,
-                                           int bx, int by, int bz, float inv_mscale) {
+                                           int bx, int by, int bz, const TileScales& ts) {
     const int nb = E.geo.nb;
     float4* grid = p.grid_out + E.node_base;
     const float mass_unit = E.mat.p_mass * pow2f(-kMassBits);
+    const float inv_f = pow2f(-ts.k_fast), inv_s = pow2f(-ts.k_slow);
+    const bool slow_used = ts.slow;
     for (int t = threadIdx.x; t < kScatterNodes; t += blockDim.x) {
-        int mq = T.m[t];
-        if (mq == 0) continue;
-        const int ti = t / (kScatterEdge * kScatterEdge);
-        const int u = t ^ ((ti & 1) << 2);  // tile_slot is its own inverse for a fixed lx
-        const int tj = (u / kScatterEdge) % kScatterEdge, tk = u % kScatterEdge;
+        const int ti = t >> 6, tj = (t >> 3) & 7, tk = t & 7;  // a warp reads 32 consecutive slots
+        const int sl = tile_slot(ti, tj, tk);
+        const int mf = T.q[0][0][sl];
+        const int ms = slow_used ? T.q[1][0][sl] : 0;
+        if ((mf | ms) == 0) continue;  // no weight reached the node (momentum is then zero too)
+        float4 add = make_float4((float)(mf + ms) * mass_unit, 0.0f, 0.0f, 0.0f);
+        if (mf) {
+            add.y = (float)T.q[0][1][sl] * inv_f;
+            add.z = (float)T.q[0][2][sl] * inv_f;
+            add.w = (float)T.q[0][3][sl] * inv_f;
+            T.q[0][0][sl] = T.q[0][1][sl] = T.q[0][2][sl] = T.q[0][3][sl] = 0;
+        }
+        if (ms) {
+            add.y += (float)T.q[1][1][sl] * inv_s;
+            add.z += (float)T.q[1][2][sl] * inv_s;
+            add.w += (float)T.q[1][3][sl] * inv_s;
+            T.q[1][0][sl] = T.q[1][1][sl] = T.q[1][2][sl] = T.q[1][3][sl] = 0;
+        }
         int gx = 4 * bx - 1 + ti, gy = 4 * by - 1 + tj, gz = 4 * bz - 1 + tk;
-        float4 add = make_float4((float)mq * mass_unit, (float)T.px[t] * inv_mscale, (float)T.py[t] * inv_mscale,
-                                 (float)T.pz[t] * inv_mscale);
         atomicAdd(&grid[node_index(gx, gy, gz, nb)], add);
         int qx = (gx >> 2) - bx + 1, qy = (gy >> 2) - by + 1, qz = (gz >> 2) - bz + 1;
         T.touched[(qx * 3 + qy) * 3 + qz] = 1u;
@@ -682,6 +770,7 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
         penalty_begin(p, cs, cw, step, p.env0.geo.dt);
         __syncthreads();
     }
+    tile_zero(T);
     for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x) {
         const int4 ch = p.chunks[w];
         const int env = ch.w;
@@ -724,12 +813,14 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
             for (int a = 0; a < 3; ++a) v[a] += E.geo.dt * acc[a];
         }
         if (active) bp = particle_bound(E.mat.p_mass, v, A, E.geo.dx);
-        tile_bound(T, bp);
+        tile_bound(T, bp, active);
         __syncthreads();
-        const int k = momentum_scale_exp(T.bound_bits);
-        if (active) flags |= scatter_particle(T, p, E, env, o, x, v, A, pow2f(k));
+        const TileScales ts = tile_scales(T);
+        float mscale;
+        const int tile = tile_of(bp, ts, mscale);
+        if (active) flags |= scatter_particle(T, p, E, env, o, x, v, A, tile, mscale);
         __syncthreads();
-        tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
+        tile_flush(T, p, E, env, bx, by, bz, ts);
         __syncthreads();
     }
     if (p.contact && shared_poses) penalty_end(p, cw);
@@ -757,9 +848,9 @@ __device__ __forceinline__ const EnvDesc& chunk_env(const TransferParams& p, con
 // applies no colliders then).
 template <int KIND, bool ONE_ENV, bool PEN, int CTA>
 __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7)) k_g2p2g(TransferParams p) {
-    // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots
-    // swizzled like the scatter tile so the 27 reads of a warp spread over the banks
-    __shared__ float Gx[kScatterNodes], Gy[kScatterNodes], Gz[kScatterNodes];
+    // gather tile: node velocities of [4 bin, 4 bin + 6) per axis, one FP32 array per component, slots laid
+    // out like the scatter tile so the 27 reads of a warp spread over the banks
+    __shared__ float Gx[kGatherSlots], Gy[kGatherSlots], Gz[kGatherSlots];
     __shared__ ScatterTile T;
     static_assert(CTA <= kLayers, "a cell's layer index stays below kLayers");
     __shared__ EnvDesc Es[2];  // several envs: the current chunk's env and the next one's
@@ -782,19 +873,31 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
     int4 next = (int)blockIdx.x < p.chunk_cap ? p.chunks[blockIdx.x] : make_int4(0, 0, 0, 0);
     const uint32_t nchunks = *p.num_chunks;
     if (blockIdx.x >= nchunks) next = make_int4(0, 0, 0, 0);
+    // A CTA's first two chunks are blockIdx.x and blockIdx.x + gridDim.x; later ones are handed out in list
+    // order by a counter (p.work), two chunks ahead, so that SMs that drew short chunks take more. Thread 0
+    // asks for chunk it + 2 at the top of iteration it and publishes it in slot (it & 1) of s_next before
+    // the iteration's last barrier; the atomic's round trip overlaps the iteration's work. A CTA asks
+    // only when it will run the iteration that reads the answer (chunk it + 1 exists), so every index
+    // handed out below nchunks is processed. The last CTA resets the counter.
+    __shared__ uint32_t s_next[2];
+    tile_zero(T);  // ordered before the first scatter by the first chunk's barriers
     if constexpr (!ONE_ENV) {
         load_env(Es[0], p.envs, next.w);
         __syncthreads();
     }
     int it = 0;
-    for (uint32_t w = blockIdx.x; w < nchunks; w += gridDim.x, ++it) {
+    uint32_t w = blockIdx.x, wn = blockIdx.x + gridDim.x;
+    for (; w < nchunks; ++it) {
         const int4 ch = next;
         const int env = ONE_ENV ? 0 : ch.w;
         const EnvDesc& E = chunk_env<ONE_ENV>(p, Es, it);
         const int kind = KIND >= 0 ? KIND : E.kind;
         const Geometry& g = E.geo;
         const float dt = g.dt;
-        if (w + gridDim.x < nchunks) next = p.chunks[w + gridDim.x];  // prefetch the next descriptor
+        if (it > 0) wn = s_next[(it + 1) & 1];  // published before the previous iteration's last barrier
+        uint32_t ticket = 0;
+        if (threadIdx.x == 0 && wn < nchunks) ticket = atomicAdd(p.work, 1u);  // chunk it + 2 (used later)
+        if (wn < nchunks) next = p.chunks[wn];  // prefetch the next descriptor
         int bx, by, bz;
         decode_bin(ch.x - (int)E.bin_base, g.nb, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
@@ -825,7 +928,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         tile_clear(T);
         __syncthreads();
         if constexpr (!ONE_ENV)
-            if (w + gridDim.x < nchunks) load_env(Es[(it + 1) & 1], p.envs, next.w);
+            if (wn < nchunks) load_env(Es[(it + 1) & 1], p.envs, next.w);
         float xn[3] = {0.0f, 0.0f, 0.0f}, vn[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
         float bp = 0.0f;
         uint32_t newkey = 0xffffffffu;
@@ -848,39 +951,62 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
             }
             // 27 weighted reads into 12 sums, M[a][c] = sum_ijk w_i w_j w_k (index_c) v_a and v, contracted
             // one axis at a time: over k the sums with weights w_k and k w_k, over j with w_j and j w_j,
-            // over i with w_i and i w_i
-            float M[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+            // over i with w_i and i w_i. The x and y components travel as one packed FP32x2 operand
+            // (one instruction for both, each lane rounded as a scalar fused multiply-add would be).
+            const float* gx = Gx + tile_slot(l0, l1, l2);
+            const float* gy = Gy + tile_slot(l0, l1, l2);
+            const float* gz = Gz + tile_slot(l0, l1, l2);
+            float2 vxy = make_float2(0.0f, 0.0f), Mxy[3] = {vxy, vxy, vxy};
+            float vz = 0.0f, Mz[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                float b0[3] = {0.0f, 0.0f, 0.0f}, bj[3] = {0.0f, 0.0f, 0.0f}, bk[3] = {0.0f, 0.0f, 0.0f};
+                float2 b0 = make_float2(0.0f, 0.0f), bj = b0, bk = b0;
+                float b0z = 0.0f, bjz = 0.0f, bkz = 0.0f;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    float a0[3] = {0.0f, 0.0f, 0.0f}, ak[3] = {0.0f, 0.0f, 0.0f};
+                    float2 a0 = make_float2(0.0f, 0.0f), ak = a0;
+                    float a0z = 0.0f, akz = 0.0f;
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const int s = tile_slot(l0 + i, l1 + j, l2 + k);
-                        const float gv[3] = {Gx[s], Gy[s], Gz[s]};
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            a0[a] = fmaf(w3[2][k], gv[a], a0[a]);
-                            if (k) ak[a] = fmaf((float)k * w3[2][k], gv[a], ak[a]);
+                        const int o = i * kPitchX + j * kPitchY + k;
+                        const float2 g = make_float2(gx[o], gy[o]);
+                        const float wk = w3[2][k];
+                        a0 = k ? __ffma2_rn(make_float2(wk, wk), g, a0) : __fmul2_rn(make_float2(wk, wk), g);
+                        a0z = fmaf(wk, gz[o], a0z);
+                        if (k) {
+                            const float kw = (float)k * wk;
+                            ak = __ffma2_rn(make_float2(kw, kw), g, ak);
+                            akz = fmaf(kw, gz[o], akz);
                         }
                     }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        b0[a] = fmaf(w3[1][j], a0[a], b0[a]);
-                        bk[a] = fmaf(w3[1][j], ak[a], bk[a]);
-                        if (j) bj[a] = fmaf((float)j * w3[1][j], a0[a], bj[a]);
+                    const float wj = w3[1][j];
+                    b0 = __ffma2_rn(make_float2(wj, wj), a0, b0);
+                    bk = __ffma2_rn(make_float2(wj, wj), ak, bk);
+                    b0z = fmaf(wj, a0z, b0z);
+                    bkz = fmaf(wj, akz, bkz);
+                    if (j) {
+                        const float jw = (float)j * wj;
+                        bj = __ffma2_rn(make_float2(jw, jw), a0, bj);
+                        bjz = fmaf(jw, a0z, bjz);
                     }
                 }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    vn[a] = fmaf(w3[0][i], b0[a], vn[a]);
-                    if (i) M[a][0] = fmaf((float)i * w3[0][i], b0[a], M[a][0]);
-                    M[a][1] = fmaf(w3[0][i], bj[a], M[a][1]);
-                    M[a][2] = fmaf(w3[0][i], bk[a], M[a][2]);
+                const float wi = w3[0][i];
+                vxy = __ffma2_rn(make_float2(wi, wi), b0, vxy);
+                vz = fmaf(wi, b0z, vz);
+                if (i) {
+                    const float iw = (float)i * wi;
+                    Mxy[0] = __ffma2_rn(make_float2(iw, iw), b0, Mxy[0]);
+                    Mz[0] = fmaf(iw, b0z, Mz[0]);
                 }
+                Mxy[1] = __ffma2_rn(make_float2(wi, wi), bj, Mxy[1]);
+                Mxy[2] = __ffma2_rn(make_float2(wi, wi), bk, Mxy[2]);
+                Mz[1] = fmaf(wi, bjz, Mz[1]);
+                Mz[2] = fmaf(wi, bkz, Mz[2]);
             }
+            vn[0] = vxy.x;
+            vn[1] = vxy.y;
+            vn[2] = vz;
+            const float M[3][3] = {{Mxy[0].x, Mxy[1].x, Mxy[2].x}, {Mxy[0].y, Mxy[1].y, Mxy[2].y}, {Mz[0], Mz[1], Mz[2]}};
             float Cn[3][3];
             const float cs = 4.0f * g.inv_dx;
 #pragma unroll
@@ -939,8 +1065,8 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
             }
         }
         if (active) bp = particle_bound(E.mat.p_mass, vn, A, g.dx);
-        // Rank within the new bin. The 64 cells of a bin fall in 32 bank classes (x index mod 2, y, z): for
-        // every stencil offset, tile nodes of cells in different classes lie in different banks (tile_slot).
+        // Rank within the new bin. The 64 cells of a bin fall in 32 bank classes (bank_class): for every
+        // stencil offset, tile nodes of cells in different classes lie in different banks (tile_slot).
         // The particles that stay in the chunk's bin take consecutive ranks in class-layered order: layer r
         // holds the r-th staying particle (in slot order) of each class, the classes in a fixed order; so
         // while layers are full, any 32 consecutive ranks -- a warp of the next substep, wherever the group
@@ -952,7 +1078,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         if (stay) {
             const int c0 = cell_base(xn[0], g.inv_dx) - ox, c1 = cell_base(xn[1], g.inv_dx) - oy,
                       c2 = cell_base(xn[2], g.inv_dx) - oz;  // each in 0..3: xn is in this bin
-            const uint32_t cls = (uint32_t)(((c0 & 1) * 4 + c1) * 4 + c2);
+            const uint32_t cls = bank_class(c0, c1, c2);
             const uint32_t lay = atomicAdd(&T.class_count[cls], 1u);  // < particles in the chunk
             atomicOr(&T.layer_mask[lay], 1u << cls);
             class_key = lay * 32u + cls;
@@ -960,7 +1086,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         // (a staying particle's rank is its layered position until the group's base is known)
         uint32_t rank = warp_hist_add(p.hist, stay ? 0xffffffffu : newkey, true);
         if (p.scatter) {
-            tile_bound(T, bp);
+            tile_bound(T, bp, active);
             const int nstay = __syncthreads_count(stay);
             if (threadIdx.x == 0 && nstay > 0) T.stay_base = atomicAdd(&p.hist[ch.x], (uint32_t)nstay);
             if (stay) {  // the earlier layers, then this layer's classes before this one
@@ -970,36 +1096,43 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
                 rank = pos + __popc(T.layer_mask[lay] & ((1u << cls) - 1u));
             }
             // ---- P2G of the new state into the next grid
-            const int k = momentum_scale_exp(T.bound_bits);
+            const TileScales ts = tile_scales(T);
             const int o[3] = {ox - 1, oy - 1, oz - 1};
-            if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, pow2f(k));
+            float mscale;
+            const int tile = tile_of(bp, ts, mscale);
+            if (active) flags |= scatter_particle(T, p, E, env, o, xn, vn, A, tile, mscale);
             if (active && !stay) p.keyrank_out[slot] = make_uint2(newkey, rank);
             __syncthreads();
             if (stay) p.keyrank_out[slot] = make_uint2(newkey, T.stay_base + rank);
-            tile_flush(T, p, E, env, bx, by, bz, pow2f(-k));
-        } else if (active) {
-            p.keyrank_out[slot] = make_uint2(newkey, rank);
+            if (threadIdx.x == 0 && wn < nchunks) s_next[it & 1] = 2u * gridDim.x + ticket;
+            tile_flush(T, p, E, env, bx, by, bz, ts);
+        } else {
+            if (active) p.keyrank_out[slot] = make_uint2(newkey, rank);
+            if (threadIdx.x == 0 && wn < nchunks) s_next[it & 1] = 2u * gridDim.x + ticket;
         }
         // With the scatter, the barriers above already order this chunk's reads of the shared tiles before
         // the next chunk's writes: the gather tile is last read before the bound barrier, the scatter tile
         // before the flush's barrier, and a thread clearing T.touched[t] is the one that read it. Without
         // the scatter, the next gather tile must wait here.
         if (!p.scatter) __syncthreads();
+        w = wn;
     }
     if constexpr (PEN)
         if (pen && shared_poses) penalty_end(p, cw);
     if (flags) atomicOr(p.status, flags);
     release_successor();
-    if (!p.tail_scan) return;
-    // With few bins, the last CTA to finish turns the new bin counts into offsets and the next chunk
-    // list. Every CTA has read its chunks and added to the counts before taking its ticket.
+    // The last CTA to finish resets the chunk counter and, with few bins, turns the new bin counts into
+    // offsets and the next chunk list. Every CTA has read its chunks and added to the counts before
+    // taking its ticket.
     __shared__ uint32_t warp_tot[2][32];
     __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(p.done, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (last) {
+    if (!last) return;
+    if (threadIdx.x == 0) *p.work = 0u;
+    if (p.tail_scan) {
         __threadfence();
         if (p.chunk == kChunk)
             scan_bins<kChunk>(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, kChunk,
@@ -1007,8 +1140,8 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         else
             scan_bins<0>(p.hist, p.cursor, p.chunks_next, p.num_chunks_next, p.bin_env, p.total_bins, p.chunk,
                          warp_tot);
-        if (threadIdx.x == 0) *p.done = 0u;
     }
+    if (threadIdx.x == 0) *p.done = 0u;
 }
 
 // ------------------------------------------------------------------------ grid update
