@@ -255,9 +255,12 @@ long long mpm_launch_count(const mpm_sim* sim);
  *   grid_out    device float[cfg->n]^3 [4] = (m, mv_x, mv_y, mv_z), 16-byte aligned; zeroed by the call
  * Scratch (bin keys and ranks, bin offsets, chunk list, sorted order; about 0.9 MB) lives in a device
  * array owned by the library, resident on every GPU that loads it until the process exits. Limits:
- * n <= 65,536 particles and cfg->n <= 64, else MPM_ERR_CAPACITY (nothing enqueued). The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, once per device, with that device
- * current): make that first call before any stream capture. Every call on a device shares the array, so
+ * n <= 65,536 particles and cfg->n <= 64, else MPM_ERR_CAPACITY (nothing enqueued). Of cfg only n (a
+ * multiple of 4, at least 8) and dt (> 0) are used and checked, with the material (MPM_ERR_INVALID_ARG).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, with that device current) and keeps it for the life of the process: make that first call
+ * before any stream capture, and do not call this entry again on a device after cudaDeviceReset (or a
+ * reset of its primary context), which may move the array. Every call on a device shares the array, so
  * calls that overlap on the GPU (different streams, or different host threads) race; serialize them.
  * Enqueued on `stream`, no host synchronization; allocates nothing. */
 mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* mat, int n, const float* x, const float* v,

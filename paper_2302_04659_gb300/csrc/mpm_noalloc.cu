@@ -8,6 +8,7 @@
 // loaded with the library and stays resident on every GPU that uses it until the process exits.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "mpm.h"
@@ -32,7 +33,10 @@ constexpr size_t kOffCounters = kOffChunks + round256(sizeof(int4) * kStaticMaxC
 constexpr size_t kStaticBytes = kOffCounters + 256;  // num_chunks, status (about 0.9 MB in all)
 
 // The scratch. Host code must not use this name as an address: it is a host-side stand-in for the
-// symbol. The device address comes from cudaGetSymbolAddress, once per device.
+// symbol. The device address comes from cudaGetSymbolAddress, once per device, and is cached for the
+// life of the process: a cudaDeviceReset (or a reset of the device's primary context) reloads the module
+// and may move the array, after which the cached address is stale, so this entry point must not be
+// called again on that device in the same process.
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
@@ -149,9 +153,11 @@ __global__ void __launch_bounds__(kChunk) k_static_p2g(Geometry g, Material mat,
 extern "C" mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* mat, int n, const float* x,
                                      const float* v, const float* C, const float* F, float* grid_out,
                                      void* stream) {
+    // only the fields this entry uses are checked: the grid size, dt and the material
     if (!cfg || !mat || n < 0 || (n > 0 && !x) || !grid_out) return MPM_ERR_INVALID_ARG;
-    size_t ws = 0;
-    mpm_status r = mpm_workspace_size(cfg, mat, &ws);  // validates cfg and mat
+    if (cfg->n < 8 || cfg->n > 256 || (cfg->n % 4) != 0) return MPM_ERR_INVALID_ARG;
+    if (!(cfg->dt > 0.0f) || !std::isfinite(cfg->dt)) return MPM_ERR_INVALID_ARG;
+    mpm_status r = check_material(mat);
     if (r != MPM_OK) return r;
     if (n > kStaticMaxParticles || cfg->n > kStaticMaxGrid) return MPM_ERR_CAPACITY;
     if ((reinterpret_cast<uintptr_t>(grid_out) & 15u) != 0) return MPM_ERR_INVALID_ARG;
@@ -190,9 +196,9 @@ extern "C" mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* 
     const size_t grid_bytes = (size_t)g.n * g.n * g.n * sizeof(float4);
     if (cudaMemsetAsync(grid_out, 0, grid_bytes, st) != cudaSuccess) return MPM_ERR_CUDA;
     if (n == 0) return MPM_OK;
-    // the counts must start at zero; the previous call's scan already zeroed them, this covers a call
-    // that was interrupted and the first call
-    // (the scan reads the counts in groups of four bins, so the group padding is cleared too)
+    // the counts must start at zero on every call: the array keeps whatever the last call (or an
+    // interrupted one) left, and the first call finds it uninitialised. The scan reads the counts in
+    // groups of four bins, so the group padding is cleared too. This clear must stay.
     if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * ((g.nblocks + 3) & ~3), st) != cudaSuccess) return MPM_ERR_CUDA;
     k_static_keys<<<(n + 255) / 256, 256, 0, st>>>(g, n, x, hist, keyrank);
     if (cudaGetLastError() != cudaSuccess) return MPM_ERR_CUDA;
