@@ -60,3 +60,15 @@ def test_flag_names_match_the_header():
     every = (mpm.MPM_FLAG_CLAMPED | mpm.MPM_FLAG_NONFINITE | mpm.MPM_FLAG_SV_CLAMPED | mpm.MPM_FLAG_FAR_MOVE
              | mpm.MPM_FLAG_INTERNAL)
     assert len(b.flag_names(every)) == 5
+
+
+def test_oracle_replicas_on_all_cores(monkeypatch):
+    """The CPU baseline runs the oracle as independent spawned replicas, one per core; its value is the
+    replicas' particle-substeps over the slowest replica's time."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench as b  # importable by name, so that spawned replicas can unpickle its functions
+    monkeypatch.setattr(b.os, "cpu_count", lambda: 2)
+    value, cores, secs = b.oracle_on_all_cores(1000, 4000, 300, 1, 2)
+    assert cores == 2 and secs > 0.0
+    assert abs(value - 2 * 300 * 2 / secs) <= 1e-9 * value
