@@ -116,7 +116,7 @@ Layout make_layout(const Totals& T, int nenv) {
     L.poses = take((kcap > (size_t)kSharedPoses ? (size_t)kPoseSteps * kcap : 1) * sizeof(ColliderNow));
     L.wrench = take(kcap * 6 * sizeof(double));
     L.counters = take(8 * sizeof(uint32_t));  // status, substep counter, num_chunks, fused-pass CTAs done,
-                                              // fused-pass chunk counter, spare
+                                              // fused-pass chunk counter, sort-assign CTAs done, spare
     // surrogate window: sums, box, gate word, stats, the wrench before the window
     L.sur = take(16 * sizeof(double) + 8 * sizeof(int) + 8 * sizeof(double) + kcap * 6 * sizeof(double));
     L.sur_reduce = take((size_t)kReduceBlocks * 4 * sizeof(Pair) + 16);  // per-block totals, ticket
@@ -161,9 +161,10 @@ struct PipeState {
     bool order_valid = false;  // perm (sorted slot -> particle) matches them too
     bool grid_valid = false;   // grid g holds the transfer of the current state
     bool rechunk = false;      // the chunk size changed since the scan: recut the chunk list
+    bool counts_pending = false;  // the bin counts of the current keys are in hist, not yet scanned
     bool operator==(const PipeState& o) const {
         return cur == o.cur && g == o.g && scanned == o.scanned && order_valid == o.order_valid &&
-               grid_valid == o.grid_valid && rechunk == o.rechunk;
+               grid_valid == o.grid_valid && rechunk == o.rechunk && counts_pending == o.counts_pending;
     }
 };
 
@@ -257,6 +258,7 @@ struct mpm_sim {
     uint32_t* num_chunks() { return at<uint32_t>(L.counters) + 2; }
     uint32_t* done() { return at<uint32_t>(L.counters) + 3; }
     uint32_t* work() { return at<uint32_t>(L.counters) + 4; }
+    uint32_t* scan_done() { return at<uint32_t>(L.counters) + 5; }
     uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
     uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
@@ -443,6 +445,7 @@ mpm_status ensure_scanned(mpm_sim* s, cudaStream_t st) {
     }
     MPM_TRY(enqueue_scan(s, st));
     s->ps.scanned = true;
+    s->ps.counts_pending = false;
     return MPM_OK;
 }
 
@@ -474,9 +477,24 @@ mpm_status ensure_grid(mpm_sim* s, cudaStream_t st) {
 // First half of a substep: the sort-assign of the current state and the grid update of its transfer.
 mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate = nullptr, uint32_t gate_run = 1,
                              double* p0_sums = nullptr) {
-    MPM_TRY(ensure_scanned(s, st));
+    // the fused pass left its bin counts unscanned: the sort-assign CTAs of this launch scan them
+    const bool scan_here = s->ps.counts_pending && !s->ps.rechunk && !gate && s->ps.grid_valid && s->tail_scan();
+    if (!scan_here) MPM_TRY(ensure_scanned(s, st));
     MPM_TRY(ensure_grid(s, st));
     AssignGridParams ap{};
+    if (scan_here) {
+        ap.scan = 1;
+        ap.hist = s->at<uint32_t>(s->L.hist);
+        ap.cursor_out = s->at<uint32_t>(s->L.cursor);
+        ap.chunks = s->at<int4>(s->L.chunks);
+        ap.num_chunks = s->num_chunks();
+        ap.bin_env = s->nenv > 1 ? s->at<uint32_t>(s->L.bin_env) : nullptr;
+        ap.total_bins = (int)s->T.bins;
+        ap.chunk = s->chunk;
+        ap.scan_done = s->scan_done();
+        s->ps.scanned = true;
+        s->ps.counts_pending = false;
+    }
     ap.gate = gate;
     ap.gate_run = gate_run;
     ap.grid = grid_params(s);
@@ -486,6 +504,7 @@ mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate =
     ap.cursor = s->at<uint32_t>(s->L.cursor);
     ap.perm = s->at<uint32_t>(s->L.perm);
     ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 1023) / 1024;  // 4 particles per thread
+    if (scan_here && ap.assign_ctas == 0) ap.assign_ctas = 1;  // someone must scan (and clear) the counts
     MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
     s->ps.order_valid = true;
     return MPM_OK;
@@ -505,13 +524,19 @@ mpm_status enqueue_particle_half(mpm_sim* s, cudaStream_t st, float advect_dt = 
     p.list_out = s->list(1 - s->ps.g);
     p.list_count_out = s->list_count(1 - s->ps.g);
     if (advect_dt > 0.0f) p.env0.geo.dt = advect_dt;
+    // Plain substeps with few bins leave the new counts for the next grid-half launch to scan; a gated
+    // window's launch (both branches enqueued, one runs) scans at the end of the fused pass as before.
+    const bool defer = s->tail_scan() && !gate && scatter;
+    if (defer) p.tail_scan = 0;
     MPM_TRY(launch(s, MPM_K_G2P2G, st, [&] { return launch_g2p2g(p, s->sms * s->fused_cps, st); }, "g2p2g"));
     s->ps.cur = 1 - s->ps.cur;
     s->ps.g = 1 - s->ps.g;
     s->ps.order_valid = false;  // assigned by the next launch
     s->ps.grid_valid = scatter;
-    s->ps.scanned = s->tail_scan();  // the fused pass's last CTA wrote the new bins
-    if (!s->ps.scanned) MPM_TRY(ensure_scanned(s, st));
+    s->ps.counts_pending = defer;
+    if (defer) s->ps.rechunk = false;  // the pending counts are cut with the current chunk size
+    s->ps.scanned = s->tail_scan() && !defer;  // the fused pass's last CTA wrote the new bins
+    if (!s->ps.scanned && !defer) MPM_TRY(ensure_scanned(s, st));
     return MPM_OK;
 }
 

@@ -538,6 +538,81 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t* hist, uint32_t* cursor,
         scan_bins<0>(hist, cursor, chunks, num_chunks, bin_env, nblocks, chunk, warp_tot);
 }
 
+// The bin counts' exclusive prefix into shared memory (cur_sh, total_bins padded to 4), each count read
+// from L2 once: a thread copies its run of 4-bin groups into cur_sh while summing, the CTA scans the
+// per-thread sums, and each thread turns its run into offsets in place. With `writer` the CTA also
+// writes the global offsets, the chunk list (chunks of at most `chunk` particles, tagged with the bin's
+// env) and its length. The counts are left in place.
+template <int CHUNK>
+__device__ __forceinline__ void scan_counts_shared(const uint32_t* hist, uint32_t* cur_sh, int nblocks, int chunk_arg,
+                                                   bool writer, uint32_t* cursor, int4* chunks, uint32_t* num_chunks,
+                                                   const uint32_t* bin_env, uint32_t (&warp_tot)[2][32]) {
+    const int chunk = CHUNK > 0 ? CHUNK : chunk_arg;
+    const int tid = threadIdx.x;
+    const int nq = (nblocks + 3) >> 2;
+    const int per = (nq + blockDim.x - 1) / blockDim.x;
+    const int q0 = min(tid * per, nq), q1 = min(q0 + per, nq);
+    const uint4* H = reinterpret_cast<const uint4*>(hist);
+    uint4* S = reinterpret_cast<uint4*>(cur_sh);
+    uint32_t cnt = 0, nch = 0;
+    for (int q = q0; q < q1; q += 8) {
+        uint4 h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = q + u < q1 ? __ldcg(&H[q + u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q + u < q1) S[q + u] = h[u];
+            const uint32_t c4[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                cnt += c4[e];
+                nch += (c4[e] + chunk - 1) / chunk;
+            }
+        }
+    }
+    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t ic = cnt, in = nch;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t tc = __shfl_up_sync(0xffffffffu, ic, d), tn = __shfl_up_sync(0xffffffffu, in, d);
+        if (lane >= d) { ic += tc; in += tn; }
+    }
+    if (lane == 31) { warp_tot[0][wid] = ic; warp_tot[1][wid] = in; }
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t vc = lane < nw ? warp_tot[0][lane] : 0u, vn = lane < nw ? warp_tot[1][lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t tc = __shfl_up_sync(0xffffffffu, vc, d), tn = __shfl_up_sync(0xffffffffu, vn, d);
+            if (lane >= d) { vc += tc; vn += tn; }
+        }
+        if (lane < nw) { warp_tot[0][lane] = vc; warp_tot[1][lane] = vn; }
+    }
+    __syncthreads();
+    uint32_t off = ic - cnt + (wid > 0 ? warp_tot[0][wid - 1] : 0u);
+    uint32_t coff = in - nch + (wid > 0 ? warp_tot[1][wid - 1] : 0u);
+    const uint4* BE = reinterpret_cast<const uint4*>(bin_env);  // null: every bin is env 0's
+    for (int q = q0; q < q1; ++q) {
+        const uint4 h = S[q];
+        const uint32_t c4[4] = {h.x, h.y, h.z, h.w};
+        const uint4 be = (writer && BE) ? BE[q] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t e4[4] = {be.x, be.y, be.z, be.w};
+        uint32_t o4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            o4[e] = off;
+            if (writer)
+                for (uint32_t s = 0; s < c4[e]; s += chunk)
+                    chunks[coff++] = make_int4(4 * q + e, (int)(off + s), (int)min((uint32_t)chunk, c4[e] - s), (int)e4[e]);
+            off += c4[e];
+        }
+        S[q] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+        if (writer) reinterpret_cast<uint4*>(cursor)[q] = S[q];
+    }
+    if (writer && tid == blockDim.x - 1) *num_chunks = coff;
+}
+
 // Grid-wide scan for many bins, kernel 1: per tile of kScanTile bins, the sums of particles and chunks.
 __global__ void __launch_bounds__(256) k_scan_tiles(ScanParams p) {
     wait_for_predecessor();
@@ -1314,12 +1389,56 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
 
 // The sort-assign of the state the previous fused pass wrote (first assign_ctas CTAs) and the grid
 // update of the transfer it scattered (the remaining CTAs): independent work, one launch.
+// With p.scan (few bins, counts not yet scanned), every sort-assign CTA first scans the bin counts into
+// shared memory for itself (a few tens of KB read from L2), so no CTA waits for another: CTA 0 also
+// writes the global offsets and the next chunk list, and the last of them to finish reading the counts
+// clears them for the next substep. The scan so runs beside the grid update instead of at the end of
+// the fused pass, where the other SMs would idle.
 template <bool ONE_ENV, bool SHARED_POSES>
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
+    extern __shared__ uint4 dyn_sh[];  // p.scan: the bin offsets (total_bins, padded to 4)
     wait_for_predecessor();  // (a CTA's exit releases the successor)
     if (p.gate && *p.gate != p.gate_run) return;  // the other branch of a gated window runs instead
     if ((int)blockIdx.x < p.assign_ctas) {
-        assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
+        if (!p.scan) {
+            assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
+            return;
+        }
+        __shared__ uint32_t warp_tot[2][32];
+        __shared__ bool last;
+        uint32_t* cur_sh = reinterpret_cast<uint32_t*>(dyn_sh);
+        // this thread's (bin, rank) pairs are requested before the scan, which does not need them
+        const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * kAssignPerThread;
+        const bool full = j0 + kAssignPerThread <= p.N;
+        uint4 kr0 = make_uint4(0u, 0u, 0u, 0u), kr1 = kr0;
+        if (full) {
+            const uint4* q = reinterpret_cast<const uint4*>(p.keyrank + j0);
+            kr0 = q[0];
+            kr1 = q[1];
+        }
+        const bool writer = blockIdx.x == 0;
+        if (p.chunk == kChunk)
+            scan_counts_shared<kChunk>(p.hist, cur_sh, p.total_bins, kChunk, writer, p.cursor_out, p.chunks,
+                                       p.num_chunks, p.bin_env, warp_tot);
+        else
+            scan_counts_shared<0>(p.hist, cur_sh, p.total_bins, p.chunk, writer, p.cursor_out, p.chunks,
+                                  p.num_chunks, p.bin_env, warp_tot);
+        __syncthreads();  // this CTA's reads of the counts are done, its offsets are in shared memory
+        if (threadIdx.x == 0) last = atomicAdd(p.scan_done, 1u) == (uint32_t)p.assign_ctas - 1u;
+        __syncthreads();
+        if (last) {  // every sort-assign CTA has read the counts: clear them for the next substep
+            uint4* H = reinterpret_cast<uint4*>(p.hist);
+            for (int q = threadIdx.x; q < (p.total_bins + 3) >> 2; q += blockDim.x) H[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (threadIdx.x == 0) *p.scan_done = 0u;
+        }
+        if (full) {
+            p.perm[cur_sh[kr0.x] + kr0.y] = (uint32_t)j0;
+            p.perm[cur_sh[kr0.z] + kr0.w] = (uint32_t)(j0 + 1);
+            p.perm[cur_sh[kr1.x] + kr1.y] = (uint32_t)(j0 + 2);
+            p.perm[cur_sh[kr1.z] + kr1.w] = (uint32_t)(j0 + 3);
+        } else {
+            for (int j = j0; j < p.N; ++j) assign_slot(j, p.N, p.keyrank, cur_sh, p.perm);
+        }
         return;
     }
     grid_update_cta<ONE_ENV, SHARED_POSES>(p.grid, blockIdx.x - p.assign_ctas);
@@ -1401,11 +1520,12 @@ static inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b -
 // Launch with programmatic stream serialization: the kernel may start while its predecessor on the
 // stream drains; it orders itself with wait_for_predecessor().
 template <typename P>
-static cudaError_t launch_dependent(void (*kernel)(P), unsigned grid, unsigned block, cudaStream_t s, const P& p) {
+static cudaError_t launch_dependent(void (*kernel)(P), unsigned grid, unsigned block, cudaStream_t s, const P& p,
+                                    size_t smem = 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1477,11 +1597,18 @@ cudaError_t launch_g2p2g(const TransferParams& p, int grid_ctas, cudaStream_t s)
                             fused_cta_threads(p.chunk), s, p);
 }
 
+size_t assign_scan_smem(int total_bins) { return (size_t)((total_bins + 3) & ~3) * sizeof(uint32_t); }
+
 cudaError_t launch_assign_grid(const AssignGridParams& p, cudaStream_t s) {
     const bool sp = p.grid.k_total <= kSharedPoses;
     auto k = p.grid.one_env ? (sp ? k_assign_grid<true, true> : k_assign_grid<true, false>)
                             : (sp ? k_assign_grid<false, true> : k_assign_grid<false, false>);
-    return launch_dependent(k, p.assign_ctas + p.grid.ctas, 256, s, p);
+    const size_t smem = p.scan ? assign_scan_smem(p.total_bins) : 0;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_dependent(k, p.assign_ctas + p.grid.ctas, 256, s, p, smem);
 }
 
 cudaError_t launch_read_state(int N, const EnvDesc* envs, int nenv, StateView src, float* x, float* v, float* C,
