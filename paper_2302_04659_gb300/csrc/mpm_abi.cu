@@ -230,7 +230,7 @@ struct mpm_sim {
     ColliderSet* stage = nullptr;  // pinned staging for collider uploads
     cudaEvent_t stage_done = nullptr;
     int sms = 0;
-    int chunk = kChunk, fused_cps = 1, grid_cps = 2, p2g_cps = 1, max_fused_cps = 1;
+    int chunk = kChunk, fused_cps = 1, grid_cps = 1, p2g_cps = 1, max_fused_cps = 1;
     long long launches = 0;
     unsigned timing_mask = 0;
     struct Ev {
@@ -504,7 +504,9 @@ mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate =
     ap.cursor = s->at<uint32_t>(s->L.cursor);
     ap.perm = s->at<uint32_t>(s->L.perm);
     ap.assign_ctas = s->ps.order_valid ? 0 : (s->N + 1023) / 1024;  // 4 particles per thread
-    if (scan_here && ap.assign_ctas == 0) ap.assign_ctas = 1;  // someone must scan (and clear) the counts
+    if (scan_here) {  // fewer, longer sort-assign CTAs (each scans the counts once); at least one, to clear them
+        ap.assign_ctas = std::max(1, (s->N + 1024 * kScanAssignRounds - 1) / (1024 * kScanAssignRounds));
+    }
     MPM_TRY(launch(s, MPM_K_GRID, st, [&] { return launch_assign_grid(ap, st); }, "assign_grid"));
     s->ps.order_valid = true;
     return MPM_OK;

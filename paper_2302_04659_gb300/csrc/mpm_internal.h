@@ -29,6 +29,10 @@ constexpr int kPoseSteps = 64;
 constexpr int kTailScanMaxBins = 16384;
 constexpr int kScanTile = 1024;  // bins per CTA of the grid-wide scan
 
+// Sort-assign CTAs that also scan the bin counts take this many runs of 1,024 particles each (one scan
+// per CTA serves them all).
+constexpr int kScanAssignRounds = 2;
+
 // Internal-consistency flag: a particle was found outside the bin it was sorted into.
 constexpr uint32_t kFlagInternal = 0x80000000u;
 

@@ -1407,14 +1407,21 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
         __shared__ uint32_t warp_tot[2][32];
         __shared__ bool last;
         uint32_t* cur_sh = reinterpret_cast<uint32_t*>(dyn_sh);
-        // this thread's (bin, rank) pairs are requested before the scan, which does not need them
-        const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * kAssignPerThread;
-        const bool full = j0 + kAssignPerThread <= p.N;
-        uint4 kr0 = make_uint4(0u, 0u, 0u, 0u), kr1 = kr0;
-        if (full) {
-            const uint4* q = reinterpret_cast<const uint4*>(p.keyrank + j0);
-            kr0 = q[0];
-            kr1 = q[1];
+        // this thread's (bin, rank) pairs are requested before the scan, which does not need them: a CTA
+        // takes kScanAssignRounds runs of blockDim.x * kAssignPerThread particles, four per thread per run
+        int j0[kScanAssignRounds];
+        bool full[kScanAssignRounds];
+        uint4 kr[kScanAssignRounds][2];
+#pragma unroll
+        for (int r = 0; r < kScanAssignRounds; ++r) {
+            j0[r] = ((blockIdx.x * kScanAssignRounds + r) * blockDim.x + threadIdx.x) * kAssignPerThread;
+            full[r] = j0[r] + kAssignPerThread <= p.N;
+            kr[r][0] = kr[r][1] = make_uint4(0u, 0u, 0u, 0u);
+            if (full[r]) {
+                const uint4* q = reinterpret_cast<const uint4*>(p.keyrank + j0[r]);
+                kr[r][0] = q[0];
+                kr[r][1] = q[1];
+            }
         }
         const bool writer = blockIdx.x == 0;
         if (p.chunk == kChunk)
@@ -1431,13 +1438,16 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
             for (int q = threadIdx.x; q < (p.total_bins + 3) >> 2; q += blockDim.x) H[q] = make_uint4(0u, 0u, 0u, 0u);
             if (threadIdx.x == 0) *p.scan_done = 0u;
         }
-        if (full) {
-            p.perm[cur_sh[kr0.x] + kr0.y] = (uint32_t)j0;
-            p.perm[cur_sh[kr0.z] + kr0.w] = (uint32_t)(j0 + 1);
-            p.perm[cur_sh[kr1.x] + kr1.y] = (uint32_t)(j0 + 2);
-            p.perm[cur_sh[kr1.z] + kr1.w] = (uint32_t)(j0 + 3);
-        } else {
-            for (int j = j0; j < p.N; ++j) assign_slot(j, p.N, p.keyrank, cur_sh, p.perm);
+#pragma unroll
+        for (int r = 0; r < kScanAssignRounds; ++r) {
+            if (full[r]) {
+                p.perm[cur_sh[kr[r][0].x] + kr[r][0].y] = (uint32_t)j0[r];
+                p.perm[cur_sh[kr[r][0].z] + kr[r][0].w] = (uint32_t)(j0[r] + 1);
+                p.perm[cur_sh[kr[r][1].x] + kr[r][1].y] = (uint32_t)(j0[r] + 2);
+                p.perm[cur_sh[kr[r][1].z] + kr[r][1].w] = (uint32_t)(j0[r] + 3);
+            } else {
+                for (int j = j0[r]; j < min(p.N, j0[r] + kAssignPerThread); ++j) assign_slot(j, p.N, p.keyrank, cur_sh, p.perm);
+            }
         }
         return;
     }
