@@ -230,7 +230,7 @@ struct mpm_sim {
     ColliderSet* stage = nullptr;  // pinned staging for collider uploads
     cudaEvent_t stage_done = nullptr;
     int sms = 0;
-    int chunk = kChunk, fused_cps = 1, grid_cps = 1, p2g_cps = 1, max_fused_cps = 1;
+    int chunk = kChunk, fused_cps = 1, grid_cps = 2, p2g_cps = 1, max_fused_cps = 1;
     long long launches = 0;
     unsigned timing_mask = 0;
     struct Ev {
