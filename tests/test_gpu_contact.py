@@ -91,7 +91,11 @@ def test_particle_contact_across_env_steps():
         amb_any |= amb
     keep = ~stencil_neighbours(sc.x, sc.n, amb_any)
     assert (~keep).sum() <= 2e-3 * sc.N
-    _check_state(out, ref, keep, sc.n, tol_scale=4.0)
+    # measured on a GB300: e_x 3.2e-8, e_v 1.1e-5, e_C 8.7e-6, e_F 1.4e-7, impulses 3.9e-5 relative;
+    # the state bounds are 0.35x the per-substep tolerances (about 3x the measured e_v)
+    errs = _check_state(out, ref, keep, sc.n, tol_scale=0.35)
+    print("contact across env steps: e_x {:.2e} e_v {:.2e} e_C {:.2e} e_F {:.2e}".format(*errs),
+          "wrench", rel(wr, wref))
     assert nsub == 4
     _check_wrench(wr, wref)
 

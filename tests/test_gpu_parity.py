@@ -168,8 +168,9 @@ def test_cube_rollout_statistics():
 
 
 def test_pinch_one_env_step_position_error():
-    """One environment step (25 substeps) of the pinch scene with the fingers closing: positions after
-    the step within 1e-3 relative of the oracle, the aggregate error bound for whole env steps."""
+    """One environment step (25 substeps) of the pinch scene with the fingers closing: positions,
+    displacements over the step and the fingers' impulses against the oracle (the aggregate bound for
+    whole env steps is 1e-3 on positions; the bounds here are about 3x the measured errors)."""
     sc, (pose, lin, ang, com) = _pinch_at(1001, 0.1)
     out, flags, (wr, nsub) = run_gpu(sc, 25, (pose, lin, ang, com))
     P = oracle_params(sc)
@@ -178,8 +179,13 @@ def test_pinch_one_env_step_position_error():
     wref = np.zeros((2, 6))
     oracle.rollout(P, ref, 25, cols, 0.0, wref)
     assert nsub == 25
-    assert rel(out["x"], ref.x) <= 1e-3
+    ex = rel(out["x"], ref.x)
     disp_gpu = out["x"].astype(np.float64) - sc.x
     disp_ref = ref.x - sc.x
-    assert rel(disp_gpu, disp_ref) <= 2e-2
-    assert rel(wr, wref) <= 1e-2
+    ed = rel(disp_gpu, disp_ref)
+    ew = rel(wr, wref)
+    print(f"pinch env step: e_x {ex:.2e}, displacement {ed:.2e}, wrench {ew:.2e}")
+    # measured on a GB300: e_x 5.5e-8, displacement 3.0e-4, wrench 8.3e-7; bounds about 3x those
+    assert ex <= 2e-7
+    assert ed <= 1e-3
+    assert ew <= 3e-6
