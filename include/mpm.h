@@ -293,7 +293,9 @@ mpm_status mpm_surrogate_features(mpm_sim* sim, const mpm_box* box, float m_scal
  * |sum_i m_i - sum_p m_p| / sum_p m_p, out[1] = momentum residual |P_hat - P_exp| / (M v_ref), where
  * P_hat is the momentum of the corrected nodes and P_exp = P_0 + (k + 1)/2 (P_1 - P_0) the first-order
  * mean momentum over k substeps from the momentum before (P_0) and after (P_1) one plain grid update;
- * out[2] = M, out[3] = |P_hat - P_exp|. Synchronizes `stream`. */
+ * out[2] = M, out[3] = |P_hat - P_exp|. v_ref = 0 takes the scene's own velocity scale: the
+ * mass-weighted RMS node speed of the transfer at the window start, sqrt(sum_i |m v_i|^2 / m_i / M).
+ * MPM_ERR_INVALID_ARG for v_ref < 0. Synchronizes `stream`. */
 mpm_status mpm_surrogate_check(mpm_sim* sim, const mpm_box* box, const float* d_dv, float dv_unit, int k,
                                double v_ref, double* out, void* stream);
 
@@ -313,7 +315,7 @@ typedef struct {
     const float* bias[4];
     float m_scale, v_scale;  /* network input: (m * m_scale, v * v_scale) */
     float dv_unit;           /* m/s per network output unit */
-    double v_ref;            /* velocity scale of the momentum residual */
+    double v_ref;            /* velocity scale of the momentum residual (m/s); 0: the scene's RMS node speed */
     double threshold;        /* fallback when the mass or momentum residual exceeds this */
     int k;                   /* substeps per window, odd */
     int margin;              /* nodes added around the material's bins for the box */

@@ -262,7 +262,7 @@ struct mpm_sim {
     uint32_t* list(int which) { return at<uint32_t>(L.list[which]); }
     uint32_t* list_count(int which) { return at<uint32_t>(L.list_meta) + which; }
     uint32_t* grid_done() { return at<uint32_t>(L.list_meta) + 2; }
-    double* sur_sums() { return at<double>(L.sur); }  // M, P0[3], P1[3], P_hat[3]
+    double* sur_sums() { return at<double>(L.sur); }  // a window's kSumWindow sums, then 3 spare at [12..15)
     int* sur_box() { return reinterpret_cast<int*>(at<char>(L.sur) + 16 * sizeof(double)); }
     uint32_t* sur_gate() { return at<uint32_t>(L.sur + 16 * sizeof(double) + 6 * sizeof(int)); }
     unsigned long long* sur_stats() { return at<unsigned long long>(L.sur + 16 * sizeof(double) + 8 * sizeof(int)); }
@@ -1241,7 +1241,7 @@ mpm_status mpm_surrogate_features(mpm_sim* s, const mpm_box* box, float m_scale,
 
 mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv, float dv_unit, int k,
                                double v_ref, double* out, void* stream) {
-    if (!s || !s->sur_pending || !valid_box(box) || !d_dv || !out || k < 1 || !(v_ref > 0.0))
+    if (!s || !s->sur_pending || !valid_box(box) || !d_dv || !out || k < 1 || !(v_ref >= 0.0))
         return MPM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* sums = s->sur_sums();
@@ -1250,7 +1250,7 @@ mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv
     MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box), d_dv,
                                 dv_unit, 0, sums + 7, st),
              "sur_check");
-    double h[10];
+    double h[kSumWindow];
     MPM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st), "copy sums");
     MPM_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     const double M = h[0];
@@ -1260,6 +1260,7 @@ mpm_status mpm_surrogate_check(mpm_sim* s, const mpm_box* box, const float* d_dv
         const double pexp = h[1 + a] + 0.5 * (k + 1) * (h[4 + a] - h[1 + a]);
         d2 += (h[7 + a] - pexp) * (h[7 + a] - pexp);
     }
+    if (v_ref == 0.0) v_ref = M > 0.0 && h[kSumK0] > 0.0 ? std::sqrt(h[kSumK0] / M) : 1e-30;  // the scene's
     out[0] = Mp > 0.0 ? std::fabs(M - Mp) / Mp : 0.0;
     out[1] = M > 0.0 ? std::sqrt(d2) / (M * v_ref) : 0.0;
     out[2] = M;
@@ -1275,7 +1276,7 @@ mpm_status mpm_surrogate_advance(mpm_sim* s, const mpm_box* box, const float* d_
     if (d_dv) {
         const Geometry& g = s->envs[0].geo;
         MPM_CUDA(launch_sur_correct(s->at<float4>(s->L.grid[s->ps.g]), g.n, g.nb, s->cfg.bound, to_sur_box(box),
-                                    d_dv, dv_unit, 1, s->sur_sums() + 10, st),
+                                    d_dv, dv_unit, 1, s->sur_sums() + 12, st),
                  "sur_apply");
         MPM_TRY(enqueue_particle_half(s, st, (float)k * s->cfg.dt));
         if (k > 1) {
@@ -1324,7 +1325,7 @@ NetLayout net_layout(int max_voxels, int max_particles = 0) {
     L.wrench = take(MPM_MAX_COLLIDERS * 6 * sizeof(double));
     L.cols = take(MPM_MAX_COLLIDERS * sizeof(ColliderSet));
     L.words = take(4 * sizeof(uint32_t));
-    L.slots = take(kGateSlots * 10 * sizeof(double));
+    L.slots = take(kGateSlots * kSumWindow * sizeof(double));
     L.total = off;
     return L;
 }
@@ -1467,7 +1468,7 @@ mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* 
         s->drop_graphs();
         return MPM_OK;
     }
-    if (net->k < 1 || net->k % 2 == 0 || net->margin < 0 || !(net->dv_unit > 0.0f) || !(net->v_ref > 0.0) ||
+    if (net->k < 1 || net->k % 2 == 0 || net->margin < 0 || !(net->dv_unit > 0.0f) || !(net->v_ref >= 0.0) ||
         max_voxels < 1 || s->env_cfg[0].max_colliders > kSharedPoses)
         return MPM_ERR_INVALID_ARG;
     MPM_TRY(resolve_pending(s));
@@ -1490,7 +1491,7 @@ mpm_status mpm_surrogate_attach(mpm_sim* s, const mpm_surrogate_net* net, void* 
     const NetLayout NL = net_layout(max_voxels, s->env_cfg[0].max_particles);
     MPM_CUDA(cudaMemset(s->sur_sums(), 0, 16 * sizeof(double)), "cudaMemset");
     MPM_CUDA(cudaMemset(s->net_ws + NL.words, 0, 4 * sizeof(uint32_t)), "cudaMemset");
-    MPM_CUDA(cudaMemset(s->net_ws + NL.slots, 0, kGateSlots * 10 * sizeof(double)), "cudaMemset");
+    MPM_CUDA(cudaMemset(s->net_ws + NL.slots, 0, kGateSlots * kSumWindow * sizeof(double)), "cudaMemset");
     return MPM_OK;
 }
 
@@ -1569,7 +1570,7 @@ mpm_status mpm_surrogate_step(mpm_sim* s, int n_substeps, int gate, void* stream
         double* slots = reinterpret_cast<double*>(s->net_ws + NL.slots);
         const double mp = (double)s->envs[0].part_count * s->envs[0].mat.p_mass;
         for (int w = 0; w < nwin && r == MPM_OK; ++w) {
-            r = enqueue_window(s, b, gate, s->cap_stream, slots + (size_t)(w % kGateSlots) * 10);
+            r = enqueue_window(s, b, gate, s->cap_stream, slots + (size_t)(w % kGateSlots) * kSumWindow);
             const int done = w % kGateSlots + 1;  // windows waiting in the slots
             if (r == MPM_OK && gate == 1 && (done == kGateSlots || w + 1 == nwin)) {
                 const cudaError_t e = launch_sur_decide(slots, done, mp, s->net.k, s->net.v_ref, s->net.threshold,

@@ -33,6 +33,11 @@ constexpr int kScanTile = 1024;  // bins per CTA of the grid-wide scan
 // per CTA serves them all).
 constexpr int kScanAssignRounds = 2;
 
+// A surrogate window's gate sums: M, P0[3], P1[3], P_hat[3] and K0 = sum_i |m v_i|^2 / m_i of the
+// transfer (the scene's velocity scale), kSumWindow doubles per window.
+constexpr int kSumK0 = 10;
+constexpr int kSumWindow = 12;
+
 // Internal-consistency flag: a particle was found outside the bin it was sorted into.
 constexpr uint32_t kFlagInternal = 0x80000000u;
 

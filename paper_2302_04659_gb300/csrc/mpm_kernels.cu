@@ -1254,7 +1254,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         __syncthreads();
     }
     constexpr uint32_t kLocalMask = (1u << kLocalBinBits) - 1u;
-    Pair p0[4] = {};  // mass and momentum of the transfer (for a surrogate's gate)
+    Pair p0[5] = {};  // mass, momentum and sum |m v|^2 / m of the transfer (for a surrogate's gate)
     for (; item < max(n_old, n_new); item += stride) {
         // item, and so env and bin, are uniform across each warp
         if (item < n_old) {  // a bin of the previous grid: zeroed for its next use
@@ -1283,6 +1283,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
             p0[1] = pair_add(p0[1], gv.y);
             p0[2] = pair_add(p0[2], gv.z);
             p0[3] = pair_add(p0[3], gv.w);
+            if (gv.x > 0.0f) p0[4] = pair_add(p0[4], (gv.y * gv.y + gv.z * gv.z + gv.w * gv.w) / gv.x);
         }
         const bool has_mass = gv.x > 0.0f;
         const float m = gv.x;
@@ -1357,19 +1358,20 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         *node = make_float4(v[0], v[1], v[2], m);
     }
     if (p.p0_sums) {  // (uniform) this CTA's sums as FP32 pairs, one FP64 atomic per component
-        __shared__ Pair ps[8][4];
+        __shared__ Pair ps[8][5];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 5; ++q)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) p0[q] = pair_add(p0[q], pair_shfl_xor(p0[q], off));
         if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ps[threadIdx.x >> 5][q] = p0[q];
+            for (int q = 0; q < 5; ++q) ps[threadIdx.x >> 5][q] = p0[q];
         __syncthreads();
-        if (threadIdx.x < 4) {
+        if (threadIdx.x < 5) {
             Pair t{0.0f, 0.0f};
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = pair_add(t, ps[w][threadIdx.x]);
-            if (t.hi != 0.0f) atomicAdd(&p.p0_sums[threadIdx.x], pair_value(t));
+            // M and P0 at p0_sums[0..4), K0 at p0_sums[kSumK0]
+            if (t.hi != 0.0f) atomicAdd(&p.p0_sums[threadIdx.x < 4 ? threadIdx.x : kSumK0], pair_value(t));
         }
     }
     __syncthreads();

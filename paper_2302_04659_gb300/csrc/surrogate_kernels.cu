@@ -141,11 +141,13 @@ __global__ void k_sur_step_restore(double* wrench, const double* wrench_saved, i
     if (threadIdx.x == 0) *counter = words[1];
 }
 
-// Mass and momentum of the transfer, before the grid update (nodes hold (m, m v)).
+// Mass and momentum of the transfer, before the grid update (nodes hold (m, m v)), into sums[0..4), and
+// sum_i |m v_i|^2 / m_i (twice the nodes' kinetic energy) into sums[kSumK0].
 __global__ void k_sur_moments(const float4* __restrict__ grid, const uint32_t* __restrict__ list,
                               const uint32_t* __restrict__ count, double* sums) {
     const uint32_t n = *count;
     Pair v[4] = {};
+    Pair ke[1] = {};
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kBlkNodes; i += gridDim.x * blockDim.x) {
         const uint32_t b = list[i / kBlkNodes] & kLocalMask;
         const float4 g = grid[(size_t)b * kBlkNodes + i % kBlkNodes];
@@ -153,8 +155,10 @@ __global__ void k_sur_moments(const float4* __restrict__ grid, const uint32_t* _
         v[1] = pair_add(v[1], g.y);
         v[2] = pair_add(v[2], g.z);
         v[3] = pair_add(v[3], g.w);
+        if (g.x > 0.0f) ke[0] = pair_add(ke[0], (g.y * g.y + g.z * g.z + g.w * g.w) / g.x);
     }
     block_sum_atomic<4>(v, sums);
+    block_sum_atomic<1>(ke, sums + kSumK0);
 }
 
 __device__ __forceinline__ bool box_node(const SurBox& b, size_t t, int& i, int& j, int& k) {
@@ -230,7 +234,7 @@ struct GateArgs {
     SurBox box;
     const float* dv;
     float unit;
-    double* sums;            // M, P0[3] (k_sur_moments), P1[3] (k_sur_features), P_hat[3] (here)
+    double* sums;            // M, P0[3] (k_sur_moments), P1[3] (k_sur_features), P_hat[3] (here), K0
     double m_particles, v_ref, threshold;
     int k;
     uint32_t* gate;
@@ -240,12 +244,14 @@ struct GateArgs {
     Pair* partials;           // per-block totals (kReduceBlocks x 3)
 };
 
-// The residuals of a window from its sums S = (M, P0[3], P1[3], P_hat[3]): the grid mass against the
+// The residuals of a window from its sums S = (M, P0[3], P1[3], P_hat[3], K0): the grid mass against the
 // particles', and the corrected grid's momentum against the momentum the first substep's change predicts
-// for the window, P0 + (k + 1)/2 (P1 - P0), relative to M v_ref.
+// for the window, P0 + (k + 1)/2 (P1 - P0), relative to M v_ref. v_ref = 0 takes the scene's own velocity
+// scale, the mass-weighted RMS node speed of the transfer sqrt(K0 / M) (K0 = sum_i |m v_i|^2 / m_i).
 __device__ __forceinline__ void window_residuals(const double* S, double m_particles, int k, double v_ref,
                                                  double& r_mass, double& r_mom) {
     const double M = S[0];
+    if (!(v_ref > 0.0)) v_ref = M > 0.0 && S[kSumK0] > 0.0 ? sqrt(S[kSumK0] / M) : 1e-30;
     double d2 = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -259,8 +265,8 @@ __device__ __forceinline__ void window_residuals(const double* S, double m_parti
 // The gate's decision from the complete sums: residuals, gate word, stats; the sums are zeroed for the
 // next window. One thread.
 __device__ void gate_decide(const GateArgs& g) {
-    double S[10];
-    for (int q = 0; q < 10; ++q) S[q] = __ldcg(&g.sums[q]);
+    double S[kSumWindow];
+    for (int q = 0; q < kSumWindow; ++q) S[q] = __ldcg(&g.sums[q]);
     double r_mass, r_mom;
     window_residuals(S, g.m_particles, g.k, g.v_ref, r_mass, r_mom);
     const bool ok = r_mass <= g.threshold && r_mom <= g.threshold;  // a NaN residual fails
@@ -270,7 +276,7 @@ __device__ void gate_decide(const GateArgs& g) {
     if (!ok && !g.any_failed) g.stats[1] += 1ull;
     reinterpret_cast<double*>(g.stats)[2] = r_mass;
     reinterpret_cast<double*>(g.stats)[3] = r_mom;
-    for (int q = 0; q < 10; ++q) g.sums[q] = 0.0;
+    for (int q = 0; q < kSumWindow; ++q) g.sums[q] = 0.0;
 }
 
 __global__ void k_sur_check_gate(GateArgs g) {
@@ -315,7 +321,7 @@ __global__ void k_sur_gate(const double* sums, double m_particles, int k, double
     reinterpret_cast<double*>(stats)[3] = r_mom;
 }
 
-// The per-step gate over the windows of a step, one warp: window w's sums are slots[10 w ..]; a window
+// The per-step gate over the windows of a step, one warp: window w's sums are slots[kSumWindow w ..]; a window
 // that fails marks the step (any_failed) for a plain redo. The stats count the windows and keep the last
 // window's residuals; the slots are zeroed for the next step.
 __global__ void k_sur_decide(double* slots, int nwin, double m_particles, int k, double v_ref, double threshold,
@@ -325,7 +331,7 @@ __global__ void k_sur_decide(double* slots, int nwin, double m_particles, int k,
     for (int w0 = 0; w0 < nwin; w0 += 32) {
         const int w = w0 + lane;
         if (w < nwin) {
-            double* S = slots + (size_t)w * 10;
+            double* S = slots + (size_t)w * kSumWindow;
             double r_mass, r_mom;
             window_residuals(S, m_particles, k, v_ref, r_mass, r_mom);
             failed |= !(r_mass <= threshold && r_mom <= threshold);  // a NaN residual fails
@@ -334,7 +340,7 @@ __global__ void k_sur_decide(double* slots, int nwin, double m_particles, int k,
                 reinterpret_cast<double*>(stats)[3] = r_mom;
             }
 #pragma unroll
-            for (int q = 0; q < 10; ++q) S[q] = 0.0;
+            for (int q = 0; q < kSumWindow; ++q) S[q] = 0.0;
         }
     }
     if (__any_sync(0xffffffffu, failed) && lane == 0) *any_failed = 1u;

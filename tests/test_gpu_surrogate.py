@@ -64,6 +64,7 @@ def test_corrected_window_matches_oracle(mods, variant):
     m_scale = sur.mass_scale(sc.material.rho, sc.n)
     mpm.mpm_surrogate_features(sim.handle, box, m_scale, sur.V_SCALE, feat.data_ptr(), mask.data_ptr())
     r = mpm.mpm_surrogate_check(sim.handle, box, dvd.data_ptr(), sur.DV_UNIT, k, 1.0)
+    r_scene = mpm.mpm_surrogate_check(sim.handle, box, dvd.data_ptr(), sur.DV_UNIT, k, 0.0)
     mpm.mpm_surrogate_advance(sim.handle, box, dvd.data_ptr(), sur.DV_UNIT, k)
     out = sim.read_state(on_device=False)
     flags = sim.status()
@@ -93,6 +94,15 @@ def test_corrected_window_matches_oracle(mods, variant):
     pexp = sums["P0"] + 0.5 * (k + 1) * (sums["P1"] - sums["P0"])
     dref = np.linalg.norm(sums["P_hat"] - pexp)
     assert abs(r[3] - dref) <= 1e-4 * max(dref, 1e-6) + 1e-6 * M
+    # v_ref = 0: the residual relative to the scene's RMS node speed, sqrt(sum_i |m v_i|^2 / m_i / M) of the
+    # transfer at the window start (the oracle's transfer of the same state)
+    g0 = oracle.p2g(P, oracle_state(sc)).reshape(-1, 4)
+    has = g0[:, 0] > 0
+    v_rms = np.sqrt(((g0[has, 1:] ** 2).sum(1) / g0[has, 0]).sum() / g0[has, 0].sum())
+    if v_rms > 0.0:
+        assert abs(r_scene[1] - dref / (M * v_rms)) <= 1e-4 * dref / (M * v_rms) + 1e-6
+    else:  # material at rest: any momentum change is infinitely large against its scale
+        assert r_scene[1] >= 1e20 or dref == 0.0
     # the features hold the updated grid over the box
     g1 = feat.cpu().numpy()
     assert np.all((g1[..., 0] > 0) == (mask.cpu().numpy() > 0))
@@ -140,6 +150,23 @@ def test_substep_refused_inside_a_window(mods):
     sim.close()
 
 
+def test_network_gradients_tc_equal_mma(mods):
+    """The network's gradients with its input gradients on the tensor cores (tcgen05) equal those of the
+    mma.sync kernels on a training window, at the BF16 tolerance."""
+    mpm, sur = mods
+    samples = sur.generate([10002], particles=20_000, env_steps=2, sample_steps=(1,), windows_per_step=(0,))
+    x, mask, target = samples[0]
+    net = sur.Network(seed=3)
+    grads = {}
+    for eng in ("mma", "tc"):
+        net.backward_engine = eng
+        net.forward(x, mask)
+        loss = net.loss_and_backward(target, mask)
+        grads[eng] = [g.clone() for g in net.grads]
+    for a, b in zip(grads["tc"], grads["mma"]):
+        assert float((a - b).norm() / b.norm().clamp_min(1e-30)) <= 1e-2
+
+
 def test_training_lowers_the_loss(mods):
     mpm, sur = mods
     samples = sur.generate([10000, 10001], particles=20_000, env_steps=3, sample_steps=(1, 2),
@@ -166,6 +193,32 @@ def test_trained_network_gains_over_the_window_without_it(mods):
     assert with_net["rel_x_max"] <= 1e-3
     assert gated["rel_x_max"] <= 1e-3
     assert with_net["rel_to_displacement_mean"] < without["rel_to_displacement_mean"]
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                    "paper_2302_04659_gb300", "weights", "surrogate_pinch64.npz")),
+                    reason="trained weights not present")
+def test_gate_passes_the_trained_network_and_fires_on_a_mis_scaled_one(mods):
+    """With the momentum residual relative to the scene's own RMS node speed, the gate separates good from
+    bad corrections on held-out scenes: the trained network's windows pass, while the same network with its
+    output scaled by 3 (weights scaled on the host) and the window without any correction fall back to
+    plain substeps. Measured on 8 held-out scenes (GB300): fallback rates 0, 1 (x2 and x5) and 1."""
+    mpm, sur = mods
+    seeds = range(20000, 20004)
+    trained = sur.Network.load(sur.WEIGHTS)
+    bad = sur.Network.load(sur.WEIGHTS)
+    bad.w[3].mul_(3.0)
+    bad.b[3].mul_(3.0)
+    bad._init_state()
+    assert sur.V_REF == 0.0
+    r_ok = sur.summarize(sur.evaluate(trained, seeds, gate=True, steps=1))
+    r_bad = sur.summarize(sur.evaluate(bad, seeds, gate=True, steps=1))
+    r_none = sur.summarize(sur.evaluate(None, seeds, gate=True, steps=1))
+    assert r_ok["fallback_rate"] <= 0.1
+    assert r_bad["fallback_rate"] >= 0.9
+    assert r_none["fallback_rate"] >= 0.9
+    # a window that fell back is the plain method itself
+    assert r_bad["rel_x_max"] <= 1e-6
 
 
 def test_attached_step_matches_host_driven_windows(mods):
