@@ -64,6 +64,21 @@ mpm_status mpm_conv3d_forward_tc(int D, int H, int W, int cin, int cout, const v
 int mpm_conv3d_tc_packed_bytes(int cin, int cout);
 mpm_status mpm_conv3d_pack_tc(int cin, int cout, const void* w, void* packed, void* stream);
 
+/* Input gradient of a layer (cin -> cout; the definition of mpm_conv3d_backward_data, with the ReLU mask of
+ * act_in when it is not NULL) on the 5th-generation tensor cores: a convolution of the output gradient
+ * with the layer's adjoint weights (mirrored taps, swapped channel roles), packed for it by
+ * mpm_conv3d_pack_tc_adjoint from the layer's BF16 weights [27][cout][cin]
+ * (mpm_conv3d_tc_adjoint_packed_bytes bytes, 0 for unsupported counts). dy: D*H*W*cp BF16 with
+ * cp = 4, 16 or 32 (the smallest of those >= cout), channels beyond cout zero (mpm_pad_channels_bf16);
+ * act_in and dx: D*H*W*cin BF16. cin, cout in 1..32. dy, w_adj_packed 16-byte aligned (act_in too when
+ * cin = 32). */
+int mpm_conv3d_tc_adjoint_packed_bytes(int cin, int cout);
+mpm_status mpm_conv3d_pack_tc_adjoint(int cin, int cout, const void* w, void* packed, void* stream);
+mpm_status mpm_conv3d_backward_data_tc(int D, int H, int W, int cin, int cout, const void* dy, const void* w_adj_packed,
+                                       const void* act_in, void* dx, void* stream);
+/* Copy nvox voxels of c BF16 channels into c_pad >= c channels, zero-filling the rest. */
+mpm_status mpm_pad_channels_bf16(int nvox, int c, int c_pad, const void* src, void* dst, void* stream);
+
 /* Tiles of the tensor-core forward over a D x H x W box, and per tile the Chebyshev distance (in voxels,
  * capped at 5) from the tile to the nearest voxel whose mask byte is set. dist: one byte per tile. */
 int mpm_conv3d_tc_tile_count(int D, int H, int W);

@@ -142,6 +142,10 @@ def _load():
                                                             ctypes.c_int, _vp]),
         "mpm_conv3d_tc_packed_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "mpm_conv3d_pack_tc": (st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+        "mpm_conv3d_tc_adjoint_packed_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+        "mpm_conv3d_pack_tc_adjoint": (st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+        "mpm_conv3d_backward_data_tc": (st, [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, _vp]),
+        "mpm_pad_channels_bf16": (st, [ctypes.c_int] * 3 + [_vp, _vp, _vp]),
         "mpm_conv3d_tc_tile_count": (ctypes.c_int, [ctypes.c_int] * 3),
         "mpm_conv3d_tc_tile_dist": (st, [ctypes.c_int] * 3 + [_vp, _vp, _vp]),
         "mpm_net_tc_status": (st, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int, _vp]),
@@ -379,6 +383,23 @@ def mpm_conv3d_tc_packed_bytes(cin, cout) -> int:
 
 def mpm_conv3d_pack_tc(cin, cout, w, packed, stream=0):
     _check("mpm_conv3d_pack_tc", _load().mpm_conv3d_pack_tc(cin, cout, w, packed, stream))
+
+
+def mpm_conv3d_tc_adjoint_packed_bytes(cin, cout) -> int:
+    return _load().mpm_conv3d_tc_adjoint_packed_bytes(cin, cout)
+
+
+def mpm_conv3d_pack_tc_adjoint(cin, cout, w, packed, stream=0):
+    _check("mpm_conv3d_pack_tc_adjoint", _load().mpm_conv3d_pack_tc_adjoint(cin, cout, w, packed, stream))
+
+
+def mpm_conv3d_backward_data_tc(D, H, W, cin, cout, dy, w_adj_packed, act_in, dx, stream=0):
+    _check("mpm_conv3d_backward_data_tc", _load().mpm_conv3d_backward_data_tc(D, H, W, cin, cout, dy, w_adj_packed,
+                                                                              act_in or None, dx, stream))
+
+
+def mpm_pad_channels_bf16(nvox, c, c_pad, src, dst, stream=0):
+    _check("mpm_pad_channels_bf16", _load().mpm_pad_channels_bf16(nvox, c, c_pad, src, dst, stream))
 
 
 def mpm_conv3d_tc_tile_count(D, H, W) -> int:

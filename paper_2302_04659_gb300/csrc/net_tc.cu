@@ -50,7 +50,11 @@ struct Args {
     void* y;
     const uint8_t* tile_dist;  // per tile: distance to the nearest mask voxel (capped), or null
     int radius;                // with tile_dist: compute tiles within this distance
+    const __nv_bfloat16* act;  // if set, [vox][cout]: outputs are zeroed where act <= 0 (a ReLU's derivative)
 };
+
+// BF16 bits that are > 0 (sign clear, not zero); a NaN's sign bit is arbitrary, it never occurs here.
+__device__ __forceinline__ bool bf16_positive(uint32_t bits16) { return (bits16 & 0x8000u) == 0u && (bits16 & 0x7fffu) != 0u; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -166,11 +170,23 @@ __device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z
     if (y >= a.H || xx >= a.W) return;
     const size_t vox = ((size_t)z0 * a.H + y) * a.W + xx;
     if (!a.y_f32 && a.cout == 32) {
-        uint32_t packed[16];
+        uint32_t packed[16], am[16];
+        if (a.act) {  // the ReLU mask of the layer that produced this gradient's input
+            const uint4* src = reinterpret_cast<const uint4*>(a.act + vox * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 u = src[q];
+                am[4 * q] = u.x; am[4 * q + 1] = u.y; am[4 * q + 2] = u.z; am[4 * q + 3] = u.w;
+            }
+        }
 #pragma unroll
         for (int n = 0; n < 32; n += 2) {
             float v0 = acc[n] + (a.bias ? a.bias[n] : 0.0f), v1 = acc[n + 1] + (a.bias ? a.bias[n + 1] : 0.0f);
             if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+            if (a.act) {
+                if (!bf16_positive(am[n / 2] & 0xffffu)) v0 = 0.0f;
+                if (!bf16_positive(am[n / 2] >> 16)) v1 = 0.0f;
+            }
             const __nv_bfloat162 p2 = __floats2bfloat162_rn(v0, v1);
             packed[n / 2] = *reinterpret_cast<const uint32_t*>(&p2);
         }
@@ -184,6 +200,7 @@ __device__ __forceinline__ void epilogue(const Args& a, uint32_t tmem_acc, int z
             if (n >= a.cout) break;
             float v = acc[n] + (a.bias ? a.bias[n] : 0.0f);
             if (a.relu) v = fmaxf(v, 0.0f);
+            if (a.act && !bf16_positive(reinterpret_cast<const uint16_t*>(a.act)[vox * a.cout + n])) v = 0.0f;
             if (a.y_f32) static_cast<float*>(a.y)[vox * a.cout + n] = v;
             else static_cast<__nv_bfloat16*>(a.y)[vox * a.cout + n] = __float2bfloat16(v);
         }
@@ -540,9 +557,13 @@ int cg_of(int cin) { return cin == 4 ? 1 : cin / 8; }
 size_t packed_bytes(int cin, int cout) { return (size_t)k_steps(cg_of(cin)) * npad_of(cout) * 32; }
 
 // The weights in the kernel's canonical K-major layout: block s (K step), k-group kg, n-group ng,
-// row r (output channel), column c (k), zero where the step has no tap or channel.
+// row r (output channel), column c (k), zero where the step has no tap or channel. With `adjoint`, w is a
+// forward layer's weights ([27][fwd_cout][fwd_cin]) and the layer packed is its input gradient, a
+// convolution of the output gradient (fwd_cout channels, padded to cin) into fwd_cin = cout channels:
+// its weight for tap t, output n, input ci is the forward weight of the mirrored tap 26 - t with the
+// channel roles swapped, w[26 - t][ci][n].
 __global__ void k_pack(const __nv_bfloat16* __restrict__ w, int cin, int cout, int npad, int cg,
-                       __nv_bfloat16* __restrict__ out) {
+                       __nv_bfloat16* __restrict__ out, int adjoint = 0, int fwd_cin = 0, int fwd_cout = 0) {
     const int S = k_steps(cg);
     const int total = S * 16 * npad;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -561,7 +582,11 @@ __global__ void k_pack(const __nv_bfloat16* __restrict__ w, int cin, int cout, i
             ci = (s % (cg / 2)) * 16 + kg * 8 + c;
         }
         __nv_bfloat16 v = __float2bfloat16(0.0f);
-        if (!zero && n < cout && ci < cin) v = w[((size_t)tap * cout + n) * cin + ci];
+        if (!adjoint) {
+            if (!zero && n < cout && ci < cin) v = w[((size_t)tap * cout + n) * cin + ci];
+        } else {  // output n = a forward input channel, input ci = a forward output channel
+            if (!zero && n < fwd_cin && ci < fwd_cout) v = w[((size_t)(26 - tap) * fwd_cout + ci) * fwd_cin + n];
+        }
         out[i] = v;
     }
 }
@@ -667,6 +692,16 @@ cudaError_t launch(const Args& a, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, kernel, a, static_cast<const CUtensorMap>(map));
 }
 
+__global__ void k_pad_channels(size_t nvox, int c, int c_pad, const __nv_bfloat16* __restrict__ src,
+                               __nv_bfloat16* __restrict__ dst) {
+    const size_t total = nvox * (size_t)c_pad;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = i / c_pad;
+        const int ch = (int)(i % c_pad);
+        dst[i] = ch < c ? src[v * c + ch] : __float2bfloat16(0.0f);
+    }
+}
+
 }  // namespace
 }  // namespace net_tc
 }  // namespace mpm
@@ -711,7 +746,7 @@ mpm_status mpm_conv3d_forward_tc(int D, int H, int W, int cin, int cout, const v
     if (cin != 4 && cin != 16 && cin != 32) return MPM_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(w_packed) % 16 || reinterpret_cast<uintptr_t>(x) % 16) return MPM_ERR_INVALID_ARG;
     Args a{D, H, W, cin, cout, static_cast<const __nv_bfloat16*>(x), static_cast<const unsigned char*>(w_packed), bias,
-           relu, y_f32, y, tile_dist, radius};
+           relu, y_f32, y, tile_dist, radius, nullptr};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const bool n16 = cout <= 16;
@@ -719,6 +754,56 @@ mpm_status mpm_conv3d_forward_tc(int D, int H, int W, int cin, int cout, const v
     else if (cin == 16) e = n16 ? launch<16, 2>(a, st) : launch<32, 2>(a, st);
     else e = n16 ? launch<16, 4>(a, st) : launch<32, 4>(a, st);
     return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_forward_tc");
+}
+
+mpm_status mpm_pad_channels_bf16(int nvox, int c, int c_pad, const void* src, void* dst, void* stream) {
+    if (nvox < 0 || c < 1 || c_pad < c || !src || !dst) return MPM_ERR_INVALID_ARG;
+    if (nvox == 0) return MPM_OK;
+    const size_t total = (size_t)nvox * c_pad;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_pad_channels<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        (size_t)nvox, c, c_pad, static_cast<const __nv_bfloat16*>(src), static_cast<__nv_bfloat16*>(dst));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_pad_channels_bf16");
+}
+
+// Channel count of the tensor-core kernels' input for c channels (the padded width).
+static int tc_cin_of(int c) { return c <= 4 ? 4 : (c <= 16 ? 16 : 32); }
+
+int mpm_conv3d_tc_adjoint_packed_bytes(int cin, int cout) {
+    if (cin < 1 || cin > 32 || cout < 1 || cout > 32) return 0;
+    return (int)packed_bytes(tc_cin_of(cout), cin);
+}
+
+mpm_status mpm_conv3d_pack_tc_adjoint(int cin, int cout, const void* w, void* packed, void* stream) {
+    if (cin < 1 || cin > 32 || cout < 1 || cout > 32 || !w || !packed) return MPM_ERR_INVALID_ARG;
+    const int acin = tc_cin_of(cout), acout = cin;
+    const int total = (int)(packed_bytes(acin, acout) / 2);
+    k_pack<<<(total + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16*>(w), acin, acout, npad_of(acout), cg_of(acin),
+        static_cast<__nv_bfloat16*>(packed), 1, cin, cout);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_pack_tc_adjoint");
+}
+
+mpm_status mpm_conv3d_backward_data_tc(int D, int H, int W, int cin, int cout, const void* dy, const void* w_adj_packed,
+                                       const void* act_in, void* dx, void* stream) {
+    if (D <= 0 || H <= 0 || W <= 0 || !dy || !w_adj_packed || !dx || cin < 1 || cin > 32 || cout < 1 || cout > 32 ||
+        (size_t)D * H * W >= ((size_t)1 << 31))
+        return MPM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(w_adj_packed) % 16 || reinterpret_cast<uintptr_t>(dy) % 16 ||
+        (act_in && cin == 32 && reinterpret_cast<uintptr_t>(act_in) % 16))
+        return MPM_ERR_INVALID_ARG;
+    const int acin = tc_cin_of(cout);
+    Args a{D, H, W, acin, cin, static_cast<const __nv_bfloat16*>(dy), static_cast<const unsigned char*>(w_adj_packed),
+           nullptr, 0, 0, dx, nullptr, 0, static_cast<const __nv_bfloat16*>(act_in)};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const bool n16 = cin <= 16;
+    if (acin == 4) e = n16 ? launch<16, 1>(a, st) : launch<32, 1>(a, st);
+    else if (acin == 16) e = n16 ? launch<16, 2>(a, st) : launch<32, 2>(a, st);
+    else e = n16 ? launch<16, 4>(a, st) : launch<32, 4>(a, st);
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_backward_data_tc");
 }
 
 mpm_status mpm_net_tc_status(unsigned* flags, int clear, void* stream) {

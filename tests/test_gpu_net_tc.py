@@ -89,3 +89,41 @@ def test_tc_masked_tiles_match_unmasked_on_the_mask(mpm):
     # tiles far from the mask are zero-filled, not left stale
     assert not (p == 7.0).any()
     assert (p == 0.0).any()
+
+
+BACK_CASES = [((2, 19, 11), 32, 32), ((5, 21, 13), 32, 3), ((3, 17, 9), 4, 32), ((1, 1, 1), 32, 32),
+              ((4, 16, 8), 16, 32)]
+
+
+@pytest.mark.parametrize("box,cin,cout", BACK_CASES)
+@pytest.mark.parametrize("masked", [0, 1])
+def test_tc_backward_data_matches_oracle(mpm, box, cin, cout, masked):
+    """The input gradient on the tensor cores (the forward kernel on the mirrored, channel-swapped weights,
+    ReLU mask of the layer's input applied in the epilogue) against the oracle's adjoint on the same
+    BF16 operands, and against the mma.sync input gradient."""
+    nvox = int(np.prod(box))
+    cp = 4 if cout <= 4 else (16 if cout <= 16 else 32)
+    dy = torch.from_numpy(RNG.normal(size=box + (cout,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    w = torch.from_numpy((0.2 * RNG.normal(size=(27, cout, cin))).astype(np.float32)).to(torch.bfloat16).cuda()
+    act = torch.from_numpy(RNG.normal(size=box + (cin,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    dyp = torch.empty(box + (cp,), dtype=torch.bfloat16, device="cuda")
+    mpm.mpm_pad_channels_bf16(nvox, cout, cp, dy.data_ptr(), dyp.data_ptr())
+    wa = torch.zeros(mpm.mpm_conv3d_tc_adjoint_packed_bytes(cin, cout), dtype=torch.uint8, device="cuda")
+    mpm.mpm_conv3d_pack_tc_adjoint(cin, cout, w.data_ptr(), wa.data_ptr())
+    dx = torch.zeros(box + (cin,), dtype=torch.bfloat16, device="cuda")
+    mpm.mpm_conv3d_backward_data_tc(*box, cin, cout, dyp.data_ptr(), wa.data_ptr(),
+                                    act.data_ptr() if masked else 0, dx.data_ptr())
+    assert mpm.mpm_net_tc_status(clear=1) == 0
+    assert torch.equal(dyp[..., :cout], dy) and (cp == cout or bool((dyp[..., cout:] == 0).all()))
+    ref = no.conv3d_backward_data(dy.float().cpu().numpy(), w.float().cpu().numpy())
+    if masked:
+        ref = ref * (act.float().cpu().numpy() > 0)
+    got = dx.float().cpu().numpy()
+    assert rel(got, ref) <= 1e-2
+    if masked:
+        assert np.all(got[act.float().cpu().numpy() <= 0] == 0.0)
+    # the mma.sync kernel of the same gradient
+    dx2 = torch.zeros(box + (cin,), dtype=torch.bfloat16, device="cuda")
+    mpm.mpm_conv3d_backward_data(mpm.MPM_NET_BF16, *box, cin, cout, dy.data_ptr(), w.data_ptr(),
+                                 act.data_ptr() if masked else 0, dx2.data_ptr())
+    assert rel(got, dx2.float().cpu().numpy()) <= 1e-2
