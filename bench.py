@@ -488,6 +488,20 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
         torch.cuda.synchronize(dev)
     secs = a.elapsed_time(b) / 1e3
     launches = sim.launches - l0
+    # ---- the fused kernel's share of the device time (events around every launch, a second pass), for its
+    # roofline fraction with the state in HBM: algorithmic bytes 192 per plasticine particle-substep, 128
+    # per fluid one (x, v, C and F or J, read and written in FP32)
+    sim.set_timing(True)
+    sim.read_timing(reset=True)
+    for s_ in range(steps):
+        env_step(warmup + s_)
+    torch.cuda.synchronize(dev)
+    kt = sim.read_timing(reset=True)
+    sim.set_timing(False)
+    share = kt["g2p2g"][0] / max(sum(v[0] for v in kt.values()), 1e-30)
+    bytes_substep = sum(sc.N * (192 if sc.material.kind == scenes.PLASTICINE else 128) for sc in envs)
+    g_s = share * secs / (steps * SUBSTEPS)
+    peak, peak_kind = measured_peak_gbs()
     # ---- latency: every step reads its impulses back (host waits), per-step events
     lat = []
     for s_ in range(steps):
@@ -498,6 +512,26 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
         e1.record(stream)
         e1.synchronize()
         lat.append(e0.elapsed_time(e1))
+    # ---- per-env request latency: closed-loop clients, one per env, each sending its next request (its
+    # tool's poses) a random think time (uniform in [0, one step]) after its previous answer. The server runs
+    # batched env steps back to back; each step serves every request that has arrived when it starts (all
+    # envs step; those without a new request keep their scripted poses) and ends when the impulses are back
+    # on the host. A request's latency runs from its arrival to that read-back (host wall clock).
+    rng = np.random.default_rng(7)
+    T = secs / steps
+    arrival = time.perf_counter() + rng.uniform(0.0, T, size=len(envs))
+    req_lat = []
+    for s_ in range(steps):
+        start = time.perf_counter()
+        if not (arrival <= start).any():  # nobody waiting: idle until the next request arrives
+            time.sleep(max(0.0, float(arrival.min()) - start))
+            start = time.perf_counter()
+        served = arrival <= start
+        env_step(warmup + 2 * steps + s_)
+        mpm.mpm_read_wrench(sim.handle, wr_h.data_ptr(), int(stream.cuda_stream))
+        end = time.perf_counter()
+        req_lat.extend(((end - arrival[served]) * 1e3).tolist())
+        arrival[served] = end + rng.uniform(0.0, T, size=int(served.sum()))
     flags = sim.status()
     shape_now = sim.get_launch()
     nenv = len(envs)
@@ -513,9 +547,18 @@ def run_batched(dev, which: str, steps: int, warmup: int, per_scene: bool, tune:
         "env_steps_per_s": nenv * steps / secs,
         "particle_substeps_per_s": N * SUBSTEPS * steps / secs,
         "ms_per_env_step": secs / steps * 1e3,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "what": "set colliders + 25 substeps + impulses to pinned host memory, all envs"},
+        "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                            "what": "one batched env step of all envs: set colliders + 25 substeps + impulses "
+                                    "read back to pinned host memory"},
+        "request_latency_ms": {"p50": float(np.percentile(req_lat, 50)), "p99": float(np.percentile(req_lat, 99)),
+                               "requests": len(req_lat),
+                               "what": "per env request, closed-loop clients with think time U[0, one step]: "
+                                       "arrival to its env's impulses on the host"},
         "gpu_launches": launches,
+        "roofline": {"kernel": "k_g2p2g", "bound": "hbm", "achieved": bytes_substep / g_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": bytes_substep / g_s / 1e9 / peak, "share_of_substep": share,
+                     "mean_launch_us": g_s * 1e6, "algorithmic_bytes_per_launch": bytes_substep,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
         "launch_shape": {"chunk": shape_now[0], "fused_ctas_per_sm": shape_now[1], "grid_ctas_per_sm": shape_now[2]},
         "autotune": tuned,
         "status_flags": flags,
@@ -733,13 +776,19 @@ def run_surrogate(dev, n_scenes: int):
     seeds = range(20000, 20000 + n_scenes)
     gated = sur.summarize(sur.evaluate(net, seeds, device=dev, gate=True))
     ungated = sur.summarize(sur.evaluate(net, seeds, device=dev, gate=False))
+    # the same windows without the network (zero correction), on a quarter of the scenes: what the
+    # network adds, and whether the gate catches a window that is not corrected
+    few = seeds[: max(1, len(seeds) // 4)]
+    none_ungated = sur.summarize(sur.evaluate(None, few, device=dev, gate=False, steps=1))
+    none_gated = sur.summarize(sur.evaluate(None, few, device=dev, gate=True, steps=1))
     meta = net.meta
     return {
         "workload": "pinch scenes, held out",
         "seeds": [seeds[0], seeds[-1]],
         "particles": 200_000,
         "window_substeps": sur.K,
-        "gate": {"threshold": sur.THRESHOLD, "v_ref": sur.V_REF, "what": "mass and momentum residuals"},
+        "gate": {"threshold": sur.THRESHOLD, "v_ref": "scene RMS node speed" if sur.V_REF == 0.0 else sur.V_REF,
+                 "what": "mass and momentum residuals"},
         "training": {k: meta.get(k) for k in ("rollouts", "seeds", "windows", "epochs")},
         "gated": gated,
         "ungated": ungated,
@@ -748,6 +797,12 @@ def run_surrogate(dev, n_scenes: int):
         "env_steps_per_s_surrogate_ungated": 1e3 / ungated["ms_per_env_step_surrogate"],
         "speedup_gated": gated["ms_per_env_step_plain"] / gated["ms_per_env_step_surrogate"],
         "speedup_ungated": ungated["ms_per_env_step_plain"] / ungated["ms_per_env_step_surrogate"],
+        "no_network": {"scenes": none_ungated["scenes"], "rel_x_mean": none_ungated["rel_x_mean"],
+                       "rel_to_displacement_mean": none_ungated["rel_to_displacement_mean"],
+                       "fallback_rate_gated": none_gated["fallback_rate"],
+                       "what": "the same windows with a zero correction, ungated; and the gate's verdict on them"},
+        "network_over_no_network_displacement_error": (ungated["rel_to_displacement_mean"]
+                                                       / max(none_ungated["rel_to_displacement_mean"], 1e-30)),
         "wall_s": time.perf_counter() - t0,
     }
 
