@@ -84,6 +84,16 @@ mpm_status mpm_pad_channels_bf16(int nvox, int c, int c_pad, const void* src, vo
 int mpm_conv3d_tc_tile_count(int D, int H, int W);
 mpm_status mpm_conv3d_tc_tile_dist(int D, int H, int W, const uint8_t* mask, uint8_t* dist, void* stream);
 
+/* Weight and bias gradients on the tensor cores (tcgen05), the same quantities as mpm_conv3d_backward_weight:
+ * dw[t][co][ci] = sum_p dy[p][co] x[p + o_t][ci] (o_t = (t/9 - 1, (t/3)%3 - 1, t%3 - 1) in (z, y, x), x zero
+ * outside the box), db[co] = sum_p dy[p][co]. BF16 products, FP32 accumulation. x: D*H*W*cin BF16 with cin 4,
+ * 16 or 32; dy: D*H*W*cd BF16 with cd = cout padded to 4, 16 or 32 (the padding channels zero, as
+ * mpm_pad_channels_bf16 writes them); x, dy and dw 16-byte aligned. dw (27*cout*cin) and db (cout) are FP32,
+ * overwritten (zeroed on the stream, then accumulated by one persistent CTA per SM). A bounded wait that runs
+ * out sets the error word of mpm_net_tc_status. */
+mpm_status mpm_conv3d_backward_weight_tc(int D, int H, int W, int cin, int cout, const void* x, const void* dy,
+                                         float* dw, float* db, void* stream);
+
 /* The tensor-core kernels' error word (nonzero: a wait ran out); clear != 0 resets it. Synchronizes. */
 mpm_status mpm_net_tc_status(unsigned* flags, int clear, void* stream);
 

@@ -145,6 +145,7 @@ def _load():
         "mpm_conv3d_tc_adjoint_packed_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "mpm_conv3d_pack_tc_adjoint": (st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
         "mpm_conv3d_backward_data_tc": (st, [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, _vp]),
+        "mpm_conv3d_backward_weight_tc": (st, [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, _vp]),
         "mpm_pad_channels_bf16": (st, [ctypes.c_int] * 3 + [_vp, _vp, _vp]),
         "mpm_conv3d_tc_tile_count": (ctypes.c_int, [ctypes.c_int] * 3),
         "mpm_conv3d_tc_tile_dist": (st, [ctypes.c_int] * 3 + [_vp, _vp, _vp]),
@@ -427,6 +428,11 @@ def mpm_conv3d_tile_flags(D, H, W, mask, dilate, flags, stream=0):
 def mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w, act_in, dx, stream=0):
     _check("mpm_conv3d_backward_data", _load().mpm_conv3d_backward_data(dtype, D, H, W, cin, cout, dy, w,
                                                                         act_in or None, dx, stream))
+
+
+def mpm_conv3d_backward_weight_tc(D, H, W, cin, cout, x, dy, dw, db, stream=0):
+    _check("mpm_conv3d_backward_weight_tc", _load().mpm_conv3d_backward_weight_tc(D, H, W, cin, cout, x, dy, dw, db,
+                                                                                  stream))
 
 
 def mpm_conv3d_backward_weight(dtype, D, H, W, cin, cout, x, dy, dw, db, stream=0):

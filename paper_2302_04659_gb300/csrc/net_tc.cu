@@ -634,6 +634,256 @@ __global__ void __launch_bounds__(kDistThreads, 4) k_tile_dist(int D, int H, int
     }
 }
 
+// ------------------------------------------------------------------------ weight gradient
+//
+// dW[t][co][ci] = sum_q dy[q - o_t][co] x[q][ci] and db[co] = sum_q dy[q][co], q over the box (dy and x zero
+// outside), as implicit GEMMs with K = the 128 voxels of a tile: for each of the 9 (dz, dy) rows of taps,
+// D[(j, co)][ci] += sum_q A[(j, co)][q] B[q][ci] with A = dy at q - (dz, dy, j - 1) and B = x at q. Both
+// operands are read MN-major from the channel planes the forward uses (one 16-byte row of 8 channels per
+// voxel, so any voxel shift is 16-byte aligned): A from three copies of dy's halo, copy j loaded shifted by
+// j - 1 voxels along x so that one descriptor stride (a plane) steps from copy to copy, B from the tile's
+// voxels of x. M = 128 rows (three copies of up to 32 channels; rows past them are read and dropped), N =
+// the input channels padded to 16 or 32, 8 K steps of 16 voxels (two rows of 8 along x). The 9
+// accumulators (9 N columns of tensor memory) stay on the CTA across its tiles and reach dW once, by
+// vector atomics; db is summed from the unshifted copy.
+struct WgArgs {
+    int D, H, W;
+    int cin, cout;
+    const __nv_bfloat16* x;   // [vox][cin] (cin 4, 16 or 32)
+    const __nv_bfloat16* dy;  // [vox][cd], cd = the output channels padded to 4, 16 or 32 (zero past cout)
+    float* dw;                // [27][cout][cin], accumulated into (zeroed by the caller)
+    float* db;                // [cout], accumulated into
+};
+
+constexpr int kWgTilePlane = TM * 16;  // 2048: 8 channels of a tile's 128 voxels (row y at y * 128 bytes)
+constexpr int kWgAPlanes = 16;         // the 128 rows of A span 16 planes from its base
+constexpr size_t kWgSmem = (size_t)kWgAPlanes * kPlaneBytes + 64;
+
+// Descriptor of an MN-major operand without swizzle: core matrices of 8 K rows (voxels) x 16 bytes (8
+// channels); the leading byte offset holds the stride between 8-voxel groups along K, the stride byte
+// offset the stride between 8-channel groups along MN (as for K-major operands, where the K stride is
+// also the leading one). Checked against the FP64 oracle; the other assignment gives wrong sums.
+__device__ __forceinline__ uint64_t wg_desc(uint32_t addr, uint32_t k_stride, uint32_t mn_stride) {
+    return smem_desc(addr, k_stride, mn_stride);
+}
+
+// kind::f16 instruction descriptor with both operands MN-major (the transpose bits 15 and 16 set).
+__host__ __device__ constexpr uint32_t instr_desc_mn(int m, int n) { return instr_desc(m, n) | (1u << 15) | (1u << 16); }
+
+// Stage tile (z0, y0, x0): the three shifted copies of dy's halo (copy j: the 10 x 18 x 3 box at x0 - j,
+// y0 - 1, z0 - 1) at planes [j CGD, (j + 1) CGD) of A, and x's tile voxels at B. The tensor-map parts
+// complete on `bar` (thread 0 issues them); the 4-channel parts are 8-byte asynchronous copies by every
+// thread into the low half of each row (the high half stays zero).
+template <int CGX, int CGD>
+__device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map_dy, const CUtensorMap* map_x,
+                                         uint32_t a_addr, uint32_t b_addr, uint32_t bar, int z0, int y0, int x0) {
+    constexpr uint32_t tma_bytes = (CGD >= 2 ? 3u * CGD * HV * 16 : 0u) + (CGX >= 2 ? (uint32_t)CGX * kWgTilePlane : 0u);
+    if constexpr (tma_bytes > 0) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tma_bytes) : "memory");
+            if constexpr (CGD >= 2)
+                for (int j = 0; j < 3; ++j)
+                    for (int q = 0; q < CGD; ++q)
+                        tma_plane(a_addr + (j * CGD + q) * kPlaneBytes, map_dy, q * 8, x0 - j, y0 - 1, z0 - 1, bar);
+            if constexpr (CGX >= 2)
+                for (int q = 0; q < CGX; ++q)
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+                        "[%6];" ::"r"(b_addr + q * kWgTilePlane),
+                        "l"(reinterpret_cast<uint64_t>(map_x)), "r"(q * 8), "r"(x0), "r"(y0), "r"(z0), "r"(bar)
+                        : "memory");
+        }
+    }
+    if constexpr (CGD == 1) {  // dy of 4 channels
+        for (int i = threadIdx.x; i < 3 * HV; i += kThreads) {
+            const int j = i / HV, h = i % HV;
+            const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - j + h % HX;
+            const bool in = z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W;
+            const __nv_bfloat16* src = in ? a.dy + (((size_t)z * a.H + yy) * a.W + xq) * 4 : a.dy;
+            cp_async8(a_addr + j * kPlaneBytes + h * 16, src, in ? 8u : 0u);
+        }
+    }
+    if constexpr (CGX == 1) {  // x of 4 channels: the tile's voxels
+        for (int m = threadIdx.x; m < TM; m += kThreads) {
+            const int yy = y0 + m / TX, xq = x0 + m % TX;
+            const bool in = yy < a.H && xq < a.W;
+            const __nv_bfloat16* src = in ? a.x + (((size_t)z0 * a.H + yy) * a.W + xq) * 4 : a.x;
+            cp_async8(b_addr + m * 16, src, in ? 8u : 0u);
+        }
+    }
+    if constexpr (CGD == 1 || CGX == 1) cp_async_wait_all();
+}
+
+// CGX: x's planes (1: 4 channels, by 8-byte copies; 2 or 4: 16 or 32 channels, by the tensor map); CGD:
+// dy's planes per copy (1: 4 channels; 2 or 4: 16 or 32). One CTA per SM; the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... run one at a time (staging, then the tile's 72 MMAs).
+template <int CGX, int CGD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wgrad_tc(WgArgs a, const __grid_constant__ CUtensorMap map_dy, const __grid_constant__ CUtensorMap map_x) {
+    constexpr int N = CGX == 4 ? 32 : 16;               // columns of one accumulator
+    constexpr uint32_t kCols = 9 * N > 256 ? 512 : 256;  // tensor memory allocated (a power of two)
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kWgAPlanes * kPlaneBytes);  // 0: staged, 1: MMAs done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+    __shared__ float db_part[kThreads];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
+    const uint32_t a_addr = smem_u32(smem), b_addr = a_addr + 3 * CGD * kPlaneBytes;
+    const uint32_t staged = smem_u32(bar), done = smem_u32(bar + 1);
+    // the planes' unwritten halves and pads are zero (the 8-byte copies fill only the low half of a row)
+    for (int i = tid; i < kWgAPlanes * kPlaneBytes / 16; i += kThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(staged));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = instr_desc_mn(TM, N);
+    constexpr bool kTma = CGX >= 2 || CGD >= 2;
+    const int co_db = tid % 32;  // this thread's bias-gradient channel, over voxels tid / 32 + 4 i
+    float db = 0.0f;
+    bool failed = false;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
+        const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
+        wg_stage<CGX, CGD>(a, &map_dy, &map_x, a_addr, b_addr, staged, z0, y0, x0);
+        if constexpr (kTma)
+            if (!mbar_wait(staged, i & 1)) failed = true;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the 8-byte copies, for the tensor core
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int g = 0; g < 9; ++g) {
+                const int dz = g / 3 - 1, dyo = g % 3 - 1;
+#pragma unroll
+                for (int ks = 0; ks < TM / 16; ++ks) {
+                    // A: the copies' voxel (1 - dz, 2 ks + 1 - dy, 1) of the halo; B: the tile's row 2 ks
+                    const uint32_t ao = a_addr + (((1 - dz) * HY + 2 * ks + 1 - dyo) * HX + 1) * 16;
+                    const uint32_t bo = b_addr + 2 * ks * TX * 16;
+                    mma_bf16(tmem + g * N, wg_desc(ao, HX * 16, kPlaneBytes), wg_desc(bo, TX * 16, kWgTilePlane),
+                             idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(done);
+        }
+        // the bias gradient from the unshifted copy (copy 1) at the tile's voxels, while the MMAs run
+        if (co_db < a.cout) {
+            const unsigned char* c1 = smem + (CGD + co_db / 8) * kPlaneBytes;
+            for (int m = tid / 32; m < TM; m += kThreads / 32) {
+                const int h = (HY + m / TX + 1) * HX + m % TX + 1;
+                db += __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(c1 + h * 16)[co_db % 8]);
+            }
+        }
+        if (!mbar_wait(done, i & 1)) failed = true;  // before the next tile's copies overwrite the operands
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        failed = __syncthreads_or(failed) != 0;
+        if (failed) break;
+    }
+    if (failed && tid == 0) {
+        atomicExch(&g_tc_error, 1u);
+        // leave nothing in flight: this tile's copies (if its wait ran out) and its MMAs (if issued)
+        if constexpr (kTma) mbar_wait(staged, i & 1);
+        mbar_wait(done, i & 1);
+    }
+    if (!failed && i > 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int r = warp * 32 + lane, j = r / (CGD * 8), co = r % (CGD * 8);
+#pragma unroll 1
+        for (int g = 0; g < 9; ++g) {
+            float v[N];
+            tmem_load<N>(tmem + ((uint32_t)(warp * 32) << 16) + g * N, v);
+            if (j >= 3 || co >= a.cout) continue;
+            const int t = (g / 3) * 9 + (g % 3) * 3 + j;
+            float* dst = a.dw + ((size_t)t * a.cout + co) * a.cin;
+            if (a.cin % 4 == 0) {
+#pragma unroll
+                for (int c = 0; c < N; c += 4)
+                    if (c < a.cin) atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]));
+            } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c)
+                    if (c < a.cin) atomicAdd(dst + c, v[c]);
+            }
+        }
+    }
+    db_part[tid] = db;
+    __syncthreads();
+    if (!failed && tid < a.cout) {
+        float s = 0.0f;
+        for (int k = tid; k < kThreads; k += 32) s += db_part[k];
+        atomicAdd(&a.db[tid], s);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// A 4-D tensor map (channels, W, H, D) of BF16 activations with `c` channels and the given box.
+cudaError_t encode_act_map(CUtensorMap* map, const __nv_bfloat16* base, int c, int W, int H, int D,
+                           const cuuint32_t (&box)[4]) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+    const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)W * c * 2, (cuuint64_t)H * W * c * 2};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(base), dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int CGX, int CGD>
+cudaError_t launch_wgrad(const WgArgs& a, cudaStream_t s) {
+    auto kernel = k_wgrad_tc<CGX, CGD>;
+    static int sms = 0;
+    if (sms == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(sms, 1);
+    }
+    const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
+    CUtensorMap map_dy{}, map_x{};
+    if constexpr (CGD >= 2) {
+        const cuuint32_t box[4] = {8, HX, HY, HZ};
+        cudaError_t e = encode_act_map(&map_dy, a.dy, 8 * CGD, a.W, a.H, a.D, box);
+        if (e != cudaSuccess) return e;
+    }
+    if constexpr (CGX >= 2) {
+        const cuuint32_t box[4] = {8, TX, TY, 1};
+        cudaError_t e = encode_act_map(&map_x, a.x, 8 * CGX, a.W, a.H, a.D, box);
+        if (e != cudaSuccess) return e;
+    }
+    k_wgrad_tc<CGX, CGD><<<std::min(tiles, sms), kThreads, kWgSmem, s>>>(a, map_dy, map_x);
+    return cudaGetLastError();
+}
+
+template <int CGX>
+cudaError_t launch_wgrad_cd(const WgArgs& a, int cgd, cudaStream_t s) {
+    return cgd == 1 ? launch_wgrad<CGX, 1>(a, s) : (cgd == 2 ? launch_wgrad<CGX, 2>(a, s) : launch_wgrad<CGX, 4>(a, s));
+}
+
 template <int NPAD, int CG>
 cudaError_t launch(const Args& a, cudaStream_t s) {
     using Kernel = void (*)(Args, const CUtensorMap);
@@ -804,6 +1054,27 @@ mpm_status mpm_conv3d_backward_data_tc(int D, int H, int W, int cin, int cout, c
     else if (acin == 16) e = n16 ? launch<16, 2>(a, st) : launch<32, 2>(a, st);
     else e = n16 ? launch<16, 4>(a, st) : launch<32, 4>(a, st);
     return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_backward_data_tc");
+}
+
+mpm_status mpm_conv3d_backward_weight_tc(int D, int H, int W, int cin, int cout, const void* x, const void* dy,
+                                         float* dw, float* db, void* stream) {
+    if (D <= 0 || H <= 0 || W <= 0 || !x || !dy || !dw || !db || cout < 1 || cout > 32 ||
+        (size_t)D * H * W >= ((size_t)1 << 31))
+        return MPM_ERR_INVALID_ARG;
+    if (cin != 4 && cin != 16 && cin != 32) return MPM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(x) % 16 || reinterpret_cast<uintptr_t>(dy) % 16 ||
+        reinterpret_cast<uintptr_t>(dw) % 16)
+        return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cout * cin, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(db, 0, sizeof(float) * cout, st);
+    if (e == cudaSuccess) {
+        const WgArgs a{D, H, W, cin, cout, static_cast<const __nv_bfloat16*>(x), static_cast<const __nv_bfloat16*>(dy),
+                       dw, db};
+        const int cgd = cg_of(tc_cin_of(cout));
+        e = cin == 4 ? launch_wgrad_cd<1>(a, cgd, st) : (cin == 16 ? launch_wgrad_cd<2>(a, cgd, st) : launch_wgrad_cd<4>(a, cgd, st));
+    }
+    return e == cudaSuccess ? MPM_OK : mpm::record_cuda_error(e, "mpm_conv3d_backward_weight_tc");
 }
 
 mpm_status mpm_net_tc_status(unsigned* flags, int clear, void* stream) {

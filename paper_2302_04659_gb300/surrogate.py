@@ -77,7 +77,7 @@ class Network:
                                           dtype=torch.uint8, device=self.device) for i in range(1, 4)]
         self._pack()
         self.engine = "tc"
-        self.backward_engine = "tc"  # input gradients on the tensor cores ("mma": the mma.sync kernels)
+        self.backward_engine = "tc"  # weight and input gradients on the tensor cores ("mma": mma.sync kernels)
         self.params = [t for pair in zip(self.w, self.b) for t in pair]
         self.grads = [torch.zeros_like(p) for p in self.params]
         self.m = [torch.zeros_like(p) for p in self.params]
@@ -181,16 +181,22 @@ class Network:
         mpm.mpm_mse_loss(mpm.MPM_NET_BF16, nvox, 3, bufs["out"].data_ptr(), 1, target.data_ptr(), mask.data_ptr(),
                          bufs["loss"].data_ptr(), g.data_ptr(), s)
         for i in range(3, -1, -1):
-            mpm.mpm_conv3d_backward_weight(mpm.MPM_NET_BF16, *dims, CHANNELS[i], CHANNELS[i + 1],
-                                           bufs["acts"][i].data_ptr(), g.data_ptr(), self.grads[2 * i].data_ptr(),
-                                           self.grads[2 * i + 1].data_ptr(), s)
+            tc = self.backward_engine == "tc"
+            dy = g
+            if tc and CHANNELS[i + 1] < 4:  # the tensor-core kernels read 4, 16 or 32 channels
+                mpm.mpm_pad_channels_bf16(nvox, CHANNELS[i + 1], 4, g.data_ptr(), bufs["gpad"].data_ptr(), s)
+                dy = bufs["gpad"]
+            if tc:  # tcgen05: voxels as the contraction, both operands read MN-major from channel planes
+                mpm.mpm_conv3d_backward_weight_tc(*dims, CHANNELS[i], CHANNELS[i + 1], bufs["acts"][i].data_ptr(),
+                                                  dy.data_ptr(), self.grads[2 * i].data_ptr(),
+                                                  self.grads[2 * i + 1].data_ptr(), s)
+            else:
+                mpm.mpm_conv3d_backward_weight(mpm.MPM_NET_BF16, *dims, CHANNELS[i], CHANNELS[i + 1],
+                                               bufs["acts"][i].data_ptr(), g.data_ptr(), self.grads[2 * i].data_ptr(),
+                                               self.grads[2 * i + 1].data_ptr(), s)
             if i > 0:
                 gx = bufs["g"][i - 1]
-                if self.backward_engine == "tc":  # tcgen05: the forward kernel on the adjoint weights
-                    dy = g
-                    if CHANNELS[i + 1] < 4:
-                        mpm.mpm_pad_channels_bf16(nvox, CHANNELS[i + 1], 4, g.data_ptr(), bufs["gpad"].data_ptr(), s)
-                        dy = bufs["gpad"]
+                if tc:  # tcgen05: the forward kernel on the adjoint weights
                     mpm.mpm_conv3d_backward_data_tc(*dims, CHANNELS[i], CHANNELS[i + 1], dy.data_ptr(),
                                                     self.wadj[i].data_ptr(), bufs["acts"][i].data_ptr(),
                                                     gx.data_ptr(), s)

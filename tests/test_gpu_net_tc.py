@@ -127,3 +127,38 @@ def test_tc_backward_data_matches_oracle(mpm, box, cin, cout, masked):
     mpm.mpm_conv3d_backward_data(mpm.MPM_NET_BF16, *box, cin, cout, dy.data_ptr(), w.data_ptr(),
                                  act.data_ptr() if masked else 0, dx2.data_ptr())
     assert rel(got, dx2.float().cpu().numpy()) <= 1e-2
+
+
+WG_CASES = CASES + [((40, 33, 17), 32, 32), ((9, 38, 40), 4, 32), ((7, 37, 23), 32, 3)]
+
+
+@pytest.mark.parametrize("box,cin,cout", WG_CASES)
+def test_tc_backward_weight_matches_oracle(mpm, box, cin, cout):
+    """The tensor-core weight and bias gradients against the FP64 oracle on the same BF16 values: the
+    products are exact in FP32, so only the FP32 accumulation order differs. The last three boxes hold more
+    tiles than there are SMs, so each CTA adds several tiles into its tensor-memory accumulators."""
+    cd = 4 if cout <= 4 else (16 if cout <= 16 else 32)
+    x = torch.from_numpy(RNG.normal(size=box + (cin,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    dy = torch.from_numpy(RNG.normal(size=box + (cout,)).astype(np.float32)).to(torch.bfloat16).cuda()
+    dyp = torch.zeros(box + (cd,), dtype=torch.bfloat16, device="cuda")
+    dyp[..., :cout] = dy
+    dw = torch.full((27, cout, cin), 5.0, dtype=torch.float32, device="cuda")  # overwritten
+    db = torch.full((cout,), 5.0, dtype=torch.float32, device="cuda")
+    mpm.mpm_conv3d_backward_weight_tc(*box, cin, cout, x.data_ptr(), dyp.data_ptr(), dw.data_ptr(), db.data_ptr())
+    assert mpm.mpm_net_tc_status(clear=1) == 0
+    ref_w, ref_b = no.conv3d_backward_weight(x.float().cpu().numpy(), dy.float().cpu().numpy())
+    got_w, got_b = dw.cpu().numpy(), db.cpu().numpy()
+    print(f"box {box} {cin}->{cout}: dw rel {rel(got_w, ref_w):.2e}, db rel {rel(got_b, ref_b):.2e}")
+    assert rel(got_w, ref_w) <= 1e-5
+    assert rel(got_b, ref_b) <= 1e-5
+    # every tap and channel pair, not only the norm: the largest error per entry against the entry scale
+    assert np.max(np.abs(got_w - ref_w)) <= 1e-5 * np.max(np.abs(ref_w)) * 8
+
+
+def test_tc_backward_weight_rejects_bad_shapes(mpm):
+    x = torch.zeros(64, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(27 * 32 * 32, dtype=torch.float32, device="cuda")
+    for cin, cout in ((8, 32), (32, 0), (32, 33)):
+        with pytest.raises(mpm.MpmError):
+            mpm.mpm_conv3d_backward_weight_tc(1, 1, 1, cin, cout, x.data_ptr(), x.data_ptr(), dw.data_ptr(),
+                                              dw.data_ptr())

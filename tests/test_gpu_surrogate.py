@@ -151,7 +151,7 @@ def test_substep_refused_inside_a_window(mods):
 
 
 def test_network_gradients_tc_equal_mma(mods):
-    """The network's gradients with its input gradients on the tensor cores (tcgen05) equal those of the
+    """The network's gradients with its weight and input gradients on the tensor cores (tcgen05) equal those of the
     mma.sync kernels on a training window, at the BF16 tolerance."""
     mpm, sur = mods
     samples = sur.generate([10002], particles=20_000, env_steps=2, sample_steps=(1,), windows_per_step=(0,))
