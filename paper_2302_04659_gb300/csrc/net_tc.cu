@@ -657,7 +657,7 @@ struct WgArgs {
 
 constexpr int kWgTilePlane = TM * 16;  // 2048: 8 channels of a tile's 128 voxels (row y at y * 128 bytes)
 constexpr int kWgAPlanes = 16;         // the 128 rows of A span 16 planes from its base
-constexpr size_t kWgSmem = (size_t)kWgAPlanes * kPlaneBytes + 64;
+constexpr size_t kWgSmem = (size_t)kWgAPlanes * kPlaneBytes + 2 * 4 * kWgTilePlane + 64;
 
 // Descriptor of an MN-major operand without swizzle: core matrices of 8 K rows (voxels) x 16 bytes (8
 // channels); the leading byte offset holds the stride between 8-voxel groups along K, the stride byte
@@ -670,21 +670,19 @@ __device__ __forceinline__ uint64_t wg_desc(uint32_t addr, uint32_t k_stride, ui
 // kind::f16 instruction descriptor with both operands MN-major (the transpose bits 15 and 16 set).
 __host__ __device__ constexpr uint32_t instr_desc_mn(int m, int n) { return instr_desc(m, n) | (1u << 15) | (1u << 16); }
 
-// Stage tile (z0, y0, x0): the three shifted copies of dy's halo (copy j: the 10 x 18 x 3 box at x0 - j,
-// y0 - 1, z0 - 1) at planes [j CGD, (j + 1) CGD) of A, and x's tile voxels at B. The tensor-map parts
+// Stage tile (z0, y0, x0): dy's halo (the 10 x 18 x 3 box at x0 - 1, y0 - 1, z0 - 1, CGD planes) into the
+// staging planes at `st_addr`, and x's tile voxels into the B buffer at `b_addr`. The tensor-map parts
 // complete on `bar` (thread 0 issues them); the 4-channel parts are 8-byte asynchronous copies by every
-// thread into the low half of each row (the high half stays zero).
+// thread into the low half of each row (the high half stays zero), waited for with cp_async_wait_all.
 template <int CGX, int CGD>
 __device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map_dy, const CUtensorMap* map_x,
-                                         uint32_t a_addr, uint32_t b_addr, uint32_t bar, int z0, int y0, int x0) {
-    constexpr uint32_t tma_bytes = (CGD >= 2 ? 3u * CGD * HV * 16 : 0u) + (CGX >= 2 ? (uint32_t)CGX * kWgTilePlane : 0u);
+                                         uint32_t st_addr, uint32_t b_addr, uint32_t bar, int z0, int y0, int x0) {
+    constexpr uint32_t tma_bytes = (CGD >= 2 ? (uint32_t)CGD * HV * 16 : 0u) + (CGX >= 2 ? (uint32_t)CGX * kWgTilePlane : 0u);
     if constexpr (tma_bytes > 0) {
         if (threadIdx.x == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tma_bytes) : "memory");
             if constexpr (CGD >= 2)
-                for (int j = 0; j < 3; ++j)
-                    for (int q = 0; q < CGD; ++q)
-                        tma_plane(a_addr + (j * CGD + q) * kPlaneBytes, map_dy, q * 8, x0 - j, y0 - 1, z0 - 1, bar);
+                for (int q = 0; q < CGD; ++q) tma_plane(st_addr + q * kPlaneBytes, map_dy, q * 8, x0 - 1, y0 - 1, z0 - 1, bar);
             if constexpr (CGX >= 2)
                 for (int q = 0; q < CGX; ++q)
                     asm volatile(
@@ -695,12 +693,11 @@ __device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map
         }
     }
     if constexpr (CGD == 1) {  // dy of 4 channels
-        for (int i = threadIdx.x; i < 3 * HV; i += kThreads) {
-            const int j = i / HV, h = i % HV;
-            const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - j + h % HX;
+        for (int h = threadIdx.x; h < HV; h += kThreads) {
+            const int z = z0 - 1 + h / (HY * HX), yy = y0 - 1 + (h / HX) % HY, xq = x0 - 1 + h % HX;
             const bool in = z >= 0 && z < a.D && yy >= 0 && yy < a.H && xq >= 0 && xq < a.W;
             const __nv_bfloat16* src = in ? a.dy + (((size_t)z * a.H + yy) * a.W + xq) * 4 : a.dy;
-            cp_async8(a_addr + j * kPlaneBytes + h * 16, src, in ? 8u : 0u);
+            cp_async8(st_addr + h * 16, src, in ? 8u : 0u);
         }
     }
     if constexpr (CGX == 1) {  // x of 4 channels: the tile's voxels
@@ -711,27 +708,48 @@ __device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map
             cp_async8(b_addr + m * 16, src, in ? 8u : 0u);
         }
     }
-    if constexpr (CGD == 1 || CGX == 1) cp_async_wait_all();
+    if constexpr (CGD == 1 || CGX == 1) asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The three shifted copies of the staged halo: copy j holds, at halo voxel (hz, hy, hx), the staged voxel
+// (hz, hy, hx + 1 - j) -- dy at (hz, hy, hx) of the box shifted by j - 1 along x -- for hx in 1..8, the
+// columns the MMAs read.
+template <int CGD>
+__device__ __forceinline__ void wg_expand(unsigned char* smem) {
+    constexpr int kRows = HZ * HY * TX;  // 432 rows of 16 bytes per plane and copy
+    const unsigned char* st = smem + 3 * CGD * kPlaneBytes;
+    for (int i = threadIdx.x; i < 3 * CGD * kRows; i += kThreads) {
+        const int jq = i / kRows, r = i % kRows, j = jq / CGD, q = jq % CGD;
+        const int h = (r / TX) * HX + r % TX + 1;  // (hz, hy) = r / TX, hx = r % TX + 1
+        const uint4 v = *reinterpret_cast<const uint4*>(st + q * kPlaneBytes + (h + 1 - j) * 16);
+        *reinterpret_cast<uint4*>(smem + (j * CGD + q) * kPlaneBytes + h * 16) = v;
+    }
 }
 
 // CGX: x's planes (1: 4 channels, by 8-byte copies; 2 or 4: 16 or 32 channels, by the tensor map); CGD:
-// dy's planes per copy (1: 4 channels; 2 or 4: 16 or 32). One CTA per SM; the tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... run one at a time (staging, then the tile's 72 MMAs).
+// dy's planes (1: 4 channels; 2 or 4: 16 or 32). One CTA per SM over the tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ..., two stages deep: tile i + 1's halo and x land (staging planes, the other B buffer) while
+// the tensor core runs tile i's 72 MMAs; then the threads expand the halo into the three copies.
 template <int CGX, int CGD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(WgArgs a, const __grid_constant__ CUtensorMap map_dy, const __grid_constant__ CUtensorMap map_x) {
     constexpr int N = CGX == 4 ? 32 : 16;               // columns of one accumulator
+    constexpr int kB = (N / 8) * kWgTilePlane;          // one B buffer
     constexpr uint32_t kCols = 9 * N > 256 ? 512 : 256;  // tensor memory allocated (a power of two)
+    constexpr bool kTma = CGX >= 2 || CGD >= 2, kAsync = CGX == 1 || CGD == 1;
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kWgAPlanes * kPlaneBytes);  // 0: staged, 1: MMAs done
+    // [0, 16 planes): the copies (planes [0, 3 CGD)), the staging planes [3 CGD, 4 CGD), the rest only read
+    // as A's dropped rows; then the two B buffers; then the barriers (0: staged, 1: MMAs done)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kWgAPlanes * kPlaneBytes + 2 * kB);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
     __shared__ float db_part[kThreads];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tx = (a.W + TX - 1) / TX, ty = (a.H + TY - 1) / TY, tiles = tx * ty * a.D;
-    const uint32_t a_addr = smem_u32(smem), b_addr = a_addr + 3 * CGD * kPlaneBytes;
+    const uint32_t a_addr = smem_u32(smem), st_addr = a_addr + 3 * CGD * kPlaneBytes;
+    const uint32_t b_addr = a_addr + kWgAPlanes * kPlaneBytes;
     const uint32_t staged = smem_u32(bar), done = smem_u32(bar + 1);
     // the planes' unwritten halves and pads are zero (the 8-byte copies fill only the low half of a row)
-    for (int i = tid; i < kWgAPlanes * kPlaneBytes / 16; i += kThreads)
+    for (int i = tid; i < (kWgAPlanes * kPlaneBytes + 2 * kB) / 16; i += kThreads)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(staged));
@@ -749,21 +767,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = instr_desc_mn(TM, N);
-    constexpr bool kTma = CGX >= 2 || CGD >= 2;
-    const int co_db = tid % 32;  // this thread's bias-gradient channel, over voxels tid / 32 + 4 i
+    auto stage = [&](int t, int buf) {
+        const int x0 = (t % tx) * TX, y0 = ((t / tx) % ty) * TY, z0 = t / (tx * ty);
+        wg_stage<CGX, CGD>(a, &map_dy, &map_x, st_addr, b_addr + buf * kB, staged, z0, y0, x0);
+    };
+    const int co_db = tid % 32;  // this thread's bias-gradient channel, over voxels tid / 32 + 4 k
     float db = 0.0f;
     bool failed = false;
     int i = 0;
+    if (blockIdx.x < tiles) stage(blockIdx.x, 0);
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
-        const int x0 = (tile % tx) * TX, y0 = ((tile / tx) % ty) * TY, z0 = tile / (tx * ty);
-        wg_stage<CGX, CGD>(a, &map_dy, &map_x, a_addr, b_addr, staged, z0, y0, x0);
+        // tile i staged, and tile i - 1's MMAs (readers of the copies and of the other B buffer) done
         if constexpr (kTma)
             if (!mbar_wait(staged, i & 1)) failed = true;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the 8-byte copies, for the tensor core
+        if constexpr (kAsync) asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (i > 0 && !mbar_wait(done, (i - 1) & 1)) failed = true;
         failed = __syncthreads_or(failed) != 0;
         if (failed) break;
+        wg_expand<CGD>(smem);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the copies, for the tensor core
+        __syncthreads();
+        if (tile + (int)gridDim.x < tiles) stage(tile + gridDim.x, (i + 1) & 1);
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t bb = b_addr + (i & 1) * kB;
 #pragma unroll
             for (int g = 0; g < 9; ++g) {
                 const int dz = g / 3 - 1, dyo = g % 3 - 1;
@@ -771,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int ks = 0; ks < TM / 16; ++ks) {
                     // A: the copies' voxel (1 - dz, 2 ks + 1 - dy, 1) of the halo; B: the tile's row 2 ks
                     const uint32_t ao = a_addr + (((1 - dz) * HY + 2 * ks + 1 - dyo) * HX + 1) * 16;
-                    const uint32_t bo = b_addr + 2 * ks * TX * 16;
+                    const uint32_t bo = bb + 2 * ks * TX * 16;
                     mma_bf16(tmem + g * N, wg_desc(ao, HX * 16, kPlaneBytes), wg_desc(bo, TX * 16, kWgTilePlane),
                              idesc, (i > 0 || ks > 0) ? 1u : 0u);
                 }
@@ -786,17 +813,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 db += __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(c1 + h * 16)[co_db % 8]);
             }
         }
-        if (!mbar_wait(done, i & 1)) failed = true;  // before the next tile's copies overwrite the operands
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (!failed && i > 0) {  // the last tile's MMAs
+        if (!mbar_wait(done, (i - 1) & 1)) failed = true;
         failed = __syncthreads_or(failed) != 0;
-        if (failed) break;
     }
     if (failed && tid == 0) {
         atomicExch(&g_tc_error, 1u);
-        // leave nothing in flight: this tile's copies (if its wait ran out) and its MMAs (if issued)
+        // leave nothing in flight: tile i's staging (if its wait ran out) and the last MMA group
         if constexpr (kTma) mbar_wait(staged, i & 1);
-        mbar_wait(done, i & 1);
+        if (i > 0) mbar_wait(done, (i - 1) & 1);
     }
+    if constexpr (kAsync) asm volatile("cp.async.wait_all;" ::: "memory");
     if (!failed && i > 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int r = warp * 32 + lane, j = r / (CGD * 8), co = r % (CGD * 8);
