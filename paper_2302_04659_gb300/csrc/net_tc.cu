@@ -670,8 +670,9 @@ __device__ __forceinline__ uint64_t wg_desc(uint32_t addr, uint32_t k_stride, ui
 // kind::f16 instruction descriptor with both operands MN-major (the transpose bits 15 and 16 set).
 __host__ __device__ constexpr uint32_t instr_desc_mn(int m, int n) { return instr_desc(m, n) | (1u << 15) | (1u << 16); }
 
-// Stage tile (z0, y0, x0): dy's halo (the 10 x 18 x 3 box at x0 - 1, y0 - 1, z0 - 1, CGD planes) into the
-// staging planes at `st_addr`, and x's tile voxels into the B buffer at `b_addr`. The tensor-map parts
+// Stage tile (z0, y0, x0): dy's halo (the 10 x 18 x 3 box at x0 - 1, y0 - 1, z0 - 1, one row of all 8 CGD
+// channels per voxel: fewer and wider tensor-map requests than plane by plane) into the staging area at
+// `st_addr`, and x's tile voxels into the B buffer at `b_addr`. The tensor-map parts
 // complete on `bar` (thread 0 issues them); the 4-channel parts are 8-byte asynchronous copies by every
 // thread into the low half of each row (the high half stays zero), waited for with cp_async_wait_all.
 template <int CGX, int CGD>
@@ -682,7 +683,7 @@ __device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map
         if (threadIdx.x == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tma_bytes) : "memory");
             if constexpr (CGD >= 2)
-                for (int q = 0; q < CGD; ++q) tma_plane(st_addr + q * kPlaneBytes, map_dy, q * 8, x0 - 1, y0 - 1, z0 - 1, bar);
+                tma_plane(st_addr, map_dy, 0, x0 - 1, y0 - 1, z0 - 1, bar);
             if constexpr (CGX >= 2)
                 for (int q = 0; q < CGX; ++q)
                     asm volatile(
@@ -711,17 +712,17 @@ __device__ __forceinline__ void wg_stage(const WgArgs& a, const CUtensorMap* map
     if constexpr (CGD == 1 || CGX == 1) asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// The three shifted copies of the staged halo: copy j holds, at halo voxel (hz, hy, hx), the staged voxel
-// (hz, hy, hx + 1 - j) -- dy at (hz, hy, hx) of the box shifted by j - 1 along x -- for hx in 1..8, the
-// columns the MMAs read.
+// The three shifted copies of the staged halo, in planes of 8 channels: copy j holds, at halo voxel (hz, hy,
+// hx), the staged voxel (hz, hy, hx + 1 - j) -- dy at (hz, hy, hx) of the box shifted by j - 1 along x --
+// for hx in 1..8, the columns the MMAs read.
 template <int CGD>
 __device__ __forceinline__ void wg_expand(unsigned char* smem) {
     constexpr int kRows = HZ * HY * TX;  // 432 rows of 16 bytes per plane and copy
-    const unsigned char* st = smem + 3 * CGD * kPlaneBytes;
+    const unsigned char* st = smem + 3 * CGD * kPlaneBytes;  // staged rows of 16 CGD bytes
     for (int i = threadIdx.x; i < 3 * CGD * kRows; i += kThreads) {
         const int jq = i / kRows, r = i % kRows, j = jq / CGD, q = jq % CGD;
         const int h = (r / TX) * HX + r % TX + 1;  // (hz, hy) = r / TX, hx = r % TX + 1
-        const uint4 v = *reinterpret_cast<const uint4*>(st + q * kPlaneBytes + (h + 1 - j) * 16);
+        const uint4 v = *reinterpret_cast<const uint4*>(st + (h + 1 - j) * 16 * CGD + q * 16);
         *reinterpret_cast<uint4*>(smem + (j * CGD + q) * kPlaneBytes + h * 16) = v;
     }
 }
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kCols = 9 * N > 256 ? 512 : 256;  // tensor memory allocated (a power of two)
     constexpr bool kTma = CGX >= 2 || CGD >= 2, kAsync = CGX == 1 || CGD == 1;
     extern __shared__ __align__(1024) unsigned char smem[];
-    // [0, 16 planes): the copies (planes [0, 3 CGD)), the staging planes [3 CGD, 4 CGD), the rest only read
+    // [0, 16 planes): the copies (planes [0, 3 CGD)), the staged halo (planes [3 CGD, 4 CGD)), the rest only read
     // as A's dropped rows; then the two B buffers; then the barriers (0: staged, 1: MMAs done)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kWgAPlanes * kPlaneBytes + 2 * kB);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
@@ -829,7 +830,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int r = warp * 32 + lane, j = r / (CGD * 8), co = r % (CGD * 8);
 #pragma unroll 1
-        for (int g = 0; g < 9; ++g) {
+        for (int gg = 0; gg < 9; ++gg) {
+            const int g = (gg + blockIdx.x) % 9;  // CTAs start on different taps: fewer atomics on one address
             float v[N];
             tmem_load<N>(tmem + ((uint32_t)(warp * 32) << 16) + g * N, v);
             if (j >= 3 || co >= a.cout) continue;
@@ -894,7 +896,7 @@ cudaError_t launch_wgrad(const WgArgs& a, cudaStream_t s) {
     const int tiles = ((a.W + TX - 1) / TX) * ((a.H + TY - 1) / TY) * a.D;
     CUtensorMap map_dy{}, map_x{};
     if constexpr (CGD >= 2) {
-        const cuuint32_t box[4] = {8, HX, HY, HZ};
+        const cuuint32_t box[4] = {8 * CGD, HX, HY, HZ};  // all channels of a voxel in one row
         cudaError_t e = encode_act_map(&map_dy, a.dy, 8 * CGD, a.W, a.H, a.D, box);
         if (e != cudaSuccess) return e;
     }
