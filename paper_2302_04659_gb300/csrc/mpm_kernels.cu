@@ -1357,6 +1357,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         if (i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi) v[0] = v[1] = v[2] = 0.0f;
         *node = make_float4(v[0], v[1], v[2], m);
     }
+    release_successor();  // the CTA's nodes are written: the next launch may be scheduled (it still waits)
     if (p.p0_sums) {  // (uniform) this CTA's sums as FP32 pairs, one FP64 atomic per component
         __shared__ Pair ps[8][5];
 #pragma unroll
@@ -1399,10 +1400,13 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
 template <bool ONE_ENV, bool SHARED_POSES>
 __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
     extern __shared__ uint4 dyn_sh[];  // p.scan: the bin offsets (total_bins, padded to 4)
-    wait_for_predecessor();  // (a CTA's exit releases the successor)
+    // the next launch is scheduled once every CTA has signalled (near its end) or exited; it still waits
+    // for this launch to complete before it touches memory
+    wait_for_predecessor();
     if (p.gate && *p.gate != p.gate_run) return;  // the other branch of a gated window runs instead
     if ((int)blockIdx.x < p.assign_ctas) {
         if (!p.scan) {
+            release_successor();
             assign_slots4(blockIdx.x * blockDim.x + threadIdx.x, p.N, p.keyrank, p.cursor, p.perm);
             return;
         }
@@ -1440,6 +1444,7 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
             for (int q = threadIdx.x; q < (p.total_bins + 3) >> 2; q += blockDim.x) H[q] = make_uint4(0u, 0u, 0u, 0u);
             if (threadIdx.x == 0) *p.scan_done = 0u;
         }
+        release_successor();  // only the stores of the permutation remain
 #pragma unroll
         for (int r = 0; r < kScanAssignRounds; ++r) {
             if (full[r]) {
