@@ -650,6 +650,7 @@ mpm_status create_impl(const mpm_config* cfg, int nenv, const mpm_env* envs, voi
         g.n = v.n;
         g.nb = v.n / 4;
         g.nblocks = g.nb * g.nb * g.nb;
+        g.nb_recip = 0xFFFFFFFFu / (uint32_t)g.nb + 1u;
         g.dx = (float)(1.0 / v.n);
         g.inv_dx = (float)v.n;
         g.dt = cfg->dt;

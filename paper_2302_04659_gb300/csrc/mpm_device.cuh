@@ -80,14 +80,18 @@ __device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&U)[3][
     S[P][P] = fmaf(cc, app, fmaf(ss, aqq, -cs2));
     S[Q][Q] = fmaf(ss, app, fmaf(cc, aqq, cs2));
     S[P][Q] = S[Q][P] = 0.0f;
+    // rows (p, q) of the rotation as packed FP32x2 pairs: (c, s) a_p + (-s, c) a_q
+    const float2 cs = make_float2(c, s), nsc = make_float2(-s, c);
     const float arp = S[R][P], arq = S[R][Q];
-    S[R][P] = S[P][R] = c * arp - s * arq;
-    S[R][Q] = S[Q][R] = s * arp + c * arq;
+    const float2 sr = __ffma2_rn(nsc, make_float2(arq, arq), __fmul2_rn(cs, make_float2(arp, arp)));
+    S[R][P] = S[P][R] = sr.x;
+    S[R][Q] = S[Q][R] = sr.y;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const float up = U[r][P], uq = U[r][Q];
-        U[r][P] = c * up - s * uq;
-        U[r][Q] = s * up + c * uq;
+        const float2 ur = __ffma2_rn(nsc, make_float2(uq, uq), __fmul2_rn(cs, make_float2(up, up)));
+        U[r][P] = ur.x;
+        U[r][Q] = ur.y;
     }
 }
 
@@ -131,16 +135,40 @@ __device__ __forceinline__ void polar_data(const float (&F)[3][3], float (&U)[3]
     }
 }
 
-// U diag(d) U^T (symmetric)
+// U diag(d) U^T (symmetric): rows of U d against pairs of rows of U, as packed FP32x2 products
 __device__ __forceinline__ void sym_from_eig(const float (&U)[3][3], const float (&d)[3], float (&M)[3][3]) {
+    float Ud[3][3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = r; c < 3; ++c) {
-            const float t = U[r][0] * d[0] * U[c][0] + U[r][1] * d[1] * U[c][1] + U[r][2] * d[2] * U[c][2];
-            M[r][c] = t;
-            M[c][r] = t;
-        }
+        for (int k = 0; k < 3; ++k) Ud[r][k] = U[r][k] * d[k];
+    // (M00, M01), (M11, M12), (M02, M22)
+    float2 m0 = make_float2(0.0f, 0.0f), m1 = m0, m2 = m0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m0 = __ffma2_rn(make_float2(Ud[0][k], Ud[0][k]), make_float2(U[0][k], U[1][k]), m0);
+        m1 = __ffma2_rn(make_float2(Ud[1][k], Ud[1][k]), make_float2(U[1][k], U[2][k]), m1);
+        m2 = __ffma2_rn(make_float2(Ud[0][k], Ud[2][k]), make_float2(U[2][k], U[2][k]), m2);
+    }
+    M[0][0] = m0.x;
+    M[0][1] = M[1][0] = m0.y;
+    M[1][1] = m1.x;
+    M[1][2] = M[2][1] = m1.y;
+    M[0][2] = M[2][0] = m2.x;
+    M[2][2] = m2.y;
+}
+
+// P = A B for 3x3 matrices, columns 0 and 1 as packed FP32x2 pairs
+__device__ __forceinline__ void matmul3(const float (&A)[3][3], const float (&B)[3][3], float (&P)[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 p01 = __fmul2_rn(make_float2(A[a][0], A[a][0]), make_float2(B[0][0], B[0][1]));
+        p01 = __ffma2_rn(make_float2(A[a][1], A[a][1]), make_float2(B[1][0], B[1][1]), p01);
+        p01 = __ffma2_rn(make_float2(A[a][2], A[a][2]), make_float2(B[2][0], B[2][1]), p01);
+        P[a][0] = p01.x;
+        P[a][1] = p01.y;
+        P[a][2] = fmaf(A[a][2], B[2][2], fmaf(A[a][1], B[1][2], A[a][0] * B[0][2]));
+    }
 }
 
 // ------------------------------------------------------------------------ constitutive update
@@ -191,10 +219,7 @@ __device__ __forceinline__ uint32_t plastic_update_and_stress(float (&F)[3][3], 
             r[i] = __fdividef(s[i], g);
         }
         sym_from_eig(U, r, M);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Fn[a][c] = M[a][0] * F[0][c] + M[a][1] * F[1][c] + M[a][2] * F[2][c];
+        matmul3(M, F, Fn);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll

@@ -54,6 +54,7 @@ struct StateView {
 struct Geometry {
     int n, nb;      // nodes and blocks per axis
     int nblocks;    // nb^3
+    uint32_t nb_recip;  // ceil(2^32 / nb): b / nb = umulhi(b, nb_recip) exactly for b < 2^19 and nb <= 64
     float dx, inv_dx, dt;
     float lo, hi;   // particle clamp range [2dx, 1-2dx]
 };

@@ -388,10 +388,14 @@ __device__ __forceinline__ void affine(const Material& mat, const float (&C)[3][
         for (int c = 0; c < 3; ++c) A[r][c] = mat.p_mass * C[r][c] + mat.stress_scale * tau[r][c];
 }
 
-__device__ __forceinline__ void decode_bin(int b, int nb, int& bx, int& by, int& bz) {
-    bz = b % nb;
-    by = (b / nb) % nb;
-    bx = b / (nb * nb);
+// Local bin b (< nb^3) to its block coordinates, dividing by nb with its 32-bit reciprocal: for b < 2^19
+// the rounding error of umulhi(b, ceil(2^32 / nb)) is below 2^-13, and b / nb's fraction is at most
+// 1 - 1/nb with nb <= 64, so the quotient is exact.
+__device__ __forceinline__ void decode_bin(int b, const Geometry& g, int& bx, int& by, int& bz) {
+    const uint32_t q1 = __umulhi((uint32_t)b, g.nb_recip), q2 = __umulhi(q1, g.nb_recip);
+    bz = b - (int)q1 * g.nb;
+    by = (int)q1 - (int)q2 * g.nb;
+    bx = (int)q2;
 }
 
 }  // namespace
@@ -853,7 +857,7 @@ __global__ void __launch_bounds__(kChunk) k_p2g(TransferParams p) {
         tile_clear(T);
         __syncthreads();
         int bx, by, bz;
-        decode_bin(ch.x - (int)E.bin_base, E.geo.nb, bx, by, bz);
+        decode_bin(ch.x - (int)E.bin_base, E.geo, bx, by, bz);
         const int o[3] = {4 * bx - 1, 4 * by - 1, 4 * bz - 1};
         const bool active = (int)threadIdx.x < ch.z;
         float x[3] = {0.0f, 0.0f, 0.0f}, v[3] = {0.0f, 0.0f, 0.0f}, A[3][3];
@@ -974,7 +978,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
         if (threadIdx.x == 0 && wn < nchunks) ticket = atomicAdd(p.work, 1u);  // chunk it + 2 (used later)
         if (wn < nchunks) next = p.chunks[wn];  // prefetch the next descriptor
         int bx, by, bz;
-        decode_bin(ch.x - (int)E.bin_base, g.nb, bx, by, bz);
+        decode_bin(ch.x - (int)E.bin_base, g, bx, by, bz);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
         // this thread's particle: its loads are issued first so they overlap the tile load below. A chunk
         // never holds more particles than the CTA has threads (the list is recut when the chunk size
@@ -1031,57 +1035,59 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
             const float* gx = Gx + tile_slot(l0, l1, l2);
             const float* gy = Gy + tile_slot(l0, l1, l2);
             const float* gz = Gz + tile_slot(l0, l1, l2);
+            // (the z component's sums with weights w and k w travel as a pair too)
             float2 vxy = make_float2(0.0f, 0.0f), Mxy[3] = {vxy, vxy, vxy};
-            float vz = 0.0f, Mz[3] = {0.0f, 0.0f, 0.0f};
+            float2 vz2 = make_float2(0.0f, 0.0f);  // (v_z, M_z2)
+            float Mz0 = 0.0f, Mz1 = 0.0f;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 float2 b0 = make_float2(0.0f, 0.0f), bj = b0, bk = b0;
-                float b0z = 0.0f, bjz = 0.0f, bkz = 0.0f;
+                float2 bz2 = make_float2(0.0f, 0.0f);  // (b0z, bkz)
+                float bjz = 0.0f;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     float2 a0 = make_float2(0.0f, 0.0f), ak = a0;
-                    float a0z = 0.0f, akz = 0.0f;
+                    float2 az2 = make_float2(0.0f, 0.0f);  // (a0z, akz)
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const int o = i * kPitchX + j * kPitchY + k;
                         const float2 g = make_float2(gx[o], gy[o]);
-                        const float wk = w3[2][k];
+                        const float wk = w3[2][k], gzo = gz[o];
                         a0 = k ? __ffma2_rn(make_float2(wk, wk), g, a0) : __fmul2_rn(make_float2(wk, wk), g);
-                        a0z = fmaf(wk, gz[o], a0z);
                         if (k) {
                             const float kw = (float)k * wk;
                             ak = __ffma2_rn(make_float2(kw, kw), g, ak);
-                            akz = fmaf(kw, gz[o], akz);
+                            az2 = __ffma2_rn(make_float2(wk, kw), make_float2(gzo, gzo), az2);
+                        } else {
+                            az2.x = wk * gzo;
                         }
                     }
                     const float wj = w3[1][j];
                     b0 = __ffma2_rn(make_float2(wj, wj), a0, b0);
                     bk = __ffma2_rn(make_float2(wj, wj), ak, bk);
-                    b0z = fmaf(wj, a0z, b0z);
-                    bkz = fmaf(wj, akz, bkz);
+                    bz2 = __ffma2_rn(make_float2(wj, wj), az2, bz2);
                     if (j) {
                         const float jw = (float)j * wj;
                         bj = __ffma2_rn(make_float2(jw, jw), a0, bj);
-                        bjz = fmaf(jw, a0z, bjz);
+                        bjz = fmaf(jw, az2.x, bjz);
                     }
                 }
                 const float wi = w3[0][i];
                 vxy = __ffma2_rn(make_float2(wi, wi), b0, vxy);
-                vz = fmaf(wi, b0z, vz);
+                vz2 = __ffma2_rn(make_float2(wi, wi), bz2, vz2);
                 if (i) {
                     const float iw = (float)i * wi;
                     Mxy[0] = __ffma2_rn(make_float2(iw, iw), b0, Mxy[0]);
-                    Mz[0] = fmaf(iw, b0z, Mz[0]);
+                    Mz0 = fmaf(iw, bz2.x, Mz0);
                 }
                 Mxy[1] = __ffma2_rn(make_float2(wi, wi), bj, Mxy[1]);
                 Mxy[2] = __ffma2_rn(make_float2(wi, wi), bk, Mxy[2]);
-                Mz[1] = fmaf(wi, bjz, Mz[1]);
-                Mz[2] = fmaf(wi, bkz, Mz[2]);
+                Mz1 = fmaf(wi, bjz, Mz1);
             }
             vn[0] = vxy.x;
             vn[1] = vxy.y;
-            vn[2] = vz;
-            const float M[3][3] = {{Mxy[0].x, Mxy[1].x, Mxy[2].x}, {Mxy[0].y, Mxy[1].y, Mxy[2].y}, {Mz[0], Mz[1], Mz[2]}};
+            vn[2] = vz2.x;
+            const float M[3][3] = {{Mxy[0].x, Mxy[1].x, Mxy[2].x}, {Mxy[0].y, Mxy[1].y, Mxy[2].y}, {Mz0, Mz1, vz2.y}};
             float Cn[3][3];
             const float cs = 4.0f * g.inv_dx;
 #pragma unroll
@@ -1105,11 +1111,7 @@ __global__ void __launch_bounds__(CTA, CTA == 256 ? (PEN ? 3 : 4) : (PEN ? 6 : 7
             if (kind == 0) {
                 float F[3][3], Ft[3][3];
                 load_mat(p.in.F, N, src, F);
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        Ft[a][c] = Gm[a][0] * F[0][c] + Gm[a][1] * F[1][c] + Gm[a][2] * F[2][c];
+                matmul3(Gm, F, Ft);
                 flags |= plastic_update_and_stress(Ft, E.mat, tau);
                 store_mat(p.out.F, N, slot, Ft);
             } else {
@@ -1291,7 +1293,7 @@ __device__ __forceinline__ void grid_update_cta(const GridParams& p, int cta) {
         float v[3] = {gv.y * im + p.dt * p.gravity[0], gv.z * im + p.dt * p.gravity[1],
                       gv.w * im + p.dt * p.gravity[2]};
         int bx, by, bz;
-        decode_bin((int)lb, g.nb, bx, by, bz);
+        decode_bin((int)lb, g, bx, by, bz);
         const int i = 4 * bx + (ln >> 4), j = 4 * by + ((ln >> 2) & 3), k = 4 * bz + (ln & 3);
         const float xi[3] = {i * g.dx, j * g.dx, k * g.dx};
         const int c_end = p.grid_colliders && __any_sync(0xffffffffu, has_mass) ? E.col_first + E.col_count : 0;

@@ -169,6 +169,7 @@ extern "C" mpm_status mpm_p2g_static(const mpm_config* cfg, const mpm_material* 
     g.n = cfg->n;
     g.nb = cfg->n / 4;
     g.nblocks = g.nb * g.nb * g.nb;
+    g.nb_recip = 0xFFFFFFFFu / (uint32_t)g.nb + 1u;
     g.dx = (float)(1.0 / cfg->n);
     g.inv_dx = (float)cfg->n;
     g.dt = cfg->dt;

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -130,3 +131,17 @@ def test_network_arguments_rejected_on_host(lib):
             case()
         assert e.value.status == lib.MPM_ERR_INVALID_ARG
 
+
+
+def test_bin_decode_by_reciprocal_is_exact():
+    """The kernels split a local bin index b < nb^3 into block coordinates by multiplying with
+    ceil(2^32 / nb) and keeping the high 32 bits, for every block count the library accepts (grids of
+    8..256 nodes per axis, nb = n / 4 = 2..64). Checked here against integer division over every bin."""
+    for nb in range(2, 65):
+        recip = (0xFFFFFFFF // nb) + 1
+        assert recip < 2 ** 32
+        b = np.arange(nb ** 3, dtype=np.uint64)
+        q1 = (b * np.uint64(recip)) >> np.uint64(32)
+        q2 = (q1 * np.uint64(recip)) >> np.uint64(32)
+        assert np.array_equal(q1, b // nb)
+        assert np.array_equal(q2, b // (nb * nb))
