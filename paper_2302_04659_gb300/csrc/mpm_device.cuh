@@ -76,9 +76,12 @@ __device__ __forceinline__ void jacobi_rotation(float (&S)[3][3], float (&U)[3][
     const float rc = rsqrtf(half);
     const float c = half * rc;
     const float s = 0.5f * s2 * rc;
-    const float cc = c * c, ss = s * s, cs2 = 2.0f * c * s * apq;
-    S[P][P] = fmaf(cc, app, fmaf(ss, aqq, -cs2));
-    S[Q][Q] = fmaf(ss, app, fmaf(cc, aqq, cs2));
+    const float2 sq = __fmul2_rn(make_float2(c, s), make_float2(c, s));  // (c^2, s^2)
+    const float cs2 = 2.0f * c * s * apq;
+    const float2 dg = __ffma2_rn(sq, make_float2(app, app),
+                                 __ffma2_rn(make_float2(sq.y, sq.x), make_float2(aqq, aqq), make_float2(-cs2, cs2)));
+    S[P][P] = dg.x;
+    S[Q][Q] = dg.y;
     S[P][Q] = S[Q][P] = 0.0f;
     // rows (p, q) of the rotation as packed FP32x2 pairs: (c, s) a_p + (-s, c) a_q
     const float2 cs = make_float2(c, s), nsc = make_float2(-s, c);

@@ -181,27 +181,36 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
         bspline_weights(f[a], w[a]);
     }
     const float m = E.mat.p_mass;
-    float Ad[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) Ad[c][r] = g.dx * A[r][c];
-    float bm[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) bm[r] = m * vn[r] - (Ad[0][r] * f[0] + Ad[1][r] * f[1] + Ad[2][r] * f[2]);
     const int l0 = bs[0] - o[0], l1 = bs[1] - o[1], l2 = bs[2] - o[2];
     const bool in_tile = (unsigned)l0 <= 5u && (unsigned)l1 <= 5u && (unsigned)l2 <= 5u;
+    // In the tile the momentum terms are in the chunk's fixed-point units: the scale folds into dx and m.
+    const float su = in_tile ? g.dx * mscale : g.dx, sm = in_tile ? m * mscale : m;
+    float Ad[3][3];  // Ad[c] = su * column c of A; the y and z rows as pairs
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Ad[c][0] = su * A[0][c];
+        const float2 yz = __fmul2_rn(make_float2(su, su), make_float2(A[1][c], A[2][c]));
+        Ad[c][1] = yz.x;
+        Ad[c][2] = yz.y;
+    }
+    float bm[3];
+    {
+        float2 byz = __fmul2_rn(make_float2(sm, sm), make_float2(vn[1], vn[2]));
+        float bx = sm * vn[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            byz = __ffma2_rn(make_float2(-f[c], -f[c]), make_float2(Ad[c][1], Ad[c][2]), byz);
+            bx = fmaf(-f[c], Ad[c][0], bx);
+        }
+        bm[0] = bx;
+        bm[1] = byz.x;
+        bm[2] = byz.y;
+    }
     if (in_tile) {
         // Node (i, j, k) receives round(w 2^22) and round(w m_k) with m_k = bm + i Ad0 + j Ad1 + k Ad2 (scaled).
         // Packed FP32x2 pairs: (mass, x) with the pair (2^22, m_k.x), and (y, z); each lane is rounded as
         // a scalar fused multiply-add would round it.
         const float wscale = pow2f(kMassBits);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            bm[r] *= mscale;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Ad[c][r] *= mscale;
-        }
         const float2 magic = make_float2(12582912.0f, 12582912.0f);
         const float2 ad2x = make_float2(0.0f, Ad[2][0]);
         const float2 ad2yz = make_float2(Ad[2][1], Ad[2][2]);
@@ -215,7 +224,9 @@ __device__ __forceinline__ uint32_t scatter_particle(ScatterTile& T, const Trans
             for (int j = 0; j < 3; ++j) {
                 const float wij = w[0][i] * w[1][j];
                 const float2 mx = make_float2(wscale, bm[0] + i * Ad[0][0] + j * Ad[1][0]);
-                const float2 myz = make_float2(bm[1] + i * Ad[0][1] + j * Ad[1][1], bm[2] + i * Ad[0][2] + j * Ad[1][2]);
+                float2 myz = make_float2(bm[1], bm[2]);
+                if (i) myz = __ffma2_rn(make_float2((float)i, (float)i), make_float2(Ad[0][1], Ad[0][2]), myz);
+                if (j) myz = __ffma2_rn(make_float2((float)j, (float)j), make_float2(Ad[1][1], Ad[1][2]), myz);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float wk = wij * w[2][k];
@@ -382,10 +393,14 @@ __device__ __forceinline__ void store_mat(float* base, int N, uint32_t i, const 
 // A = m C - dt V0 (4/dx^2) tau: the MLS-MPM affine momentum with the stress impulse folded in.
 __device__ __forceinline__ void affine(const Material& mat, const float (&C)[3][3], const float (&tau)[3][3],
                                        float (&A)[3][3]) {
+    const float2 m2 = make_float2(mat.p_mass, mat.p_mass), s2 = make_float2(mat.stress_scale, mat.stress_scale);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A[r][c] = mat.p_mass * C[r][c] + mat.stress_scale * tau[r][c];
+    for (int r = 0; r < 3; ++r) {
+        const float2 a = __ffma2_rn(s2, make_float2(tau[r][0], tau[r][1]), __fmul2_rn(m2, make_float2(C[r][0], C[r][1])));
+        A[r][0] = a.x;
+        A[r][1] = a.y;
+        A[r][2] = fmaf(mat.stress_scale, tau[r][2], mat.p_mass * C[r][2]);
+    }
 }
 
 // Local bin b (< nb^3) to its block coordinates, dividing by nb with its 32-bit reciprocal: for b < 2^19
