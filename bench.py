@@ -759,6 +759,93 @@ def run_conv_scan(dev, reps: int = 20):
     return {"what": "k_conv_tc forward, graph-replayed launches, CUDA events", "rows": out}
 
 
+def run_train_timing(dev, reps: int = 20):
+    """The surrogate network's training kernels on the pinch window box (33 x 38 x 40 nodes): per layer,
+    the weight and bias gradients with the tcgen05 kernel (mpm_conv3d_backward_weight_tc) and with the
+    mma.sync kernel it replaced (mpm_conv3d_backward_weight), each `reps` calls replayed from a CUDA graph
+    (device time, no host launch cost), with the largest relative difference of their dW; then one
+    training step (forward, masked MSE, backward) per backward engine, launched eagerly. Random inputs."""
+    import torch
+
+    from paper_2302_04659_gb300 import _native as mpm
+    from paper_2302_04659_gb300 import surrogate as sur
+
+    torch.manual_seed(0)
+    D, H, W = 33, 38, 40
+    C = sur.CHANNELS
+    st = torch.cuda.Stream(dev)
+
+    def graph_time(fn):
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                fn()
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for _ in range(reps):
+                fn()
+        with torch.cuda.stream(st):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record()
+            g.replay()
+            b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps * 1e3
+
+    layers = []
+    for i in range(4):
+        cin, cout = C[i], C[i + 1]
+        cd = 4 if cout <= 4 else (16 if cout <= 16 else 32)
+        x = torch.randn(D, H, W, cin, device=dev).to(torch.bfloat16).contiguous()
+        dy = torch.randn(D, H, W, cout, device=dev).to(torch.bfloat16).contiguous()
+        dyp = torch.zeros(D, H, W, cd, device=dev, dtype=torch.bfloat16)
+        dyp[..., :cout] = dy
+        dw_m, db_m = torch.zeros(27 * cout * cin, device=dev), torch.zeros(cout, device=dev)
+        dw_t, db_t = torch.zeros_like(dw_m), torch.zeros_like(db_m)
+        s = st.cuda_stream
+
+        def mma():
+            mpm.mpm_conv3d_backward_weight(mpm.MPM_NET_BF16, D, H, W, cin, cout, x.data_ptr(), dy.data_ptr(),
+                                           dw_m.data_ptr(), db_m.data_ptr(), s)
+
+        def tc():
+            mpm.mpm_conv3d_backward_weight_tc(D, H, W, cin, cout, x.data_ptr(), dyp.data_ptr(), dw_t.data_ptr(),
+                                              db_t.data_ptr(), s)
+
+        t_m, t_t = graph_time(mma), graph_time(tc)
+        diff = float((dw_t - dw_m).abs().max() / dw_m.abs().max().clamp_min(1e-30))
+        flops = 2.0 * D * H * W * 27 * cin * cout
+        layers.append({"cin": cin, "cout": cout, "us_mma_sync": t_m, "us_tcgen05": t_t,
+                       "tflops_tcgen05": flops / t_t / 1e6, "max_rel_diff_dw": diff})
+    net = sur.Network(device=dev)
+    xin = torch.randn(D, H, W, 4, device=dev).to(torch.bfloat16)
+    mask = torch.ones(D, H, W, dtype=torch.uint8, device=dev)
+    target = torch.randn(D, H, W, 3, device=dev)
+    steps = {}
+    for eng in ("mma", "tc"):
+        net.backward_engine = eng
+
+        def step():
+            net.forward(xin, mask)
+            net.loss_and_backward(target, mask)
+
+        step()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            step()
+        b.record()
+        b.synchronize()
+        steps["us_" + ("mma_sync" if eng == "mma" else "tcgen05")] = a.elapsed_time(b) / reps * 1e3
+    return {"box": [D, H, W], "weight_gradient": layers,
+            "train_step": dict(steps, what="forward + masked MSE + backward, eager launches, CUDA events"),
+            "what": "weight gradients graph-replayed (device time); dW compared between the two kernels"}
+
+
 def run_surrogate(dev, n_scenes: int):
     """The learned grid surrogate (the committed trained weights) against the plain method on held-out
     pinch scenes (seeds 20000 + i, 200,000 particles, 64^3 grid, two capsule fingers; none of them among the
@@ -938,7 +1025,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10, help="timed env steps of the batched workloads")
     ap.add_argument("--surrogate-scenes", type=int, default=256,
                     help="held-out scenes of the surrogate evaluation (0 skips it)")
-    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact", "render", "conv"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "surrogate", "contact", "render", "conv", "train"], default=None,
                     help="run one batched workload alone and print its section (profiling runs)")
     ap.add_argument("--envs", type=int, default=0, help="with --only: number of envs (default: the workload's)")
     ap.add_argument("--no-tune", action="store_true", help="with --only: keep the default launch shape")
@@ -961,6 +1048,8 @@ def main():
             out = run_render(dev, args.batched_steps * 5)
         elif args.only == "conv":
             out = run_conv_scan(dev)
+        elif args.only == "train":
+            out = run_train_timing(dev)
         else:
             out = run_batched(dev, "batch256" if args.only == "batched" else "serve1024", args.batched_steps,
                               3, per_scene=False, tune=not args.no_tune, nenv=args.envs)
