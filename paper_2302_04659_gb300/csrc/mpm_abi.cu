@@ -492,6 +492,7 @@ mpm_status enqueue_grid_half(mpm_sim* s, cudaStream_t st, const uint32_t* gate =
         ap.total_bins = (int)s->T.bins;
         ap.chunk = s->chunk;
         ap.scan_done = s->scan_done();
+        ap.status = s->status();
         s->ps.scanned = true;
         s->ps.counts_pending = false;
     }

@@ -165,7 +165,8 @@ struct AssignGridParams {  // the sort-assign of the new state and the grid upda
     uint32_t* perm;
     int assign_ctas;          // the first assign_ctas CTAs assign sorted slots (0: no assign)
     // scan = 1: the counts in `hist` are not scanned yet; each assign CTA scans them for itself (the first
-    // also writes cursor_out, chunks and num_chunks; the last to finish clears hist)
+    // also writes cursor_out, chunks and num_chunks) and counts itself in scan_done; the first grid-update
+    // CTA waits (bounded) for all of them, then clears hist and scan_done
     int scan;
     uint32_t* hist;
     uint32_t* cursor_out;
@@ -174,7 +175,8 @@ struct AssignGridParams {  // the sort-assign of the new state and the grid upda
     const uint32_t* bin_env;
     int total_bins;
     int chunk;
-    uint32_t* scan_done;      // assign CTAs done reading the counts, reset by the last one
+    uint32_t* scan_done;      // assign CTAs done reading the counts, reset by the CTA that clears hist
+    uint32_t* status;         // error flags (a bounded wait that ran out sets kFlagInternal)
     const uint32_t* gate;     // if set, the launch runs only when *gate == gate_run (read after the wait)
     uint32_t gate_run;
 };

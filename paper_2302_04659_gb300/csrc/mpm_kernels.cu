@@ -1428,7 +1428,6 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
             return;
         }
         __shared__ uint32_t warp_tot[2][32];
-        __shared__ bool last;
         uint32_t* cur_sh = reinterpret_cast<uint32_t*>(dyn_sh);
         // this thread's (bin, rank) pairs are requested before the scan, which does not need them: a CTA
         // takes kScanAssignRounds runs of blockDim.x * kAssignPerThread particles, four per thread per run
@@ -1454,13 +1453,8 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
             scan_counts_shared<0>(p.hist, cur_sh, p.total_bins, p.chunk, writer, p.cursor_out, p.chunks,
                                   p.num_chunks, p.bin_env, warp_tot);
         __syncthreads();  // this CTA's reads of the counts are done, its offsets are in shared memory
-        if (threadIdx.x == 0) last = atomicAdd(p.scan_done, 1u) == (uint32_t)p.assign_ctas - 1u;
-        __syncthreads();
-        if (last) {  // every sort-assign CTA has read the counts: clear them for the next substep
-            uint4* H = reinterpret_cast<uint4*>(p.hist);
-            for (int q = threadIdx.x; q < (p.total_bins + 3) >> 2; q += blockDim.x) H[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (threadIdx.x == 0) *p.scan_done = 0u;
-        }
+        // count this CTA as done reading (no answer awaited: the first grid-update CTA clears the counts)
+        if (threadIdx.x == 0) atomicAdd(p.scan_done, 1u);
         release_successor();  // only the stores of the permutation remain
 #pragma unroll
         for (int r = 0; r < kScanAssignRounds; ++r) {
@@ -1476,6 +1470,26 @@ __global__ void __launch_bounds__(256) k_assign_grid(AssignGridParams p) {
         return;
     }
     grid_update_cta<ONE_ENV, SHARED_POSES>(p.grid, blockIdx.x - p.assign_ctas);
+    if (p.scan && (int)blockIdx.x == p.assign_ctas) {
+        // Every sort-assign CTA has read the counts once scan_done reaches their number: clear the counts
+        // for the next substep. They have lower block indices, so they were scheduled before this CTA.
+        __shared__ bool ok;
+        if (threadIdx.x == 0) {
+            uint32_t n = 0;
+            for (uint32_t it = 0; it < (1u << 20); ++it) {
+                n = *(volatile uint32_t*)p.scan_done;
+                if (n >= (uint32_t)p.assign_ctas) break;
+            }
+            ok = n >= (uint32_t)p.assign_ctas;
+            if (!ok) atomicOr(p.status, kFlagInternal);
+        }
+        __syncthreads();
+        if (ok) {
+            uint4* H = reinterpret_cast<uint4*>(p.hist);
+            for (int q = threadIdx.x; q < (p.total_bins + 3) >> 2; q += blockDim.x) H[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (threadIdx.x == 0) *p.scan_done = 0u;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------ readback
