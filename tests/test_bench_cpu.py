@@ -72,3 +72,12 @@ def test_oracle_replicas_on_all_cores(monkeypatch):
     value, cores, secs = b.oracle_on_all_cores(1000, 4000, 300, 1, 2)
     assert cores == 2 and secs > 0.0
     assert abs(value - 2 * 300 * 2 / secs) <= 1e-9 * value
+
+
+def test_every_bench_section_is_selectable():
+    """Each profiling section of the bench (--only) is offered on its command line."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
+                         timeout=300).stdout
+    for section in ("batched", "serving", "surrogate", "contact", "render", "conv", "train"):
+        assert section in out, section
