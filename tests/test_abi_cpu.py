@@ -125,12 +125,18 @@ def test_network_arguments_rejected_on_host(lib):
         lambda: lib.mpm_conv3d_backward_weight(lib.MPM_NET_BF16, 4, 4, 4, 40, 32, 1, 1, 1, 1),
         lambda: lib.mpm_mse_loss(lib.MPM_NET_BF16, 0, 3, 1, 1, 1, 1, 1, 1),
         lambda: lib.mpm_adam_step(10, 1, 1, 1, 1, 0, 1e-3),
+        # the tensor-core weight gradient: input channels 4, 16 or 32; output 1..32; 16-byte alignment
+        lambda: lib.mpm_conv3d_backward_weight_tc(4, 4, 4, 8, 32, 16, 16, 16, 16),
+        lambda: lib.mpm_conv3d_backward_weight_tc(4, 4, 4, 32, 0, 16, 16, 16, 16),
+        lambda: lib.mpm_conv3d_backward_weight_tc(4, 4, 4, 32, 33, 16, 16, 16, 16),
+        lambda: lib.mpm_conv3d_backward_weight_tc(0, 4, 4, 32, 32, 16, 16, 16, 16),
+        lambda: lib.mpm_conv3d_backward_weight_tc(4, 4, 4, 32, 32, 8, 16, 16, 16),
+        lambda: lib.mpm_conv3d_backward_weight_tc(4, 4, 4, 32, 32, 16, 16, 4, 16),
     ]
     for case in cases:
         with pytest.raises(lib.MpmError) as e:
             case()
         assert e.value.status == lib.MPM_ERR_INVALID_ARG
-
 
 
 def test_bin_decode_by_reciprocal_is_exact():
